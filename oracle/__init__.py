@@ -1,0 +1,227 @@
+"""Plain FP64 CPU oracle of the block-AMR unsplit Euler step (ctypes binding).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product library
+(``paper_2208_11630_gb300``) never imports it, and the two share no code; the
+only common module is the seeded input generator, which holds no method
+arithmetic.
+
+The C sources (``oracle.c``, ``riemann_exact.c``) restate the scheme from its
+textbook definitions; see ``fx_oracle.h`` for what each routine computes and
+how it is pinned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = [os.path.join(_HERE, f) for f in ("oracle.c", "riemann_exact.c")]
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (-O2, OpenMP, no FP contraction)."""
+    newest = max(os.path.getmtime(f) for f in _SRC + [os.path.join(_HERE, "fx_oracle.h")])
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-Wall", "-Wno-unknown-pragmas", "-o", tmp] + _SRC + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int)
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            L.or_mesh_create.restype = ctypes.c_void_p
+            L.or_mesh_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ip, ip, i64p, ip, dp, dp, ip, ctypes.c_double]
+            L.or_mesh_destroy.argtypes = [ctypes.c_void_p]
+            L.or_last_error.restype = ctypes.c_char_p
+            L.or_set_threads.argtypes = [ctypes.c_int]
+            L.or_get_threads.restype = ctypes.c_int
+            L.or_prim_to_cons.argtypes = [ctypes.c_void_p, dp, dp]
+            L.or_cons_to_prim.argtypes = [ctypes.c_void_p, dp, dp]
+            L.or_guardcell_fill.argtypes = [ctypes.c_void_p, dp]
+            L.or_compute_dt.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_int, dp]
+            L.or_hydro_advance.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_double, ctypes.c_int,
+                                           dp, ctypes.c_int, ip]
+            L.or_conserved_totals.argtypes = [ctypes.c_void_p, dp, dp]
+            L.or_mc.restype = ctypes.c_double
+            L.or_mc.argtypes = [ctypes.c_double, ctypes.c_double]
+            L.or_hllc.argtypes = [dp, dp, ctypes.c_int, ctypes.c_double, dp]
+            L.or_riemann_star.argtypes = [dp, dp, ctypes.c_double, dp]
+            L.or_riemann_sample.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp]
+            _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a: np.ndarray):
+    assert a.dtype == np.int32 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def set_threads(n: int) -> None:
+    lib().or_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().or_get_threads())
+
+
+class OracleMesh:
+    """The oracle's view of a block set; ``mesh`` is an ``inputs.Mesh``."""
+
+    def __init__(self, mesh, gamma: float = 1.4):
+        L = lib()
+        self.mesh = mesh
+        self.gamma = float(gamma)
+        self._level = np.ascontiguousarray(mesh.level, dtype=np.int32)
+        self._origin = np.ascontiguousarray(mesh.origin, dtype=np.int64)
+        self._parent = np.ascontiguousarray(mesh.parent, dtype=np.int32)
+        nroot = np.array(mesh.nroot, dtype=np.int32)
+        lo = np.array(mesh.lo, dtype=np.float64)
+        hi = np.array(mesh.hi, dtype=np.float64)
+        bc = mesh.bc_flat()
+        self._h = L.or_mesh_create(mesh.ndim, mesh.nxb, mesh.ng, mesh.nb, _ip(nroot),
+                                   _ip(self._level),
+                                   self._origin.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                   _ip(self._parent), _dp(lo), _dp(hi), _ip(bc), self.gamma)
+        if not self._h:
+            raise ValueError(L.or_last_error().decode())
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().or_mesh_destroy(h)
+            self._h = None
+
+    # -- EOS ------------------------------------------------------------
+    def prim_to_cons(self, W: np.ndarray) -> np.ndarray:
+        U = np.zeros_like(W)
+        lib().or_prim_to_cons(self._h, _dp(W), _dp(U))
+        return U
+
+    def cons_to_prim(self, U: np.ndarray) -> np.ndarray:
+        W = np.zeros_like(U)
+        lib().or_cons_to_prim(self._h, _dp(U), _dp(W))
+        return W
+
+    # -- step pieces ------------------------------------------------------
+    def guardcell_fill(self, U: np.ndarray) -> None:
+        if lib().or_guardcell_fill(self._h, _dp(U)):
+            raise RuntimeError(lib().or_last_error().decode())
+
+    def compute_dt(self, U: np.ndarray, cfl: float = 0.8, form: int = 0) -> float:
+        dt = np.zeros(1)
+        lib().or_compute_dt(self._h, _dp(U), float(cfl), int(form), _dp(dt))
+        return float(dt[0])
+
+    def hydro_advance(self, U: np.ndarray, dt: float, reflux: bool = True,
+                      want_bflux: bool = False, select=None):
+        """Advance the leaves one step from ``U`` (guards filled).  Returns
+        ``(Unew, status, bflux)``; ``Unew`` starts as a copy of ``U``."""
+        m = self.mesh
+        Unew = U.copy()
+        bflux = None
+        bptr = None
+        if want_bflux:
+            nf = m.nxb ** (m.ndim - 1)
+            bflux = np.zeros((m.nb, 2 * m.ndim, 5, nf))
+            bptr = _dp(bflux)
+        if select is not None:
+            sel = np.ascontiguousarray(select, dtype=np.int32)
+            st = lib().or_hydro_advance(self._h, _dp(U), _dp(Unew), float(dt), int(reflux), bptr,
+                                        len(sel), _ip(sel))
+        else:
+            st = lib().or_hydro_advance(self._h, _dp(U), _dp(Unew), float(dt), int(reflux), bptr,
+                                        0, None)
+        return Unew, st, bflux
+
+    def conserved_totals(self, U: np.ndarray) -> np.ndarray:
+        out = np.zeros(5)
+        lib().or_conserved_totals(self._h, _dp(U), _dp(out))
+        return out
+
+    def step(self, U: np.ndarray, cfl: float = 0.8, dt: float | None = None, form: int = 0,
+             reflux: bool = True, t_end: float | None = None, t: float = 0.0):
+        """One full step: dt, guard fill, advance.  Returns ``(Unew, dt)``."""
+        U = U.copy()
+        if dt is None:
+            dt = self.compute_dt(U, cfl, form)
+        if t_end is not None:
+            dt = min(dt, t_end - t)
+        self.guardcell_fill(U)
+        Unew, st, _ = self.hydro_advance(U, dt, reflux)
+        if st:
+            raise FloatingPointError("unphysical state after step")
+        return Unew, dt
+
+    def run(self, U: np.ndarray, nsteps: int | None = None, t_end: float | None = None,
+            cfl: float = 0.8, form: int = 0, reflux: bool = True, max_steps: int = 100000):
+        t = 0.0
+        n = 0
+        while True:
+            if nsteps is not None and n >= nsteps:
+                break
+            if t_end is not None and t >= t_end * (1 - 1e-14):
+                break
+            if n >= max_steps:
+                raise RuntimeError("too many steps")
+            U, dt = self.step(U, cfl=cfl, form=form, reflux=reflux, t_end=t_end, t=t)
+            t += dt
+            n += 1
+        return U, t, n
+
+
+def mc(a: float, b: float) -> float:
+    return float(lib().or_mc(float(a), float(b)))
+
+
+def hllc(WL, WR, direction: int, gamma: float = 1.4) -> np.ndarray:
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    F = np.zeros(5)
+    lib().or_hllc(_dp(WL), _dp(WR), int(direction), float(gamma), _dp(F))
+    return F
+
+
+def riemann_star(WL, WR, gamma: float = 1.4) -> np.ndarray:
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    out = np.zeros(4)
+    if lib().or_riemann_star(_dp(WL), _dp(WR), float(gamma), _dp(out)):
+        raise ValueError("vacuum")
+    return out
+
+
+def riemann_sample(WL, WR, xi, gamma: float = 1.4) -> np.ndarray:
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    xi = np.atleast_1d(np.asarray(xi, dtype=np.float64))
+    out = np.zeros((xi.size, 3))
+    o = np.zeros(3)
+    for n, x in enumerate(xi.ravel()):
+        lib().or_riemann_sample(_dp(WL), _dp(WR), float(gamma), float(x), _dp(o))
+        out[n] = o
+    return out

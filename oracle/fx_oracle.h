@@ -1,0 +1,103 @@
+/*
+ * fx_oracle.h -- plain FP64 CPU oracle of the block-AMR unsplit Euler step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the correctness reference for the
+ * CUDA path.  Only the tests, the smoke check and the benchmark's CPU-baseline
+ * leg may load it; the product library never links or calls it, and the two
+ * share no code.
+ *
+ * What it computes (Flash-X, arXiv 2208.11630, Section 2: "block-by-block
+ * update, interspersed with fine-coarse boundary resolution" on a uniform or
+ * octree AMR grid; Section 2.2: unsplit predictor-corrector compressible hydro
+ * with a perfect-gas EOS).  The paper names the method family only; the
+ * concrete scheme is the textbook one:
+ *   - perfect-gas EOS, p = (gamma-1)(E - |m|^2 / (2 rho)), c = sqrt(gamma p / rho);
+ *   - MC-limited piecewise-linear slopes of the primitive variables
+ *     (van Leer 1977);
+ *   - MUSCL-Hancock half-step predictor in primitive form (Toro, "Riemann
+ *     Solvers and Numerical Methods for Fluid Dynamics", ch. 14);
+ *   - HLLC flux with Davis wave-speed estimates (Toro, Spruce & Speares 1994;
+ *     Toro ch. 10);
+ *   - conservative unsplit update, fine-to-coarse flux correction
+ *     (Berger & Colella 1989), restriction into parents;
+ *   - CFL time step from the maximum signal speed.
+ * Guard cells: same-level copy, outflow (zero-gradient) or periodic physical
+ * boundaries, restriction of finer data, conservative MC-limited linear
+ * prolongation of coarser data.
+ *
+ * Layout: U[block][var][z][y][x], var = (rho, mx, my, mz, E), P = nxb + 2 ng
+ * cells per padded axis, one z-plane in 2D.  Everything is FP64.
+ *
+ * Parity status of each function is recorded beside it:
+ *   "pinned"   -- checked by the CPU tests against closed forms, invariants,
+ *                 brute force or textbook values;
+ *   "unpinned" -- no independent check exists (none in this file).
+ */
+#ifndef FX_ORACLE_H
+#define FX_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct or_mesh or_mesh;
+
+/* Build the oracle's own view of a block set (levels, origins in the block's
+ * level lattice, parents).  bc[6] = {x-, x+, y-, y+, z-, z+}, 0 = outflow,
+ * 1 = periodic.  Returns NULL on invalid input (message via or_last_error). */
+or_mesh *or_mesh_create(int ndim, int nxb, int ng, int nb, const int nroot[3],
+                        const int *level, const int64_t *origin, const int *parent,
+                        const double lo[3], const double hi[3], const int bc[6],
+                        double gamma);
+void or_mesh_destroy(or_mesh *m);
+const char *or_last_error(void);
+void or_set_threads(int n);
+int or_get_threads(void);
+
+/* EOS conversions over every cell of every block (pinned: round trip). */
+void or_prim_to_cons(const or_mesh *m, const double *W, double *U);
+void or_cons_to_prim(const or_mesh *m, const double *U, double *W);
+
+/* Guard-cell fill of all leaves (pinned: brute-force global indexing,
+ * linear-field prolongation, restrict-of-prolong identity).  Returns 0 or -1. */
+int or_guardcell_fill(const or_mesh *m, double *U);
+
+/* CFL time step: dt = cfl / max over leaf interior cells of
+ * sum_d (|u_d| + c) / dx_d (form 0) or max_d (|u_d| + c) / dx_d (form 1).
+ * Pinned: uniform-state closed form, order independence. */
+int or_compute_dt(const or_mesh *m, const double *U, double cfl, int form, double *dt);
+
+/* One hydro step of the leaves: reads U (guards filled), writes interiors of
+ * Unew, then applies flux correction (if reflux != 0) and restricts into
+ * parents.  If bflux != NULL it receives every leaf's block-boundary fluxes,
+ * [nb][2*ndim faces: x-, x+, y-, y+, z-, z+][5][nxb^(ndim-1)] (transverse
+ * index order: the lower axis fastest).  If sel != NULL only the nsel listed
+ * leaves are advanced and no correction or restriction is done.
+ * Returns 0, or -4 if a new interior cell has rho <= 0 or p <= 0.
+ * Pinned: Sod exact solution (L1 convergence), conservation, uniform state,
+ * mirror symmetry, decomposition invariance, scalar-advection special case,
+ * geometric reflux check. */
+int or_hydro_advance(const or_mesh *m, const double *U, double *Unew, double dt,
+                     int reflux, double *bflux, int nsel, const int *sel);
+
+/* Sum over leaf interior cells of U dV per variable (compensated sums, fixed
+ * order).  Pinned by conservation tests. */
+void or_conserved_totals(const or_mesh *m, const double *U, double out[5]);
+
+/* Point functions for unit pins. */
+double or_mc(double a, double b);
+void or_hllc(const double WL[5], const double WR[5], int dir, double gamma, double F[5]);
+
+/* Exact Riemann solver for the 1D Euler equations (test tool; Toro ch. 4).
+ * star[4] = {p*, u*, rho*L, rho*R}; returns -1 on vacuum generation. */
+int or_riemann_star(const double WL[3], const double WR[3], double gamma, double star[4]);
+/* Sample the self-similar solution at xi = x / t: out = {rho, u, p}. */
+int or_riemann_sample(const double WL[3], const double WR[3], double gamma, double xi,
+                      double out[3]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,726 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle of the block-AMR unsplit Euler step.
+ *
+ * TEST INFRASTRUCTURE ONLY (tests, smoke check, benchmark CPU baseline).  It
+ * shares no code with the CUDA path.  Every routine is a direct, unoptimised
+ * restatement of the definition it cites; loops run over cells, the only
+ * parallelism is OpenMP over independent blocks.
+ *
+ * Scheme (Flash-X, arXiv 2208.11630, Section 2 and Section 2.2; concrete
+ * formulas from the textbook methods the hydro solver family uses):
+ *   EOS        perfect gas, p = (gamma-1)(E - |m|^2/(2 rho))
+ *   slopes     MC limiter on primitives (van Leer 1977)
+ *   predictor  MUSCL-Hancock half step, primitive quasi-linear form (Toro ch. 14)
+ *   flux       HLLC, Davis speeds (Toro, Spruce & Speares 1994; Toro ch. 10)
+ *   update     unsplit conservative update, directions summed x, y, z
+ *   AMR        restriction (pairwise mean of children), MC-limited conservative
+ *              linear prolongation, fine-to-coarse flux correction
+ *              (Berger & Colella 1989)
+ *   dt         CFL max-reduction of the signal speed
+ *
+ * Readings where the paper is silent (all listed in the design notes):
+ *   primitive (not characteristic) reconstruction; primitive-form Hancock;
+ *   Davis wave speeds; positivity fallback to first order for a cell whose
+ *   face states are not positive; sum-form CFL by default; MC prolongation on
+ *   conserved variables; pairwise summation in restriction and flux averaging.
+ *
+ * Build with -ffp-contract=off so that x86 and Arm hosts give identical bits.
+ */
+#include "fx_oracle.h"
+
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_MAXLEV 16
+
+struct or_mesh {
+  int ndim, nxb, ng, nb, P, PZ, lmax;
+  int nroot[3];
+  double lo[3], hi[3], gamma;
+  int bc[3][2];
+  int *level, *parent, *leaf, *child; /* child: [nb][8] */
+  int64_t *origin;                    /* [nb][3] */
+  int64_t ncell[OR_MAXLEV][3];        /* cells per axis at each level */
+  int64_t nblk[OR_MAXLEV][3];         /* blocks per axis at each level */
+  double dx[OR_MAXLEV][3];
+  int *lut[OR_MAXLEV];                /* dense block lookup per level */
+};
+
+static char g_err[256];
+static int g_threads = 0;
+
+const char *or_last_error(void) { return g_err; }
+
+void or_set_threads(int n) { g_threads = n; }
+
+int or_get_threads(void) {
+#ifdef _OPENMP
+  return g_threads > 0 ? g_threads : omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+static void set_err(const char *s) { snprintf(g_err, sizeof g_err, "%s", s); }
+
+/* ------------------------------------------------------------------------ */
+/* indexing                                                                  */
+/* ------------------------------------------------------------------------ */
+
+static size_t cell_index(const or_mesh *m, int b, int v, int k, int j, int i) {
+  return ((((size_t)b * 5 + v) * m->PZ + k) * m->P + j) * m->P + i;
+}
+
+static int lookup(const or_mesh *m, int l, const int64_t bcoord[3]) {
+  if (l < 0 || l > m->lmax) return -1;
+  for (int d = 0; d < 3; d++)
+    if (bcoord[d] < 0 || bcoord[d] >= m->nblk[l][d]) return -1;
+  int64_t idx = (bcoord[2] * m->nblk[l][1] + bcoord[1]) * m->nblk[l][0] + bcoord[0];
+  return m->lut[l][idx];
+}
+
+/* ------------------------------------------------------------------------ */
+/* mesh                                                                      */
+/* ------------------------------------------------------------------------ */
+
+void or_mesh_destroy(or_mesh *m) {
+  if (!m) return;
+  for (int l = 0; l < OR_MAXLEV; l++) free(m->lut[l]);
+  free(m->level); free(m->parent); free(m->leaf); free(m->child); free(m->origin);
+  free(m);
+}
+
+or_mesh *or_mesh_create(int ndim, int nxb, int ng, int nb, const int nroot[3],
+                        const int *level, const int64_t *origin, const int *parent,
+                        const double lo[3], const double hi[3], const int bc[6],
+                        double gamma) {
+  if ((ndim != 2 && ndim != 3) || nxb < 2 || (nxb % 2) || ng < 2 || nb < 1) {
+    set_err("bad ndim/nxb/ng/nb");
+    return NULL;
+  }
+  or_mesh *m = (or_mesh *)calloc(1, sizeof *m);
+  m->ndim = ndim; m->nxb = nxb; m->ng = ng; m->nb = nb;
+  m->P = nxb + 2 * ng; m->PZ = ndim == 3 ? m->P : 1;
+  m->gamma = gamma;
+  for (int d = 0; d < 3; d++) {
+    m->nroot[d] = d < ndim ? nroot[d] : 1;
+    m->lo[d] = lo[d]; m->hi[d] = hi[d];
+    m->bc[d][0] = bc[2 * d]; m->bc[d][1] = bc[2 * d + 1];
+  }
+  m->level = (int *)malloc(sizeof(int) * nb);
+  m->parent = (int *)malloc(sizeof(int) * nb);
+  m->leaf = (int *)malloc(sizeof(int) * nb);
+  m->child = (int *)malloc(sizeof(int) * nb * 8);
+  m->origin = (int64_t *)malloc(sizeof(int64_t) * nb * 3);
+  m->lmax = 0;
+  for (int b = 0; b < nb; b++) {
+    m->level[b] = level[b];
+    m->parent[b] = parent[b];
+    m->leaf[b] = 1;
+    for (int c = 0; c < 8; c++) m->child[b * 8 + c] = -1;
+    for (int d = 0; d < 3; d++) m->origin[b * 3 + d] = d < ndim ? origin[b * 3 + d] : 0;
+    if (level[b] < 0 || level[b] >= OR_MAXLEV) { set_err("bad level"); or_mesh_destroy(m); return NULL; }
+    if (level[b] > m->lmax) m->lmax = level[b];
+  }
+  for (int l = 0; l <= m->lmax; l++) {
+    int64_t tot = 1;
+    for (int d = 0; d < 3; d++) {
+      if (d < ndim) {
+        m->nblk[l][d] = (int64_t)m->nroot[d] << l;
+        m->ncell[l][d] = m->nblk[l][d] * nxb;
+        m->dx[l][d] = (hi[d] - lo[d]) / (double)m->ncell[l][d];
+      } else {
+        m->nblk[l][d] = 1; m->ncell[l][d] = 1; m->dx[l][d] = 1.0;
+      }
+      tot *= m->nblk[l][d];
+    }
+    m->lut[l] = (int *)malloc(sizeof(int) * tot);
+    for (int64_t i = 0; i < tot; i++) m->lut[l][i] = -1;
+  }
+  for (int b = 0; b < nb; b++) {
+    int64_t bcoord[3];
+    for (int d = 0; d < 3; d++) {
+      int64_t o = m->origin[b * 3 + d];
+      if (o % nxb) { set_err("origin not a multiple of nxb"); or_mesh_destroy(m); return NULL; }
+      bcoord[d] = o / nxb;
+    }
+    int l = m->level[b];
+    for (int d = 0; d < 3; d++)
+      if (bcoord[d] < 0 || bcoord[d] >= m->nblk[l][d]) { set_err("block outside domain"); or_mesh_destroy(m); return NULL; }
+    int64_t idx = (bcoord[2] * m->nblk[l][1] + bcoord[1]) * m->nblk[l][0] + bcoord[0];
+    if (m->lut[l][idx] >= 0) { set_err("duplicate block"); or_mesh_destroy(m); return NULL; }
+    m->lut[l][idx] = b;
+  }
+  for (int b = 0; b < nb; b++) {
+    int p = m->parent[b];
+    if (p < 0) continue;
+    if (p >= nb || m->level[p] != m->level[b] - 1) { set_err("bad parent"); or_mesh_destroy(m); return NULL; }
+    int oct = 0;
+    for (int d = 0; d < ndim; d++) {
+      int64_t rel = m->origin[b * 3 + d] - 2 * m->origin[p * 3 + d];
+      if (rel != 0 && rel != nxb) { set_err("child not inside parent"); or_mesh_destroy(m); return NULL; }
+      if (rel) oct |= 1 << d;
+    }
+    m->child[p * 8 + oct] = b;
+    m->leaf[p] = 0;
+  }
+  for (int b = 0; b < nb; b++) {
+    if (m->leaf[b]) continue;
+    for (int c = 0; c < (1 << ndim); c++)
+      if (m->child[b * 8 + c] < 0) { set_err("parent with missing child"); or_mesh_destroy(m); return NULL; }
+  }
+  return m;
+}
+
+/* ------------------------------------------------------------------------ */
+/* EOS                                                                       */
+/* ------------------------------------------------------------------------ */
+
+static void prim_from_cons(const double U[5], double gamma, double W[5]) {
+  double rho = U[0];
+  W[0] = rho;
+  W[1] = U[1] / rho;
+  W[2] = U[2] / rho;
+  W[3] = U[3] / rho;
+  W[4] = (gamma - 1.0) * (U[4] - 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / rho);
+}
+
+static void cons_from_prim(const double W[5], double gamma, double U[5]) {
+  double rho = W[0];
+  U[0] = rho;
+  U[1] = rho * W[1];
+  U[2] = rho * W[2];
+  U[3] = rho * W[3];
+  U[4] = W[4] / (gamma - 1.0) + 0.5 * rho * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+}
+
+static size_t ncells_total(const or_mesh *m) {
+  return (size_t)m->nb * m->PZ * m->P * m->P;
+}
+
+void or_prim_to_cons(const or_mesh *m, const double *W, double *U) {
+  size_t per = (size_t)m->PZ * m->P * m->P;
+  for (int b = 0; b < m->nb; b++)
+    for (size_t c = 0; c < per; c++) {
+      double w[5], u[5];
+      for (int v = 0; v < 5; v++) w[v] = W[((size_t)b * 5 + v) * per + c];
+      cons_from_prim(w, m->gamma, u);
+      for (int v = 0; v < 5; v++) U[((size_t)b * 5 + v) * per + c] = u[v];
+    }
+  (void)ncells_total;
+}
+
+void or_cons_to_prim(const or_mesh *m, const double *U, double *W) {
+  size_t per = (size_t)m->PZ * m->P * m->P;
+  for (int b = 0; b < m->nb; b++)
+    for (size_t c = 0; c < per; c++) {
+      double w[5], u[5];
+      for (int v = 0; v < 5; v++) u[v] = U[((size_t)b * 5 + v) * per + c];
+      prim_from_cons(u, m->gamma, w);
+      for (int v = 0; v < 5; v++) W[((size_t)b * 5 + v) * per + c] = w[v];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* MC limiter (van Leer 1977)                                                */
+/* ------------------------------------------------------------------------ */
+
+double or_mc(double a, double b) {
+  if (a * b <= 0.0) return 0.0;
+  double s = fmin(fmin(2.0 * fabs(a), 2.0 * fabs(b)), 0.5 * fabs(a + b));
+  return a > 0.0 ? s : -s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* guard cells                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Interior value of a cell of the level-l lattice that lies inside some block
+ * of level l; a non-leaf block's value is the pairwise mean of its children
+ * (restriction).  g must lie inside the domain. */
+static double interior_value(const or_mesh *m, const double *U, int l, const int64_t g[3],
+                             int v) {
+  int64_t bcoord[3];
+  for (int d = 0; d < 3; d++) bcoord[d] = g[d] / m->nxb;
+  int b = lookup(m, l, bcoord);
+  if (b < 0) return NAN;
+  if (m->leaf[b]) {
+    int loc[3];
+    for (int d = 0; d < 3; d++) loc[d] = (int)(g[d] - m->origin[b * 3 + d]) + (d < m->ndim ? m->ng : 0);
+    return U[cell_index(m, b, v, loc[2], loc[1], loc[0])];
+  }
+  /* restriction: pairwise sums x first, then y, then z */
+  double f[8];
+  for (int c = 0; c < (1 << m->ndim); c++) {
+    int64_t gf[3];
+    for (int d = 0; d < 3; d++) gf[d] = d < m->ndim ? 2 * g[d] + ((c >> d) & 1) : 0;
+    f[c] = interior_value(m, U, l + 1, gf, v);
+  }
+  if (m->ndim == 2) return ((f[0] + f[1]) + (f[2] + f[3])) * 0.25;
+  return (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) * 0.125;
+}
+
+/* Value of a guard cell at level-l lattice position g (may lie outside the
+ * domain).  Returns 0 on success. */
+static int guard_value(const or_mesh *m, const double *U, int l, const int64_t gin[3], int v,
+                       double *out) {
+  int64_t g[3];
+  for (int d = 0; d < 3; d++) {
+    g[d] = gin[d];
+    if (d >= m->ndim) { g[d] = 0; continue; }
+    int64_t N = m->ncell[l][d];
+    if (g[d] < 0 || g[d] >= N) {
+      if (m->bc[d][g[d] < 0 ? 0 : 1] == 1) {
+        g[d] = ((g[d] % N) + N) % N;            /* periodic: wrap */
+      } else {
+        g[d] = g[d] < 0 ? 0 : N - 1;            /* outflow: nearest interior cell */
+      }
+    }
+  }
+  int64_t bcoord[3];
+  for (int d = 0; d < 3; d++) bcoord[d] = g[d] / m->nxb;
+  int b = lookup(m, l, bcoord);
+  if (b >= 0) {
+    *out = interior_value(m, U, l, g, v);
+    return 0;
+  }
+  /* covered by a coarser leaf: conservative MC-limited linear prolongation */
+  if (l == 0) return -1;
+  int64_t gc[3], cb[3];
+  for (int d = 0; d < 3; d++) { gc[d] = g[d] / 2; cb[d] = gc[d] / m->nxb; }
+  if (m->ndim == 2) { gc[2] = 0; cb[2] = 0; }
+  int c = lookup(m, l - 1, cb);
+  if (c < 0 || !m->leaf[c]) return -1;
+  int loc[3];
+  for (int d = 0; d < 3; d++) loc[d] = (int)(gc[d] - m->origin[c * 3 + d]) + (d < m->ndim ? m->ng : 0);
+  double uc = U[cell_index(m, c, v, loc[2], loc[1], loc[0])];
+  double val = uc;
+  for (int d = 0; d < m->ndim; d++) {
+    int lm[3] = {loc[0], loc[1], loc[2]}, lp[3] = {loc[0], loc[1], loc[2]};
+    lm[d] -= 1; lp[d] += 1;
+    double um = U[cell_index(m, c, v, lm[2], lm[1], lm[0])];
+    double up = U[cell_index(m, c, v, lp[2], lp[1], lp[0])];
+    double sigma = or_mc(uc - um, up - uc);
+    double s = (g[d] % 2 == 0) ? -0.25 : 0.25;
+    val = val + s * sigma;
+  }
+  *out = val;
+  return 0;
+}
+
+int or_guardcell_fill(const or_mesh *m, double *U) {
+  int fail = 0;
+  int P = m->P, PZ = m->PZ, ng = m->ng, n = m->nxb;
+  for (int l = 0; l <= m->lmax; l++) {
+#pragma omp parallel for schedule(dynamic) num_threads(or_get_threads()) reduction(| : fail)
+    for (int b = 0; b < m->nb; b++) {
+      if (m->level[b] != l || !m->leaf[b]) continue;
+      for (int k = 0; k < PZ; k++)
+        for (int j = 0; j < P; j++)
+          for (int i = 0; i < P; i++) {
+            int inside = (i >= ng && i < ng + n) && (j >= ng && j < ng + n) &&
+                         (m->ndim == 2 || (k >= ng && k < ng + n));
+            if (inside) continue;
+            int64_t g[3];
+            g[0] = m->origin[b * 3 + 0] + (i - ng);
+            g[1] = m->origin[b * 3 + 1] + (j - ng);
+            g[2] = m->ndim == 3 ? m->origin[b * 3 + 2] + (k - ng) : 0;
+            for (int v = 0; v < 5; v++) {
+              double val;
+              if (guard_value(m, U, l, g, v, &val)) { fail |= 1; val = NAN; }
+              U[cell_index(m, b, v, k, j, i)] = val;
+            }
+          }
+    }
+  }
+  if (fail) { set_err("guard cell without a source block (mesh not 2:1 balanced?)"); return -1; }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* time step                                                                 */
+/* ------------------------------------------------------------------------ */
+
+int or_compute_dt(const or_mesh *m, const double *U, double cfl, int form, double *dt) {
+  double smax = 0.0;
+  int n = m->nxb, ng = m->ng;
+  int nz = m->ndim == 3 ? n : 1, kz = m->ndim == 3 ? ng : 0;
+#pragma omp parallel for schedule(static) num_threads(or_get_threads()) reduction(max : smax)
+  for (int b = 0; b < m->nb; b++) {
+    if (!m->leaf[b]) continue;
+    const double *dx = m->dx[m->level[b]];
+    for (int k = 0; k < nz; k++)
+      for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) {
+          double u[5], w[5];
+          for (int v = 0; v < 5; v++) u[v] = U[cell_index(m, b, v, k + kz, j + ng, i + ng)];
+          prim_from_cons(u, m->gamma, w);
+          double c = sqrt(m->gamma * w[4] / w[0]);
+          double s = 0.0;
+          for (int d = 0; d < m->ndim; d++) {
+            double sd = (fabs(w[1 + d]) + c) / dx[d];
+            if (form == 0) s = s + sd;
+            else s = fmax(s, sd);
+          }
+          if (!(s <= smax)) smax = s;   /* NaN propagates */
+        }
+  }
+  *dt = cfl / smax;
+  return isfinite(*dt) ? 0 : -4;
+}
+
+/* ------------------------------------------------------------------------ */
+/* HLLC flux (Toro, Spruce & Speares 1994)                                   */
+/* ------------------------------------------------------------------------ */
+
+static void phys_flux(const double W[5], const double Uc[5], int d, double F[5]) {
+  int nrm = 1 + d;
+  double un = W[nrm];
+  F[0] = W[0] * un;
+  for (int k = 0; k < 3; k++) F[1 + k] = W[0] * un * W[1 + k];
+  F[nrm] += W[4];
+  F[4] = un * (Uc[4] + W[4]);
+}
+
+void or_hllc(const double WL[5], const double WR[5], int d, double gamma, double F[5]) {
+  int nrm = 1 + d;
+  double rL = WL[0], pL = WL[4], uL = WL[nrm];
+  double rR = WR[0], pR = WR[4], uR = WR[nrm];
+  double cL = sqrt(gamma * pL / rL), cR = sqrt(gamma * pR / rR);
+  double SL = fmin(uL - cL, uR - cR);
+  double SR = fmax(uL + cL, uR + cR);
+  double UL[5], UR[5], FL[5], FR[5];
+  cons_from_prim(WL, gamma, UL);
+  cons_from_prim(WR, gamma, UR);
+  phys_flux(WL, UL, d, FL);
+  phys_flux(WR, UR, d, FR);
+  double Sst = (pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) /
+               (rL * (SL - uL) - rR * (SR - uR));
+  const double *WK, *UK, *FK;
+  double SK;
+  if (SL >= 0.0) { for (int q = 0; q < 5; q++) F[q] = FL[q]; return; }
+  if (Sst >= 0.0) { WK = WL; UK = UL; FK = FL; SK = SL; }
+  else if (SR > 0.0) { WK = WR; UK = UR; FK = FR; SK = SR; }
+  else { for (int q = 0; q < 5; q++) F[q] = FR[q]; return; }
+  double rK = WK[0], uK = WK[nrm], pK = WK[4];
+  double fac = rK * (SK - uK) / (SK - Sst);
+  double Us[5];
+  Us[0] = fac;
+  for (int k = 0; k < 3; k++) Us[1 + k] = fac * WK[1 + k];
+  Us[nrm] = fac * Sst;
+  Us[4] = fac * (UK[4] / rK + (Sst - uK) * (Sst + pK / (rK * (SK - uK))));
+  for (int q = 0; q < 5; q++) F[q] = FK[q] + SK * (Us[q] - UK[q]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* hydro step of one leaf block                                              */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  double *W;    /* [5][PZ][P][P] primitives */
+  double *FSm;  /* [3][5][PZ][P][P] face state at the lower face of a cell, per direction */
+  double *FSp;  /* [3][5][PZ][P][P] face state at the upper face */
+  double *F;    /* [3][5][PZ][P][P] flux through the lower face of a cell */
+} or_work;
+
+static size_t wi(const or_mesh *m, int v, int k, int j, int i) {
+  return (((size_t)v * m->PZ + k) * m->P + j) * m->P + i;
+}
+
+static int advance_block(const or_mesh *m, const double *U, double *Unew, double dt, int b,
+                         or_work *w, double *bflux) {
+  int P = m->P, PZ = m->PZ, ng = m->ng, n = m->nxb, nd = m->ndim;
+  size_t per = (size_t)5 * PZ * P * P;
+  double gamma = m->gamma;
+  const double *dx = m->dx[m->level[b]];
+  int lo[3], hi[3];  /* padded index range of the interior, per axis */
+  for (int d = 0; d < 3; d++) {
+    lo[d] = d < nd ? ng : 0;
+    hi[d] = d < nd ? ng + n : 1;
+  }
+  /* 1. primitives on every padded cell */
+  for (int k = 0; k < PZ; k++)
+    for (int j = 0; j < P; j++)
+      for (int i = 0; i < P; i++) {
+        double u[5], q[5];
+        for (int v = 0; v < 5; v++) u[v] = U[cell_index(m, b, v, k, j, i)];
+        prim_from_cons(u, gamma, q);
+        for (int v = 0; v < 5; v++) w->W[wi(m, v, k, j, i)] = q[v];
+      }
+  /* 2. slopes, Hancock predictor and face states on the interior grown by one */
+  for (int k = lo[2] - (nd == 3); k < hi[2] + (nd == 3); k++)
+    for (int j = lo[1] - 1; j < hi[1] + 1; j++)
+      for (int i = lo[0] - 1; i < hi[0] + 1; i++) {
+        double W0[5], dW[3][5] = {{0}}, Wh[5], fm[3][5], fp[3][5];
+        for (int v = 0; v < 5; v++) W0[v] = w->W[wi(m, v, k, j, i)];
+        for (int d = 0; d < nd; d++) {
+          int om[3] = {i, j, k}, op[3] = {i, j, k};
+          om[d] -= 1; op[d] += 1;
+          for (int v = 0; v < 5; v++) {
+            double wm = w->W[wi(m, v, om[2], om[1], om[0])];
+            double wp = w->W[wi(m, v, op[2], op[1], op[0])];
+            dW[d][v] = or_mc(W0[v] - wm, wp - W0[v]);
+          }
+        }
+        /* primitive quasi-linear form: A_d(W) dW_d for each direction */
+        double acc[5] = {0, 0, 0, 0, 0};
+        for (int d = 0; d < nd; d++) {
+          int nrm = 1 + d;
+          double un = W0[nrm], r = W0[0], p = W0[4];
+          double a[5];
+          a[0] = un * dW[d][0] + r * dW[d][nrm];
+          for (int t = 0; t < 3; t++) a[1 + t] = un * dW[d][1 + t];
+          a[nrm] = a[nrm] + dW[d][4] / r;
+          a[4] = gamma * p * dW[d][nrm] + un * dW[d][4];
+          for (int v = 0; v < 5; v++) acc[v] = acc[v] + a[v] / dx[d];
+        }
+        for (int v = 0; v < 5; v++) Wh[v] = W0[v] - 0.5 * dt * acc[v];
+        int bad = 0;
+        for (int d = 0; d < nd; d++)
+          for (int v = 0; v < 5; v++) {
+            fm[d][v] = Wh[v] - 0.5 * dW[d][v];
+            fp[d][v] = Wh[v] + 0.5 * dW[d][v];
+          }
+        for (int d = 0; d < nd; d++)
+          if (!(fm[d][0] > 0.0) || !(fm[d][4] > 0.0) || !(fp[d][0] > 0.0) || !(fp[d][4] > 0.0))
+            bad = 1;
+        if (bad) /* positivity fallback: first order for this cell */
+          for (int d = 0; d < nd; d++)
+            for (int v = 0; v < 5; v++) { fm[d][v] = W0[v]; fp[d][v] = W0[v]; }
+        for (int d = 0; d < nd; d++)
+          for (int v = 0; v < 5; v++) {
+            w->FSm[d * per + wi(m, v, k, j, i)] = fm[d][v];
+            w->FSp[d * per + wi(m, v, k, j, i)] = fp[d][v];
+          }
+      }
+  /* 3. HLLC flux through the lower face of every cell that owns a face of the
+   *    interior: along d the cell index runs lo..hi (hi = upper block face). */
+  for (int d = 0; d < nd; d++) {
+    int hk = hi[2] + (d == 2), hj = hi[1] + (d == 1), hii = hi[0] + (d == 0);
+    for (int k = lo[2]; k < hk; k++)
+      for (int j = lo[1]; j < hj; j++)
+        for (int i = lo[0]; i < hii; i++) {
+          int o[3] = {i, j, k};
+          o[d] -= 1;
+          double WL[5], WR[5], F[5];
+          for (int v = 0; v < 5; v++) {
+            WL[v] = w->FSp[d * per + wi(m, v, o[2], o[1], o[0])];
+            WR[v] = w->FSm[d * per + wi(m, v, k, j, i)];
+          }
+          or_hllc(WL, WR, d, gamma, F);
+          for (int v = 0; v < 5; v++) w->F[d * per + wi(m, v, k, j, i)] = F[v];
+        }
+  }
+  /* 4. conservative update of the interior, directions summed x, y, z */
+  int bad = 0;
+  for (int k = lo[2]; k < hi[2]; k++)
+    for (int j = lo[1]; j < hi[1]; j++)
+      for (int i = lo[0]; i < hi[0]; i++) {
+        double un[5];
+        for (int v = 0; v < 5; v++) {
+          double div = 0.0;
+          for (int d = 0; d < nd; d++) {
+            int o[3] = {i, j, k};
+            o[d] += 1;
+            double fl = w->F[d * per + wi(m, v, k, j, i)];
+            double fr = w->F[d * per + wi(m, v, o[2], o[1], o[0])];
+            div = div + (fl - fr) / dx[d];
+          }
+          un[v] = U[cell_index(m, b, v, k, j, i)] + dt * div;
+          Unew[cell_index(m, b, v, k, j, i)] = un[v];
+        }
+        double q[5];
+        prim_from_cons(un, gamma, q);
+        if (!(q[0] > 0.0) || !(q[4] > 0.0)) bad = 1;
+      }
+  /* 5. block-boundary fluxes for flux correction */
+  if (bflux) {
+    int nf = nd == 3 ? n * n : n;
+    for (int d = 0; d < nd; d++)
+      for (int s = 0; s < 2; s++) {
+        double *dst = bflux + (((size_t)b * 2 * nd + 2 * d + s) * 5) * nf;
+        int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2; /* transverse axes, lower first */
+        for (int v = 0; v < 5; v++)
+          for (int t2 = 0; t2 < (nd == 3 ? n : 1); t2++)
+            for (int t1 = 0; t1 < n; t1++) {
+              int c[3];
+              c[d] = s == 0 ? lo[d] : hi[d];
+              c[a1] = lo[a1] + t1;
+              if (nd == 3) c[a2] = lo[a2] + t2; else c[2] = 0;
+              dst[(size_t)v * nf + (size_t)t2 * n + t1] = w->F[d * per + wi(m, v, c[2], c[1], c[0])];
+            }
+      }
+  }
+  return bad;
+}
+
+static void reflux_block(const or_mesh *m, double *Unew, double dt, int c, const double *bflux) {
+  int nd = m->ndim, n = m->nxb, ng = m->ng, l = m->level[c];
+  int nf = nd == 3 ? n * n : n;
+  if (l >= m->lmax) return;
+  for (int d = 0; d < nd; d++)
+    for (int s = 0; s < 2; s++) {
+      /* same-level neighbour across this face */
+      int64_t bc[3];
+      for (int e = 0; e < 3; e++) bc[e] = m->origin[c * 3 + e] / n;
+      bc[d] += s ? 1 : -1;
+      int64_t NB = m->nblk[l][d];
+      if (bc[d] < 0 || bc[d] >= NB) {
+        if (m->bc[d][s] != 1) continue;
+        bc[d] = (bc[d] + NB) % NB;
+      }
+      int nb = lookup(m, l, bc);
+      if (nb < 0 || m->leaf[nb]) continue;
+      int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
+      /* fine-lattice index of the fine cells on the far side of the face */
+      int64_t NF = m->ncell[l + 1][d];
+      int64_t gfd = s ? 2 * (m->origin[c * 3 + d] + n) : 2 * m->origin[c * 3 + d] - 1;
+      gfd = ((gfd % NF) + NF) % NF;
+      int fine_face = s ? 0 : 1; /* the fine block's lower (s=+) or upper face */
+      const double *Fc = bflux + (((size_t)c * 2 * nd + 2 * d + s) * 5) * nf;
+      for (int t2 = 0; t2 < (nd == 3 ? n : 1); t2++)
+        for (int t1 = 0; t1 < n; t1++)
+          for (int v = 0; v < 5; v++) {
+            double f[4];
+            int cnt = 0;
+            for (int b2 = 0; b2 < (nd == 3 ? 2 : 1); b2++)
+              for (int b1 = 0; b1 < 2; b1++) {
+                int64_t gf[3] = {0, 0, 0};
+                gf[d] = gfd;
+                gf[a1] = 2 * (m->origin[c * 3 + a1] + t1) + b1;
+                if (nd == 3) gf[a2] = 2 * (m->origin[c * 3 + a2] + t2) + b2;
+                int64_t fb[3];
+                for (int e = 0; e < 3; e++) fb[e] = gf[e] / n;
+                int fblk = lookup(m, l + 1, fb);
+                int u1 = (int)(gf[a1] - m->origin[fblk * 3 + a1]);
+                int u2 = nd == 3 ? (int)(gf[a2] - m->origin[fblk * 3 + a2]) : 0;
+                const double *Ff = bflux + (((size_t)fblk * 2 * nd + 2 * d + fine_face) * 5) * nf;
+                f[cnt++] = Ff[(size_t)v * nf + (size_t)u2 * n + u1];
+              }
+            double fbar = nd == 3 ? ((f[0] + f[1]) + (f[2] + f[3])) * 0.25 : (f[0] + f[1]) * 0.5;
+            double fc = Fc[(size_t)v * nf + (size_t)t2 * n + t1];
+            int cc[3];
+            cc[d] = s ? ng + n - 1 : ng;
+            cc[a1] = ng + t1;
+            if (nd == 3) cc[a2] = ng + t2; else cc[2] = 0;
+            size_t idx = cell_index(m, c, v, cc[2], cc[1], cc[0]);
+            double corr = dt * (fc - fbar) / m->dx[l][d];
+            if (s) Unew[idx] = Unew[idx] + corr;
+            else Unew[idx] = Unew[idx] - corr;
+          }
+    }
+}
+
+static void restrict_block(const or_mesh *m, double *U, int p) {
+  int nd = m->ndim, n = m->nxb, ng = m->ng;
+  int nz = nd == 3 ? n : 1, kz = nd == 3 ? ng : 0;
+  for (int v = 0; v < 5; v++)
+    for (int k = 0; k < nz; k++)
+      for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) {
+          int cx = 2 * i >= n, cy = 2 * j >= n, cz = nd == 3 && 2 * k >= n;
+          int ch = m->child[p * 8 + cx + 2 * cy + 4 * cz];
+          int fi = 2 * i - cx * n, fj = 2 * j - cy * n, fk = 2 * k - cz * n;
+          double f[8];
+          for (int c = 0; c < (1 << nd); c++) {
+            int a = c & 1, bb = (c >> 1) & 1, cc = (c >> 2) & 1;
+            f[c] = U[cell_index(m, ch, v, nd == 3 ? fk + cc + ng : 0, fj + bb + ng, fi + a + ng)];
+          }
+          double val = nd == 2 ? ((f[0] + f[1]) + (f[2] + f[3])) * 0.25
+                               : (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) * 0.125;
+          U[cell_index(m, p, v, k + kz, j + ng, i + ng)] = val;
+        }
+}
+
+int or_hydro_advance(const or_mesh *m, const double *U, double *Unew, double dt, int reflux,
+                     double *bflux, int nsel, const int *sel) {
+  size_t per = (size_t)5 * m->PZ * m->P * m->P;
+  int nd = m->ndim, n = m->nxb;
+  int nf = nd == 3 ? n * n : n;
+  double *flux = bflux;
+  int own = 0;
+  if (!flux && !sel && m->lmax > 0) {
+    flux = (double *)calloc((size_t)m->nb * 2 * nd * 5 * nf, sizeof(double));
+    own = 1;
+  }
+  int count = sel ? nsel : m->nb;
+  int bad = 0;
+#pragma omp parallel num_threads(or_get_threads()) reduction(| : bad)
+  {
+    or_work w;
+    w.W = (double *)malloc(sizeof(double) * per);
+    w.FSm = (double *)malloc(sizeof(double) * per * 3);
+    w.FSp = (double *)malloc(sizeof(double) * per * 3);
+    w.F = (double *)malloc(sizeof(double) * per * 3);
+#pragma omp for schedule(dynamic)
+    for (int t = 0; t < count; t++) {
+      int b = sel ? sel[t] : t;
+      if (!m->leaf[b]) continue;
+      bad |= advance_block(m, U, Unew, dt, b, &w, flux);
+    }
+    free(w.W); free(w.FSm); free(w.FSp); free(w.F);
+  }
+  if (!sel && m->lmax > 0) {
+    if (reflux) {
+#pragma omp parallel for schedule(dynamic) num_threads(or_get_threads())
+      for (int b = 0; b < m->nb; b++)
+        if (m->leaf[b]) reflux_block(m, Unew, dt, b, flux);
+    }
+    for (int l = m->lmax - 1; l >= 0; l--) {
+#pragma omp parallel for schedule(dynamic) num_threads(or_get_threads())
+      for (int b = 0; b < m->nb; b++)
+        if (!m->leaf[b] && m->level[b] == l) restrict_block(m, Unew, b);
+    }
+    /* positivity after correction */
+    int nz = nd == 3 ? n : 1, kz = nd == 3 ? m->ng : 0;
+    for (int b = 0; b < m->nb && !bad; b++) {
+      if (!m->leaf[b]) continue;
+      for (int k = 0; k < nz; k++)
+        for (int j = 0; j < n; j++)
+          for (int i = 0; i < n; i++) {
+            double u[5], q[5];
+            for (int v = 0; v < 5; v++) u[v] = Unew[cell_index(m, b, v, k + kz, j + m->ng, i + m->ng)];
+            prim_from_cons(u, m->gamma, q);
+            if (!(q[0] > 0.0) || !(q[4] > 0.0)) bad = 1;
+          }
+    }
+  }
+  if (own) free(flux);
+  return bad ? -4 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* conserved totals                                                          */
+/* ------------------------------------------------------------------------ */
+
+void or_conserved_totals(const or_mesh *m, const double *U, double out[5]) {
+  int n = m->nxb, ng = m->ng, nd = m->ndim;
+  int nz = nd == 3 ? n : 1, kz = nd == 3 ? ng : 0;
+  for (int v = 0; v < 5; v++) {
+    double sum = 0.0, comp = 0.0;
+    for (int b = 0; b < m->nb; b++) {
+      if (!m->leaf[b]) continue;
+      const double *dx = m->dx[m->level[b]];
+      double dV = dx[0] * dx[1] * (nd == 3 ? dx[2] : 1.0);
+      double bs = 0.0, bcmp = 0.0;
+      for (int k = 0; k < nz; k++)
+        for (int j = 0; j < n; j++)
+          for (int i = 0; i < n; i++) {
+            double y = U[cell_index(m, b, v, k + kz, j + ng, i + ng)] - bcmp;
+            double t = bs + y;
+            bcmp = (t - bs) - y;
+            bs = t;
+          }
+      double y = bs * dV - comp;
+      double t = sum + y;
+      comp = (t - sum) - y;
+      sum = t;
+    }
+    out[v] = sum;
+  }
+}
