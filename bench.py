@@ -1,0 +1,334 @@
+"""Benchmark of the block-AMR Euler hot path on GB300.
+
+One step = dt max-reduction + guard-cell fill + fused MUSCL-Hancock/HLLC
+update (+ flux correction and restriction on AMR meshes) of the whole block
+set, through the C ABI (libfx).  Default workload: the 3D Kelvin-Helmholtz
+shear layer, 256^3 cells as 4096 blocks of 16^3 (+4 guard cells), periodic,
+FP64 -- the configuration the zone-updates/s metric is quoted on.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+
+Multi-GPU (torchrun, one rank per GPU): every rank advances its own
+independent replica of the workload (no data-path collective); value is the
+sum of zones over ranks divided by the slowest rank's time (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "zone-updates/s"
+UNIT = "zone-updates/s"
+HBM_BYTES_PER_ZONE = {"f64": 80.0, "f32bulk": 40.0}
+# FP64 arithmetic per zone update, counted on the scheme's definition
+# (each +, -, *, /, sqrt = 1): primitives 12, MC slopes 105, Hancock predictor
+# 77, face states 60, HLLC 3 x 98, update 55.
+ALGO_FLOPS_PER_ZONE = 603.0
+# FP64 peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz.
+FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (also exercised by the gloo CPU tests)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(zones_local: float, seconds_local: float, device=None):
+    """Whole-job throughput: sum of zones over ranks / max time over ranks."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return zones_local, seconds_local
+    z = torch.tensor([zones_local], dtype=torch.float64, device=device)
+    t = torch.tensor([seconds_local], dtype=torch.float64, device=device)
+    dist.all_reduce(z, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(z.item()), float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline
+# ---------------------------------------------------------------------------
+
+def oracle_sample(workload: str, target_s: float = 12.0, max_steps: int = 50):
+    """Time the FP64 oracle, as it is, on a bounded sample of the workload:
+    the same block size, physics and boundaries on 4^3 blocks (64^3 cells),
+    full steps (dt, guard fill, update) on all host cores."""
+    import oracle
+    from paper_2208_11630_gb300 import inputs
+    if workload == "kh3d":
+        mesh = inputs.uniform_mesh(3, (4, 4, 4), 16, 4, inputs.PERIODIC)
+        W = inputs.kh_state(mesh)
+        desc = "KH shear layer, 64^3 cells as 4^3 blocks of 16^3 (+4 guard), periodic"
+    else:
+        mesh, W, _, _ = inputs.workload(workload, scale=None if workload != "advection3d" else 4)
+        desc = f"{workload} sample"
+    om = oracle.OracleMesh(mesh, 1.4)
+    U = om.prim_to_cons(W)
+    zones = mesh.leaf_zones()
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps:
+        U, _ = om.step(U, cfl=0.8)
+        steps += 1
+        if time.perf_counter() - t0 > target_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": zones * steps / dt, "unit": UNIT, "cores": oracle.get_threads(),
+            "kind": "oracle", "sample": f"{desc}; {steps} full steps in {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2208_11630_gb300 import inputs
+    oracle.build()
+    mesh = inputs.uniform_mesh(3, (4, 4, 4), 16, 4, inputs.PERIODIC)
+    om = oracle.OracleMesh(mesh, 1.4)
+    U = om.prim_to_cons(inputs.kh_state(mesh))
+    zones = mesh.leaf_zones()
+    for _ in range(args.warmup):
+        U, _ = om.step(U)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U, _ = om.step(U)
+    sec = time.perf_counter() - t0
+    v = zones * args.steps / sec
+    sample = ("FP64 CPU oracle, KH shear layer 64^3 cells as 4^3 blocks of 16^3 (+4 guard), "
+              f"periodic; each step one full step of that sample; {args.steps} steps")
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, "kh3d_64^3_sample"),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.get_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args, name):
+    return {"workload": name, "blocks": 4096 if "256" in name else 64, "nxb": 16, "nguard": 4,
+            "cells": 256 ** 3 if "256" in name else 64 ** 3, "bc": "periodic", "cfl": 0.8,
+            "precision": args.precision,
+            "l2": "inputs larger than L2 (2.26 GB per FP64 state buffer vs 129 MB L2)"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2208_11630_gb300 import fx, inputs
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    fx.load()
+
+    mesh, W, gamma, cfl = inputs.workload(args.workload)
+    zones_per_step = mesh.leaf_zones()
+    bs = fx.BlockSet(mesh, gamma, device=dev)
+    bs.set_primitive(W)
+    U0 = bs.state()          # host copy of the initial state (for the e2e leg)
+    del W
+    stream = torch.cuda.Stream(device=dev)
+    sptr = stream.cuda_stream
+    dtp = bs.dt.data_ptr()
+
+    def step():
+        fx.fx_compute_dt(bs.ctx, bs.bs, cfl, dtp, sptr)
+        fx.fx_guardcell_fill(bs.ctx, bs.bs, sptr)
+        fx.fx_hydro_advance(bs.ctx, bs.bs, dtp, sptr)
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    if bs.status() != 0:
+        raise RuntimeError("non-physical state during warm-up")
+
+    # ---- device-timed region
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = fx.load().fx_kernel_launches()
+    start.record(stream)
+    for k in range(args.steps):
+        fx.fx_compute_dt(bs.ctx, bs.bs, cfl, dtp, sptr)
+        fx.fx_guardcell_fill(bs.ctx, bs.bs, sptr)
+        ev[k][0].record(stream)
+        fx.fx_hydro_advance(bs.ctx, bs.bs, dtp, sptr)
+        ev[k][1].record(stream)
+    end.record(stream)
+    torch.cuda.synchronize()
+    launches = fx.load().fx_kernel_launches() - l0
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    sec = start.elapsed_time(end) / 1e3
+    hydro_s = np.mean([a.elapsed_time(b) for a, b in ev]) / 1e3
+    if bs.status() != 0:
+        raise RuntimeError("non-physical state in the timed region")
+    zones_all, sec_max = aggregate(zones_per_step * args.steps, sec, dev)
+    value = zones_all / sec_max
+
+    # ---- end-to-end through host buffers (pinned), one step per call
+    host_in = torch.from_numpy(U0).to(bs.dtype).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    fx.fx_run_host(bs.ctx, bs.bs, host_in.numpy(), host_out.numpy(), 1, cfl, stream=sptr)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        fx.fx_run_host(bs.ctx, bs.bs, host_in.numpy(), host_out.numpy(), 1, cfl, stream=sptr)
+    e2e_sec = time.perf_counter() - t0
+    ez, esec = aggregate(zones_per_step * e2e_steps, e2e_sec, dev)
+    state_bytes = host_in.numel() * host_in.element_size()
+
+    peaks, peak_kind = load_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved_flops = ALGO_FLOPS_PER_ZONE * zones_per_step / hydro_s
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sec_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": workload_config(args, "kh3d_256^3") | {"replicas": ws},
+        "roofline": {
+            "bound": "alu", "kernel": "k_hydro<3,16,double,double>",
+            "achieved": achieved_flops / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
+            "unit": "TFLOP/s", "frac": achieved_flops / FP64_PEAK_FLOPS, "traffic": None,
+            "peak_kind": "derived FP64 DFMA rate (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+            "algorithmic_flops_per_zone": ALGO_FLOPS_PER_ZONE,
+            "hydro_ms": hydro_s * 1e3,
+            "hbm_frac_of_step": (HBM_BYTES_PER_ZONE["f64"] * value / ws) / (hbm_peak * 1e9),
+            "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind,
+        },
+        "e2e": {"value": ez / esec, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = oracle_sample(args.workload)
+        except Exception as e:  # report, never fake
+            line["cpu_baseline"] = {"value": None, "error": str(e)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    bs.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="kh3d")
+    ap.add_argument("--precision", default="f64", choices=["f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,190 @@
+/*
+ * fx.h -- C ABI of libfx, the GB300 (sm_103a) block-AMR compressible Euler
+ * hot path.
+ *
+ * The operations follow the problem statement of Flash-X (arXiv 2208.11630):
+ * physics units update the mesh one block at a time and call Grid functions
+ * between those updates to reconcile block boundaries across refinement
+ * levels (Section 2); the mesh is a uniform grid or an octree AMR grid
+ * (PARAMESH, Section 2); the compressible hydro solver is explicit, unsplit
+ * and of predictor-corrector type, with a perfect-gas EOS (Section 2.2).  The concrete scheme (MC-limited MUSCL-Hancock, HLLC, Berger-
+ * Colella flux correction, CFL max-reduction) is the textbook one; the paper
+ * prints no equations.
+ *
+ * Conventions shared by every call:
+ *   - Return value: FX_OK (0) or a negative FX_ERR_* code; nothing throws.
+ *     The text of the last error of a context is in fx_last_error().
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Every call is stream-ordered and asynchronous unless
+ *     its comment says it synchronises.
+ *   - Ownership: state buffers are owned by the caller and only borrowed; the
+ *     library owns its mesh tables, flux registers and reduction scratch and
+ *     frees them in fx_blocks_destroy / fx_finalize.
+ *   - Threads: one context per host thread.
+ *   - Layout of a state buffer: U[block][var][z][y][x], x fastest,
+ *     var = (rho, m_x, m_y, m_z, E), P = nxb + 2*nguard cells per padded
+ *     axis, one z-plane in 2D (m_z stays 0).  Element type: double for
+ *     FX_F64, float for FX_F32BULK.  Interior cell (i, j, k) is at padded
+ *     index (i + nguard, j + nguard, k + nguard) (k + 0 in 2D).
+ *   - Device errors (a non-positive density or pressure after an update) are
+ *     latched in a device status word and reported by fx_status().
+ */
+#ifndef FX_H
+#define FX_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FX_API __attribute__((visibility("default")))
+#else
+#define FX_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fx_ctx fx_ctx;        /* opaque: options, last error          */
+typedef struct fx_blocks fx_blocks;  /* opaque: one block set (mesh + state) */
+
+enum {
+  FX_OK = 0,
+  FX_ERR_ARG = -1,         /* invalid argument                              */
+  FX_ERR_CUDA = -2,        /* a CUDA runtime call failed                    */
+  FX_ERR_OOM = -3,         /* device or host allocation failed              */
+  FX_ERR_UNPHYSICAL = -4,  /* rho <= 0 or p <= 0 (or NaN) after an update   */
+  FX_ERR_TIMEOUT = -5,     /* a bounded device wait gave up                 */
+  FX_ERR_STATE = -6,       /* call out of order (e.g. no state attached)    */
+  FX_ERR_MESH = -7         /* mesh not a valid 2:1-balanced octree          */
+};
+
+enum { FX_F64 = 0, FX_F32BULK = 1 };        /* state element type            */
+enum { FX_BC_OUTFLOW = 0, FX_BC_PERIODIC = 1 };
+
+/* fx_init: create a context for a perfect gas with ratio of specific heats
+ * `gamma` (> 1), default block size `nxb` interior cells per axis (a
+ * multiple of 8 in 8..64) and `nguard` guard cells per side (2..nxb/2; the
+ * scheme reads 2).
+ * Paper: the perfect-gas EOS of Section 2.2; blocks with guard cells of the
+ * Grid unit, Section 2.  *out receives the context.  Errors: FX_ERR_ARG,
+ * FX_ERR_CUDA (no usable device), FX_ERR_OOM. */
+FX_API int fx_init(double gamma, int nxb, int nguard, fx_ctx **out);
+
+/* fx_finalize: destroy a context (block sets must be destroyed first). */
+FX_API int fx_finalize(fx_ctx *ctx);
+
+/* fx_set_option: set a numeric option of the context.
+ *   "cfl_form"  0 = dt from the sum over directions of (|u_d|+c)/dx_d
+ *               (default), 1 = from the maximum over directions;
+ *   "reflux"    1 = apply fine-to-coarse flux correction (default), 0 = off.
+ * Errors: FX_ERR_ARG for an unknown key or value. */
+FX_API int fx_set_option(fx_ctx *ctx, const char *key, double value);
+
+/* fx_last_error: NUL-terminated text of the last error of `ctx` (owned by
+ * the context, valid until its next call). */
+FX_API const char *fx_last_error(const fx_ctx *ctx);
+
+/* fx_blocks_create: describe a block set and attach its two state buffers.
+ * Paper: uniform grid or PARAMESH octree of blocks (Section 2).
+ *   ndim        2 or 3;
+ *   nblocks     number of blocks (leaves and non-leaf parents);
+ *   nxb         interior cells per axis of every block (0 = context default);
+ *   nroot[3]    level-0 blocks per axis (entries beyond ndim ignored);
+ *   level[nb]   refinement level of each block, 0 = coarsest;
+ *   origin[nb][3] lower-corner cell index of each block in the lattice of its
+ *               own level (level l has nroot[d]*nxb*2^l cells along d);
+ *   parent[nb]  index of the parent block, -1 for level-0 blocks.  A block
+ *               is a leaf iff it is nobody's parent; non-leaf blocks hold the
+ *               restriction of their children;
+ *   lo[3], hi[3] physical domain; bc[6] = {x-, x+, y-, y+, z-, z+}
+ *               boundary kinds (FX_BC_*; periodic must be set on both sides);
+ *   precision   FX_F64 or FX_F32BULK (element type of the state buffers);
+ *   U0, U1      caller-owned device buffers of nblocks*5*PZ*P*P elements,
+ *               16-byte aligned.  U0 holds the initial state; U1 receives the
+ *               first update; they alternate afterwards (fx_blocks_current).
+ * The mesh must be 2:1 balanced (every guard region is covered by a block of
+ * the same level or by a leaf one level coarser).  Host arrays are copied;
+ * the call synchronises.  Errors: FX_ERR_ARG, FX_ERR_MESH, FX_ERR_OOM,
+ * FX_ERR_CUDA. */
+FX_API int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroot[3],
+                     const int *level, const int64_t *origin, const int *parent,
+                     const double lo[3], const double hi[3], const int bc[6],
+                     int precision, void *U0, void *U1, fx_blocks **out);
+
+/* fx_blocks_destroy: free the library-owned tables of a block set (the
+ * caller's buffers are untouched). */
+FX_API int fx_blocks_destroy(fx_blocks *bs);
+
+/* fx_blocks_current: index (0 or 1) of the buffer that holds the current
+ * state; flips after every fx_hydro_advance.  Negative on error. */
+FX_API int fx_blocks_current(const fx_blocks *bs);
+
+/* fx_prim_to_cons: fill the current buffer from primitive variables
+ * W[block][var][z][y][x] (device, double, var = rho, u, v, w, p; same
+ * layout and size as a state buffer) using the perfect-gas EOS
+ * E = p/(gamma-1) + rho |v|^2 / 2 (Section 2.2).  Every cell is converted. */
+FX_API int fx_prim_to_cons(fx_ctx *ctx, fx_blocks *bs, const double *W_dev, void *stream);
+
+/* fx_guardcell_fill: fill the guard cells of every leaf of the current
+ * buffer -- the Grid's reconciliation of block boundaries across levels
+ * (Section 2):
+ *   1. restrict every non-leaf block from its children (pairwise mean),
+ *      finest level first;
+ *   2. same-level copy from neighbour blocks, with outflow (zero-gradient)
+ *      or periodic physical boundaries;
+ *   3. level by level, conservative MC-limited linear prolongation into the
+ *      guards of leaves next to a coarser leaf.
+ * All nguard layers are filled, corners and edges included. */
+FX_API int fx_guardcell_fill(fx_ctx *ctx, fx_blocks *bs, void *stream);
+
+/* fx_compute_dt: CFL time step from the current buffer's leaf interiors,
+ * dt = cfl / max_cells sum_d (|u_d| + c) / dx_d, c = sqrt(gamma p / rho)
+ * (the maximum over d with cfl_form = 1).  The maximum is an exact,
+ * order-independent reduction.  `dt_dev` is a device double that receives
+ * dt (kept on the device so that a captured graph needs no host trip). */
+FX_API int fx_compute_dt(fx_ctx *ctx, fx_blocks *bs, double cfl, double *dt_dev, void *stream);
+
+/* fx_hydro_advance: one unsplit second-order step of all leaves with the
+ * time step read from the device double *dt_dev -- the per-block physics
+ * update of Section 2 with the predictor-corrector hydro of Section 2.2:
+ * primitive variables, MC-limited slopes, MUSCL-Hancock half step, HLLC
+ * fluxes, conservative update into the other buffer; then the fine-to-coarse
+ * flux correction at coarse-fine faces (if the "reflux" option is on) and
+ * restriction into the parents.  Requires filled guards.  The new state's
+ * buffer becomes current. */
+FX_API int fx_hydro_advance(fx_ctx *ctx, fx_blocks *bs, const double *dt_dev, void *stream);
+
+/* fx_step: fx_compute_dt, fx_guardcell_fill and fx_hydro_advance in order. */
+FX_API int fx_step(fx_ctx *ctx, fx_blocks *bs, double cfl, double *dt_dev, void *stream);
+
+/* fx_conserved_totals: out_host[v] = sum over leaf interior cells of U_v dV
+ * for the current buffer, summed per block in a fixed order on the device
+ * and over blocks with compensated summation on the host.  Synchronises. */
+FX_API int fx_conserved_totals(fx_ctx *ctx, fx_blocks *bs, double out_host[5], void *stream);
+
+/* fx_status: synchronise the device and report the latched device status of
+ * the block set (FX_OK or FX_ERR_UNPHYSICAL); clears the latch. */
+FX_API int fx_status(fx_ctx *ctx, fx_blocks *bs);
+
+/* fx_run_host: end-to-end convenience for callers that hold the state in
+ * host memory.  Copies U_host_in (page-locked host memory recommended) into
+ * the current buffer, runs `nsteps` full steps with CFL number `cfl`, and
+ * copies the current buffer to U_host_out.  *t_host (may be NULL) receives
+ * the simulated time advanced.  Synchronises. */
+FX_API int fx_run_host(fx_ctx *ctx, fx_blocks *bs, const void *U_host_in, void *U_host_out,
+                int nsteps, double cfl, double *t_host, void *stream);
+
+/* fx_block_fluxes: device pointer to the flux registers of block `b`
+ * ([2*ndim faces x-,x+,y-,y+,z-,z+][5][nxb^(ndim-1)], lower transverse axis
+ * fastest) written by the last fx_hydro_advance, or NULL if the block has no
+ * coarse-fine face.  For diagnostics and tests. */
+FX_API const double *fx_block_fluxes(const fx_blocks *bs, int b);
+
+/* fx_kernel_launches: number of CUDA kernels this library has launched in
+ * the process so far (all contexts).  Diagnostics for benchmarks. */
+FX_API long long fx_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FX_H */

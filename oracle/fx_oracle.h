@@ -6,10 +6,11 @@
  * leg may load it; the product library never links or calls it, and the two
  * share no code.
  *
- * What it computes (Flash-X, arXiv 2208.11630, Section 2: "block-by-block
- * update, interspersed with fine-coarse boundary resolution" on a uniform or
- * octree AMR grid; Section 2.2: unsplit predictor-corrector compressible hydro
- * with a perfect-gas EOS).  The paper names the method family only; the
+ * What it computes (Flash-X, arXiv 2208.11630, Section 2: physics advances
+ * the mesh one block at a time, with Grid calls in between that reconcile
+ * block boundaries across refinement levels, on a uniform or octree AMR grid;
+ * Section 2.2: an unsplit predictor-corrector compressible hydro solver with
+ * a perfect-gas EOS).  The paper names the method family only; the
  * concrete scheme is the textbook one:
  *   - perfect-gas EOS, p = (gamma-1)(E - |m|^2 / (2 rho)), c = sqrt(gamma p / rho);
  *   - MC-limited piecewise-linear slopes of the primitive variables

@@ -1,0 +1,72 @@
+// fx_internal.h -- types and kernel launchers shared by the libfx host code
+// and its CUDA translation units.  Not part of the public ABI (include/fx.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#define FX_MAXLEV 16
+
+namespace fx {
+
+// Guard-cell source of one neighbour slot of a leaf block.  Slot index
+// (sx+1) + 3 (sy+1) + 9 (sz+1) for sx, sy, sz in {-1, 0, 1}.
+enum SlotKind : int { SLOT_NONE = -1, SLOT_COPY = 0, SLOT_PROLONG = 1 };
+
+// Everything a kernel needs to know about a block set, passed by value.
+struct DevMesh {
+  int ndim, nxb, ng, P, PZ, nb, lmax;
+  long long vstride;             // elements of one variable of one block: PZ*P*P
+  long long bstride;             // elements of one block: 5*vstride
+  int bc[3][2];                  // FX_BC_* per axis and side
+  int ncell[FX_MAXLEV][3];       // cells per axis at each level
+  double dx[FX_MAXLEV][3];       // cell widths at each level
+  double idx[FX_MAXLEV][3];      // reciprocal cell widths
+  double gamma;
+  const int *level;              // [nb]
+  const int *origin;             // [nb][3], cell index in the block's level lattice
+  const int2 *slots;             // [nb][27] (kind, source block)
+  const int *child;              // [nb][8], -1 if none
+  const int *regidx;             // [nb] flux-register slot, -1 if none
+  int nfaces;                    // 2*ndim
+  int nface_cells;               // nxb^(ndim-1)
+};
+
+// Reflux work item: a coarse leaf with at least one face on a finer
+// neighbour.  fine[f][q] = register slot of the fine child that covers
+// transverse quarter q (q = h1 + 2 h2) of face f, -1 if the face is not
+// corrected.
+struct RefluxItem {
+  int block;
+  int fine[6][4];
+};
+
+// Launchers.  Each returns the launch status (cudaGetLastError).
+cudaError_t launch_prim_to_cons(const DevMesh &m, const double *W, void *U, int prec,
+                                cudaStream_t s);
+cudaError_t launch_restrict(const DevMesh &m, void *U, int prec, const int *parents, int n,
+                            cudaStream_t s);
+cudaError_t launch_guard_copy(const DevMesh &m, void *U, int prec, const int *leaves, int n,
+                              cudaStream_t s);
+cudaError_t launch_guard_prolong(const DevMesh &m, void *U, int prec, const int *leaves, int n,
+                                 cudaStream_t s);
+cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, const int *leaves,
+                         int n, const double *dt, double *regs, int *status, cudaStream_t s);
+cudaError_t launch_reflux(const DevMesh &m, void *Unew, int prec, const RefluxItem *items, int n,
+                          const double *dt, const double *regs, int *status, cudaStream_t s);
+cudaError_t launch_dt(const DevMesh &m, const void *U, int prec, const int *leaves, int n,
+                      double cfl, int form, double *dt_out, unsigned long long *scratch,
+                      cudaStream_t s);
+cudaError_t launch_totals(const DevMesh &m, const void *U, int prec, const int *leaves, int n,
+                          double *out, cudaStream_t s);
+
+// Process-wide count of kernels launched by the library.
+void count_launch(int n = 1);
+long long launch_count();
+
+// Shared memory the hydro kernel needs for a given configuration (bytes).
+size_t hydro_smem_bytes(int ndim, int tile, int prec);
+
+}  // namespace fx

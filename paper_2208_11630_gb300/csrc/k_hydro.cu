@@ -1,0 +1,420 @@
+// k_hydro.cu -- fused unsplit MUSCL-Hancock / HLLC update of leaf blocks.
+//
+// Paper: Flash-X (arXiv 2208.11630), Section 2.2 -- an unsplit compressible
+// hydro solver of predictor-corrector type, applied one block at a time
+// (Section 2).  Concrete scheme (textbook): primitive variables, MC-
+// limited slopes (van Leer 1977), Hancock half-step predictor in primitive
+// form (Toro ch. 14), HLLC flux with Davis speeds (Toro, Spruce & Speares
+// 1994), conservative update summed over x, y, z.  A cell whose predicted face
+// states are not all positive in density and pressure falls back to first
+// order (zero slopes, no predictor).
+//
+// GB300 design.  One CTA owns a T x T column tile of one block and marches it
+// along z.  Shared memory holds a ring of three primitive planes (radius-2
+// halo in x and y) and the x/y face states of the current plane; each face
+// flux is computed once by one thread and written over the face state it
+// consumed.  The thread owning column (i, j) keeps its z face states and z
+// fluxes in registers, so no z data touches shared memory.  Per plane: load
+// + primitives, predictor, fluxes, update, three barriers.
+#include "fx_internal.h"
+
+namespace fx {
+namespace {
+
+template <typename R>
+__device__ __forceinline__ R mc_lim(R a, R b) {
+  if (a * b <= R(0)) return R(0);
+  R s = fmin(fmin(R(2) * fabs(a), R(2) * fabs(b)), R(0.5) * fabs(a + b));
+  return a > R(0) ? s : -s;
+}
+
+// HLLC flux along direction D from primitive left/right states.
+template <int D, typename R>
+__device__ __forceinline__ void hllc(const R (&WL)[5], const R (&WR)[5], R g, R igm1,
+                                     R (&F)[5]) {
+  constexpr int N = 1 + D;
+  const R rL = WL[0], uL = WL[N], pL = WL[4];
+  const R rR = WR[0], uR = WR[N], pR = WR[4];
+  const R cL = sqrt(g * pL / rL), cR = sqrt(g * pR / rR);
+  const R SL = fmin(uL - cL, uR - cR);
+  const R SR = fmax(uL + cL, uR + cR);
+  const R EL = pL * igm1 + R(0.5) * rL * (WL[1] * WL[1] + WL[2] * WL[2] + WL[3] * WL[3]);
+  const R ER = pR * igm1 + R(0.5) * rR * (WR[1] * WR[1] + WR[2] * WR[2] + WR[3] * WR[3]);
+  const R dL = SL - uL, dR = SR - uR;
+  const R Sst = (pR - pL + rL * uL * dL - rR * uR * dR) / (rL * dL - rR * dR);
+  // Branches: S_L >= 0 -> F_L; S* >= 0 -> F*_L; S_R > 0 -> F*_R; else F_R.
+  const bool caseA = SL >= R(0);
+  const bool useL = caseA || Sst >= R(0);
+  const bool star = !caseA && (useL || SR > R(0));
+  R W[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) W[q] = useL ? WL[q] : WR[q];
+  const R EK = useL ? EL : ER;
+  const R SK = useL ? SL : SR;
+  const R rK = W[0], uK = W[N], pK = W[4];
+  const R mK = rK * uK;
+  F[0] = mK;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) F[1 + t] = mK * W[1 + t];
+  F[N] += pK;
+  F[4] = uK * (EK + pK);
+  // star state of side K (computed for every face; used only where selected)
+  const R dK = SK - uK;
+  const R fac = rK * dK / (SK - Sst);
+  R Us[5], UK[5];
+  Us[0] = fac;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) Us[1 + t] = fac * W[1 + t];
+  Us[N] = fac * Sst;
+  Us[4] = fac * (EK / rK + (Sst - uK) * (Sst + pK / (rK * dK)));
+  UK[0] = rK;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) UK[1 + t] = rK * W[1 + t];
+  UK[4] = EK;
+  if (star) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) F[q] = F[q] + SK * (Us[q] - UK[q]);
+  }
+}
+
+template <typename S, typename R>
+__device__ __forceinline__ void prim(const S *u, long long vs, R gm1, R (&w)[5]) {
+  const R r = R(u[0]), mx = R(u[vs]), my = R(u[2 * vs]), mz = R(u[3 * vs]), E = R(u[4 * vs]);
+  const R ir = R(1) / r;
+  w[0] = r;
+  w[1] = mx * ir;
+  w[2] = my * ir;
+  w[3] = mz * ir;
+  w[4] = gm1 * (E - R(0.5) * (mx * mx + my * my + mz * mz) * ir);
+}
+
+// Shared-memory map, in elements of R.
+template <int T>
+struct Smem {
+  static constexpr int W4 = T + 4;          // ring plane width (radius-2 halo)
+  static constexpr int W2 = T + 2;          // face-state row width (radius-1)
+  static constexpr int RING = 5 * W4 * W4;  // one primitive plane
+  static constexpr int FX = 5 * T * W2;     // x face states [v][j][i+1]
+  static constexpr int FY = 5 * W2 * T;     // y face states [v][j+1][i]
+  static constexpr int total(int nplanes) { return nplanes * RING + 2 * FX + 2 * FY; }
+};
+
+// Slopes, Hancock predictor and face states of the cell at tile-local (i, j)
+// of the plane in ring slot s0 (neighbour planes in sm, sp).  Returns the
+// lower/upper face states per direction in fm/fp.
+template <int NDIM, int T, typename R>
+__device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int s0, int sp, int i,
+                                        int j, R hdt, const R (&idx)[3], R g,
+                                        R (&fm)[3][5], R (&fp)[3][5]) {
+  using SM = Smem<T>;
+  const int c = (j + 2) * SM::W4 + (i + 2);
+  const R *p0 = ring + s0 * SM::RING;
+  R W0[5], dW[3][5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) W0[v] = p0[v * SM::W4 * SM::W4 + c];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const R *q = p0 + v * SM::W4 * SM::W4 + c;
+    dW[0][v] = mc_lim(W0[v] - q[-1], q[1] - W0[v]);
+    dW[1][v] = mc_lim(W0[v] - q[-SM::W4], q[SM::W4] - W0[v]);
+    if (NDIM == 3) {
+      const R wm = ring[sm * SM::RING + v * SM::W4 * SM::W4 + c];
+      const R wp = ring[sp * SM::RING + v * SM::W4 * SM::W4 + c];
+      dW[2][v] = mc_lim(W0[v] - wm, wp - W0[v]);
+    } else {
+      dW[2][v] = R(0);
+    }
+  }
+  // primitive quasi-linear form: sum_d A_d(W) dW_d / dx_d
+  R acc[5] = {R(0), R(0), R(0), R(0), R(0)};
+  const R r = W0[0], pr = W0[4];
+#pragma unroll
+  for (int d = 0; d < NDIM; ++d) {
+    const int n = 1 + d;
+    const R un = W0[n];
+    R a[5];
+    a[0] = un * dW[d][0] + r * dW[d][n];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) a[1 + t] = un * dW[d][1 + t];
+    a[n] = a[n] + dW[d][4] / r;
+    a[4] = g * pr * dW[d][n] + un * dW[d][4];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v] = acc[v] + a[v] * idx[d];
+  }
+  R Wh[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Wh[v] = W0[v] - hdt * acc[v];
+  bool bad = false;
+#pragma unroll
+  for (int d = 0; d < NDIM; ++d) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      fm[d][v] = Wh[v] - R(0.5) * dW[d][v];
+      fp[d][v] = Wh[v] + R(0.5) * dW[d][v];
+    }
+    bad |= !(fm[d][0] > R(0)) || !(fm[d][4] > R(0)) || !(fp[d][0] > R(0)) || !(fp[d][4] > R(0));
+  }
+  if (bad) {
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) { fm[d][v] = W0[v]; fp[d][v] = W0[v]; }
+  }
+}
+
+template <int NDIM, int T, typename S, typename R>
+__global__ void __launch_bounds__(T *T, (T == 16 ? 2 : 6))
+k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__restrict__ leaves,
+        int tiles, const double *__restrict__ dtp, double *__restrict__ regs,
+        int *__restrict__ status) {
+  using SM = Smem<T>;
+  constexpr int NT = T * T;
+  constexpr int NPL = NDIM == 3 ? 3 : 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *ring = reinterpret_cast<R *>(smem_raw);
+  R *fxm = ring + NPL * SM::RING;   // x lower-face states, then x fluxes
+  R *fxp = fxm + SM::FX;
+  R *fym = fxp + SM::FX;            // y lower-face states, then y fluxes
+  R *fyp = fym + SM::FY;
+
+  const int tid = threadIdx.x;
+  const int tpb = tiles * tiles;
+  const int b = leaves[blockIdx.x / tpb];
+  const int tile = blockIdx.x % tpb;
+  const int x0 = (tile % tiles) * T, y0 = (tile / tiles) * T;
+  const int n = m.nxb, ng = m.ng, P = m.P;
+  const int lev = m.level[b];
+  const long long vs = m.vstride;
+  const double dt = *dtp;
+  const R g = R(m.gamma), gm1 = R(m.gamma - 1.0), igm1 = R(1.0 / (m.gamma - 1.0));
+  const R hdt = R(0.5 * dt);
+  R idx[3];
+  idx[0] = R(m.idx[lev][0]);
+  idx[1] = R(m.idx[lev][1]);
+  idx[2] = R(m.idx[lev][2]);
+  const double didx = m.idx[lev][0], didy = m.idx[lev][1], didz = m.idx[lev][2];
+  const S *Ub = U + (long long)b * m.bstride;
+  S *Unb = Unew + (long long)b * m.bstride;
+  const int ti = tid % T, tj = tid / T;
+  const int zoff = NDIM == 3 ? ng : 0;
+  const int ridx = m.regidx[b];
+  double *reg = ridx >= 0 ? regs + (long long)ridx * m.nfaces * 5 * m.nface_cells : nullptr;
+  const int nfc = m.nface_cells;
+
+  auto load_plane = [&](int p, int slot) {
+    R *dst = ring + slot * SM::RING;
+    const long long zp = p + zoff;
+    for (int c = tid; c < SM::W4 * SM::W4; c += NT) {
+      const int ii = c % SM::W4, jj = c / SM::W4;
+      const int gx = x0 + ii - 2 + ng, gy = y0 + jj - 2 + ng;
+      R w[5];
+      prim<S, R>(Ub + (zp * P + gy) * P + gx, vs, gm1, w);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) dst[v * SM::W4 * SM::W4 + c] = w[v];
+    }
+  };
+  auto slot_of = [&](int p) { return NDIM == 3 ? ((p % 3) + 3) % 3 : 0; };
+
+  // register state of the thread's column: pending update of the cell below
+  double accxy[5], fzl[5];
+  R zprev[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) { accxy[v] = 0.0; fzl[v] = 0.0; zprev[v] = R(0); }
+
+  const int pstart = NDIM == 3 ? -1 : 0;
+  const int pend = NDIM == 3 ? n : 0;   // inclusive
+  if (NDIM == 3) {
+    load_plane(-2, slot_of(-2));
+    load_plane(-1, slot_of(-1));
+  }
+  for (int p = pstart; p <= pend; ++p) {
+    const bool inner = p >= 0 && p < (NDIM == 3 ? n : 1);
+    const int s0 = slot_of(p), sm = slot_of(p - 1), sp = slot_of(p + 1);
+    if (NDIM == 3) load_plane(p + 1, sp);
+    else load_plane(0, 0);
+    __syncthreads();
+
+    // ---- predictor: own column cell, then (inner planes) the radius-1 ring
+    R zm[5], zp[5];
+    {
+      R fm[3][5], fp[3][5];
+      predict<NDIM, T, R>(ring, sm, s0, sp, ti, tj, hdt, idx, g, fm, fp);
+      if (inner) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          fxm[v * T * SM::W2 + tj * SM::W2 + ti + 1] = fm[0][v];
+          fxp[v * T * SM::W2 + tj * SM::W2 + ti + 1] = fp[0][v];
+          fym[v * SM::W2 * T + (tj + 1) * T + ti] = fm[1][v];
+          fyp[v * SM::W2 * T + (tj + 1) * T + ti] = fp[1][v];
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) { zm[v] = fm[2][v]; zp[v] = fp[2][v]; }
+    }
+    if (inner) {
+      for (int c = tid; c < 4 * T; c += NT) {
+        const int side = c / T, e = c % T;
+        int i, j;
+        if (side == 0) { i = -1; j = e; }
+        else if (side == 1) { i = T; j = e; }
+        else if (side == 2) { i = e; j = -1; }
+        else { i = e; j = T; }
+        R fm[3][5], fp[3][5];
+        predict<NDIM, T, R>(ring, sm, s0, sp, i, j, hdt, idx, g, fm, fp);
+        if (side < 2) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            fxm[v * T * SM::W2 + j * SM::W2 + i + 1] = fm[0][v];
+            fxp[v * T * SM::W2 + j * SM::W2 + i + 1] = fp[0][v];
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            fym[v * SM::W2 * T + (j + 1) * T + i] = fm[1][v];
+            fyp[v * SM::W2 * T + (j + 1) * T + i] = fp[1][v];
+          }
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- fluxes: x and y faces of inner planes (in place over the lower-face
+    // state), z face below the thread's own cell
+    const int zglob = p;  // interior z index of this plane
+    if (inner) {
+      for (int f = tid; f < 2 * (T + 1) * T; f += NT) {
+        const int dir = f >= (T + 1) * T;
+        const int ff = dir ? f - (T + 1) * T : f;
+        int a, e;  // a: face index along the normal (0..T), e: transverse
+        if (ff < T * T) { a = ff % T; e = ff / T; }
+        else { a = T; e = ff - T * T; }
+        R WL[5], WR[5], F[5];
+        if (!dir) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            WL[v] = fxp[v * T * SM::W2 + e * SM::W2 + a];
+            WR[v] = fxm[v * T * SM::W2 + e * SM::W2 + a + 1];
+          }
+          hllc<0, R>(WL, WR, g, igm1, F);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) fxm[v * T * SM::W2 + e * SM::W2 + a + 1] = F[v];
+          if (reg && ((a == 0 && x0 == 0) || (a == T && x0 + T == n))) {
+            const int face = a == 0 ? 0 : 1;
+            const int t1 = y0 + e, t2 = NDIM == 3 ? zglob : 0;
+#pragma unroll
+            for (int v = 0; v < 5; ++v)
+              reg[(face * 5 + v) * nfc + t2 * n + t1] = double(F[v]);
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            WL[v] = fyp[v * SM::W2 * T + a * T + e];
+            WR[v] = fym[v * SM::W2 * T + (a + 1) * T + e];
+          }
+          hllc<1, R>(WL, WR, g, igm1, F);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) fym[v * SM::W2 * T + (a + 1) * T + e] = F[v];
+          if (reg && ((a == 0 && y0 == 0) || (a == T && y0 + T == n))) {
+            const int face = a == 0 ? 2 : 3;
+            const int t1 = x0 + e, t2 = NDIM == 3 ? zglob : 0;
+#pragma unroll
+            for (int v = 0; v < 5; ++v)
+              reg[(face * 5 + v) * nfc + t2 * n + t1] = double(F[v]);
+          }
+        }
+      }
+    }
+    R Fz[5];
+    if (NDIM == 3 && p >= 0) {
+      hllc<2, R>(zprev, zm, g, igm1, Fz);
+      if (reg && (p == 0 || p == n)) {
+        const int face = p == 0 ? 4 : 5;
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+          reg[(face * 5 + v) * nfc + (y0 + tj) * n + (x0 + ti)] = double(Fz[v]);
+      }
+    }
+    __syncthreads();
+
+    // ---- update: finish the cell below (3D), start this plane's cell
+    if (NDIM == 3 && p >= 1) {
+      const long long o = ((long long)(p - 1 + ng) * P + (y0 + tj + ng)) * P + (x0 + ti + ng);
+      double un[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double div = accxy[v] + (fzl[v] - double(Fz[v])) * didz;
+        un[v] = double(Ub[o + v * vs]) + dt * div;
+        Unb[o + v * vs] = S(un[v]);
+      }
+      if (!(un[0] > 0.0) || !(2.0 * un[4] * un[0] > un[1] * un[1] + un[2] * un[2] + un[3] * un[3]))
+        atomicOr(status, 1);
+    }
+    if (inner) {
+      const R *Fx = fxm + tj * SM::W2 + ti + 1;
+      const R *Fy = fym + (tj + 1) * T + ti;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double fx = (double(Fx[v * T * SM::W2]) - double(Fx[v * T * SM::W2 + 1])) * didx;
+        const double fy = (double(Fy[v * SM::W2 * T]) - double(Fy[v * SM::W2 * T + T])) * didy;
+        accxy[v] = fx + fy;
+        if (NDIM == 3) fzl[v] = double(Fz[v]);
+      }
+      if (NDIM == 2) {
+        const long long o = (long long)(y0 + tj + ng) * P + (x0 + ti + ng);
+        double un[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          un[v] = double(Ub[o + v * vs]) + dt * accxy[v];
+          Unb[o + v * vs] = S(un[v]);
+        }
+        if (!(un[0] > 0.0) ||
+            !(2.0 * un[4] * un[0] > un[1] * un[1] + un[2] * un[2] + un[3] * un[3]))
+          atomicOr(status, 1);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) zprev[v] = zp[v];
+  }
+}
+
+template <int NDIM, int T, typename S, typename R>
+cudaError_t launch_t(const DevMesh &m, const void *U, void *Unew, const int *leaves, int n,
+                     const double *dt, double *regs, int *status, cudaStream_t s) {
+  const int tiles = m.nxb / T;
+  const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(R);
+  auto kern = k_hydro<NDIM, T, S, R>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  kern<<<n * tiles * tiles, T * T, smem, s>>>(m, static_cast<const S *>(U), static_cast<S *>(Unew),
+                                              leaves, tiles, dt, regs, status);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t hydro_smem_bytes(int ndim, int tile, int prec) {
+  const size_t el = prec == 0 ? sizeof(double) : sizeof(float);
+  const int np = ndim == 3 ? 3 : 1;
+  return (tile == 16 ? Smem<16>::total(np) : Smem<8>::total(np)) * el;
+}
+
+cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, const int *leaves,
+                         int n, const double *dt, double *regs, int *status, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int T = (m.nxb % 16 == 0) ? 16 : 8;
+  if (prec != 0) return cudaErrorNotSupported;
+  if (m.ndim == 3) {
+    return T == 16 ? launch_t<3, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, s)
+                   : launch_t<3, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, s);
+  }
+  return T == 16 ? launch_t<2, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, s)
+                 : launch_t<2, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, s);
+}
+
+}  // namespace fx

@@ -1,0 +1,138 @@
+// k_reduce.cu -- CFL time step (max-reduction) and conserved totals.
+//
+// Paper: Flash-X (arXiv 2208.11630), Section 2 -- hyperbolic equations are
+// advanced with explicit methods, whose stable step is set by the largest
+// signal speed on the mesh.  dt = cfl / max_cells sum_d (|u_d| + c) / dx_d
+// (or the maximum over d), c = sqrt(gamma p / rho) of the perfect gas
+// (Section 2.2).  The maximum of non-negative doubles is taken on their bit
+// patterns with atomicMax, which is exact and independent of order; the last
+// CTA to finish writes dt and re-arms the two scratch words.
+#include "fx_internal.h"
+
+namespace fx {
+namespace {
+
+template <typename S>
+__global__ void k_dt(DevMesh m, const S *__restrict__ U, const int *__restrict__ leaves, int nleaves,
+                     double cfl, int form, double *__restrict__ dt_out,
+                     unsigned long long *__restrict__ scratch) {
+  const int n = m.nxb, ng = m.ng, P = m.P, nd = m.ndim;
+  const int nz = nd == 3 ? n : 1;
+  const long long ncell = (long long)n * n * nz;
+  const long long total = ncell * nleaves;
+  const double g = m.gamma, gm1 = m.gamma - 1.0;
+  double smax = 0.0;
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total;
+       w += (long long)gridDim.x * blockDim.x) {
+    const int b = leaves[w / ncell];
+    const int c = (int)(w % ncell);
+    const int i = c % n, j = (c / n) % n, k = c / (n * n);
+    const S *u = U + (long long)b * m.bstride +
+                 ((long long)(nd == 3 ? k + ng : 0) * P + (j + ng)) * P + (i + ng);
+    const long long vs = m.vstride;
+    const double r = double(u[0]), mx = double(u[vs]), my = double(u[2 * vs]),
+                 mz = double(u[3 * vs]), E = double(u[4 * vs]);
+    const double ir = 1.0 / r;
+    const double p = gm1 * (E - 0.5 * (mx * mx + my * my + mz * mz) * ir);
+    const double cs = sqrt(g * p * ir);
+    const int lev = m.level[b];
+    const double vel[3] = {mx * ir, my * ir, mz * ir};
+    double s = 0.0;
+    for (int d = 0; d < nd; ++d) {
+      const double sd = (fabs(vel[d]) + cs) * m.idx[lev][d];
+      s = form == 0 ? s + sd : fmax(s, sd);
+    }
+    if (!(s <= smax)) smax = s;   // keeps a NaN
+  }
+  // warp and CTA maximum on the bit patterns (non-negative doubles and NaN
+  // order like their bits)
+  unsigned long long bits = __double_as_longlong(smax);
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long other = __shfl_down_sync(0xffffffffu, bits, o);
+    bits = other > bits ? other : bits;
+  }
+  __shared__ unsigned long long wmax[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) wmax[warp] = bits;
+  __syncthreads();
+  if (warp == 0) {
+    bits = lane < (blockDim.x >> 5) ? wmax[lane] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long other = __shfl_down_sync(0xffffffffu, bits, o);
+      bits = other > bits ? other : bits;
+    }
+    if (lane == 0) {
+      atomicMax(&scratch[0], bits);
+      __threadfence();
+      const unsigned long long done = atomicAdd(&scratch[1], 1ull);
+      if (done == gridDim.x - 1) {
+        __threadfence();
+        const unsigned long long mb = atomicAdd(&scratch[0], 0ull);
+        *dt_out = cfl / __longlong_as_double(mb);
+        scratch[0] = 0ull;
+        scratch[1] = 0ull;
+      }
+    }
+  }
+}
+
+// One CTA per leaf: per-variable sums over the interior in a fixed order
+// (strided per thread, then a shared-memory tree), times the cell volume.
+template <typename S>
+__global__ void k_totals(DevMesh m, const S *__restrict__ U, const int *__restrict__ leaves,
+                         double *__restrict__ out) {
+  const int b = leaves[blockIdx.x];
+  const int n = m.nxb, ng = m.ng, P = m.P, nd = m.ndim;
+  const int nz = nd == 3 ? n : 1;
+  const int ncell = n * n * nz;
+  __shared__ double red[5][256];
+  double acc[5] = {0, 0, 0, 0, 0};
+  const S *Ub = U + (long long)b * m.bstride;
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    const int i = c % n, j = (c / n) % n, k = c / (n * n);
+    const long long o = ((long long)(nd == 3 ? k + ng : 0) * P + (j + ng)) * P + (i + ng);
+    for (int v = 0; v < 5; ++v) acc[v] += double(Ub[o + v * m.vstride]);
+  }
+  for (int v = 0; v < 5; ++v) red[v][threadIdx.x] = acc[v];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int v = 0; v < 5; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) {
+    const int lev = m.level[b];
+    const double dV = m.dx[lev][0] * m.dx[lev][1] * (nd == 3 ? m.dx[lev][2] : 1.0);
+    out[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0] * dV;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_dt(const DevMesh &m, const void *U, int prec, const int *leaves, int n,
+                      double cfl, int form, double *dt_out, unsigned long long *scratch,
+                      cudaStream_t s) {
+  if (n <= 0) return cudaErrorInvalidValue;
+  const long long total = (long long)n * m.nxb * m.nxb * (m.ndim == 3 ? m.nxb : 1);
+  long long grid = (total + 255) / 256;
+  if (grid > 152 * 8) grid = 152 * 8;
+  if (prec == 0)
+    k_dt<double><<<(int)grid, 256, 0, s>>>(m, static_cast<const double *>(U), leaves, n, cfl, form,
+                                           dt_out, scratch);
+  else
+    k_dt<float><<<(int)grid, 256, 0, s>>>(m, static_cast<const float *>(U), leaves, n, cfl, form,
+                                          dt_out, scratch);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_totals(const DevMesh &m, const void *U, int prec, const int *leaves, int n,
+                          double *out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (prec == 0) k_totals<double><<<n, 256, 0, s>>>(m, static_cast<const double *>(U), leaves, out);
+  else k_totals<float><<<n, 256, 0, s>>>(m, static_cast<const float *>(U), leaves, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace fx

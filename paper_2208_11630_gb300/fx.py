@@ -1,0 +1,263 @@
+"""Thin ctypes binding of libfx (include/fx.h).
+
+Functions keep the C names and only marshal arguments: every step of the hot
+path runs in the library's CUDA kernels.  PyTorch supplies device memory and
+streams.  There is no CPU fallback: if ``libfx.so`` cannot be built or loaded,
+or no CUDA device is present, these calls raise.
+
+``BlockSet`` is a small convenience wrapper that owns the two state tensors
+of one block set and forwards to the C calls.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+FX_OK = 0
+FX_ERR = {-1: "FX_ERR_ARG", -2: "FX_ERR_CUDA", -3: "FX_ERR_OOM", -4: "FX_ERR_UNPHYSICAL",
+          -5: "FX_ERR_TIMEOUT", -6: "FX_ERR_STATE", -7: "FX_ERR_MESH"}
+FX_F64 = 0
+FX_F32BULK = 1
+FX_BC_OUTFLOW = 0
+FX_BC_PERIODIC = 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+_lock = threading.Lock()
+
+
+class FxError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        super().__init__(f"{FX_ERR.get(code, code)}: {msg}")
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "libfx.so")
+
+
+def load(build: bool = True):
+    """Load libfx.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build:
+            from . import _build
+            _build.build()
+        L = ctypes.CDLL(lib_path())
+        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        c_int, c_double = ctypes.c_int, ctypes.c_double
+        sig = {
+            "fx_init": (c_int, [c_double, c_int, c_int, ctypes.POINTER(vp)]),
+            "fx_finalize": (c_int, [vp]),
+            "fx_set_option": (c_int, [vp, ctypes.c_char_p, c_double]),
+            "fx_last_error": (ctypes.c_char_p, [vp]),
+            "fx_blocks_create": (c_int, [vp, c_int, c_int, c_int, ip, ip, i64p, ip, dp, dp, ip,
+                                         c_int, vp, vp, ctypes.POINTER(vp)]),
+            "fx_blocks_destroy": (c_int, [vp]),
+            "fx_blocks_current": (c_int, [vp]),
+            "fx_prim_to_cons": (c_int, [vp, vp, vp, vp]),
+            "fx_guardcell_fill": (c_int, [vp, vp, vp]),
+            "fx_compute_dt": (c_int, [vp, vp, c_double, vp, vp]),
+            "fx_hydro_advance": (c_int, [vp, vp, vp, vp]),
+            "fx_step": (c_int, [vp, vp, c_double, vp, vp]),
+            "fx_conserved_totals": (c_int, [vp, vp, dp, vp]),
+            "fx_status": (c_int, [vp, vp]),
+            "fx_run_host": (c_int, [vp, vp, vp, vp, c_int, c_double, dp, vp]),
+            "fx_block_fluxes": (vp, [vp, c_int]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(ctx, rc):
+    if rc != FX_OK:
+        msg = load().fx_last_error(ctx).decode() if ctx else ""
+        raise FxError(rc, msg)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- raw calls
+
+def fx_init(gamma: float, nxb: int, nguard: int):
+    ctx = ctypes.c_void_p()
+    rc = load().fx_init(float(gamma), int(nxb), int(nguard), ctypes.byref(ctx))
+    if rc != FX_OK:
+        raise FxError(rc, "fx_init")
+    return ctx
+
+
+def fx_finalize(ctx):
+    _check(None, load().fx_finalize(ctx))
+
+
+def fx_set_option(ctx, key: str, value: float):
+    _check(ctx, load().fx_set_option(ctx, key.encode(), float(value)))
+
+
+def fx_blocks_create(ctx, mesh, precision: int, U0_ptr: int, U1_ptr: int):
+    level = np.ascontiguousarray(mesh.level, dtype=np.int32)
+    origin = np.ascontiguousarray(mesh.origin, dtype=np.int64)
+    parent = np.ascontiguousarray(mesh.parent, dtype=np.int32)
+    nroot = np.array(mesh.nroot, dtype=np.int32)
+    lo = np.array(mesh.lo, dtype=np.float64)
+    hi = np.array(mesh.hi, dtype=np.float64)
+    bc = mesh.bc_flat()
+    ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    bs = ctypes.c_void_p()
+    rc = load().fx_blocks_create(ctx, mesh.ndim, mesh.nb, mesh.nxb, ip(nroot), ip(level),
+                                 origin.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ip(parent),
+                                 dp(lo), dp(hi), ip(bc), int(precision), ctypes.c_void_p(U0_ptr),
+                                 ctypes.c_void_p(U1_ptr), ctypes.byref(bs))
+    _check(ctx, rc)
+    return bs
+
+
+def fx_blocks_destroy(bs):
+    load().fx_blocks_destroy(bs)
+
+
+def fx_blocks_current(bs) -> int:
+    return int(load().fx_blocks_current(bs))
+
+
+def fx_prim_to_cons(ctx, bs, W_ptr: int, stream=None):
+    _check(ctx, load().fx_prim_to_cons(ctx, bs, ctypes.c_void_p(W_ptr), _stream_ptr(stream)))
+
+
+def fx_guardcell_fill(ctx, bs, stream=None):
+    _check(ctx, load().fx_guardcell_fill(ctx, bs, _stream_ptr(stream)))
+
+
+def fx_compute_dt(ctx, bs, cfl: float, dt_ptr: int, stream=None):
+    _check(ctx, load().fx_compute_dt(ctx, bs, float(cfl), ctypes.c_void_p(dt_ptr), _stream_ptr(stream)))
+
+
+def fx_hydro_advance(ctx, bs, dt_ptr: int, stream=None):
+    _check(ctx, load().fx_hydro_advance(ctx, bs, ctypes.c_void_p(dt_ptr), _stream_ptr(stream)))
+
+
+def fx_step(ctx, bs, cfl: float, dt_ptr: int, stream=None):
+    _check(ctx, load().fx_step(ctx, bs, float(cfl), ctypes.c_void_p(dt_ptr), _stream_ptr(stream)))
+
+
+def fx_conserved_totals(ctx, bs, stream=None) -> np.ndarray:
+    out = np.zeros(5)
+    _check(ctx, load().fx_conserved_totals(ctx, bs, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           _stream_ptr(stream)))
+    return out
+
+
+def fx_status(ctx, bs) -> int:
+    return int(load().fx_status(ctx, bs))
+
+
+def fx_run_host(ctx, bs, host_in: np.ndarray, host_out: np.ndarray, nsteps: int, cfl: float,
+                stream=None, want_time: bool = False):
+    t = np.zeros(1)
+    tp = t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if want_time else None
+    _check(ctx, load().fx_run_host(ctx, bs, ctypes.c_void_p(host_in.ctypes.data),
+                                   ctypes.c_void_p(host_out.ctypes.data), int(nsteps), float(cfl),
+                                   tp, _stream_ptr(stream)))
+    return float(t[0]) if want_time else None
+
+
+def fx_block_fluxes(bs, b: int) -> int:
+    return load().fx_block_fluxes(bs, int(b)) or 0
+
+
+# ---------------------------------------------------------------- convenience
+
+class BlockSet:
+    """One block set with its two device state buffers (torch tensors)."""
+
+    def __init__(self, mesh, gamma: float = 1.4, precision: int = FX_F64, device="cuda",
+                 options: dict | None = None, ctx=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise FxError(-2, "no CUDA device: libfx has no CPU path")
+        self.mesh = mesh
+        self.precision = precision
+        self.dtype = torch.float64 if precision == FX_F64 else torch.float32
+        self.own_ctx = ctx is None
+        self.ctx = ctx if ctx is not None else fx_init(gamma, mesh.nxb, mesh.ng)
+        for k, v in (options or {}).items():
+            fx_set_option(self.ctx, k, v)
+        self.U = [torch.zeros(mesh.shape, dtype=self.dtype, device=device) for _ in range(2)]
+        self.dt = torch.zeros(1, dtype=torch.float64, device=device)
+        self.bs = fx_blocks_create(self.ctx, mesh, precision, self.U[0].data_ptr(),
+                                   self.U[1].data_ptr())
+
+    def close(self):
+        if getattr(self, "bs", None):
+            fx_blocks_destroy(self.bs)
+            self.bs = None
+        if getattr(self, "own_ctx", False) and getattr(self, "ctx", None):
+            fx_finalize(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def current(self):
+        return self.U[fx_blocks_current(self.bs)]
+
+    def set_primitive(self, W: np.ndarray, stream=None):
+        import torch
+        Wd = torch.as_tensor(np.ascontiguousarray(W, dtype=np.float64), device=self.U[0].device)
+        fx_prim_to_cons(self.ctx, self.bs, Wd.data_ptr(), stream)
+        torch.cuda.current_stream().synchronize()
+
+    def set_conserved(self, U: np.ndarray):
+        import torch
+        self.current.copy_(torch.as_tensor(U, dtype=self.dtype))
+
+    def fill(self, stream=None):
+        fx_guardcell_fill(self.ctx, self.bs, stream)
+
+    def compute_dt(self, cfl: float = 0.8, stream=None) -> float:
+        fx_compute_dt(self.ctx, self.bs, cfl, self.dt.data_ptr(), stream)
+        return float(self.dt.item())
+
+    def advance(self, dt: float | None = None, stream=None):
+        if dt is not None:
+            self.dt.fill_(dt)
+        fx_hydro_advance(self.ctx, self.bs, self.dt.data_ptr(), stream)
+
+    def step(self, cfl: float = 0.8, stream=None):
+        fx_step(self.ctx, self.bs, cfl, self.dt.data_ptr(), stream)
+
+    def run(self, nsteps: int, cfl: float = 0.8, stream=None):
+        for _ in range(nsteps):
+            self.step(cfl, stream)
+
+    def totals(self, stream=None) -> np.ndarray:
+        return fx_conserved_totals(self.ctx, self.bs, stream)
+
+    def status(self) -> int:
+        return fx_status(self.ctx, self.bs)
+
+    def state(self) -> np.ndarray:
+        return self.current.double().cpu().numpy()
