@@ -210,8 +210,9 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     fx.load()
 
-    mesh, W, gamma, cfl = inputs.workload(args.workload)
+    mesh, W, gamma, cfl = inputs.workload(args.workload, scale=args.scale)
     zones_per_step = mesh.leaf_zones()
+    wname = f"{args.workload}_{mesh.nroot[0] * mesh.nxb}^3" if args.workload == "kh3d" else args.workload
     bs = fx.BlockSet(mesh, gamma, device=dev)
     bs.set_primitive(W)
     U0 = bs.state()          # host copy of the initial state (for the e2e leg)
@@ -262,19 +263,23 @@ def run_ours(args):
     value = zones_all / sec_max
 
     # ---- end-to-end through host buffers (pinned), one step per call
-    host_in = torch.from_numpy(U0).to(bs.dtype).pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
-    e2e_steps = max(3, min(args.steps, 10))
-    fx.fx_run_host(bs.ctx, bs.bs, host_in.numpy(), host_out.numpy(), 1, cfl, stream=sptr)
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(U0).to(bs.dtype).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        e2e_steps = max(3, min(args.steps, 10))
         fx.fx_run_host(bs.ctx, bs.bs, host_in.numpy(), host_out.numpy(), 1, cfl, stream=sptr)
-    e2e_sec = time.perf_counter() - t0
-    ez, esec = aggregate(zones_per_step * e2e_steps, e2e_sec, dev)
-    state_bytes = host_in.numel() * host_in.element_size()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            fx.fx_run_host(bs.ctx, bs.bs, host_in.numpy(), host_out.numpy(), 1, cfl, stream=sptr)
+        e2e_sec = time.perf_counter() - t0
+        ez, esec = aggregate(zones_per_step * e2e_steps, e2e_sec, dev)
+        state_bytes = host_in.numel() * host_in.element_size()
+        e2e = {"value": ez / esec, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+               "d2h_bytes_per_step": state_bytes}
 
     peaks, peak_kind = load_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -284,7 +289,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * sec_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": workload_config(args, "kh3d_256^3") | {"replicas": ws},
+        "config": workload_config(args, wname) | {"replicas": ws, "blocks": mesh.nb,
+                                                  "cells": zones_per_step},
         "roofline": {
             "bound": "alu", "kernel": "k_hydro<3,16,double,double>",
             "achieved": achieved_flops / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
@@ -295,8 +301,7 @@ def run_ours(args):
             "hbm_frac_of_step": (HBM_BYTES_PER_ZONE["f64"] * value / ws) / (hbm_peak * 1e9),
             "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind,
         },
-        "e2e": {"value": ez / esec, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
-                "d2h_bytes_per_step": state_bytes},
+        "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk,
     }
@@ -321,7 +326,10 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="kh3d")
     ap.add_argument("--precision", default="f64", choices=["f64"])
+    ap.add_argument("--scale", type=int, default=None,
+                    help="blocks per axis (default: the full workload, 16 for kh3d)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -62,6 +62,7 @@ def lib():
             L.or_hydro_advance.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_double, ctypes.c_int,
                                            dp, ctypes.c_int, ip]
             L.or_conserved_totals.argtypes = [ctypes.c_void_p, dp, dp]
+            L.or_restrict_parents.argtypes = [ctypes.c_void_p, dp]
             L.or_mc.restype = ctypes.c_double
             L.or_mc.argtypes = [ctypes.c_double, ctypes.c_double]
             L.or_hllc.argtypes = [dp, dp, ctypes.c_int, ctypes.c_double, dp]
@@ -157,6 +158,9 @@ class OracleMesh:
             st = lib().or_hydro_advance(self._h, _dp(U), _dp(Unew), float(dt), int(reflux), bptr,
                                         0, None)
         return Unew, st, bflux
+
+    def restrict_parents(self, U: np.ndarray) -> None:
+        lib().or_restrict_parents(self._h, _dp(U))
 
     def conserved_totals(self, U: np.ndarray) -> np.ndarray:
         out = np.zeros(5)

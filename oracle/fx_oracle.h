@@ -83,6 +83,12 @@ int or_compute_dt(const or_mesh *m, const double *U, double cfl, int form, doubl
 int or_hydro_advance(const or_mesh *m, const double *U, double *Unew, double dt,
                      int reflux, double *bflux, int nsel, const int *sel);
 
+/* Restriction of every non-leaf block from its children, finest level first:
+ * each parent cell is the pairwise mean (x pairs, then y, then z) of the
+ * 2^d child cells it covers.  Pinned: uniform state, linear-field exactness
+ * via prolongation, conservation with flux correction. */
+void or_restrict_parents(const or_mesh *m, double *U);
+
 /* Sum over leaf interior cells of U dV per variable (compensated sums, fixed
  * order).  Pinned by conservation tests. */
 void or_conserved_totals(const or_mesh *m, const double *U, double out[5]);

@@ -637,6 +637,14 @@ static void restrict_block(const or_mesh *m, double *U, int p) {
         }
 }
 
+void or_restrict_parents(const or_mesh *m, double *U) {
+  for (int l = m->lmax - 1; l >= 0; l--) {
+#pragma omp parallel for schedule(dynamic) num_threads(or_get_threads())
+    for (int b = 0; b < m->nb; b++)
+      if (!m->leaf[b] && m->level[b] == l) restrict_block(m, U, b);
+  }
+}
+
 int or_hydro_advance(const or_mesh *m, const double *U, double *Unew, double dt, int reflux,
                      double *bflux, int nsel, const int *sel) {
   size_t per = (size_t)5 * m->PZ * m->P * m->P;

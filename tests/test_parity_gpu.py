@@ -92,6 +92,7 @@ def test_guard_fill(orc, fx, case):
     # parents hold the bit-exact restriction of their children
     par = ~leaf
     if par.any():
+        om.restrict_parents(U)
         assert np.array_equal(mesh.interior(G)[par], mesh.interior(U)[par])
 
 
@@ -114,8 +115,14 @@ def test_one_step(orc, fx, case):
     bs.step(0.8)
     assert bs.status() == 0
     assert float(bs.dt.item()) == pytest.approx(dto, rel=1e-15)
-    err = max_rel_err(mesh, bs.state(), Uo)
+    G = bs.state()
+    err = max_rel_err(mesh, G, Uo)
     assert err <= 1e-12, err
+    par = ~mesh.is_leaf().astype(bool)
+    if par.any():   # restricted parents follow their children
+        a, b = mesh.interior(G)[par], mesh.interior(Uo)[par]
+        s = np.maximum(np.abs(b).max(axis=(0, 2, 3, 4), keepdims=True), 1e-300)
+        assert (np.abs(a - b) / np.maximum(np.abs(b), s)).max() <= 1e-12
 
 
 @pytest.mark.parametrize("case,nsteps", [("sod2d", 50), ("sod2d", 100), ("kh64", 100),
@@ -146,7 +153,7 @@ class _DevPtr:
     """Borrowed view of library-owned device memory (read-only use)."""
 
     def __init__(self, ptr, n):
-        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f8", "data": (ptr, True),
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f8", "data": (ptr, False),
                                          "version": 2, "strides": None}
 
 
@@ -185,7 +192,7 @@ def test_conservation_and_uniform_state(orc, fx):
     T0 = bs.totals()
     np.testing.assert_allclose(T0, om.conserved_totals(U), rtol=1e-14, atol=1e-15)
     bs.run(100, 0.8)
-    A = om.conserved_totals(np.abs(U))
+    A = om.conserved_totals(np.abs(U)) + om.conserved_totals(np.abs(bs.state()))
     assert np.all(np.abs(bs.totals() - T0) / A <= 1e-13)
     for mesh in (mesh_2level(4, 8, 4), inputs.uniform_mesh(2, (3, 2), 16, 4)):
         bs = gpu_blockset(fx, mesh, inputs.uniform_state(mesh))
@@ -225,9 +232,10 @@ def test_bad_mesh_is_rejected(fx):
     flags = np.zeros(base.nb, dtype=bool)
     flags[0] = True
     m1 = inputs.refine(base, flags)
-    # refine one child again: a level-2 block next to level-0 leaves violates 2:1
+    # refine the child on the +x side of block 0 again: its level-2 children
+    # touch the level-0 block at +x, which violates 2:1 balance
     f2 = np.zeros(m1.nb, dtype=bool)
-    f2[base.nb] = True
+    f2[base.nb + 1] = True
     m2 = inputs.refine(m1, f2)
     ctx = fx.fx_init(1.4, 8, 4)
     U = [torch.zeros(m2.shape, dtype=torch.float64, device="cuda") for _ in range(2)]
