@@ -32,6 +32,7 @@
 #ifndef FX_H
 #define FX_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -179,6 +180,33 @@ FX_API int fx_run_host(fx_ctx *ctx, fx_blocks *bs, const void *U_host_in, void *
  * fastest) written by the last fx_hydro_advance, or NULL if the block has no
  * coarse-fine face.  For diagnostics and tests. */
 FX_API const double *fx_block_fluxes(const fx_blocks *bs, int b);
+
+/* Largest block count fx_compute_dt_noalloc accepts (size of its fixed
+ * device scratch, one 8-byte partial per block plus a counter: 256 KB). */
+#define FX_NOALLOC_MAX_BLOCKS 32768
+
+/* fx_compute_dt_noalloc: the CFL time step of fx_compute_dt for callers that
+ * cannot allocate device memory (a host callback, an allocator's own
+ * bookkeeping, a process whose device memory belongs to another runtime, a
+ * loop that forbids allocation after start-up).  The paper has no counterpart;
+ * this entry point exists only so that such callers need no block set.
+ *   U_dev      caller-owned device state, FP64, layout of a state buffer
+ *              (nblocks blocks of one refinement level; every block counts);
+ *   dx[3]      cell widths (dx[2] ignored in 2D); gamma, cfl, cfl_form as in
+ *              fx_init / fx_compute_dt / fx_set_option("cfl_form");
+ *   dt_dev     caller-owned device double that receives dt;
+ *   errbuf     optional caller buffer (errlen bytes) for an error message.
+ * It allocates nothing: its scratch is a fixed array inside the library that
+ * every GPU loading the library holds until exit.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) with the device
+ * current; make that first call before any stream capture.  The call clears
+ * the scratch counter on `stream` before the kernel.  All calls share the
+ * scratch: calls that may overlap on the GPU race and must be ordered by the
+ * caller.  Errors: FX_ERR_ARG (including nblocks > FX_NOALLOC_MAX_BLOCKS),
+ * FX_ERR_CUDA. */
+FX_API int fx_compute_dt_noalloc(const double *U_dev, int ndim, int nblocks, int nxb, int nguard,
+                                 const double dx[3], double gamma, double cfl, int cfl_form,
+                                 double *dt_dev, void *stream, char *errbuf, size_t errlen);
 
 /* fx_kernel_launches: number of CUDA kernels this library has launched in
  * the process so far (all contexts).  Diagnostics for benchmarks. */

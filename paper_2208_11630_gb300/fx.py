@@ -70,6 +70,10 @@ def load(build: bool = True):
             "fx_status": (c_int, [vp, vp]),
             "fx_run_host": (c_int, [vp, vp, vp, vp, c_int, c_double, dp, vp]),
             "fx_block_fluxes": (vp, [vp, c_int]),
+            "fx_kernel_launches": (ctypes.c_longlong, []),
+            "fx_compute_dt_noalloc": (c_int, [vp, c_int, c_int, c_int, c_int, dp, c_double,
+                                              c_double, c_int, vp, vp, ctypes.c_char_p,
+                                              ctypes.c_size_t]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -178,6 +182,22 @@ def fx_run_host(ctx, bs, host_in: np.ndarray, host_out: np.ndarray, nsteps: int,
                                    ctypes.c_void_p(host_out.ctypes.data), int(nsteps), float(cfl),
                                    tp, _stream_ptr(stream)))
     return float(t[0]) if want_time else None
+
+
+def fx_compute_dt_noalloc(U_ptr: int, ndim: int, nblocks: int, nxb: int, nguard: int, dx,
+                          gamma: float, cfl: float, cfl_form: int, dt_ptr: int, stream=None):
+    """dt for callers that cannot allocate device memory (see fx.h).  Returns
+    ``(rc, message)``; the library allocates nothing, not even for errors."""
+    dxa = np.ascontiguousarray(dx, dtype=np.float64)
+    buf = ctypes.create_string_buffer(256)
+    rc = load().fx_compute_dt_noalloc(ctypes.c_void_p(U_ptr), int(ndim), int(nblocks), int(nxb),
+                                      int(nguard), dxa.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      float(gamma), float(cfl), int(cfl_form), ctypes.c_void_p(dt_ptr),
+                                      _stream_ptr(stream), buf, ctypes.sizeof(buf))
+    return int(rc), buf.value.decode()
+
+
+FX_NOALLOC_MAX_BLOCKS = 32768
 
 
 def fx_block_fluxes(bs, b: int) -> int:
