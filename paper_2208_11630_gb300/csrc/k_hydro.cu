@@ -21,25 +21,50 @@
 namespace fx {
 namespace {
 
-template <typename R>
-__device__ __forceinline__ R mc_lim(R a, R b) {
-  if (a * b <= R(0)) return R(0);
-  R s = fmin(fmin(R(2) * fabs(a), R(2) * fabs(b)), R(0.5) * fabs(a + b));
-  return a > R(0) ? s : -s;
+// Half of van Leer's MC slope: 0 if a and b differ in sign or one is zero,
+// else sign(a) min(|a|, |b|, |a+b|/4) -- exactly MC(a, b) / 2, since scaling by
+// powers of two is exact.  The sign tests run on the integer pipe.
+__device__ __forceinline__ double mc_half(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  const bool same = ((ia ^ ib) >= 0) && (ia << 1) != 0 && (ib << 1) != 0;
+  const double m = fmin(fmin(fabs(a), fabs(b)), 0.25 * fabs(a + b));
+  return same ? copysign(m, a) : 0.0;
 }
 
-// HLLC flux along direction D from primitive left/right states.
+__device__ __forceinline__ float mc_half(float a, float b) {
+  const int ia = __float_as_int(a), ib = __float_as_int(b);
+  const bool same = ((ia ^ ib) >= 0) && (ia << 1) != 0 && (ib << 1) != 0;
+  const float m = fminf(fminf(fabsf(a), fabsf(b)), 0.25f * fabsf(a + b));
+  return same ? copysignf(m, a) : 0.0f;
+}
+
+// x > 0 (false for zero, negative and NaN; +inf counts as positive), tested on
+// the bit pattern.
+__device__ __forceinline__ bool positive(double x) {
+  return (unsigned long long)__double_as_longlong(x) - 1ull < 0x7ff0000000000000ull;
+}
+__device__ __forceinline__ bool positive(float x) {
+  return (unsigned)__float_as_int(x) - 1u < 0x7f800000u;
+}
+
+__device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+
+// HLLC flux along direction D from primitive left/right states.  One
+// reciprocal square root per side gives both the sound speed and 1/rho:
+// r = (gamma p rho)^(-1/2), c = gamma p r, 1/rho = c r.  The star state of the
+// upwind side K needs two divisions: S* and 1/(S_K - S*).
 template <int D, typename R>
 __device__ __forceinline__ void hllc(const R (&WL)[5], const R (&WR)[5], R g, R igm1,
                                      R (&F)[5]) {
   constexpr int N = 1 + D;
   const R rL = WL[0], uL = WL[N], pL = WL[4];
   const R rR = WR[0], uR = WR[N], pR = WR[4];
-  const R cL = sqrt(g * pL / rL), cR = sqrt(g * pR / rR);
+  const R gpL = g * pL, gpR = g * pR;
+  const R qL = rsqrt_r(gpL * rL), qR = rsqrt_r(gpR * rR);
+  const R cL = gpL * qL, cR = gpR * qR;
   const R SL = fmin(uL - cL, uR - cR);
   const R SR = fmax(uL + cL, uR + cR);
-  const R EL = pL * igm1 + R(0.5) * rL * (WL[1] * WL[1] + WL[2] * WL[2] + WL[3] * WL[3]);
-  const R ER = pR * igm1 + R(0.5) * rR * (WR[1] * WR[1] + WR[2] * WR[2] + WR[3] * WR[3]);
   const R dL = SL - uL, dR = SR - uR;
   const R Sst = (pR - pL + rL * uL * dL - rR * uR * dR) / (rL * dL - rR * dR);
   // Branches: S_L >= 0 -> F_L; S* >= 0 -> F*_L; S_R > 0 -> F*_R; else F_R.
@@ -49,36 +74,39 @@ __device__ __forceinline__ void hllc(const R (&WL)[5], const R (&WR)[5], R g, R 
   R W[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) W[q] = useL ? WL[q] : WR[q];
-  const R EK = useL ? EL : ER;
   const R SK = useL ? SL : SR;
+  const R irK = useL ? cL * qL : cR * qR;
   const R rK = W[0], uK = W[N], pK = W[4];
+  const R ke = R(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+  const R EK = pK * igm1 + rK * ke;          // total energy of side K
+  const R eK = pK * igm1 * irK + ke;         // E_K / rho_K
   const R mK = rK * uK;
   F[0] = mK;
 #pragma unroll
   for (int t = 0; t < 3; ++t) F[1 + t] = mK * W[1 + t];
   F[N] += pK;
   F[4] = uK * (EK + pK);
-  // star state of side K (computed for every face; used only where selected)
-  const R dK = SK - uK;
-  const R fac = rK * dK / (SK - Sst);
-  R Us[5], UK[5];
-  Us[0] = fac;
-#pragma unroll
-  for (int t = 0; t < 3; ++t) Us[1 + t] = fac * W[1 + t];
-  Us[N] = fac * Sst;
-  Us[4] = fac * (EK / rK + (Sst - uK) * (Sst + pK / (rK * dK)));
-  UK[0] = rK;
-#pragma unroll
-  for (int t = 0; t < 3; ++t) UK[1 + t] = rK * W[1 + t];
-  UK[4] = EK;
   if (star) {
+    const R dK = SK - uK;
+    const R inv = R(1) / (SK - Sst);
+    const R fac = rK * dK * inv;                       // rho*_K
+    const R ds = Sst - uK;
+    R Us[5];
+    Us[0] = fac;
 #pragma unroll
-    for (int q = 0; q < 5; ++q) F[q] = F[q] + SK * (Us[q] - UK[q]);
+    for (int t = 0; t < 3; ++t) Us[1 + t] = fac * W[1 + t];
+    Us[N] = fac * Sst;
+    Us[4] = fac * (eK + ds * Sst) + ds * pK * inv;     // rho*_K e*_K
+    F[0] = F[0] + SK * (Us[0] - rK);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) F[1 + t] = F[1 + t] + SK * (Us[1 + t] - rK * W[1 + t]);
+    F[4] = F[4] + SK * (Us[4] - EK);
   }
 }
 
+// Primitives (rho, u, v, w, p) and 1/rho of one cell.
 template <typename S, typename R>
-__device__ __forceinline__ void prim(const S *u, long long vs, R gm1, R (&w)[5]) {
+__device__ __forceinline__ void prim(const S *u, long long vs, R gm1, R (&w)[6]) {
   const R r = R(u[0]), mx = R(u[vs]), my = R(u[2 * vs]), mz = R(u[3 * vs]), E = R(u[4 * vs]);
   const R ir = R(1) / r;
   w[0] = r;
@@ -86,6 +114,7 @@ __device__ __forceinline__ void prim(const S *u, long long vs, R gm1, R (&w)[5])
   w[2] = my * ir;
   w[3] = mz * ir;
   w[4] = gm1 * (E - R(0.5) * (mx * mx + my * my + mz * mz) * ir);
+  w[5] = ir;
 }
 
 // Shared-memory map, in elements of R.
@@ -93,68 +122,74 @@ template <int T>
 struct Smem {
   static constexpr int W4 = T + 4;          // ring plane width (radius-2 halo)
   static constexpr int W2 = T + 2;          // face-state row width (radius-1)
-  static constexpr int RING = 5 * W4 * W4;  // one primitive plane
+  static constexpr int NV = 6;              // rho, u, v, w, p, 1/rho
+  static constexpr int RING = NV * W4 * W4; // one primitive plane
   static constexpr int FX = 5 * T * W2;     // x face states [v][j][i+1]
   static constexpr int FY = 5 * W2 * T;     // y face states [v][j+1][i]
   static constexpr int total(int nplanes) { return nplanes * RING + 2 * FX + 2 * FY; }
 };
 
 // Slopes, Hancock predictor and face states of the cell at tile-local (i, j)
-// of the plane in ring slot s0 (neighbour planes in sm, sp).  Returns the
-// lower/upper face states per direction in fm/fp.
+// of the plane in ring slot s0 (neighbour planes in sm, sp).  Works with half
+// slopes h = dW/2 throughout: the predictor is linear in the slopes, so
+// A(W) h (2/dx) is exactly A(W) dW / dx, and the face states are W* -+ h.
+// Returns the lower/upper face states per direction in fm/fp.
 template <int NDIM, int T, typename R>
 __device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int s0, int sp, int i,
-                                        int j, R hdt, const R (&idx)[3], R g,
+                                        int j, R hdt, const R (&idx2)[3], R g,
                                         R (&fm)[3][5], R (&fp)[3][5]) {
   using SM = Smem<T>;
+  constexpr int PL = SM::W4 * SM::W4;
   const int c = (j + 2) * SM::W4 + (i + 2);
   const R *p0 = ring + s0 * SM::RING;
-  R W0[5], dW[3][5];
+  R W0[5], h[3][5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) W0[v] = p0[v * SM::W4 * SM::W4 + c];
+  for (int v = 0; v < 5; ++v) W0[v] = p0[v * PL + c];
+  const R ir = p0[5 * PL + c];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    const R *q = p0 + v * SM::W4 * SM::W4 + c;
-    dW[0][v] = mc_lim(W0[v] - q[-1], q[1] - W0[v]);
-    dW[1][v] = mc_lim(W0[v] - q[-SM::W4], q[SM::W4] - W0[v]);
+    const R *q = p0 + v * PL + c;
+    h[0][v] = mc_half(W0[v] - q[-1], q[1] - W0[v]);
+    h[1][v] = mc_half(W0[v] - q[-SM::W4], q[SM::W4] - W0[v]);
     if (NDIM == 3) {
-      const R wm = ring[sm * SM::RING + v * SM::W4 * SM::W4 + c];
-      const R wp = ring[sp * SM::RING + v * SM::W4 * SM::W4 + c];
-      dW[2][v] = mc_lim(W0[v] - wm, wp - W0[v]);
+      const R wm = ring[sm * SM::RING + v * PL + c];
+      const R wp = ring[sp * SM::RING + v * PL + c];
+      h[2][v] = mc_half(W0[v] - wm, wp - W0[v]);
     } else {
-      dW[2][v] = R(0);
+      h[2][v] = R(0);
     }
   }
   // primitive quasi-linear form: sum_d A_d(W) dW_d / dx_d
   R acc[5] = {R(0), R(0), R(0), R(0), R(0)};
-  const R r = W0[0], pr = W0[4];
+  const R r = W0[0], gp = g * W0[4];
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
     const int n = 1 + d;
     const R un = W0[n];
     R a[5];
-    a[0] = un * dW[d][0] + r * dW[d][n];
+    a[0] = un * h[d][0] + r * h[d][n];
 #pragma unroll
-    for (int t = 0; t < 3; ++t) a[1 + t] = un * dW[d][1 + t];
-    a[n] = a[n] + dW[d][4] / r;
-    a[4] = g * pr * dW[d][n] + un * dW[d][4];
+    for (int t = 0; t < 3; ++t) a[1 + t] = un * h[d][1 + t];
+    a[n] = a[n] + h[d][4] * ir;
+    a[4] = gp * h[d][n] + un * h[d][4];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) acc[v] = acc[v] + a[v] * idx[d];
+    for (int v = 0; v < 5; ++v) acc[v] = acc[v] + a[v] * idx2[d];
   }
   R Wh[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) Wh[v] = W0[v] - hdt * acc[v];
-  bool bad = false;
+  bool ok = true;
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      fm[d][v] = Wh[v] - R(0.5) * dW[d][v];
-      fp[d][v] = Wh[v] + R(0.5) * dW[d][v];
+      fm[d][v] = Wh[v] - h[d][v];
+      fp[d][v] = Wh[v] + h[d][v];
     }
-    bad |= !(fm[d][0] > R(0)) || !(fm[d][4] > R(0)) || !(fp[d][0] > R(0)) || !(fp[d][4] > R(0));
+    ok = ok && positive(fm[d][0]) && positive(fm[d][4]) && positive(fp[d][0]) &&
+         positive(fp[d][4]);
   }
-  if (bad) {
+  if (!ok) {
 #pragma unroll
     for (int d = 0; d < NDIM; ++d)
 #pragma unroll
@@ -188,10 +223,10 @@ k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__r
   const double dt = *dtp;
   const R g = R(m.gamma), gm1 = R(m.gamma - 1.0), igm1 = R(1.0 / (m.gamma - 1.0));
   const R hdt = R(0.5 * dt);
-  R idx[3];
-  idx[0] = R(m.idx[lev][0]);
-  idx[1] = R(m.idx[lev][1]);
-  idx[2] = R(m.idx[lev][2]);
+  R idx2[3];
+  idx2[0] = R(2.0 * m.idx[lev][0]);
+  idx2[1] = R(2.0 * m.idx[lev][1]);
+  idx2[2] = R(2.0 * m.idx[lev][2]);
   const double didx = m.idx[lev][0], didy = m.idx[lev][1], didz = m.idx[lev][2];
   const S *Ub = U + (long long)b * m.bstride;
   S *Unb = Unew + (long long)b * m.bstride;
@@ -207,10 +242,10 @@ k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__r
     for (int c = tid; c < SM::W4 * SM::W4; c += NT) {
       const int ii = c % SM::W4, jj = c / SM::W4;
       const int gx = x0 + ii - 2 + ng, gy = y0 + jj - 2 + ng;
-      R w[5];
+      R w[6];
       prim<S, R>(Ub + (zp * P + gy) * P + gx, vs, gm1, w);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) dst[v * SM::W4 * SM::W4 + c] = w[v];
+      for (int v = 0; v < 6; ++v) dst[v * SM::W4 * SM::W4 + c] = w[v];
     }
   };
   auto slot_of = [&](int p) { return NDIM == 3 ? ((p % 3) + 3) % 3 : 0; };
@@ -238,7 +273,7 @@ k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__r
     R zm[5], zp[5];
     {
       R fm[3][5], fp[3][5];
-      predict<NDIM, T, R>(ring, sm, s0, sp, ti, tj, hdt, idx, g, fm, fp);
+      predict<NDIM, T, R>(ring, sm, s0, sp, ti, tj, hdt, idx2, g, fm, fp);
       if (inner) {
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
@@ -260,7 +295,7 @@ k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__r
         else if (side == 2) { i = e; j = -1; }
         else { i = e; j = T; }
         R fm[3][5], fp[3][5];
-        predict<NDIM, T, R>(ring, sm, s0, sp, i, j, hdt, idx, g, fm, fp);
+        predict<NDIM, T, R>(ring, sm, s0, sp, i, j, hdt, idx2, g, fm, fp);
         if (side < 2) {
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
