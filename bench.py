@@ -210,10 +210,11 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     fx.load()
 
+    prec = fx.FX_F64 if args.precision == "f64" else fx.FX_F32BULK
     mesh, W, gamma, cfl = inputs.workload(args.workload, scale=args.scale)
     zones_per_step = mesh.leaf_zones()
     wname = f"{args.workload}_{mesh.nroot[0] * mesh.nxb}^3" if args.workload == "kh3d" else args.workload
-    bs = fx.BlockSet(mesh, gamma, device=dev)
+    bs = fx.BlockSet(mesh, gamma, precision=prec, device=dev)
     bs.set_primitive(W)
     U0 = bs.state()          # host copy of the initial state (for the e2e leg)
     del W
@@ -284,23 +285,30 @@ def run_ours(args):
     peaks, peak_kind = load_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved_flops = ALGO_FLOPS_PER_ZONE * zones_per_step / hydro_s
+    bpz = HBM_BYTES_PER_ZONE[args.precision]
+    if args.precision == "f64":
+        roof = {"bound": "alu", "kernel": "k_hydro<3,16,double,double>",
+                "achieved": achieved_flops / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
+                "unit": "TFLOP/s", "frac": achieved_flops / FP64_PEAK_FLOPS, "traffic": None,
+                "peak_kind": "derived FP64 DFMA rate (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "algorithmic_flops_per_zone": ALGO_FLOPS_PER_ZONE}
+    else:
+        gbs = bpz * zones_per_step / hydro_s / 1e9
+        roof = {"bound": "hbm", "kernel": "k_hydro<3,16,float,float>", "achieved": gbs,
+                "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak, "traffic": None,
+                "peak_kind": peak_kind, "algorithmic_bytes_per_zone": bpz}
+    roof.update({"hydro_ms": hydro_s * 1e3,
+                 "hbm_frac_of_step": (bpz * value / ws) / (hbm_peak * 1e9),
+                 "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * sec_max / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "f64" else "f32",
         "data": "synthetic",
         "config": workload_config(args, wname) | {"replicas": ws, "blocks": mesh.nb,
                                                   "cells": zones_per_step},
-        "roofline": {
-            "bound": "alu", "kernel": "k_hydro<3,16,double,double>",
-            "achieved": achieved_flops / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
-            "unit": "TFLOP/s", "frac": achieved_flops / FP64_PEAK_FLOPS, "traffic": None,
-            "peak_kind": "derived FP64 DFMA rate (152 SMs x 2 DFMA/clk x 2.07 GHz)",
-            "algorithmic_flops_per_zone": ALGO_FLOPS_PER_ZONE,
-            "hydro_ms": hydro_s * 1e3,
-            "hbm_frac_of_step": (HBM_BYTES_PER_ZONE["f64"] * value / ws) / (hbm_peak * 1e9),
-            "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind,
-        },
+        "roofline": roof,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -325,7 +333,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="kh3d")
-    ap.add_argument("--precision", default="f64", choices=["f64"])
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32bulk"])
     ap.add_argument("--scale", type=int, default=None,
                     help="blocks per axis (default: the full workload, 16 for kh3d)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

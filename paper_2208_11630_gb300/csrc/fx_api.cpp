@@ -169,7 +169,6 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
     return fail(ctx, FX_ERR_ARG, "nxb must be a multiple of 8 in [8, 64] with nguard <= nxb/2");
   if (precision != FX_F64 && precision != FX_F32BULK)
     return fail(ctx, FX_ERR_ARG, "precision must be FX_F64 or FX_F32BULK");
-  if (precision == FX_F32BULK) return fail(ctx, FX_ERR_ARG, "FX_F32BULK is not available yet");
   if (((uintptr_t)U0 | (uintptr_t)U1) & 15) return fail(ctx, FX_ERR_ARG, "state buffers must be 16-byte aligned");
   for (int d = 0; d < ndim; ++d) {
     if (nroot[d] < 1 || !(hi[d] > lo[d])) return fail(ctx, FX_ERR_ARG, "bad nroot or domain");

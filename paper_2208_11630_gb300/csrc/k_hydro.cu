@@ -16,7 +16,15 @@
 // consumed.  The thread owning column (i, j) keeps its z face states and z
 // fluxes in registers, so no z data touches shared memory.  Per plane: load
 // + primitives, predictor, fluxes, update, three barriers.
+//
+// Precision variants: FP64 state and arithmetic; or FP32-bulk -- FP32 state,
+// FP32 reconstruction and Riemann solver, and an update that adds to U the
+// exactly differenced fluxes (TwoSum) scaled by dt/dx with a single final
+// rounding, which matches an FP64 accumulation up to a fraction of an FP32
+// ulp at a tiny fraction of the cost of FP64 arithmetic on this GPU.
 #include "fx_internal.h"
+
+#include <type_traits>
 
 namespace fx {
 namespace {
@@ -50,6 +58,21 @@ __device__ __forceinline__ bool positive(float x) {
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 
+// Quotient and reciprocal: IEEE division in FP64; the fast (MUFU-based,
+// ~2 ulp) forms in FP32, whose error is far below the FP32 storage rounding.
+__device__ __forceinline__ double div_r(double a, double b) { return a / b; }
+__device__ __forceinline__ float div_r(float a, float b) { return __fdividef(a, b); }
+
+// c * (a - b) with the difference a - b taken exactly (Knuth's TwoSum error
+// term), so that nearly equal face fluxes lose no digits before scaling.
+__device__ __forceinline__ float scaled_diff(float a, float b, float c) {
+  const float nb = -b;
+  const float s = a + nb;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (nb - bb);
+  return fmaf(c, s, c * e);
+}
+
 // HLLC flux along direction D from primitive left/right states.  One
 // reciprocal square root per side gives both the sound speed and 1/rho:
 // r = (gamma p rho)^(-1/2), c = gamma p r, 1/rho = c r.  The star state of the
@@ -66,7 +89,7 @@ __device__ __forceinline__ void hllc(const R (&WL)[5], const R (&WR)[5], R g, R 
   const R SL = fmin(uL - cL, uR - cR);
   const R SR = fmax(uL + cL, uR + cR);
   const R dL = SL - uL, dR = SR - uR;
-  const R Sst = (pR - pL + rL * uL * dL - rR * uR * dR) / (rL * dL - rR * dR);
+  const R Sst = div_r(pR - pL + rL * uL * dL - rR * uR * dR, rL * dL - rR * dR);
   // Branches: S_L >= 0 -> F_L; S* >= 0 -> F*_L; S_R > 0 -> F*_R; else F_R.
   const bool caseA = SL >= R(0);
   const bool useL = caseA || Sst >= R(0);
@@ -88,7 +111,7 @@ __device__ __forceinline__ void hllc(const R (&WL)[5], const R (&WR)[5], R g, R 
   F[4] = uK * (EK + pK);
   if (star) {
     const R dK = SK - uK;
-    const R inv = R(1) / (SK - Sst);
+    const R inv = div_r(R(1), SK - Sst);
     const R fac = rK * dK * inv;                       // rho*_K
     const R ds = Sst - uK;
     R Us[5];
@@ -108,7 +131,7 @@ __device__ __forceinline__ void hllc(const R (&WL)[5], const R (&WR)[5], R g, R 
 template <typename S, typename R>
 __device__ __forceinline__ void prim(const S *u, long long vs, R gm1, R (&w)[6]) {
   const R r = R(u[0]), mx = R(u[vs]), my = R(u[2 * vs]), mz = R(u[3 * vs]), E = R(u[4 * vs]);
-  const R ir = R(1) / r;
+  const R ir = div_r(R(1), r);
   w[0] = r;
   w[1] = mx * ir;
   w[2] = my * ir;
@@ -198,7 +221,7 @@ __device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int 
 }
 
 template <int NDIM, int T, typename S, typename R>
-__global__ void __launch_bounds__(T *T, (T == 16 ? 2 : 6))
+__global__ void __launch_bounds__(T *T, (T == 16 ? (sizeof(R) == 4 ? 3 : 2) : 6))
 k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__restrict__ leaves,
         int tiles, const double *__restrict__ dtp, double *__restrict__ regs,
         int *__restrict__ status) {
@@ -251,10 +274,16 @@ k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__r
   auto slot_of = [&](int p) { return NDIM == 3 ? ((p % 3) + 3) % 3 : 0; };
 
   // register state of the thread's column: pending update of the cell below
-  double accxy[5], fzl[5];
+  // (x+y part of its flux divergence, flux through its lower z face)
+  constexpr bool kF32 = std::is_same<R, float>::value;
+  R txy[5], fzl[5];
   R zprev[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) { accxy[v] = 0.0; fzl[v] = 0.0; zprev[v] = R(0); }
+  for (int v = 0; v < 5; ++v) { txy[v] = R(0); fzl[v] = R(0); zprev[v] = R(0); }
+  // FP32 path: dt/dx per direction; FP64 path: 1/dx and dt separately
+  const float cx = float(dt * m.idx[lev][0]), cy = float(dt * m.idx[lev][1]),
+              cz = float(dt * m.idx[lev][2]);
+  (void)cx; (void)cy; (void)cz;
 
   const int pstart = NDIM == 3 ? -1 : 0;
   const int pend = NDIM == 3 ? n : 0;   // inclusive
@@ -371,17 +400,25 @@ k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__r
     }
     __syncthreads();
 
-    // ---- update: finish the cell below (3D), start this plane's cell
+    // ---- update: finish the cell below (3D), start this plane's cell.
+    // FP64: U + dt ((Fx- - Fx+)/dx + (Fy- - Fy+)/dy + (Fz- - Fz+)/dz).
+    // FP32 storage: exact flux differences scaled by dt/dx, summed, one
+    // rounding when added to U.
     if (NDIM == 3 && p >= 1) {
       const long long o = ((long long)(p - 1 + ng) * P + (y0 + tj + ng)) * P + (x0 + ti + ng);
-      double un[5];
+      R un[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double div = accxy[v] + (fzl[v] - double(Fz[v])) * didz;
-        un[v] = double(Ub[o + v * vs]) + dt * div;
+        if constexpr (kF32) {
+          const float d = txy[v] + scaled_diff(fzl[v], Fz[v], cz);
+          un[v] = float(Ub[o + v * vs]) + d;
+        } else {
+          const double div = txy[v] + (fzl[v] - Fz[v]) * didz;
+          un[v] = double(Ub[o + v * vs]) + dt * div;
+        }
         Unb[o + v * vs] = S(un[v]);
       }
-      if (!(un[0] > 0.0) || !(2.0 * un[4] * un[0] > un[1] * un[1] + un[2] * un[2] + un[3] * un[3]))
+      if (!(un[0] > R(0)) || !(R(2) * un[4] * un[0] > un[1] * un[1] + un[2] * un[2] + un[3] * un[3]))
         atomicOr(status, 1);
     }
     if (inner) {
@@ -389,21 +426,26 @@ k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__r
       const R *Fy = fym + (tj + 1) * T + ti;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double fx = (double(Fx[v * T * SM::W2]) - double(Fx[v * T * SM::W2 + 1])) * didx;
-        const double fy = (double(Fy[v * SM::W2 * T]) - double(Fy[v * SM::W2 * T + T])) * didy;
-        accxy[v] = fx + fy;
-        if (NDIM == 3) fzl[v] = double(Fz[v]);
+        const R fxl = Fx[v * T * SM::W2], fxr = Fx[v * T * SM::W2 + 1];
+        const R fyl = Fy[v * SM::W2 * T], fyr = Fy[v * SM::W2 * T + T];
+        if constexpr (kF32) {
+          txy[v] = scaled_diff(fxl, fxr, cx) + scaled_diff(fyl, fyr, cy);
+        } else {
+          txy[v] = (fxl - fxr) * didx + (fyl - fyr) * didy;
+        }
+        if (NDIM == 3) fzl[v] = Fz[v];
       }
       if (NDIM == 2) {
         const long long o = (long long)(y0 + tj + ng) * P + (x0 + ti + ng);
-        double un[5];
+        R un[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          un[v] = double(Ub[o + v * vs]) + dt * accxy[v];
+          if constexpr (kF32) un[v] = float(Ub[o + v * vs]) + txy[v];
+          else un[v] = double(Ub[o + v * vs]) + dt * txy[v];
           Unb[o + v * vs] = S(un[v]);
         }
-        if (!(un[0] > 0.0) ||
-            !(2.0 * un[4] * un[0] > un[1] * un[1] + un[2] * un[2] + un[3] * un[3]))
+        if (!(un[0] > R(0)) ||
+            !(R(2) * un[4] * un[0] > un[1] * un[1] + un[2] * un[2] + un[3] * un[3]))
           atomicOr(status, 1);
       }
     }
@@ -443,13 +485,18 @@ cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, 
                          int n, const double *dt, double *regs, int *status, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int T = (m.nxb % 16 == 0) ? 16 : 8;
-  if (prec != 0) return cudaErrorNotSupported;
-  if (m.ndim == 3) {
-    return T == 16 ? launch_t<3, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, s)
-                   : launch_t<3, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, s);
+  if (prec == 0) {
+    if (m.ndim == 3)
+      return T == 16 ? launch_t<3, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, s)
+                     : launch_t<3, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, s);
+    return T == 16 ? launch_t<2, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, s)
+                   : launch_t<2, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, s);
   }
-  return T == 16 ? launch_t<2, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, s)
-                 : launch_t<2, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, s);
+  if (m.ndim == 3)
+    return T == 16 ? launch_t<3, 16, float, float>(m, U, Unew, leaves, n, dt, regs, status, s)
+                   : launch_t<3, 8, float, float>(m, U, Unew, leaves, n, dt, regs, status, s);
+  return T == 16 ? launch_t<2, 16, float, float>(m, U, Unew, leaves, n, dt, regs, status, s)
+                 : launch_t<2, 8, float, float>(m, U, Unew, leaves, n, dt, regs, status, s);
 }
 
 }  // namespace fx

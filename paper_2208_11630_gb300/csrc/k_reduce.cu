@@ -20,8 +20,10 @@ __global__ void k_dt(DevMesh m, const S *__restrict__ U, const int *__restrict__
   const int nz = nd == 3 ? n : 1;
   const long long ncell = (long long)n * n * nz;
   const long long total = ncell * nleaves;
-  const double g = m.gamma, gm1 = m.gamma - 1.0;
-  double smax = 0.0;
+  // the signal speed is computed in the state's precision
+  using C = S;
+  const C g = C(m.gamma), gm1 = C(m.gamma - 1.0);
+  C smax = C(0);
   for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total;
        w += (long long)gridDim.x * blockDim.x) {
     const int b = leaves[w / ncell];
@@ -30,23 +32,22 @@ __global__ void k_dt(DevMesh m, const S *__restrict__ U, const int *__restrict__
     const S *u = U + (long long)b * m.bstride +
                  ((long long)(nd == 3 ? k + ng : 0) * P + (j + ng)) * P + (i + ng);
     const long long vs = m.vstride;
-    const double r = double(u[0]), mx = double(u[vs]), my = double(u[2 * vs]),
-                 mz = double(u[3 * vs]), E = double(u[4 * vs]);
-    const double ir = 1.0 / r;
-    const double p = gm1 * (E - 0.5 * (mx * mx + my * my + mz * mz) * ir);
-    const double cs = sqrt(g * p * ir);
+    const C r = u[0], mx = u[vs], my = u[2 * vs], mz = u[3 * vs], E = u[4 * vs];
+    const C ir = C(1) / r;
+    const C p = gm1 * (E - C(0.5) * (mx * mx + my * my + mz * mz) * ir);
+    const C cs = sqrt(g * p * ir);
     const int lev = m.level[b];
-    const double vel[3] = {mx * ir, my * ir, mz * ir};
-    double s = 0.0;
+    const C vel[3] = {mx * ir, my * ir, mz * ir};
+    C s = C(0);
     for (int d = 0; d < nd; ++d) {
-      const double sd = (fabs(vel[d]) + cs) * m.idx[lev][d];
+      const C sd = (fabs(vel[d]) + cs) * C(m.idx[lev][d]);
       s = form == 0 ? s + sd : fmax(s, sd);
     }
     if (!(s <= smax)) smax = s;   // keeps a NaN
   }
   // warp and CTA maximum on the bit patterns (non-negative doubles and NaN
   // order like their bits)
-  unsigned long long bits = __double_as_longlong(smax);
+  unsigned long long bits = __double_as_longlong(double(smax));
   for (int o = 16; o > 0; o >>= 1) {
     unsigned long long other = __shfl_down_sync(0xffffffffu, bits, o);
     bits = other > bits ? other : bits;

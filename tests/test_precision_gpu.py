@@ -1,0 +1,123 @@
+"""FP32-bulk path (FP32 state, FP32 reconstruction and Riemann solver, exact
+flux differences in the update) against the FP64 oracle, and the precision
+study of the smooth-advection workload.
+
+Tolerances come from FP32 arithmetic: the initial state is rounded to FP32
+(2^-24 relative); one step adds O(10) roundings of 2^-24 on the values and
+slopes it combines, so one step stays below 1e-5 relative and 100 steps below
+1e-3 (errors grow roughly linearly and are amplified where limiters switch).
+The measured errors are printed for the record.
+"""
+import numpy as np
+import pytest
+
+from paper_2208_11630_gb300 import inputs
+from tests.helpers import leaf_interior, max_rel_err
+from tests.test_oracle_scheme import mesh_2level
+from tests.test_parity_gpu import CASES
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2208_11630_gb300 import fx as _fx
+    _fx.load()
+    return _fx
+
+
+def f32_blockset(fx, mesh, W, options=None):
+    bs = fx.BlockSet(mesh, 1.4, precision=fx.FX_F32BULK, options=options)
+    bs.set_primitive(W)
+    return bs
+
+
+@pytest.mark.parametrize("case", ["sod2d", "kh64", "amr_sedov_small", "smooth3d_nxb32",
+                                  "blocky3d_outflow", "amr_smooth_periodic"])
+def test_f32bulk_one_step(orc, fx, case):
+    mesh, W = CASES[case]()
+    om = orc.OracleMesh(mesh)
+    U = om.prim_to_cons(W)
+    bs = f32_blockset(fx, mesh, W)
+    Uo, dto = om.step(U)
+    bs.step(0.8)
+    assert bs.status() == 0
+    assert float(bs.dt.item()) == pytest.approx(dto, rel=1e-6)
+    err = max_rel_err(mesh, bs.state(), Uo)
+    print(f"\nf32bulk one step {case}: max rel err {err:.3e}")
+    assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("case", ["sod2d", "kh64", "amr_sedov_small"])
+def test_f32bulk_100_steps(orc, fx, case):
+    mesh, W = CASES[case]()
+    om = orc.OracleMesh(mesh)
+    U = om.prim_to_cons(W)
+    bs = f32_blockset(fx, mesh, W)
+    Uo, _, _ = om.run(U, nsteps=100)
+    bs.run(100, 0.8)
+    assert bs.status() == 0
+    err = max_rel_err(mesh, bs.state(), Uo)
+    print(f"\nf32bulk 100 steps {case}: max rel err {err:.3e}")
+    assert err <= 1e-3, err
+
+
+def test_f32bulk_uniform_state_and_conservation(orc, fx):
+    for mesh in (mesh_2level(4, 8, 4), inputs.uniform_mesh(2, (3, 2), 16, 4),
+                 inputs.uniform_mesh(3, (2, 2, 2), 16, 4, inputs.PERIODIC)):
+        bs = f32_blockset(fx, mesh, inputs.uniform_state(mesh))
+        U0 = bs.state()
+        bs.run(3, 0.8)
+        assert np.array_equal(leaf_interior(mesh, bs.state()), leaf_interior(mesh, U0))
+    mesh = inputs.uniform_mesh(3, (2, 2, 2), 16, 4, inputs.PERIODIC)
+    bs = f32_blockset(fx, mesh, inputs.kh_state(mesh))
+    T0 = bs.totals()
+    bs.run(100, 0.8)
+    A = orc.OracleMesh(mesh).conserved_totals(np.abs(bs.state()))
+    drift = np.abs(bs.totals() - T0) / A
+    print(f"\nf32bulk conservation drift after 100 steps: {drift}")
+    # FP32 storage rounds every cell every step; the FP64 sums see that noise
+    assert np.all(drift <= 1e-6), drift
+
+
+def test_advection_precision_study_64(orc, fx):
+    """One domain crossing (t = 1) of the smooth-advection state at 64^3:
+    GPU FP64 against the oracle (1e-10), FP32-bulk against the oracle (stated),
+    and the L1 density error of all three against the exact translated
+    profile, which is dominated by truncation, not by precision."""
+    mesh = inputs.uniform_mesh(3, (4, 4, 4), 16, 4, inputs.PERIODIC)
+    W = inputs.advection_state(mesh)
+    om = orc.OracleMesh(mesh)
+    Uo, t_or, n_or = om.run(om.prim_to_cons(W), t_end=1.0)
+    results = {}
+    for prec in ("f64", "f32bulk"):
+        bs = fx.BlockSet(mesh, 1.4, precision=fx.FX_F64 if prec == "f64" else fx.FX_F32BULK)
+        bs.set_primitive(W)
+        t = 0.0
+        while t < 1.0 * (1 - 1e-14):      # the oracle's rule: last step clipped to t = 1
+            dt = min(bs.compute_dt(0.8), 1.0 - t)
+            bs.fill()
+            bs.advance(dt)
+            t += dt
+        assert bs.status() == 0
+        results[prec] = bs.state()
+    def l1(U):
+        err = 0.0
+        for b in range(mesh.nb):
+            x, y, z = mesh.cell_centers(b)
+            ex = inputs.advection_density(x, y, z, 1.0)
+            err += np.abs(mesh.interior(U[b:b + 1])[0, 0] - ex).sum()
+        return err / 64 ** 3
+    e64 = max_rel_err(mesh, results["f64"], Uo)
+    e32 = max_rel_err(mesh, results["f32bulk"], Uo)
+    l1s = {k: l1(v) for k, v in (("oracle", Uo), ("f64", results["f64"]),
+                                  ("f32bulk", results["f32bulk"]))}
+    print(f"\nadvection 64^3 crossing ({n_or} oracle steps): GPU f64 vs oracle {e64:.3e}, "
+          f"f32bulk vs oracle {e32:.3e}, L1 vs exact {l1s}")
+    assert e64 <= 1e-10
+    assert e32 <= 1e-3
+    assert abs(l1s["f32bulk"] - l1s["oracle"]) <= 1e-3 * l1s["oracle"]
