@@ -138,6 +138,14 @@ FX_API int fx_prim_to_cons(fx_ctx *ctx, fx_blocks *bs, const double *W_dev, void
  * All nguard layers are filled, corners and edges included. */
 FX_API int fx_guardcell_fill(fx_ctx *ctx, fx_blocks *bs, void *stream);
 
+/* fx_guardcell_fill_amr: the coarse-fine part of the guard fill -- what the
+ * fused fx_hydro_advance does not read directly from same-level neighbours
+ * (Section 2's reconciliation of block boundaries across levels):
+ * restriction of every parent, the same-level guards of coarse leaves that
+ * feed a prolongation, and the prolonged guards of leaves next to a coarser
+ * leaf.  A no-op on a uniform grid.  Enough for fx_hydro_advance. */
+FX_API int fx_guardcell_fill_amr(fx_ctx *ctx, fx_blocks *bs, void *stream);
+
 /* fx_compute_dt: CFL time step from the current buffer's leaf interiors,
  * dt = cfl / max_cells sum_d (|u_d| + c) / dx_d, c = sqrt(gamma p / rho)
  * (the maximum over d with cfl_form = 1).  The maximum is an exact,
@@ -151,11 +159,15 @@ FX_API int fx_compute_dt(fx_ctx *ctx, fx_blocks *bs, double cfl, double *dt_dev,
  * primitive variables, MC-limited slopes, MUSCL-Hancock half step, HLLC
  * fluxes, conservative update into the other buffer; then the fine-to-coarse
  * flux correction at coarse-fine faces (if the "reflux" option is on) and
- * restriction into the parents.  Requires filled guards.  The new state's
- * buffer becomes current. */
+ * restriction into the parents.  Same-level neighbour data are read straight
+ * from the neighbours' interiors (identical to the guard copy); guards covered
+ * by a coarser leaf must have been filled (fx_guardcell_fill or fx_step).  The
+ * new state's buffer becomes current. */
 FX_API int fx_hydro_advance(fx_ctx *ctx, fx_blocks *bs, const double *dt_dev, void *stream);
 
-/* fx_step: fx_compute_dt, fx_guardcell_fill and fx_hydro_advance in order. */
+/* fx_step: fx_compute_dt, fx_guardcell_fill_amr and fx_hydro_advance in
+ * order.  Same-level guards are not written (the fused update reads the
+ * neighbours); call fx_guardcell_fill to materialise every guard cell. */
 FX_API int fx_step(fx_ctx *ctx, fx_blocks *bs, double cfl, double *dt_dev, void *stream);
 
 /* fx_conserved_totals: out_host[v] = sum over leaf interior cells of U_v dV

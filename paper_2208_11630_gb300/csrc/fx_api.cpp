@@ -48,6 +48,7 @@ struct fx_blocks {
   int leaves_off = 0, nleaves = 0;
   std::vector<int> par_off, par_cnt;        // parents per level
   std::vector<int> pro_off, pro_cnt;        // leaves with prolongation slots per level
+  int src_off = 0, nsrc = 0;                // coarse leaves that feed a prolongation
   double *d_regs = nullptr;
   int nreg = 0;
   std::vector<int> regidx;
@@ -364,6 +365,16 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
     for (int b : pro_by_level[l]) lists.push_back(b);
     bs->pro_cnt[l] = (int)lists.size() - bs->pro_off[l];
   }
+  {
+    std::vector<char> is_src(nb, 0);
+    for (int b = 0; b < nb; ++b)
+      for (int q = 0; q < 27; ++q)
+        if (slots[27 * b + q].x == fx::SLOT_PROLONG) is_src[slots[27 * b + q].y] = 1;
+    bs->src_off = (int)lists.size();
+    for (int b = 0; b < nb; ++b)
+      if (is_src[b]) lists.push_back(b);
+    bs->nsrc = (int)lists.size() - bs->src_off;
+  }
 
   // ---- device tables
   int rc;
@@ -477,10 +488,34 @@ int fx_hydro_advance(fx_ctx *ctx, fx_blocks *bs, const double *dt_dev, void *str
   return FX_OK;
 }
 
+// The part of the guard fill that the fused hydro kernel still needs: parents
+// restricted (they are same-level sources), the guards of coarse leaves that
+// feed a prolongation, and the prolonged guards themselves.  Same-level guards
+// of every other leaf are read by the hydro kernel from the neighbours.
+static int fill_for_fused_advance(fx_ctx *ctx, fx_blocks *bs, cudaStream_t s) {
+  void *U = bs->U[bs->cur];
+  for (int l = bs->lmax; l >= 0; --l)
+    FX_CUDA(fx::launch_restrict(bs->dm, U, bs->prec, bs->d_lists + bs->par_off[l], bs->par_cnt[l], s),
+            "restrict launch");
+  FX_CUDA(fx::launch_guard_copy(bs->dm, U, bs->prec, bs->d_lists + bs->src_off, bs->nsrc, s),
+          "guard copy launch");
+  for (int l = 1; l <= bs->lmax; ++l)
+    FX_CUDA(fx::launch_guard_prolong(bs->dm, U, bs->prec, bs->d_lists + bs->pro_off[l],
+                                     bs->pro_cnt[l], s),
+            "guard prolong launch");
+  (void)ctx;
+  return FX_OK;
+}
+
+int fx_guardcell_fill_amr(fx_ctx *ctx, fx_blocks *bs, void *stream) {
+  if (!ctx || !bs) return FX_ERR_ARG;
+  return fill_for_fused_advance(ctx, bs, (cudaStream_t)stream);
+}
+
 int fx_step(fx_ctx *ctx, fx_blocks *bs, double cfl, double *dt_dev, void *stream) {
   int rc = fx_compute_dt(ctx, bs, cfl, dt_dev, stream);
   if (rc) return rc;
-  rc = fx_guardcell_fill(ctx, bs, stream);
+  rc = fx_guardcell_fill_amr(ctx, bs, stream);
   if (rc) return rc;
   return fx_hydro_advance(ctx, bs, dt_dev, stream);
 }

@@ -10,7 +10,9 @@
 // order (zero slopes, no predictor).
 //
 // GB300 design.  One CTA owns a T x T column tile of one block and marches it
-// along z.  Shared memory holds a ring of three primitive planes (radius-2
+// along z.  Guard cells of same-level neighbours are read directly from the
+// neighbour's interior while the tile is loaded (the guard copy is fused
+// away); only guards covered by a coarser leaf come from the padded array.  Shared memory holds a ring of three primitive planes (radius-2
 // halo in x and y) and the x/y face states of the current plane; each face
 // flux is computed once by one thread and written over the face state it
 // consumed.  The thread owning column (i, j) keeps its z face states and z
@@ -259,14 +261,47 @@ k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__r
   double *reg = ridx >= 0 ? regs + (long long)ridx * m.nfaces * 5 * m.nface_cells : nullptr;
   const int nfc = m.nface_cells;
 
+  // Guard sources of this block: a same-level slot is read straight from the
+  // neighbour's interior (the value the guard copy would have written); a
+  // slot covered by a coarser leaf is read from this block's own guards,
+  // which the prolongation pass filled.
+  __shared__ int2 slots[27];
+  if (tid < 27) slots[tid] = m.slots[b * 27 + tid];
+  __syncthreads();
+  const int ox = m.origin[3 * b], oy = m.origin[3 * b + 1], oz = m.origin[3 * b + 2];
   auto load_plane = [&](int p, int slot) {
     R *dst = ring + slot * SM::RING;
-    const long long zp = p + zoff;
+    const int zpad = p + zoff;
+    const int sz = NDIM == 3 ? (zpad < ng ? 0 : (zpad >= ng + n ? 2 : 1)) : 1;
     for (int c = tid; c < SM::W4 * SM::W4; c += NT) {
       const int ii = c % SM::W4, jj = c / SM::W4;
       const int gx = x0 + ii - 2 + ng, gy = y0 + jj - 2 + ng;
+      const int sx = gx < ng ? 0 : (gx >= ng + n ? 2 : 1);
+      const int sy = gy < ng ? 0 : (gy >= ng + n ? 2 : 1);
+      const S *src = Ub + ((long long)zpad * P + gy) * P + gx;
+      if (sx != 1 || sy != 1 || sz != 1) {
+        const int2 sl = slots[sx + 3 * sy + 9 * sz];
+        if (sl.x == SLOT_COPY) {
+          const int N0 = m.ncell[lev][0], N1 = m.ncell[lev][1];
+          int ax = ox + gx - ng, ay = oy + gy - ng;
+          if (ax < 0) ax = m.bc[0][0] == 1 ? ax + N0 : 0;
+          else if (ax >= N0) ax = m.bc[0][1] == 1 ? ax - N0 : N0 - 1;
+          if (ay < 0) ay = m.bc[1][0] == 1 ? ay + N1 : 0;
+          else if (ay >= N1) ay = m.bc[1][1] == 1 ? ay - N1 : N1 - 1;
+          int lz = 0;
+          if (NDIM == 3) {
+            const int N2 = m.ncell[lev][2];
+            int az = oz + zpad - ng;
+            if (az < 0) az = m.bc[2][0] == 1 ? az + N2 : 0;
+            else if (az >= N2) az = m.bc[2][1] == 1 ? az - N2 : N2 - 1;
+            lz = az - m.origin[3 * sl.y + 2] + ng;
+          }
+          const int lx = ax - m.origin[3 * sl.y] + ng, ly = ay - m.origin[3 * sl.y + 1] + ng;
+          src = U + (long long)sl.y * m.bstride + ((long long)lz * P + ly) * P + lx;
+        }
+      }
       R w[6];
-      prim<S, R>(Ub + (zp * P + gy) * P + gx, vs, gm1, w);
+      prim<S, R>(src, vs, gm1, w);
 #pragma unroll
       for (int v = 0; v < 6; ++v) dst[v * SM::W4 * SM::W4 + c] = w[v];
     }

@@ -63,6 +63,7 @@ def load(build: bool = True):
             "fx_blocks_current": (c_int, [vp]),
             "fx_prim_to_cons": (c_int, [vp, vp, vp, vp]),
             "fx_guardcell_fill": (c_int, [vp, vp, vp]),
+            "fx_guardcell_fill_amr": (c_int, [vp, vp, vp]),
             "fx_compute_dt": (c_int, [vp, vp, c_double, vp, vp]),
             "fx_hydro_advance": (c_int, [vp, vp, vp, vp]),
             "fx_step": (c_int, [vp, vp, c_double, vp, vp]),
@@ -149,6 +150,10 @@ def fx_prim_to_cons(ctx, bs, W_ptr: int, stream=None):
 
 def fx_guardcell_fill(ctx, bs, stream=None):
     _check(ctx, load().fx_guardcell_fill(ctx, bs, _stream_ptr(stream)))
+
+
+def fx_guardcell_fill_amr(ctx, bs, stream=None):
+    _check(ctx, load().fx_guardcell_fill_amr(ctx, bs, _stream_ptr(stream)))
 
 
 def fx_compute_dt(ctx, bs, cfl: float, dt_ptr: int, stream=None):

@@ -62,3 +62,18 @@ def max_rel_err(mesh, a, b):
 def leaf_interior(mesh, U):
     leaf = mesh.is_leaf().astype(bool)
     return mesh.interior(U)[leaf]
+
+
+def max_rel_err_vec(mesh, a, b):
+    """Like ``max_rel_err`` but the three momentum components share one scale,
+    the largest momentum magnitude |m| over the compared cells.  Used where a
+    component is near zero everywhere (e.g. m_z of a 3D shear layer after one
+    step), so that its absolute roundoff is judged against the flow's
+    momentum rather than against its own vanishing maximum."""
+    leaf = mesh.is_leaf().astype(bool)
+    ia = np.moveaxis(mesh.interior(a)[leaf], 1, 0).reshape(5, -1)
+    ib = np.moveaxis(mesh.interior(b)[leaf], 1, 0).reshape(5, -1)
+    s = np.abs(ib).max(axis=1)
+    s[1:4] = np.sqrt((ib[1:4] ** 2).sum(axis=0)).max()
+    s = np.where(s == 0, 1.0, s)[:, None]
+    return float((np.abs(ia - ib) / np.maximum(np.abs(ib), s)).max())

@@ -6,13 +6,16 @@ Tolerances come from FP32 arithmetic: the initial state is rounded to FP32
 (2^-24 relative); one step adds O(10) roundings of 2^-24 on the values and
 slopes it combines, so one step stays below 1e-5 relative and 100 steps below
 1e-3 (errors grow roughly linearly and are amplified where limiters switch).
-The measured errors are printed for the record.
+The three momentum components share one error scale, the largest |m|
+(``max_rel_err_vec``): a component that is nearly zero everywhere is judged
+against the flow's momentum, not against its own vanishing maximum.  The
+measured errors are printed for the record.
 """
 import numpy as np
 import pytest
 
 from paper_2208_11630_gb300 import inputs
-from tests.helpers import leaf_interior, max_rel_err
+from tests.helpers import leaf_interior, max_rel_err, max_rel_err_vec
 from tests.test_oracle_scheme import mesh_2level
 from tests.test_parity_gpu import CASES
 
@@ -47,7 +50,7 @@ def test_f32bulk_one_step(orc, fx, case):
     bs.step(0.8)
     assert bs.status() == 0
     assert float(bs.dt.item()) == pytest.approx(dto, rel=1e-6)
-    err = max_rel_err(mesh, bs.state(), Uo)
+    err = max_rel_err_vec(mesh, bs.state(), Uo)
     print(f"\nf32bulk one step {case}: max rel err {err:.3e}")
     assert err <= 1e-5, err
 
@@ -61,7 +64,7 @@ def test_f32bulk_100_steps(orc, fx, case):
     Uo, _, _ = om.run(U, nsteps=100)
     bs.run(100, 0.8)
     assert bs.status() == 0
-    err = max_rel_err(mesh, bs.state(), Uo)
+    err = max_rel_err_vec(mesh, bs.state(), Uo)
     print(f"\nf32bulk 100 steps {case}: max rel err {err:.3e}")
     assert err <= 1e-3, err
 
@@ -113,7 +116,7 @@ def test_advection_precision_study_64(orc, fx):
             err += np.abs(mesh.interior(U[b:b + 1])[0, 0] - ex).sum()
         return err / 64 ** 3
     e64 = max_rel_err(mesh, results["f64"], Uo)
-    e32 = max_rel_err(mesh, results["f32bulk"], Uo)
+    e32 = max_rel_err_vec(mesh, results["f32bulk"], Uo)
     l1s = {k: l1(v) for k, v in (("oracle", Uo), ("f64", results["f64"]),
                                   ("f32bulk", results["f32bulk"]))}
     print(f"\nadvection 64^3 crossing ({n_or} oracle steps): GPU f64 vs oracle {e64:.3e}, "
