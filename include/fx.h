@@ -116,6 +116,12 @@ FX_API int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const i
  * caller's buffers are untouched). */
 FX_API int fx_blocks_destroy(fx_blocks *bs);
 
+/* fx_blocks_mark_dirty: tell the library that the caller wrote the current
+ * state buffer directly (not through an fx_* call), so that the next
+ * fx_compute_dt reads the state instead of reusing the signal-speed maximum
+ * of the last update. */
+FX_API int fx_blocks_mark_dirty(fx_blocks *bs);
+
 /* fx_blocks_current: index (0 or 1) of the buffer that holds the current
  * state; flips after every fx_hydro_advance.  Negative on error. */
 FX_API int fx_blocks_current(const fx_blocks *bs);
@@ -150,7 +156,11 @@ FX_API int fx_guardcell_fill_amr(fx_ctx *ctx, fx_blocks *bs, void *stream);
  * dt = cfl / max_cells sum_d (|u_d| + c) / dx_d, c = sqrt(gamma p / rho)
  * (the maximum over d with cfl_form = 1).  The maximum is an exact,
  * order-independent reduction.  `dt_dev` is a device double that receives
- * dt (kept on the device so that a captured graph needs no host trip). */
+ * dt (kept on the device so that a captured graph needs no host trip).
+ * When the current state was produced by fx_hydro_advance and nothing wrote
+ * it since, the update already reduced its signal speeds and only the final
+ * division runs; otherwise the state is read again.  A caller that writes
+ * the state buffers itself must call fx_blocks_mark_dirty afterwards. */
 FX_API int fx_compute_dt(fx_ctx *ctx, fx_blocks *bs, double cfl, double *dt_dev, void *stream);
 
 /* fx_hydro_advance: one unsplit second-order step of all leaves with the

@@ -54,7 +54,12 @@ struct fx_blocks {
   std::vector<int> regidx;
   RefluxItem *d_refl = nullptr;
   int nrefl = 0;
-  unsigned long long *d_scratch = nullptr;  // dt max bits + CTA counter
+  unsigned long long *d_scratch = nullptr;  // [0] dt max bits, [1] CTA counter,
+                                            // [2] signal-speed max of the last update
+  unsigned char *d_rmask = nullptr;         // [nb] faces (bit 2d+s) the reflux corrects
+  long long epoch = 0;                      // bumped on every write of the current state
+  long long next_epoch = -1;                // epoch described by d_scratch[2]
+  int next_form = 0;
   int *d_status = nullptr;
   double *d_dt = nullptr;                   // dt scratch for fx_run_host
   double *d_totals = nullptr;               // [nleaves][5]
@@ -97,7 +102,7 @@ void free_blocks(fx_blocks *bs) {
   cudaFree(bs->d_level); cudaFree(bs->d_origin); cudaFree(bs->d_child);
   cudaFree(bs->d_regidx); cudaFree(bs->d_slots); cudaFree(bs->d_lists);
   cudaFree(bs->d_regs); cudaFree(bs->d_refl); cudaFree(bs->d_scratch);
-  cudaFree(bs->d_status); cudaFree(bs->d_dt); cudaFree(bs->d_totals);
+  cudaFree(bs->d_status); cudaFree(bs->d_dt); cudaFree(bs->d_totals); cudaFree(bs->d_rmask);
 }
 
 struct Lattice {
@@ -343,6 +348,10 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
         if (it.fine[f][q] >= 0) it.fine[f][q] = reg(it.fine[f][q]);
   }
   bs->nrefl = (int)refl.size();
+  std::vector<unsigned char> rmask(nb, 0);
+  for (auto &it : refl)
+    for (int f = 0; f < 6; ++f)
+      if (it.fine[f][0] >= 0) rmask[it.block] |= (unsigned char)(1u << f);
 
   // ---- work lists: leaves | parents per level | prolong leaves per level
   std::vector<int> lists;
@@ -385,17 +394,18 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
   if ((rc = upload(bs, &bs->d_slots, slots))) return bail(rc, ctx->err);
   if ((rc = upload(bs, &bs->d_lists, lists))) return bail(rc, ctx->err);
   if ((rc = upload(bs, &bs->d_refl, refl))) return bail(rc, ctx->err);
+  if (bs->nrefl > 0 && (rc = upload(bs, &bs->d_rmask, rmask))) return bail(rc, ctx->err);
   const int nfc = ndim == 3 ? n * n : n;
   if (bs->nreg > 0) {
     if (cudaMalloc(&bs->d_regs, sizeof(double) * (size_t)bs->nreg * 2 * ndim * 5 * nfc) != cudaSuccess)
       return bail(FX_ERR_OOM, "cudaMalloc of flux registers failed");
   }
-  if (cudaMalloc(&bs->d_scratch, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+  if (cudaMalloc(&bs->d_scratch, 3 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&bs->d_status, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&bs->d_dt, sizeof(double)) != cudaSuccess ||
       cudaMalloc(&bs->d_totals, sizeof(double) * 5 * (size_t)bs->nleaves) != cudaSuccess)
     return bail(FX_ERR_OOM, "cudaMalloc of scratch failed");
-  if (cudaMemset(bs->d_scratch, 0, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+  if (cudaMemset(bs->d_scratch, 0, 3 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemset(bs->d_status, 0, sizeof(int)) != cudaSuccess)
     return bail(FX_ERR_CUDA, "cudaMemset of scratch failed");
 
@@ -442,6 +452,7 @@ int fx_prim_to_cons(fx_ctx *ctx, fx_blocks *bs, const double *W_dev, void *strea
   if (!ctx || !bs || !W_dev) return FX_ERR_ARG;
   FX_CUDA(fx::launch_prim_to_cons(bs->dm, W_dev, bs->U[bs->cur], bs->prec, (cudaStream_t)stream),
           "prim_to_cons launch");
+  ++bs->epoch;
   return FX_OK;
 }
 
@@ -464,9 +475,22 @@ int fx_guardcell_fill(fx_ctx *ctx, fx_blocks *bs, void *stream) {
 int fx_compute_dt(fx_ctx *ctx, fx_blocks *bs, double cfl, double *dt_dev, void *stream) {
   if (!ctx || !bs || !dt_dev || !(cfl > 0.0)) return FX_ERR_ARG;
   if (bs->nleaves == 0) return fail(ctx, FX_ERR_STATE, "no leaves");
+  if (bs->next_epoch == bs->epoch && bs->next_form == ctx->cfl_form) {
+    // the last update already reduced this state's signal speeds
+    FX_CUDA(fx::launch_dt_finalize(bs->d_scratch + 2, cfl, dt_dev, (cudaStream_t)stream),
+            "dt finalize launch");
+    bs->next_epoch = -1;
+    return FX_OK;
+  }
   FX_CUDA(fx::launch_dt(bs->dm, bs->U[bs->cur], bs->prec, bs->d_lists + bs->leaves_off, bs->nleaves,
                         cfl, ctx->cfl_form, dt_dev, bs->d_scratch, (cudaStream_t)stream),
           "dt launch");
+  return FX_OK;
+}
+
+int fx_blocks_mark_dirty(fx_blocks *bs) {
+  if (!bs) return FX_ERR_ARG;
+  ++bs->epoch;
   return FX_OK;
 }
 
@@ -474,17 +498,24 @@ int fx_hydro_advance(fx_ctx *ctx, fx_blocks *bs, const double *dt_dev, void *str
   if (!ctx || !bs || !dt_dev) return FX_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   void *Uo = bs->U[bs->cur], *Un = bs->U[1 - bs->cur];
+  unsigned long long *smax = bs->d_scratch + 2;
+  const bool refl = ctx->reflux && bs->nrefl > 0;
+  FX_CUDA(cudaMemsetAsync(smax, 0, sizeof(unsigned long long), s), "signal max reset");
   FX_CUDA(fx::launch_hydro(bs->dm, Uo, Un, bs->prec, bs->d_lists + bs->leaves_off, bs->nleaves,
-                           dt_dev, bs->d_regs, bs->d_status, s),
+                           dt_dev, bs->d_regs, bs->d_status, smax, refl ? bs->d_rmask : nullptr,
+                           ctx->cfl_form, s),
           "hydro launch");
-  if (ctx->reflux && bs->nrefl > 0)
+  if (refl)
     FX_CUDA(fx::launch_reflux(bs->dm, Un, bs->prec, bs->d_refl, bs->nrefl, dt_dev, bs->d_regs,
-                              bs->d_status, s),
+                              bs->d_status, smax, ctx->cfl_form, s),
             "reflux launch");
   for (int l = bs->lmax; l >= 0; --l)
     FX_CUDA(fx::launch_restrict(bs->dm, Un, bs->prec, bs->d_lists + bs->par_off[l], bs->par_cnt[l], s),
             "restrict launch");
   bs->cur = 1 - bs->cur;
+  ++bs->epoch;
+  bs->next_epoch = bs->epoch;
+  bs->next_form = ctx->cfl_form;
   return FX_OK;
 }
 
@@ -559,6 +590,7 @@ int fx_run_host(fx_ctx *ctx, fx_blocks *bs, const void *U_host_in, void *U_host_
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)bs->nb * bs->dm.bstride * bs->elsize;
   FX_CUDA(cudaMemcpyAsync(bs->U[bs->cur], U_host_in, bytes, cudaMemcpyHostToDevice, s), "state upload");
+  ++bs->epoch;
   double t = 0.0;
   for (int i = 0; i < nsteps; ++i) {
     int rc = fx_step(ctx, bs, cfl, bs->d_dt, stream);

@@ -52,10 +52,19 @@ cudaError_t launch_guard_copy(const DevMesh &m, void *U, int prec, const int *le
                               cudaStream_t s);
 cudaError_t launch_guard_prolong(const DevMesh &m, void *U, int prec, const int *leaves, int n,
                                  cudaStream_t s);
+// smax (may be null): receives atomicMax of the bit patterns of the new
+// state's CFL signal speeds (form 0 = sum over directions, 1 = max); cells on
+// the faces flagged in rmask[block] (bit 2d+s) are left to the reflux kernel.
 cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, const int *leaves,
-                         int n, const double *dt, double *regs, int *status, cudaStream_t s);
+                         int n, const double *dt, double *regs, int *status,
+                         unsigned long long *smax, const unsigned char *rmask, int form,
+                         cudaStream_t s);
 cudaError_t launch_reflux(const DevMesh &m, void *Unew, int prec, const RefluxItem *items, int n,
-                          const double *dt, const double *regs, int *status, cudaStream_t s);
+                          const double *dt, const double *regs, int *status,
+                          unsigned long long *smax, int form, cudaStream_t s);
+// dt = cfl / (maximum held in *smax), then re-arms *smax to zero.
+cudaError_t launch_dt_finalize(unsigned long long *smax, double cfl, double *dt_out,
+                               cudaStream_t s);
 cudaError_t launch_dt(const DevMesh &m, const void *U, int prec, const int *leaves, int n,
                       double cfl, int form, double *dt_out, unsigned long long *scratch,
                       cudaStream_t s);

@@ -15,7 +15,8 @@ namespace {
 template <typename S>
 __global__ void k_reflux(DevMesh m, S *__restrict__ Unew, const RefluxItem *__restrict__ items,
                          const double *__restrict__ dtp, const double *__restrict__ regs,
-                         int *__restrict__ status) {
+                         int *__restrict__ status, unsigned long long *__restrict__ smax,
+                         int form) {
   __shared__ RefluxItem it;
   if (threadIdx.x == 0) it = items[blockIdx.x];
   __syncthreads();
@@ -70,9 +71,22 @@ __global__ void k_reflux(DevMesh m, S *__restrict__ Unew, const RefluxItem *__re
       }
     }
     if (touched) {
-      for (int v = 0; v < 5; ++v) Uc[o + v * m.vstride] = S(u[v]);
+      S us[5];
+      for (int v = 0; v < 5; ++v) { us[v] = S(u[v]); Uc[o + v * m.vstride] = us[v]; }
       if (!(u[0] > 0.0) || !(2.0 * u[4] * u[0] > u[1] * u[1] + u[2] * u[2] + u[3] * u[3]))
         atomicOr(status, 1);
+      if (smax) {
+        // CFL signal speed of the corrected cell, in the state's precision
+        const S ir = S(1) / us[0];
+        const S pr = S(m.gamma - 1.0) * (us[4] - S(0.5) * (us[1] * us[1] + us[2] * us[2] + us[3] * us[3]) * ir);
+        const S cs = sqrt(S(m.gamma) * pr * ir);
+        S sg = S(0);
+        for (int d = 0; d < nd; ++d) {
+          const S sd = (fabs(us[1 + d] * ir) + cs) * S(m.idx[lev][d]);
+          sg = form == 0 ? sg + sd : fmax(sg, sd);
+        }
+        atomicMax(smax, (unsigned long long)__double_as_longlong(double(sg)));
+      }
     }
   }
 }
@@ -80,12 +94,13 @@ __global__ void k_reflux(DevMesh m, S *__restrict__ Unew, const RefluxItem *__re
 }  // namespace
 
 cudaError_t launch_reflux(const DevMesh &m, void *Unew, int prec, const RefluxItem *items, int n,
-                          const double *dt, const double *regs, int *status, cudaStream_t s) {
+                          const double *dt, const double *regs, int *status,
+                          unsigned long long *smax, int form, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int ncell = m.nxb * m.nxb * (m.ndim == 3 ? m.nxb : 1);
   dim3 grid(n, (ncell + 255) / 256);
-  if (prec == 0) k_reflux<double><<<grid, 256, 0, s>>>(m, static_cast<double *>(Unew), items, dt, regs, status);
-  else k_reflux<float><<<grid, 256, 0, s>>>(m, static_cast<float *>(Unew), items, dt, regs, status);
+  if (prec == 0) k_reflux<double><<<grid, 256, 0, s>>>(m, static_cast<double *>(Unew), items, dt, regs, status, smax, form);
+  else k_reflux<float><<<grid, 256, 0, s>>>(m, static_cast<float *>(Unew), items, dt, regs, status, smax, form);
   count_launch();
   return cudaGetLastError();
 }

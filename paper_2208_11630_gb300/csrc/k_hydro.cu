@@ -223,10 +223,11 @@ __device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int 
 }
 
 template <int NDIM, int T, typename S, typename R>
-__global__ void __launch_bounds__(T *T, (T == 16 ? (sizeof(R) == 4 ? 3 : 2) : 6))
+__global__ void __launch_bounds__(T *T, (T == 16 ? (sizeof(R) == 4 ? 4 : 2) : 6))
 k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__restrict__ leaves,
         int tiles, const double *__restrict__ dtp, double *__restrict__ regs,
-        int *__restrict__ status) {
+        int *__restrict__ status, unsigned long long *__restrict__ smax_out,
+        const unsigned char *__restrict__ rmask, int cfl_form) {
   using SM = Smem<T>;
   constexpr int NT = T * T;
   constexpr int NPL = NDIM == 3 ? 3 : 1;
@@ -319,6 +320,31 @@ k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__r
   const float cx = float(dt * m.idx[lev][0]), cy = float(dt * m.idx[lev][1]),
               cz = float(dt * m.idx[lev][2]);
   (void)cx; (void)cy; (void)cz;
+  // Signal speed of the new state, for the next step's CFL dt (same formula
+  // and precision as the standalone reduction).  Cells that the flux
+  // correction will still change (on a face in rmask) are left to it.
+  const unsigned fmask = rmask ? rmask[b] : 0u;
+  const R sidx[3] = {R(m.idx[lev][0]), R(m.idx[lev][1]), R(m.idx[lev][2])};
+  R smax_t = R(0);
+  auto signal = [&](const R (&u)[5], int ci, int cj, int ck) {
+    if (fmask) {
+      const int cc[3] = {ci, cj, ck};
+      for (int d = 0; d < NDIM; ++d) {
+        if (((fmask >> (2 * d)) & 1u) && cc[d] == 0) return;
+        if (((fmask >> (2 * d + 1)) & 1u) && cc[d] == n - 1) return;
+      }
+    }
+    const R ir = R(1) / u[0];
+    const R pr = gm1 * (u[4] - R(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * ir);
+    const R cs = sqrt(g * pr * ir);
+    R sg = R(0);
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+      const R sd = (fabs(u[1 + d] * ir) + cs) * sidx[d];
+      sg = cfl_form == 0 ? sg + sd : fmax(sg, sd);
+    }
+    if (!(sg <= smax_t)) smax_t = sg;   // keeps a NaN
+  };
 
   const int pstart = NDIM == 3 ? -1 : 0;
   const int pend = NDIM == 3 ? n : 0;   // inclusive
@@ -384,9 +410,16 @@ k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__r
       for (int f = tid; f < 2 * (T + 1) * T; f += NT) {
         const int dir = f >= (T + 1) * T;
         const int ff = dir ? f - (T + 1) * T : f;
-        int a, e;  // a: face index along the normal (0..T), e: transverse
-        if (ff < T * T) { a = ff % T; e = ff / T; }
-        else { a = T; e = ff - T * T; }
+        // a: face index along the normal (0..T), e: transverse index; the
+        // lanes of a warp take consecutive x so shared-memory rows stay
+        // contiguous for both directions
+        int a, e;
+        if (ff < T * T) {
+          if (!dir) { a = ff % T; e = ff / T; }
+          else { a = ff / T; e = ff % T; }
+        } else {
+          a = T; e = ff - T * T;
+        }
         R WL[5], WR[5], F[5];
         if (!dir) {
 #pragma unroll
@@ -455,6 +488,7 @@ k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__r
       }
       if (!(un[0] > R(0)) || !(R(2) * un[4] * un[0] > un[1] * un[1] + un[2] * un[2] + un[3] * un[3]))
         atomicOr(status, 1);
+      if (smax_out) signal(un, x0 + ti, y0 + tj, p - 1);
     }
     if (inner) {
       const R *Fx = fxm + tj * SM::W2 + ti + 1;
@@ -482,16 +516,27 @@ k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__r
         if (!(un[0] > R(0)) ||
             !(R(2) * un[4] * un[0] > un[1] * un[1] + un[2] * un[2] + un[3] * un[3]))
           atomicOr(status, 1);
+        if (smax_out) signal(un, x0 + ti, y0 + tj, 0);
       }
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v) zprev[v] = zp[v];
   }
+  if (smax_out) {
+    // maximum over the CTA on the bit patterns of non-negative doubles
+    unsigned long long bits = __double_as_longlong(double(smax_t));
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long other = __shfl_down_sync(0xffffffffu, bits, o);
+      bits = other > bits ? other : bits;
+    }
+    if ((tid & 31) == 0) atomicMax(smax_out, bits);
+  }
 }
 
 template <int NDIM, int T, typename S, typename R>
 cudaError_t launch_t(const DevMesh &m, const void *U, void *Unew, const int *leaves, int n,
-                     const double *dt, double *regs, int *status, cudaStream_t s) {
+                     const double *dt, double *regs, int *status, unsigned long long *smax,
+                     const unsigned char *rmask, int form, cudaStream_t s) {
   const int tiles = m.nxb / T;
   const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(R);
   auto kern = k_hydro<NDIM, T, S, R>;
@@ -503,7 +548,7 @@ cudaError_t launch_t(const DevMesh &m, const void *U, void *Unew, const int *lea
     attr_done = true;
   }
   kern<<<n * tiles * tiles, T * T, smem, s>>>(m, static_cast<const S *>(U), static_cast<S *>(Unew),
-                                              leaves, tiles, dt, regs, status);
+                                              leaves, tiles, dt, regs, status, smax, rmask, form);
   count_launch();
   return cudaGetLastError();
 }
@@ -517,21 +562,23 @@ size_t hydro_smem_bytes(int ndim, int tile, int prec) {
 }
 
 cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, const int *leaves,
-                         int n, const double *dt, double *regs, int *status, cudaStream_t s) {
+                         int n, const double *dt, double *regs, int *status,
+                         unsigned long long *smax, const unsigned char *rmask, int form,
+                         cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int T = (m.nxb % 16 == 0) ? 16 : 8;
   if (prec == 0) {
     if (m.ndim == 3)
-      return T == 16 ? launch_t<3, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, s)
-                     : launch_t<3, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, s);
-    return T == 16 ? launch_t<2, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, s)
-                   : launch_t<2, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, s);
+      return T == 16 ? launch_t<3, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
+                     : launch_t<3, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
+    return T == 16 ? launch_t<2, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
+                   : launch_t<2, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
   }
   if (m.ndim == 3)
-    return T == 16 ? launch_t<3, 16, float, float>(m, U, Unew, leaves, n, dt, regs, status, s)
-                   : launch_t<3, 8, float, float>(m, U, Unew, leaves, n, dt, regs, status, s);
-  return T == 16 ? launch_t<2, 16, float, float>(m, U, Unew, leaves, n, dt, regs, status, s)
-                 : launch_t<2, 8, float, float>(m, U, Unew, leaves, n, dt, regs, status, s);
+    return T == 16 ? launch_t<3, 16, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
+                   : launch_t<3, 8, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
+  return T == 16 ? launch_t<2, 16, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
+                 : launch_t<2, 8, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
 }
 
 }  // namespace fx

@@ -108,7 +108,20 @@ __global__ void k_totals(DevMesh m, const S *__restrict__ U, const int *__restri
   }
 }
 
+__global__ void k_dt_finalize(unsigned long long *__restrict__ smax, double cfl,
+                              double *__restrict__ dt_out) {
+  *dt_out = cfl / __longlong_as_double(*smax);
+  *smax = 0ull;
+}
+
 }  // namespace
+
+cudaError_t launch_dt_finalize(unsigned long long *smax, double cfl, double *dt_out,
+                               cudaStream_t s) {
+  k_dt_finalize<<<1, 1, 0, s>>>(smax, cfl, dt_out);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_dt(const DevMesh &m, const void *U, int prec, const int *leaves, int n,
                       double cfl, int form, double *dt_out, unsigned long long *scratch,

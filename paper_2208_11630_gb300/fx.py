@@ -61,6 +61,7 @@ def load(build: bool = True):
                                          c_int, vp, vp, ctypes.POINTER(vp)]),
             "fx_blocks_destroy": (c_int, [vp]),
             "fx_blocks_current": (c_int, [vp]),
+            "fx_blocks_mark_dirty": (c_int, [vp]),
             "fx_prim_to_cons": (c_int, [vp, vp, vp, vp]),
             "fx_guardcell_fill": (c_int, [vp, vp, vp]),
             "fx_guardcell_fill_amr": (c_int, [vp, vp, vp]),
@@ -138,6 +139,10 @@ def fx_blocks_create(ctx, mesh, precision: int, U0_ptr: int, U1_ptr: int):
 
 def fx_blocks_destroy(bs):
     load().fx_blocks_destroy(bs)
+
+
+def fx_blocks_mark_dirty(bs):
+    load().fx_blocks_mark_dirty(bs)
 
 
 def fx_blocks_current(bs) -> int:
@@ -258,6 +263,7 @@ class BlockSet:
     def set_conserved(self, U: np.ndarray):
         import torch
         self.current.copy_(torch.as_tensor(U, dtype=self.dtype))
+        fx_blocks_mark_dirty(self.bs)
 
     def fill(self, stream=None):
         fx_guardcell_fill(self.ctx, self.bs, stream)

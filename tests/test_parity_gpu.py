@@ -274,3 +274,21 @@ def test_full_size_kh_sampled(orc, fx):
 def _one(mesh):
     m = inputs.uniform_mesh(3, (1, 1, 1), mesh.nxb, mesh.ng)
     return m
+
+
+@pytest.mark.parametrize("case", ["kh64", "sod2d", "amr_smooth_periodic", "amr_sedov_small"])
+def test_fused_dt_equals_standalone_reduction(fx, case):
+    """After an update the next dt comes from the signal speeds the update
+    (and the flux correction) reduced on the fly; it must equal a fresh
+    reduction over the stored state."""
+    mesh, W = CASES[case]()
+    for prec in (fx.FX_F64, fx.FX_F32BULK):
+        bs = fx.BlockSet(mesh, 1.4, precision=prec)
+        bs.set_primitive(W)
+        bs.step(0.8)
+        bs.step(0.8)
+        fused = bs.compute_dt(0.8)
+        fx.fx_blocks_mark_dirty(bs.bs)
+        fresh = bs.compute_dt(0.8)
+        assert fused == pytest.approx(fresh, rel=1e-15), (prec, fused, fresh)
+        bs.close()
