@@ -187,11 +187,18 @@ def run_reference(args):
     return 0
 
 
-def workload_config(args, name):
-    return {"workload": name, "blocks": 4096 if "256" in name else 64, "nxb": 16, "nguard": 4,
-            "cells": 256 ** 3 if "256" in name else 64 ** 3, "bc": "periodic", "cfl": 0.8,
+def workload_config(args, name, mesh=None):
+    if mesh is None:
+        return {"workload": name, "blocks": 64, "nxb": 16, "nguard": 4, "cells": 64 ** 3,
+                "bc": "periodic", "cfl": 0.8, "precision": args.precision}
+    state_bytes = mesh.nb * 5 * mesh.PZ * mesh.P * mesh.P * (8 if args.precision == "f64" else 4)
+    bc = "periodic" if mesh.bc[0][0] == 1 else "outflow"
+    return {"workload": name, "blocks": mesh.nb, "leaf_blocks": int(mesh.is_leaf().sum()),
+            "nxb": mesh.nxb, "nguard": mesh.ng, "cells": mesh.leaf_zones(), "bc": bc, "cfl": 0.8,
             "precision": args.precision,
-            "l2": "inputs larger than L2 (2.26 GB per FP64 state buffer vs 129 MB L2)"}
+            "l2": (f"inputs larger than L2 ({state_bytes / 1e9:.2f} GB per state buffer vs 129 MB L2)"
+                   if state_bytes > 129e6 else
+                   f"state ({state_bytes / 1e6:.1f} MB) fits in L2: launch-latency workload")}
 
 
 # ---------------------------------------------------------------------------
@@ -214,7 +221,11 @@ def run_ours(args):
     prec = fx.FX_F64 if args.precision == "f64" else fx.FX_F32BULK
     mesh, W, gamma, cfl = inputs.workload(args.workload, scale=args.scale)
     zones_per_step = mesh.leaf_zones()
-    wname = f"{args.workload}_{mesh.nroot[0] * mesh.nxb}^3" if args.workload == "kh3d" else args.workload
+    edge = mesh.nroot[0] * mesh.nxb
+    wname = {"kh3d": f"kh3d_{edge}^3", "advection3d": f"advection3d_{edge}^3",
+             "sod2d": f"sod2d_{edge}^2", "sedov_amr": f"sedov_amr_{edge}^3_base_2level"}.get(
+                 args.workload, args.workload)
+    kname = f"k_hydro<{mesh.ndim},{16 if mesh.nxb % 16 == 0 else 8},{'double' if prec == 0 else 'float'}>"
     bs = fx.BlockSet(mesh, gamma, precision=prec, device=dev)
     bs.set_primitive(W)
     U0 = bs.state()          # host copy of the initial state (for the e2e leg)
@@ -288,14 +299,14 @@ def run_ours(args):
     achieved_flops = ALGO_FLOPS_PER_ZONE * zones_per_step / hydro_s
     bpz = HBM_BYTES_PER_ZONE[args.precision]
     if args.precision == "f64":
-        roof = {"bound": "alu", "kernel": "k_hydro<3,16,double,double>",
+        roof = {"bound": "alu", "kernel": kname,
                 "achieved": achieved_flops / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
                 "unit": "TFLOP/s", "frac": achieved_flops / FP64_PEAK_FLOPS, "traffic": None,
                 "peak_kind": "derived FP64 DFMA rate (152 SMs x 2 DFMA/clk x 2.07 GHz)",
                 "algorithmic_flops_per_zone": ALGO_FLOPS_PER_ZONE}
     else:
         gbs = bpz * zones_per_step / hydro_s / 1e9
-        roof = {"bound": "hbm", "kernel": "k_hydro<3,16,float,float>", "achieved": gbs,
+        roof = {"bound": "hbm", "kernel": kname, "achieved": gbs,
                 "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak, "traffic": None,
                 "peak_kind": peak_kind, "algorithmic_bytes_per_zone": bpz}
     roof.update({"hydro_ms": hydro_s * 1e3,
@@ -307,8 +318,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "f64" else "f32",
         "data": "synthetic",
-        "config": workload_config(args, wname) | {"replicas": ws, "blocks": mesh.nb,
-                                                  "cells": zones_per_step},
+        "config": workload_config(args, wname, mesh) | {"replicas": ws},
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": int(launches),

@@ -292,3 +292,23 @@ def test_fused_dt_equals_standalone_reduction(fx, case):
         fresh = bs.compute_dt(0.8)
         assert fused == pytest.approx(fresh, rel=1e-15), (prec, fused, fresh)
         bs.close()
+
+
+def test_full_size_sedov_amr(orc, fx):
+    """The Sedov configuration at full size (8^3 coarse blocks of 16^3, 128
+    refined, 1024 fine blocks; 1,408 leaves): three fused steps on the GPU
+    against the oracle on every leaf, parents included."""
+    mesh, W, gamma, cfl = inputs.workload("sedov_amr")
+    om = orc.OracleMesh(mesh, gamma)
+    U = om.prim_to_cons(W)
+    bs = gpu_blockset(fx, mesh, W)
+    bs.set_conserved(U)
+    Uo, _, _ = om.run(U, nsteps=3)
+    bs.run(3, cfl)
+    assert bs.status() == 0
+    G = bs.state()
+    assert max_rel_err(mesh, G, Uo) <= 1e-12
+    par = ~mesh.is_leaf().astype(bool)
+    a, b = mesh.interior(G)[par], mesh.interior(Uo)[par]
+    s = np.maximum(np.abs(b).max(axis=(0, 2, 3, 4), keepdims=True), 1e-300)
+    assert (np.abs(a - b) / np.maximum(np.abs(b), s)).max() <= 1e-12
