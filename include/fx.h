@@ -203,6 +203,48 @@ FX_API int fx_run_host(fx_ctx *ctx, fx_blocks *bs, const void *U_host_in, void *
  * coarse-fine face.  For diagnostics and tests. */
 FX_API const double *fx_block_fluxes(const fx_blocks *bs, int b);
 
+/* ---- batched stepping of many block sets ----------------------------------
+ * A batch advances many independent block sets (requests) together: each
+ * step is one CUDA graph replay in which every phase of the step -- dt,
+ * coarse-fine guard fill, the fused update, flux correction, restriction --
+ * is one kernel launch over a work list spanning all requests, the update
+ * being a persistent kernel per (dimension, precision, tile) group.  Block
+ * sets of different sizes, block counts, levels and precisions mix freely;
+ * each keeps its own dt.  This is the paper's block-by-block update (Section
+ * 2) organised for one GPU; the batching itself has no counterpart in the
+ * paper.  A block set in a batch must not be stepped or destroyed directly
+ * until fx_batch_remove returns it. */
+typedef struct fx_batch fx_batch;
+
+/* fx_batch_create: empty batch with room for `max_requests` block sets. */
+FX_API int fx_batch_create(fx_ctx *ctx, int max_requests, fx_batch **out);
+/* fx_batch_destroy: synchronise and free the batch (block sets are released). */
+FX_API int fx_batch_destroy(fx_batch *b);
+/* fx_batch_add: add block set `bs` to advance `nsteps` steps with CFL number
+ * `cfl` from its current state; *slot_out receives its slot.  It joins at the
+ * next fx_batch_run (the graph is re-captured).  Synchronises `stream`. */
+FX_API int fx_batch_add(fx_batch *b, fx_blocks *bs, double cfl, int nsteps, void *stream,
+                        int *slot_out);
+/* fx_batch_run: `nsteps` batched steps; every request with steps left
+ * advances one step per batched step.  Asynchronous on `stream`. */
+FX_API int fx_batch_run(fx_batch *b, int nsteps, void *stream);
+/* fx_batch_poll: steps_left[slot] for every slot (-1 = empty).  Synchronises. */
+FX_API int fx_batch_poll(fx_batch *b, int *steps_left, void *stream);
+/* fx_batch_remove: release the block set in `slot` (cancelling it if steps
+ * remain); its current buffer is whatever the batch produced.  Synchronises. */
+FX_API int fx_batch_remove(fx_batch *b, int slot, void *stream);
+/* fx_batch_tune: autotune the update launch of each (dimension, precision)
+ * group whose blocks allow 16x16 tiles: the tile edge (16 or 8) and the CTAs
+ * per SM of the persistent kernel, by timing each candidate on the batch's
+ * own blocks with dt = 0 (which leaves every state unchanged).  Choices are
+ * cached per (dimension, precision, SM count, size class).  `report` (may be
+ * NULL; room for 193 ints) receives (tile, ctas, microseconds) triples, 0
+ * terminated.  Synchronises. */
+FX_API int fx_batch_tune(fx_batch *b, void *stream, int *report);
+/* fx_batch_choice: the launch choice in use for a (ndim, precision) group. */
+FX_API int fx_batch_choice(const fx_batch *b, int ndim, int precision, int *tile,
+                           int *ctas_per_sm);
+
 /* Largest block count fx_compute_dt_noalloc accepts (size of its fixed
  * device scratch, one 8-byte partial per block plus a counter: 256 KB). */
 #define FX_NOALLOC_MAX_BLOCKS 32768

@@ -57,6 +57,9 @@ struct fx_blocks {
   unsigned long long *d_scratch = nullptr;  // [0] dt max bits, [1] CTA counter,
                                             // [2] signal-speed max of the last update
   unsigned char *d_rmask = nullptr;         // [nb] faces (bit 2d+s) the reflux corrects
+  std::vector<int> h_lists;                 // host copy of the work lists
+  std::vector<RefluxItem> h_refl;
+  int in_batch = 0;                         // owned by a batch: stepped only through it
   long long epoch = 0;                      // bumped on every write of the current state
   long long next_epoch = -1;                // epoch described by d_scratch[2]
   int next_form = 0;
@@ -393,6 +396,8 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
   if ((rc = upload(bs, &bs->d_regidx, bs->regidx))) return bail(rc, ctx->err);
   if ((rc = upload(bs, &bs->d_slots, slots))) return bail(rc, ctx->err);
   if ((rc = upload(bs, &bs->d_lists, lists))) return bail(rc, ctx->err);
+  bs->h_lists = lists;
+  bs->h_refl = refl;
   if ((rc = upload(bs, &bs->d_refl, refl))) return bail(rc, ctx->err);
   if (bs->nrefl > 0 && (rc = upload(bs, &bs->d_rmask, rmask))) return bail(rc, ctx->err);
   const int nfc = ndim == 3 ? n * n : n;
@@ -496,6 +501,7 @@ int fx_blocks_mark_dirty(fx_blocks *bs) {
 
 int fx_hydro_advance(fx_ctx *ctx, fx_blocks *bs, const double *dt_dev, void *stream) {
   if (!ctx || !bs || !dt_dev) return FX_ERR_ARG;
+  if (bs->in_batch) return fail(ctx, FX_ERR_STATE, "block set is owned by a batch");
   cudaStream_t s = (cudaStream_t)stream;
   void *Uo = bs->U[bs->cur], *Un = bs->U[1 - bs->cur];
   unsigned long long *smax = bs->d_scratch + 2;
@@ -609,6 +615,420 @@ int fx_run_host(fx_ctx *ctx, fx_blocks *bs, const void *U_host_in, void *U_host_
 }
 
 long long fx_kernel_launches(void) { return fx::launch_count(); }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batched, graph-replayed stepping of many block sets
+// ---------------------------------------------------------------------------
+
+using fx::BatchReq;
+
+namespace {
+
+struct Range {
+  int off = 0, n = 0;
+};
+
+struct HydroGroup {
+  int ndim, tile, prec;
+  Range r;
+  int ctas;   // CTAs per SM (0 = as many as fit)
+};
+
+// Tuned launch choice for one (ndim, precision) group of block sets whose
+// nxb allows 16x16 tiles: the tile edge and the CTAs per SM.
+struct Choice {
+  int tile = 16;
+  int ctas = 0;
+};
+
+std::map<std::tuple<int, int, int, int>, Choice> g_tune_cache;  // (ndim, prec, nsm, log2 items)
+
+}  // namespace
+
+struct fx_batch {
+  fx_ctx *ctx = nullptr;
+  int max_req = 0, nsm = 0;
+  std::vector<fx_blocks *> slot;
+  std::vector<BatchReq> h_req;
+  BatchReq *d_req = nullptr;
+  double *d_dt = nullptr;
+  int4 *d_items = nullptr;
+  size_t items_cap = 0;
+  unsigned int *d_ctr = nullptr;     // work counters, one per hydro group
+  cudaStream_t cap = nullptr;        // private capture stream
+  cudaGraphExec_t exec = nullptr;
+  bool dirty = true;
+  int lmax = 0;
+  Range rst[2][FX_MAXLEV], cpy[2], pro[2][FX_MAXLEV], rfx[2];
+  std::vector<HydroGroup> groups;
+  Choice choice[2][2];               // [ndim - 2][prec]
+  bool tuned[2][2] = {{false, false}, {false, false}};
+};
+
+namespace {
+
+constexpr int kMaxGroups = 8;
+
+// Work lists of the batched step for the current composition.
+int build_lists(fx_batch *b, const Choice (&ch)[2][2]) {
+  std::vector<int4> rst[2][FX_MAXLEV], cpy[2], pro[2][FX_MAXLEV], rfx[2];
+  std::map<std::tuple<int, int, int>, std::vector<int4>> hyd;
+  b->lmax = 0;
+  for (int r = 0; r < b->max_req; ++r) {
+    fx_blocks *bs = b->slot[r];
+    if (!bs) continue;
+    const int pr = bs->prec, nd = bs->ndim, n = bs->nxb;
+    const std::vector<int> &L = bs->h_lists;
+    const int ncell = n * n * (nd == 3 ? n : 1);
+    const int chunks = (ncell + 255) / 256;
+    b->lmax = std::max(b->lmax, bs->lmax);
+    for (int l = 0; l <= bs->lmax; ++l) {
+      for (int q = 0; q < bs->par_cnt[l]; ++q)
+        for (int c = 0; c < chunks; ++c) rst[pr][l].push_back(make_int4(r, L[bs->par_off[l] + q], c, 0));
+      for (int q = 0; q < bs->pro_cnt[l]; ++q)
+        for (int k = 0; k < bs->PZ; ++k) pro[pr][l].push_back(make_int4(r, L[bs->pro_off[l] + q], k, 0));
+    }
+    for (int q = 0; q < bs->nsrc; ++q)
+      for (int k = 0; k < bs->PZ; ++k) cpy[pr].push_back(make_int4(r, L[bs->src_off + q], k, 0));
+    for (int q = 0; q < bs->nrefl; ++q)
+      for (int c = 0; c < chunks; ++c) rfx[pr].push_back(make_int4(r, q, c, chunks));
+    const int T = (n % 16 == 0) ? ch[nd - 2][pr].tile : 8;
+    const int tiles = n / T;
+    auto &H = hyd[std::make_tuple(nd, T, pr)];
+    for (int q = 0; q < bs->nleaves; ++q)
+      for (int t = 0; t < tiles * tiles; ++t)
+        H.push_back(make_int4(r, L[bs->leaves_off + q], t, tiles));
+  }
+  std::vector<int4> all;
+  auto put = [&](std::vector<int4> &v, Range &rg) {
+    rg.off = (int)all.size();
+    rg.n = (int)v.size();
+    all.insert(all.end(), v.begin(), v.end());
+  };
+  for (int p = 0; p < 2; ++p) {
+    for (int l = 0; l < FX_MAXLEV; ++l) {
+      put(rst[p][l], b->rst[p][l]);
+      put(pro[p][l], b->pro[p][l]);
+    }
+    put(cpy[p], b->cpy[p]);
+    put(rfx[p], b->rfx[p]);
+  }
+  b->groups.clear();
+  for (auto &kv : hyd) {
+    HydroGroup g;
+    g.ndim = std::get<0>(kv.first);
+    g.tile = std::get<1>(kv.first);
+    g.prec = std::get<2>(kv.first);
+    g.ctas = g.tile == 16 || true ? ch[g.ndim - 2][g.prec].ctas : 0;
+    put(kv.second, g.r);
+    b->groups.push_back(g);
+  }
+  if ((int)b->groups.size() > kMaxGroups) return FX_ERR_STATE;
+  if (all.size() > b->items_cap) {
+    cudaFree(b->d_items);
+    b->d_items = nullptr;
+    size_t cap = std::max<size_t>(all.size(), 2 * b->items_cap);
+    if (cudaMalloc(&b->d_items, cap * sizeof(int4)) != cudaSuccess) return FX_ERR_OOM;
+    b->items_cap = cap;
+  }
+  if (!all.empty() &&
+      cudaMemcpy(b->d_items, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess)
+    return FX_ERR_CUDA;
+  return FX_OK;
+}
+
+cudaError_t record_step(fx_batch *b, cudaStream_t s) {
+  cudaError_t e;
+#define FXB(call) do { e = (call); if (e != cudaSuccess) return e; } while (0)
+  FXB(fx::launch_batch_begin(b->d_req, b->max_req, s));
+  for (int l = b->lmax - 1; l >= 0; --l)
+    for (int p = 0; p < 2; ++p)
+      FXB(fx::launch_batch_phase(fx::BATCH_RESTRICT_PRE, p, b->d_req, b->d_items + b->rst[p][l].off,
+                                 b->rst[p][l].n, s));
+  for (int p = 0; p < 2; ++p)
+    FXB(fx::launch_batch_phase(fx::BATCH_COPY, p, b->d_req, b->d_items + b->cpy[p].off, b->cpy[p].n, s));
+  for (int l = 1; l <= b->lmax; ++l)
+    for (int p = 0; p < 2; ++p)
+      FXB(fx::launch_batch_phase(fx::BATCH_PROLONG, p, b->d_req, b->d_items + b->pro[p][l].off,
+                                 b->pro[p][l].n, s));
+  for (size_t g = 0; g < b->groups.size(); ++g) {
+    const HydroGroup &G = b->groups[g];
+    FXB(cudaMemsetAsync(b->d_ctr + g, 0, sizeof(unsigned int), s));
+    FXB(fx::launch_hydro_batch(G.ndim, G.tile, G.prec, b->d_req, b->d_items + G.r.off, G.r.n,
+                               b->d_ctr + g, G.ctas, b->nsm, s));
+  }
+  for (int p = 0; p < 2; ++p)
+    FXB(fx::launch_batch_phase(fx::BATCH_REFLUX, p, b->d_req, b->d_items + b->rfx[p].off, b->rfx[p].n, s));
+  for (int l = b->lmax - 1; l >= 0; --l)
+    for (int p = 0; p < 2; ++p)
+      FXB(fx::launch_batch_phase(fx::BATCH_RESTRICT_POST, p, b->d_req, b->d_items + b->rst[p][l].off,
+                                 b->rst[p][l].n, s));
+  FXB(fx::launch_batch_end(b->d_req, b->max_req, s));
+#undef FXB
+  return cudaSuccess;
+}
+
+int capture(fx_batch *b) {
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  int rc = build_lists(b, b->choice);
+  if (rc) return fail(b->ctx, rc, "building the batch work lists failed");
+  for (const HydroGroup &G : b->groups) {   // attributes before capture
+    int fit = 0;
+    cudaError_t e = fx::hydro_batch_fit(G.ndim, G.tile, G.prec, &fit);
+    if (e != cudaSuccess) return cuda_fail(b->ctx, e, "batched kernel set-up");
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(b->ctx, e, "begin capture");
+  cudaError_t er = record_step(b, b->cap);
+  e = cudaStreamEndCapture(b->cap, &g);
+  if (er != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(b->ctx, er, "recording the batched step");
+  }
+  if (e != cudaSuccess) return cuda_fail(b->ctx, e, "end capture");
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(b->ctx, e, "graph instantiate");
+  b->dirty = false;
+  return FX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fx_batch_create(fx_ctx *ctx, int max_requests, fx_batch **out) {
+  if (!ctx || !out || max_requests < 1 || max_requests > (1 << 20)) return FX_ERR_ARG;
+  *out = nullptr;
+  fx_batch *b = new (std::nothrow) fx_batch;
+  if (!b) return fail(ctx, FX_ERR_OOM, "host allocation failed");
+  b->ctx = ctx;
+  b->max_req = max_requests;
+  b->slot.assign(max_requests, nullptr);
+  b->h_req.assign(max_requests, BatchReq{});
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaMalloc(&b->d_req, sizeof(BatchReq) * max_requests) != cudaSuccess ||
+      cudaMalloc(&b->d_dt, sizeof(double) * max_requests) != cudaSuccess ||
+      cudaMalloc(&b->d_ctr, sizeof(unsigned int) * kMaxGroups) != cudaSuccess ||
+      cudaMemset(b->d_req, 0, sizeof(BatchReq) * max_requests) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaFree(b->d_req); cudaFree(b->d_dt); cudaFree(b->d_ctr);
+    delete b;
+    return fail(ctx, FX_ERR_OOM, "batch allocation failed");
+  }
+  *out = b;
+  return FX_OK;
+}
+
+int fx_batch_destroy(fx_batch *b) {
+  if (!b) return FX_ERR_ARG;
+  cudaDeviceSynchronize();
+  for (fx_blocks *bs : b->slot)
+    if (bs) bs->in_batch = 0;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  cudaFree(b->d_req); cudaFree(b->d_dt); cudaFree(b->d_ctr); cudaFree(b->d_items);
+  delete b;
+  return FX_OK;
+}
+
+int fx_batch_add(fx_batch *b, fx_blocks *bs, double cfl, int nsteps, void *stream, int *slot_out) {
+  if (!b || !bs || !(cfl > 0.0) || nsteps < 1) return FX_ERR_ARG;
+  if (bs->in_batch) return fail(b->ctx, FX_ERR_STATE, "block set already in a batch");
+  int s = -1;
+  for (int r = 0; r < b->max_req; ++r)
+    if (!b->slot[r]) { s = r; break; }
+  if (s < 0) return fail(b->ctx, FX_ERR_STATE, "batch is full");
+  cudaStream_t st = (cudaStream_t)stream;
+  BatchReq &q = b->h_req[s];
+  q = BatchReq{};
+  q.m = bs->dm;
+  q.U[0] = bs->U[0];
+  q.U[1] = bs->U[1];
+  q.cur = bs->cur;
+  q.steps_left = nsteps;
+  q.prec = bs->prec;
+  q.form = bs->ctx->cfl_form;
+  q.reflux = (bs->ctx->reflux && bs->nrefl > 0) ? 1 : 0;
+  q.nrefl = bs->nrefl;
+  q.cfl = cfl;
+  q.dt = b->d_dt + s;
+  q.regs = bs->d_regs;
+  q.status = bs->d_status;
+  q.scratch = bs->d_scratch;
+  q.rmask = q.reflux ? bs->d_rmask : nullptr;
+  q.refl = bs->d_refl;
+  // the first batched step needs the signal-speed maximum of the current state
+  if (!(bs->next_epoch == bs->epoch && bs->next_form == q.form)) {
+    FX_CUDA(fx::launch_signal_max(bs->dm, bs->U[bs->cur], bs->prec, bs->d_lists + bs->leaves_off,
+                                  bs->nleaves, q.form, bs->d_scratch + 2, bs->d_scratch, st),
+            "signal max launch");
+  }
+  FX_CUDA(cudaMemcpyAsync(b->d_req + s, &q, sizeof(BatchReq), cudaMemcpyHostToDevice, st),
+          "batch descriptor upload");
+  FX_CUDA(cudaStreamSynchronize(st), "batch add sync");
+  b->slot[s] = bs;
+  bs->in_batch = 1;
+  b->dirty = true;
+  if (slot_out) *slot_out = s;
+  return FX_OK;
+}
+
+int fx_batch_run(fx_batch *b, int nsteps, void *stream) {
+  if (!b || nsteps < 0) return FX_ERR_ARG;
+  if (b->dirty) {
+    // the new composition is captured after everything already queued
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(b->ctx, e, "batch sync");
+    int rc = capture(b);
+    if (rc) return rc;
+  }
+  for (int i = 0; i < nsteps; ++i) {
+    cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(b->ctx, e, "graph launch");
+  }
+  return FX_OK;
+}
+
+int fx_batch_poll(fx_batch *b, int *steps_left, void *stream) {
+  if (!b || !steps_left) return FX_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int> h(b->max_req, 0);
+  cudaError_t e = cudaMemcpy2DAsync(h.data(), sizeof(int), &b->d_req[0].steps_left, sizeof(BatchReq),
+                                    sizeof(int), b->max_req, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(b->ctx, e, "poll copy");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(b->ctx, e, "poll sync");
+  for (int r = 0; r < b->max_req; ++r) steps_left[r] = b->slot[r] ? h[r] : -1;
+  return FX_OK;
+}
+
+int fx_batch_remove(fx_batch *b, int slot, void *stream) {
+  if (!b || slot < 0 || slot >= b->max_req || !b->slot[slot]) return FX_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  fx_blocks *bs = b->slot[slot];
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(b->ctx, e, "remove sync");
+  BatchReq q;
+  e = cudaMemcpy(&q, b->d_req + slot, sizeof(BatchReq), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(b->ctx, e, "descriptor read");
+  // a request still running is cancelled: the captured graph skips it
+  const int zero = 0;
+  e = cudaMemcpy(&b->d_req[slot].steps_left, &zero, sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(b->ctx, e, "descriptor write");
+  bs->cur = q.cur;
+  ++bs->epoch;
+  bs->next_epoch = bs->epoch;        // the last update left its signal maximum
+  bs->next_form = q.form;
+  bs->in_batch = 0;
+  b->slot[slot] = nullptr;           // free for reuse (a new occupant recaptures)
+  return FX_OK;
+}
+
+int fx_batch_tune(fx_batch *b, void *stream, int *report) {
+  if (!b) return FX_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(b->ctx, e, "tune sync");
+  // dt = 0 makes every timed update leave the state unchanged: the new
+  // buffer receives a copy of the current one and the signal maximum of the
+  // current state is reproduced; the next batched step recomputes dt
+  e = cudaMemset(b->d_dt, 0, sizeof(double) * b->max_req);
+  if (e != cudaSuccess) return cuda_fail(b->ctx, e, "tune dt reset");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int nrep = 0;
+  for (int nd = 2; nd <= 3; ++nd)
+    for (int pr = 0; pr < 2; ++pr) {
+      // is there a group of 16-capable block sets of this kind?
+      size_t nitems = 0;
+      for (fx_blocks *bs : b->slot)
+        if (bs && bs->ndim == nd && bs->prec == pr && bs->nxb % 16 == 0)
+          nitems += (size_t)bs->nleaves * (bs->nxb / 16) * (bs->nxb / 16);
+      if (!nitems) continue;
+      int lg = 0;
+      while ((size_t(1) << (lg + 1)) <= nitems) ++lg;
+      auto key = std::make_tuple(nd, pr, b->nsm, lg);
+      auto hit = g_tune_cache.find(key);
+      if (hit != g_tune_cache.end()) {
+        b->choice[nd - 2][pr] = hit->second;
+        b->tuned[nd - 2][pr] = true;
+        continue;
+      }
+      float best = 1e30f;
+      Choice bestc;
+      for (int tile : {16, 8}) {
+        int fit = 0;
+        e = fx::hydro_batch_fit(nd, tile, pr, &fit);
+        if (e != cudaSuccess) break;
+        for (int ctas = 1; ctas <= fit; ++ctas) {
+          Choice ch[2][2];
+          for (int a = 0; a < 2; ++a)
+            for (int c = 0; c < 2; ++c) ch[a][c] = b->choice[a][c];
+          ch[nd - 2][pr].tile = tile;
+          ch[nd - 2][pr].ctas = ctas;
+          if (build_lists(b, ch)) break;
+          const HydroGroup *G = nullptr;
+          int gi = 0;
+          for (size_t g = 0; g < b->groups.size(); ++g)
+            if (b->groups[g].ndim == nd && b->groups[g].prec == pr && b->groups[g].tile == tile) {
+              G = &b->groups[g];
+              gi = (int)g;
+            }
+          if (!G) continue;
+          float tot = 0.f;
+          for (int rep = 0; rep < 4; ++rep) {
+            cudaMemsetAsync(b->d_ctr + gi, 0, sizeof(unsigned int), st);
+            cudaEventRecord(e0, st);
+            fx::launch_hydro_batch(nd, tile, pr, b->d_req, b->d_items + G->r.off, G->r.n,
+                                   b->d_ctr + gi, ctas, b->nsm, st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tot += ms;   // first launch warms up
+          }
+          if (report && nrep < 64) {
+            report[3 * nrep] = tile;
+            report[3 * nrep + 1] = ctas;
+            report[3 * nrep + 2] = (int)(tot * 1000.f / 3.f);   // microseconds
+            ++nrep;
+          }
+          if (tot < best) { best = tot; bestc.tile = tile; bestc.ctas = ctas; }
+        }
+      }
+      b->choice[nd - 2][pr] = bestc;
+      b->tuned[nd - 2][pr] = true;
+      g_tune_cache[key] = bestc;
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(b->ctx, e, "tuning");
+  if (report) report[3 * nrep] = 0;
+  b->dirty = true;
+  return FX_OK;
+}
+
+int fx_batch_choice(const fx_batch *b, int ndim, int precision, int *tile, int *ctas_per_sm) {
+  if (!b || (ndim != 2 && ndim != 3) || (precision != 0 && precision != 1)) return FX_ERR_ARG;
+  if (tile) *tile = b->choice[ndim - 2][precision].tile;
+  if (ctas_per_sm) *ctas_per_sm = b->choice[ndim - 2][precision].ctas;
+  return FX_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
 
 const double *fx_block_fluxes(const fx_blocks *bs, int b) {
   if (!bs || b < 0 || b >= bs->nb || bs->regidx[b] < 0 || !bs->d_regs) return nullptr;

@@ -43,6 +43,26 @@ struct RefluxItem {
   int fine[6][4];
 };
 
+// One block set inside a batch (device-resident; kernels of the batched step
+// read it, the step-end kernel flips `cur` and counts `steps_left` down).
+struct BatchReq {
+  DevMesh m;
+  void *U[2];
+  int cur;                        // index of the current state buffer
+  int steps_left;                 // > 0: advanced by the next batched step
+  int prec;                       // 0 FP64, 1 FP32-bulk
+  int form;                       // CFL form
+  int reflux;                     // apply flux correction
+  int nrefl;                      // reflux work items
+  double cfl;
+  double *dt;                     // this request's dt (device)
+  double *regs;                   // flux registers (or null)
+  int *status;                    // device status word
+  unsigned long long *scratch;    // [2] = signal-speed max of the current state
+  const unsigned char *rmask;     // faces corrected by reflux, per block (or null)
+  const RefluxItem *refl;         // reflux work items (or null)
+};
+
 // Launchers.  Each returns the launch status (cudaGetLastError).
 cudaError_t launch_prim_to_cons(const DevMesh &m, const double *W, void *U, int prec,
                                 cudaStream_t s);
@@ -70,6 +90,33 @@ cudaError_t launch_dt(const DevMesh &m, const void *U, int prec, const int *leav
                       cudaStream_t s);
 cudaError_t launch_totals(const DevMesh &m, const void *U, int prec, const int *leaves, int n,
                           double *out, cudaStream_t s);
+
+// Phases of the batched step (see k_batch.cu).
+enum BatchPhase : int {
+  BATCH_RESTRICT_PRE = 0,
+  BATCH_COPY = 1,
+  BATCH_PROLONG = 2,
+  BATCH_REFLUX = 3,
+  BATCH_RESTRICT_POST = 4
+};
+cudaError_t launch_batch_begin(BatchReq *reqs, int n, cudaStream_t s);
+cudaError_t launch_batch_end(BatchReq *reqs, int n, cudaStream_t s);
+cudaError_t launch_batch_phase(int phase, int prec, const BatchReq *reqs, const int4 *items, int n,
+                               cudaStream_t s);
+// Signal-speed maximum of a state (bit pattern) into *max_out, without
+// forming dt; scratch as for launch_dt.
+cudaError_t launch_signal_max(const DevMesh &m, const void *U, int prec, const int *leaves, int n,
+                              int form, unsigned long long *max_out, unsigned long long *scratch,
+                              cudaStream_t s);
+// Occupancy of the batched hydro kernel (CTAs per SM), setting its shared
+// memory attribute on first use.
+cudaError_t hydro_batch_fit(int ndim, int tile, int prec, int *fit);
+
+// Batched persistent hydro kernel over (request, block, tile, tiles) items.
+// ctas_per_sm <= 0 means as many as fit.
+cudaError_t launch_hydro_batch(int ndim, int tile, int prec, const BatchReq *reqs,
+                               const int4 *items, int nitems, unsigned int *counter,
+                               int ctas_per_sm, int nsm, cudaStream_t s);
 
 // Process-wide count of kernels launched by the library.
 void count_launch(int n = 1);

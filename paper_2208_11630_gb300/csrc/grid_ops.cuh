@@ -1,0 +1,241 @@
+// grid_ops.cuh -- device bodies of the Grid-side operations, shared by the
+// per-block-set kernels (k_grid.cu, k_amr.cu) and the batched step
+// (k_batch.cu).  Each body handles one unit of work (a parent chunk, a padded
+// z-plane of a leaf, a chunk of a coarse block's cells) for one block set
+// described by a DevMesh.
+//
+// Paper: Flash-X (arXiv 2208.11630), Section 2 -- the Grid reconciles block
+// boundaries across refinement levels between the per-block physics updates.
+// Operators (textbook block-AMR): pairwise-mean restriction, same-level copy
+// with outflow/periodic boundaries, MC-limited conservative linear
+// prolongation, Berger & Colella (1989) flux correction.
+#pragma once
+
+#include "fx_internal.h"
+
+namespace fx {
+namespace ops {
+
+template <typename S>
+__device__ __forceinline__ double ld(const S *p) { return static_cast<double>(*p); }
+
+template <typename S>
+__device__ __forceinline__ void st(S *p, double v) { *p = static_cast<S>(v); }
+
+__device__ __forceinline__ int apply_bc(int g, int N, int kind_lo, int kind_hi) {
+  if (g < 0) return kind_lo == 1 ? ((g % N) + N) % N : 0;
+  if (g >= N) return kind_hi == 1 ? g % N : N - 1;
+  return g;
+}
+
+// van Leer's MC limiter.
+__device__ __forceinline__ double mc_lim(double a, double b) {
+  if (a * b <= 0.0) return 0.0;
+  double s = fmin(fmin(2.0 * fabs(a), 2.0 * fabs(b)), 0.5 * fabs(a + b));
+  return a > 0.0 ? s : -s;
+}
+
+__device__ __forceinline__ int slot_of(int i, int lo, int hi) {
+  return i < lo ? 0 : (i >= hi ? 2 : 1);
+}
+
+// Parent p, interior cells [chunk*blockDim, (chunk+1)*blockDim): the pairwise
+// mean of the 2^d child cells (x pairs first, then y, then z), which restricts
+// a uniform field to itself exactly.
+template <typename S>
+__device__ __forceinline__ void restrict_cells(const DevMesh &m, S *__restrict__ U, int p,
+                                               int chunk) {
+  const int n = m.nxb, ng = m.ng, P = m.P;
+  const int nz = m.ndim == 3 ? n : 1;
+  const int ncell = n * n * nz;
+  const int c = chunk * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int i = c % n, j = (c / n) % n, k = c / (n * n);
+  const int cx = 2 * i >= n, cy = 2 * j >= n, cz = (m.ndim == 3) && (2 * k >= n);
+  const int ch = m.child[p * 8 + cx + 2 * cy + 4 * cz];
+  const int fi = 2 * i - cx * n + ng, fj = 2 * j - cy * n + ng;
+  const int fk = m.ndim == 3 ? 2 * k - cz * n + ng : 0;
+  const S *F = U + (long long)ch * m.bstride;
+  S *D = U + (long long)p * m.bstride;
+  const int dk = m.ndim == 3 ? k + ng : 0;
+  for (int v = 0; v < 5; ++v) {
+    const S *f = F + v * m.vstride + ((long long)fk * P + fj) * P + fi;
+    double r;
+    if (m.ndim == 2) {
+      r = ((ld(f) + ld(f + 1)) + (ld(f + P) + ld(f + P + 1))) * 0.25;
+    } else {
+      const S *g = f + (long long)P * P;
+      r = (((ld(f) + ld(f + 1)) + (ld(f + P) + ld(f + P + 1))) +
+           ((ld(g) + ld(g + 1)) + (ld(g + P) + ld(g + P + 1)))) * 0.125;
+    }
+    st(D + v * m.vstride + ((long long)dk * P + (j + ng)) * P + (i + ng), r);
+  }
+}
+
+// Leaf b, padded z-plane k, whole CTA: every guard cell whose slot is a
+// same-level copy reads the source block's interior at the boundary-mapped
+// global position.
+template <typename S>
+__device__ __forceinline__ void guard_copy_plane(const DevMesh &m, S *__restrict__ U, int b,
+                                                 int k) {
+  __shared__ int2 sl[27];
+  __syncthreads();
+  if (threadIdx.x < 27) sl[threadIdx.x] = m.slots[b * 27 + threadIdx.x];
+  __syncthreads();
+  const int P = m.P, ng = m.ng, n = m.nxb, lev = m.level[b];
+  const int sz = m.ndim == 3 ? slot_of(k, ng, ng + n) : 1;
+  const int ox = m.origin[3 * b], oy = m.origin[3 * b + 1], oz = m.origin[3 * b + 2];
+  S *Ub = U + (long long)b * m.bstride;
+  for (int c = threadIdx.x; c < P * P; c += blockDim.x) {
+    const int i = c % P, j = c / P;
+    const int sx = slot_of(i, ng, ng + n), sy = slot_of(j, ng, ng + n);
+    if (sx == 1 && sy == 1 && sz == 1) continue;
+    const int2 s = sl[sx + 3 * sy + 9 * sz];
+    if (s.x != SLOT_COPY) continue;
+    const int gx = apply_bc(ox + i - ng, m.ncell[lev][0], m.bc[0][0], m.bc[0][1]);
+    const int gy = apply_bc(oy + j - ng, m.ncell[lev][1], m.bc[1][0], m.bc[1][1]);
+    const int src = s.y;
+    const int lx = gx - m.origin[3 * src] + ng, ly = gy - m.origin[3 * src + 1] + ng;
+    int lz = 0;
+    if (m.ndim == 3) {
+      const int gz = apply_bc(oz + k - ng, m.ncell[lev][2], m.bc[2][0], m.bc[2][1]);
+      lz = gz - m.origin[3 * src + 2] + ng;
+    }
+    const S *Us = U + (long long)src * m.bstride + ((long long)lz * P + ly) * P + lx;
+    S *Ud = Ub + ((long long)k * P + j) * P + i;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Ud[v * m.vstride] = Us[v * m.vstride];
+  }
+}
+
+// Leaf b, padded z-plane k, whole CTA: guard cells covered by a coarser leaf
+// get U_c + sum_d s_d MC(U_c - U_{c-e_d}, U_{c+e_d} - U_c), s_d = -1/4 for the
+// lower fine half of the coarse cell along d and +1/4 for the upper half,
+// summed x, y, z.  The coarse leaf's own guards (depth 1) must be filled.
+template <typename S>
+__device__ __forceinline__ void guard_prolong_plane(const DevMesh &m, S *__restrict__ U, int b,
+                                                    int k) {
+  __shared__ int2 sl[27];
+  __syncthreads();
+  if (threadIdx.x < 27) sl[threadIdx.x] = m.slots[b * 27 + threadIdx.x];
+  __syncthreads();
+  const int P = m.P, ng = m.ng, n = m.nxb, lev = m.level[b];
+  const int sz = m.ndim == 3 ? slot_of(k, ng, ng + n) : 1;
+  const int ox = m.origin[3 * b], oy = m.origin[3 * b + 1], oz = m.origin[3 * b + 2];
+  S *Ub = U + (long long)b * m.bstride;
+  const long long sP = P, sPP = (long long)P * P;
+  for (int c = threadIdx.x; c < P * P; c += blockDim.x) {
+    const int i = c % P, j = c / P;
+    const int sx = slot_of(i, ng, ng + n), sy = slot_of(j, ng, ng + n);
+    if (sx == 1 && sy == 1 && sz == 1) continue;
+    const int2 s = sl[sx + 3 * sy + 9 * sz];
+    if (s.x != SLOT_PROLONG) continue;
+    int g[3];
+    g[0] = apply_bc(ox + i - ng, m.ncell[lev][0], m.bc[0][0], m.bc[0][1]);
+    g[1] = apply_bc(oy + j - ng, m.ncell[lev][1], m.bc[1][0], m.bc[1][1]);
+    g[2] = m.ndim == 3 ? apply_bc(oz + k - ng, m.ncell[lev][2], m.bc[2][0], m.bc[2][1]) : 0;
+    const int cb = s.y;
+    const int cx = (g[0] >> 1) - m.origin[3 * cb] + ng;
+    const int cy = (g[1] >> 1) - m.origin[3 * cb + 1] + ng;
+    const int cz = m.ndim == 3 ? (g[2] >> 1) - m.origin[3 * cb + 2] + ng : 0;
+    const S *C = U + (long long)cb * m.bstride + (cz * sPP + cy * sP + cx);
+    S *Ud = Ub + ((long long)k * P + j) * P + i;
+    const long long step[3] = {1, sP, sPP};
+    for (int v = 0; v < 5; ++v) {
+      const S *cv = C + v * m.vstride;
+      const double uc = ld(cv);
+      double val = uc;
+      for (int d = 0; d < m.ndim; ++d) {
+        const double um = ld(cv - step[d]), up = ld(cv + step[d]);
+        const double sig = mc_lim(uc - um, up - uc);
+        const double off = (g[d] & 1) ? 0.25 : -0.25;
+        val = val + off * sig;
+      }
+      st(Ud + v * m.vstride, val);
+    }
+  }
+}
+
+// Coarse leaf it.block, cells [first, ncell) strided by `stride`: replace the
+// coarse face flux F_c by the pairwise mean F_bar of the fine face fluxes,
+//   upper face: U_c += dt/dx (F_c - F_bar); lower face: U_c -= dt/dx (F_c - F_bar),
+// in the order x-, x+, y-, y+, z-, z+.  If smax is given, the corrected cell's
+// CFL signal speed (state precision) joins the maximum.
+template <typename S>
+__device__ __forceinline__ void reflux_cells(const DevMesh &m, S *__restrict__ Unew,
+                                             const RefluxItem &it, double dt,
+                                             const double *__restrict__ regs,
+                                             int *__restrict__ status,
+                                             unsigned long long *__restrict__ smax, int form,
+                                             int first, int stride) {
+  const int c = it.block;
+  const int n = m.nxb, ng = m.ng, P = m.P, nd = m.ndim;
+  const int nz = nd == 3 ? n : 1;
+  const int lev = m.level[c];
+  const int nfc = m.nface_cells;
+  const long long rstride = (long long)m.nfaces * 5 * nfc;
+  const double *Fc = regs + (long long)m.regidx[c] * rstride;
+  S *Uc = Unew + (long long)c * m.bstride;
+  const int ncell = n * n * nz;
+  for (int cell = first; cell < ncell; cell += stride) {
+    const int ci[3] = {cell % n, (cell / n) % n, cell / (n * n)};
+    bool surf = false;   // only cells on the block surface can be corrected
+    for (int d = 0; d < nd; ++d) surf |= (ci[d] == 0 || ci[d] == n - 1);
+    if (!surf) continue;
+    const long long o = ((long long)(nd == 3 ? ci[2] + ng : 0) * P + (ci[1] + ng)) * P + (ci[0] + ng);
+    double u[5];
+    bool touched = false;
+    for (int d = 0; d < nd; ++d) {
+      const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
+      for (int s = 0; s < 2; ++s) {
+        const int f = 2 * d + s;
+        if (it.fine[f][0] < 0) continue;
+        if (ci[d] != (s ? n - 1 : 0)) continue;
+        if (!touched) {
+          for (int v = 0; v < 5; ++v) u[v] = double(Uc[o + v * m.vstride]);
+          touched = true;
+        }
+        const int t1 = ci[a1], t2 = nd == 3 ? ci[a2] : 0;
+        const int h1 = 2 * t1 >= n, h2 = nd == 3 && 2 * t2 >= n;
+        const double *Ff = regs + (long long)it.fine[f][h1 + 2 * h2] * rstride;
+        const int ff = 2 * d + (s ? 0 : 1);
+        const int u1 = 2 * t1 - h1 * n, u2 = nd == 3 ? 2 * t2 - h2 * n : 0;
+        for (int v = 0; v < 5; ++v) {
+          const double *fv = Ff + (long long)(ff * 5 + v) * nfc;
+          double fbar;
+          if (nd == 3) {
+            fbar = ((fv[u2 * n + u1] + fv[u2 * n + u1 + 1]) +
+                    (fv[(u2 + 1) * n + u1] + fv[(u2 + 1) * n + u1 + 1])) * 0.25;
+          } else {
+            fbar = (fv[u1] + fv[u1 + 1]) * 0.5;
+          }
+          const double fc = Fc[(long long)(f * 5 + v) * nfc + t2 * n + t1];
+          const double corr = dt * (fc - fbar) * m.idx[lev][d];
+          u[v] = s ? u[v] + corr : u[v] - corr;
+        }
+      }
+    }
+    if (touched) {
+      S us[5];
+      for (int v = 0; v < 5; ++v) { us[v] = S(u[v]); Uc[o + v * m.vstride] = us[v]; }
+      if (!(u[0] > 0.0) || !(2.0 * u[4] * u[0] > u[1] * u[1] + u[2] * u[2] + u[3] * u[3]))
+        atomicOr(status, 1);
+      if (smax) {
+        // CFL signal speed of the corrected cell, in the state's precision
+        const S ir = S(1) / us[0];
+        const S pr = S(m.gamma - 1.0) *
+                     (us[4] - S(0.5) * (us[1] * us[1] + us[2] * us[2] + us[3] * us[3]) * ir);
+        const S cs = sqrt(S(m.gamma) * pr * ir);
+        S sg = S(0);
+        for (int d = 0; d < nd; ++d) {
+          const S sd = (fabs(us[1 + d] * ir) + cs) * S(m.idx[lev][d]);
+          sg = form == 0 ? sg + sd : fmax(sg, sd);
+        }
+        atomicMax(smax, (unsigned long long)__double_as_longlong(double(sg)));
+      }
+    }
+  }
+}
+
+}  // namespace ops
+}  // namespace fx

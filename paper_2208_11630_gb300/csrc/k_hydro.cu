@@ -222,12 +222,17 @@ __device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int 
   }
 }
 
+// One T x T column tile of leaf block b, marched along z.  Called by the
+// per-block-set kernel (one CTA per tile) and by the batched persistent
+// kernel (each CTA loops over tiles of many block sets).
 template <int NDIM, int T, typename S, typename R>
-__global__ void __launch_bounds__(T *T, (T == 16 ? (sizeof(R) == 4 ? 4 : 2) : 6))
-k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__restrict__ leaves,
-        int tiles, const double *__restrict__ dtp, double *__restrict__ regs,
-        int *__restrict__ status, unsigned long long *__restrict__ smax_out,
-        const unsigned char *__restrict__ rmask, int cfl_form) {
+__device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict__ U,
+                                           S *__restrict__ Unew, int b, int tile, int tiles,
+                                           double dt, double *__restrict__ regs,
+                                           int *__restrict__ status,
+                                           unsigned long long *__restrict__ smax_out,
+                                           const unsigned char *__restrict__ rmask,
+                                           int cfl_form) {
   using SM = Smem<T>;
   constexpr int NT = T * T;
   constexpr int NPL = NDIM == 3 ? 3 : 1;
@@ -239,14 +244,11 @@ k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__r
   R *fyp = fym + SM::FY;
 
   const int tid = threadIdx.x;
-  const int tpb = tiles * tiles;
-  const int b = leaves[blockIdx.x / tpb];
-  const int tile = blockIdx.x % tpb;
+  __syncthreads();   // the previous tile of this CTA is done with shared memory
   const int x0 = (tile % tiles) * T, y0 = (tile / tiles) * T;
   const int n = m.nxb, ng = m.ng, P = m.P;
   const int lev = m.level[b];
   const long long vs = m.vstride;
-  const double dt = *dtp;
   const R g = R(m.gamma), gm1 = R(m.gamma - 1.0), igm1 = R(1.0 / (m.gamma - 1.0));
   const R hdt = R(0.5 * dt);
   R idx2[3];
@@ -534,6 +536,41 @@ k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__r
 }
 
 template <int NDIM, int T, typename S, typename R>
+__global__ void __launch_bounds__(T *T, (T == 16 ? (sizeof(R) == 4 ? 4 : 2) : 6))
+k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__restrict__ leaves,
+        int tiles, const double *__restrict__ dtp, double *__restrict__ regs,
+        int *__restrict__ status, unsigned long long *__restrict__ smax_out,
+        const unsigned char *__restrict__ rmask, int cfl_form) {
+  const int tpb = tiles * tiles;
+  hydro_tile<NDIM, T, S, R>(m, U, Unew, leaves[blockIdx.x / tpb], blockIdx.x % tpb, tiles, *dtp,
+                            regs, status, smax_out, rmask, cfl_form);
+}
+
+// Persistent batched kernel: the CTAs pull (request, leaf, tile) items from a
+// shared counter until the list is exhausted; items of finished requests are
+// skipped.  Each request brings its own mesh, buffers, dt and scratch.
+template <int NDIM, int T, typename S, typename R>
+__global__ void __launch_bounds__(T *T, (T == 16 ? (sizeof(R) == 4 ? 4 : 2) : 6))
+k_hydro_batch(const BatchReq *__restrict__ reqs, const int4 *__restrict__ items, int nitems,
+              unsigned int *__restrict__ counter) {
+  __shared__ int item_s;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int it = item_s;
+    __syncthreads();
+    if (it >= nitems) return;
+    const int4 w = items[it];            // (request, block, tile, tiles per axis)
+    const BatchReq &r = reqs[w.x];
+    if (r.steps_left <= 0) continue;
+    const int c = r.cur;
+    hydro_tile<NDIM, T, S, R>(r.m, static_cast<const S *>(r.U[c]), static_cast<S *>(r.U[1 - c]),
+                              w.y, w.z, w.w, *r.dt, r.regs, r.status, r.scratch + 2, r.rmask,
+                              r.form);
+  }
+}
+
+template <int NDIM, int T, typename S, typename R>
 cudaError_t launch_t(const DevMesh &m, const void *U, void *Unew, const int *leaves, int n,
                      const double *dt, double *regs, int *status, unsigned long long *smax,
                      const unsigned char *rmask, int form, cudaStream_t s) {
@@ -553,7 +590,68 @@ cudaError_t launch_t(const DevMesh &m, const void *U, void *Unew, const int *lea
   return cudaGetLastError();
 }
 
+template <int NDIM, int T, typename S, typename R>
+cudaError_t launch_batch_t(const BatchReq *reqs, const int4 *items, int nitems,
+                           unsigned int *counter, int ctas_per_sm, int nsm, cudaStream_t s) {
+  const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(R);
+  auto kern = k_hydro_batch<NDIM, T, S, R>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  int fit = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kern, T * T, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = ctas_per_sm > 0 ? (ctas_per_sm < fit ? ctas_per_sm : fit) : fit;
+  if (per_sm < 1) per_sm = 1;
+  int grid = per_sm * nsm;
+  if (grid > nitems) grid = nitems;
+  if (grid < 1) return cudaSuccess;
+  kern<<<grid, T * T, smem, s>>>(reqs, items, nitems, counter);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int NDIM, int T, typename S, typename R>
+cudaError_t fit_t(int *fit) {
+  const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(R);
+  auto kern = k_hydro_batch<NDIM, T, S, R>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(fit, kern, T * T, smem);
+}
+
 }  // namespace
+
+cudaError_t hydro_batch_fit(int ndim, int tile, int prec, int *fit) {
+  if (prec == 0) {
+    if (ndim == 3) return tile == 16 ? fit_t<3, 16, double, double>(fit) : fit_t<3, 8, double, double>(fit);
+    return tile == 16 ? fit_t<2, 16, double, double>(fit) : fit_t<2, 8, double, double>(fit);
+  }
+  if (ndim == 3) return tile == 16 ? fit_t<3, 16, float, float>(fit) : fit_t<3, 8, float, float>(fit);
+  return tile == 16 ? fit_t<2, 16, float, float>(fit) : fit_t<2, 8, float, float>(fit);
+}
+
+cudaError_t launch_hydro_batch(int ndim, int tile, int prec, const BatchReq *reqs,
+                               const int4 *items, int nitems, unsigned int *counter,
+                               int ctas_per_sm, int nsm, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  if (prec == 0) {
+    if (ndim == 3)
+      return tile == 16 ? launch_batch_t<3, 16, double, double>(reqs, items, nitems, counter, ctas_per_sm, nsm, s)
+                        : launch_batch_t<3, 8, double, double>(reqs, items, nitems, counter, ctas_per_sm, nsm, s);
+    return tile == 16 ? launch_batch_t<2, 16, double, double>(reqs, items, nitems, counter, ctas_per_sm, nsm, s)
+                      : launch_batch_t<2, 8, double, double>(reqs, items, nitems, counter, ctas_per_sm, nsm, s);
+  }
+  if (ndim == 3)
+    return tile == 16 ? launch_batch_t<3, 16, float, float>(reqs, items, nitems, counter, ctas_per_sm, nsm, s)
+                      : launch_batch_t<3, 8, float, float>(reqs, items, nitems, counter, ctas_per_sm, nsm, s);
+  return tile == 16 ? launch_batch_t<2, 16, float, float>(reqs, items, nitems, counter, ctas_per_sm, nsm, s)
+                    : launch_batch_t<2, 8, float, float>(reqs, items, nitems, counter, ctas_per_sm, nsm, s);
+}
 
 size_t hydro_smem_bytes(int ndim, int tile, int prec) {
   const size_t el = prec == 0 ? sizeof(double) : sizeof(float);

@@ -73,6 +73,14 @@ def load(build: bool = True):
             "fx_run_host": (c_int, [vp, vp, vp, vp, c_int, c_double, dp, vp]),
             "fx_block_fluxes": (vp, [vp, c_int]),
             "fx_kernel_launches": (ctypes.c_longlong, []),
+            "fx_batch_create": (c_int, [vp, c_int, ctypes.POINTER(vp)]),
+            "fx_batch_destroy": (c_int, [vp]),
+            "fx_batch_add": (c_int, [vp, vp, c_double, c_int, vp, ip]),
+            "fx_batch_run": (c_int, [vp, c_int, vp]),
+            "fx_batch_poll": (c_int, [vp, ip, vp]),
+            "fx_batch_remove": (c_int, [vp, c_int, vp]),
+            "fx_batch_tune": (c_int, [vp, vp, ip]),
+            "fx_batch_choice": (c_int, [vp, c_int, c_int, ip, ip]),
             "fx_compute_dt_noalloc": (c_int, [vp, c_int, c_int, c_int, c_int, dp, c_double,
                                               c_double, c_int, vp, vp, ctypes.c_char_p,
                                               ctypes.c_size_t]),
@@ -212,6 +220,66 @@ FX_NOALLOC_MAX_BLOCKS = 32768
 
 def fx_block_fluxes(bs, b: int) -> int:
     return load().fx_block_fluxes(bs, int(b)) or 0
+
+
+# ---------------------------------------------------------------- batches
+
+class Batch:
+    """Many block sets advanced together by one replayed CUDA graph per step
+    (thin wrapper over the fx_batch_* calls)."""
+
+    def __init__(self, ctx, max_requests: int):
+        self.ctx = ctx
+        self.max_requests = int(max_requests)
+        h = ctypes.c_void_p()
+        _check(ctx, load().fx_batch_create(ctx, self.max_requests, ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().fx_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, blockset, cfl: float, nsteps: int, stream=None) -> int:
+        slot = ctypes.c_int(-1)
+        _check(self.ctx, load().fx_batch_add(self.h, blockset.bs, float(cfl), int(nsteps),
+                                             _stream_ptr(stream), ctypes.byref(slot)))
+        return slot.value
+
+    def run(self, nsteps: int = 1, stream=None):
+        _check(self.ctx, load().fx_batch_run(self.h, int(nsteps), _stream_ptr(stream)))
+
+    def poll(self, stream=None) -> np.ndarray:
+        out = np.zeros(self.max_requests, dtype=np.int32)
+        _check(self.ctx, load().fx_batch_poll(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                              _stream_ptr(stream)))
+        return out
+
+    def remove(self, slot: int, stream=None):
+        _check(self.ctx, load().fx_batch_remove(self.h, int(slot), _stream_ptr(stream)))
+
+    def tune(self, stream=None):
+        rep = np.zeros(193, dtype=np.int32)
+        _check(self.ctx, load().fx_batch_tune(self.h, _stream_ptr(stream),
+                                              rep.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        out = []
+        for i in range(64):
+            if rep[3 * i] == 0:
+                break
+            out.append((int(rep[3 * i]), int(rep[3 * i + 1]), int(rep[3 * i + 2])))
+        return out
+
+    def choice(self, ndim: int, precision: int):
+        t, c = ctypes.c_int(), ctypes.c_int()
+        _check(self.ctx, load().fx_batch_choice(self.h, int(ndim), int(precision), ctypes.byref(t),
+                                                ctypes.byref(c)))
+        return t.value, c.value
 
 
 # ---------------------------------------------------------------- convenience

@@ -1,0 +1,138 @@
+"""Batched, graph-replayed stepping of many block sets (fx_batch_*).
+
+Checks: a batch of mixed requests (2D/3D, uniform/AMR, FP64/FP32-bulk,
+nxb 8/16/32, different block counts and step counts) gives, per request, the
+same state as stepping that block set alone (and, for FP64, the oracle within
+1e-12); a request's result is bit-identical alone and in the mix; finished
+requests stop; tuning leaves every state unchanged.
+"""
+import numpy as np
+import pytest
+
+from paper_2208_11630_gb300 import inputs
+from tests.helpers import max_rel_err
+from tests.test_oracle_scheme import mesh_2level
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2208_11630_gb300 import fx as _fx
+    _fx.load()
+    return _fx
+
+
+def _cases():
+    m_kh = inputs.uniform_mesh(3, (3, 2, 2), 16, 4, inputs.PERIODIC)
+    m_sod = inputs.uniform_mesh(2, (8, 4), 16, 4, inputs.OUTFLOW)
+    m_amr = mesh_2level(4, 8, 4, inputs.PERIODIC)
+    m_sed = mesh_2level(4, 16, 4)
+    m_32 = inputs.uniform_mesh(3, (2, 1, 1), 32, 4, inputs.PERIODIC)
+    m_8 = inputs.uniform_mesh(3, (3, 3, 2), 8, 4, inputs.OUTFLOW)
+    return [
+        ("kh_f64", m_kh, inputs.kh_state(m_kh), 0, 7),
+        ("sod_f64", m_sod, inputs.sod_state(m_sod), 0, 12),
+        ("amr_f64", m_amr, inputs.random_smooth_state(m_amr, 3), 0, 5),
+        ("sedov_f32", m_sed, inputs.sedov_state(m_sed), 1, 6),
+        ("nxb32_f32", m_32, inputs.random_smooth_state(m_32, 4), 1, 9),
+        ("nxb8_f64", m_8, inputs.random_blocky_state(m_8, 5), 0, 4),
+        ("kh_f32", m_kh, inputs.kh_state(m_kh), 1, 8),
+    ]
+
+
+def _blockset(fx, mesh, W, prec, ctx=None):
+    bs = fx.BlockSet(mesh, 1.4, precision=prec, ctx=ctx)
+    bs.set_primitive(W)
+    return bs
+
+
+def test_batch_matches_single_and_oracle(orc, fx):
+    cases = _cases()
+    ctx = fx.fx_init(1.4, 16, 4)
+    batch = fx.Batch(ctx, 16)
+    sets, slots = [], []
+    for name, mesh, W, prec, k in cases:
+        bs = _blockset(fx, mesh, W, prec)
+        slots.append(batch.add(bs, 0.8, k))
+        sets.append(bs)
+    kmax = max(c[4] for c in cases)
+    batch.run(kmax + 2)                  # extra steps: finished requests must stop
+    assert np.all(batch.poll()[:len(cases)] == 0)
+    for (name, mesh, W, prec, k), bs, slot in zip(cases, sets, slots):
+        batch.remove(slot)
+        assert bs.status() == 0, name
+        ref = _blockset(fx, mesh, W, prec)
+        ref.run(k, 0.8)
+        got, want = bs.state(), ref.state()
+        assert max_rel_err(mesh, got, want) <= 1e-14, name
+        if prec == 0:
+            om = orc.OracleMesh(mesh)
+            Uo, _, _ = om.run(om.prim_to_cons(W), nsteps=k)
+            assert max_rel_err(mesh, got, Uo) <= 1e-12, name
+        # a released block set continues on its own (fused dt carried over)
+        bs.step(0.8)
+        ref.step(0.8)
+        assert max_rel_err(mesh, bs.state(), ref.state()) <= 1e-14, name
+    batch.close()
+    fx.fx_finalize(ctx)
+
+
+def test_alone_equals_in_the_mix_bitwise(fx):
+    cases = _cases()
+    name, mesh, W, prec, k = cases[0]
+    ctx = fx.fx_init(1.4, 16, 4)
+    alone = fx.Batch(ctx, 4)
+    a = _blockset(fx, mesh, W, prec)
+    sa = alone.add(a, 0.8, k)
+    alone.run(k)
+    alone.remove(sa)
+    mix = fx.Batch(ctx, 16)
+    others = []
+    for c in cases[1:]:
+        bs = _blockset(fx, c[1], c[2], c[3])
+        mix.add(bs, 0.8, c[4])
+        others.append(bs)
+    b = _blockset(fx, mesh, W, prec)
+    sb = mix.add(b, 0.8, k)
+    mix.run(k)
+    mix.remove(sb)
+    assert np.array_equal(a.state(), b.state())
+    alone.close()
+    mix.close()
+    fx.fx_finalize(ctx)
+
+
+def test_tuning_leaves_states_unchanged_and_picks_a_choice(fx):
+    ctx = fx.fx_init(1.4, 16, 4)
+    batch = fx.Batch(ctx, 8)
+    sets, slots = [], []
+    cases = _cases()[:4]
+    for name, mesh, W, prec, k in cases:
+        bs = _blockset(fx, mesh, W, prec)
+        slots.append(batch.add(bs, 0.8, 3))
+        sets.append(bs)
+    cur = [bs.current.clone() for bs in sets]
+    report = batch.tune()
+    assert report, "tuner timed no candidate"
+    for (t, c, us) in report:
+        assert t in (8, 16) and c >= 1 and us > 0
+    for bs, c0 in zip(sets, cur):
+        # the current buffer is untouched; the other one may hold a copy of it
+        assert torch.equal(bs.current, c0)
+    tile, ctas = batch.choice(3, 0)
+    assert tile in (8, 16)
+    batch.run(3)
+    assert np.all(batch.poll()[:4] == 0)
+    # whatever tile the tuner picked, results equal the single-set path
+    for (name, mesh, W, prec, k), bs, slot in zip(cases, sets, slots):
+        batch.remove(slot)
+        ref = _blockset(fx, mesh, W, prec)
+        ref.run(3, 0.8)
+        assert max_rel_err(mesh, bs.state(), ref.state()) <= 1e-14, name
+    batch.close()
+    fx.fx_finalize(ctx)
