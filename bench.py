@@ -337,6 +337,43 @@ def run_ours(args):
     return 0
 
 
+def run_serve(args):
+    """Serving stream: capacity with every request present at t = 0, then
+    Poisson streams at 0.5, 0.8 and 0.95 of that capacity (continuous
+    batching), and the plain per-request FP64 path on the 0.8 stream."""
+    import torch
+    from paper_2208_11630_gb300 import fx, serve
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(0)
+    fx.load()
+    inf = float("inf")
+    reqs = serve.make_stream(args.serve_requests, inf, seed=11630, blocks=(8, args.serve_max_blocks))
+    probs = serve.prepare(reqs)
+    budget = args.serve_budget_gb * 1e9
+    serve.serve(serve.with_arrivals(reqs[:8], inf), probs, budget, realtime=False)   # warm-up
+    sat = serve.serve(serve.with_arrivals(reqs, inf), probs, budget, realtime=False)
+    cap = sat["requests_per_s"]
+    runs = {"saturated": sat}
+    for frac in (0.5, 0.8, 0.95):
+        runs[f"rate_{frac}"] = serve.serve(serve.with_arrivals(reqs, frac * cap), probs, budget)
+    base = serve.serve_per_request(serve.with_arrivals(reqs, 0.8 * cap), probs,
+                                   precision=fx.FX_F64)
+    line = {"metric": "served zone-updates/s", "value": runs["rate_0.8"]["zone_updates_per_s"],
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "dtype": "mixed f64/f32bulk",
+            "config": {"workload": "serving stream", "requests": len(reqs),
+                       "blocks": f"log-uniform 8..{args.serve_max_blocks}", "nxb": "8/16/32",
+                       "k": "1..20", "precision": "50% FP64, 50% FP32-bulk",
+                       "setups": "sod/kh/sedov/advection", "budget_gb": args.serve_budget_gb,
+                       "arrivals": "Poisson, seed 11630, rate = fraction of saturated capacity"},
+            "capacity_requests_per_s": cap, "runs": runs,
+            "baseline_per_request_fp64_at_0.8": base}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -349,11 +386,17 @@ def main(argv=None):
                     help="blocks per axis (default: the full workload, 16 for kh3d)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="run the serving stream instead")
+    ap.add_argument("--serve-requests", type=int, default=160)
+    ap.add_argument("--serve-max-blocks", type=int, default=512)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serve(args)
     return run_ours(args)
 
 
