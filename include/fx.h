@@ -235,11 +235,13 @@ FX_API int fx_batch_poll(fx_batch *b, int *steps_left, void *stream);
 FX_API int fx_batch_remove(fx_batch *b, int slot, void *stream);
 /* fx_batch_tune: autotune the update launch of each (dimension, precision)
  * group whose blocks allow 16x16 tiles: the tile edge (16 or 8) and the CTAs
- * per SM of the persistent kernel, by timing each candidate on the batch's
- * own blocks with dt = 0 (which leaves every state unchanged).  Choices are
- * cached per (dimension, precision, SM count, size class).  `report` (may be
- * NULL; room for 193 ints) receives (tile, ctas, microseconds) triples, 0
- * terminated.  Synchronises. */
+ * per SM of the persistent kernel, by timing each candidate on a sample of
+ * the batch's own work items with dt = 0 (after a coarse-fine guard fill;
+ * neither changes any state) and scaling to the whole group.  Choices are
+ * cached per (dimension, precision, SM count, set of block edges).  `report`
+ * (may be NULL; room for 193 ints) receives (tile, ctas, estimated
+ * microseconds per update of the group) triples, 0 terminated.
+ * Synchronises. */
 FX_API int fx_batch_tune(fx_batch *b, void *stream, int *report);
 /* fx_batch_choice: the launch choice in use for a (ndim, precision) group. */
 FX_API int fx_batch_choice(const fx_batch *b, int ndim, int precision, int *tile,

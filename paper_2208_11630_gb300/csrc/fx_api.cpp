@@ -643,7 +643,8 @@ struct Choice {
   int ctas = 0;
 };
 
-std::map<std::tuple<int, int, int, int>, Choice> g_tune_cache;  // (ndim, prec, nsm, log2 items)
+// (ndim, prec, SM count, mask of the 16-capable block edges in the group)
+std::map<std::tuple<int, int, int, int>, Choice> g_tune_cache;
 
 }  // namespace
 
@@ -767,6 +768,27 @@ cudaError_t record_step(fx_batch *b, cudaStream_t s) {
                                  b->rst[p][l].n, s));
   FXB(fx::launch_batch_end(b->d_req, b->max_req, s));
 #undef FXB
+  return cudaSuccess;
+}
+
+// The coarse-fine fill of the current buffers (restriction, copies feeding
+// prolongation, prolongation): what an update needs to read valid guards.
+cudaError_t record_fill(fx_batch *b, cudaStream_t s) {
+  cudaError_t e;
+  for (int l = b->lmax - 1; l >= 0; --l)
+    for (int p = 0; p < 2; ++p)
+      if ((e = fx::launch_batch_phase(fx::BATCH_RESTRICT_PRE, p, b->d_req, b->d_items + b->rst[p][l].off,
+                                      b->rst[p][l].n, s)) != cudaSuccess)
+        return e;
+  for (int p = 0; p < 2; ++p)
+    if ((e = fx::launch_batch_phase(fx::BATCH_COPY, p, b->d_req, b->d_items + b->cpy[p].off,
+                                    b->cpy[p].n, s)) != cudaSuccess)
+      return e;
+  for (int l = 1; l <= b->lmax; ++l)
+    for (int p = 0; p < 2; ++p)
+      if ((e = fx::launch_batch_phase(fx::BATCH_PROLONG, p, b->d_req, b->d_items + b->pro[p][l].off,
+                                      b->pro[p][l].n, s)) != cudaSuccess)
+        return e;
   return cudaSuccess;
 }
 
@@ -946,18 +968,19 @@ int fx_batch_tune(fx_batch *b, void *stream, int *report) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  // valid guards for every request before any timed update
+  if (build_lists(b, b->choice)) return fail(b->ctx, FX_ERR_OOM, "tuning work lists");
+  e = record_fill(b, st);
+  if (e != cudaSuccess) return cuda_fail(b->ctx, e, "tuning guard fill");
   int nrep = 0;
   for (int nd = 2; nd <= 3; ++nd)
     for (int pr = 0; pr < 2; ++pr) {
       // is there a group of 16-capable block sets of this kind?
-      size_t nitems = 0;
+      int mask = 0;
       for (fx_blocks *bs : b->slot)
-        if (bs && bs->ndim == nd && bs->prec == pr && bs->nxb % 16 == 0)
-          nitems += (size_t)bs->nleaves * (bs->nxb / 16) * (bs->nxb / 16);
-      if (!nitems) continue;
-      int lg = 0;
-      while ((size_t(1) << (lg + 1)) <= nitems) ++lg;
-      auto key = std::make_tuple(nd, pr, b->nsm, lg);
+        if (bs && bs->ndim == nd && bs->prec == pr && bs->nxb % 16 == 0) mask |= 1 << (bs->nxb / 16);
+      if (!mask) continue;
+      auto key = std::make_tuple(nd, pr, b->nsm, mask);
       auto hit = g_tune_cache.find(key);
       if (hit != g_tune_cache.end()) {
         b->choice[nd - 2][pr] = hit->second;
@@ -985,11 +1008,16 @@ int fx_batch_tune(fx_batch *b, void *stream, int *report) {
               gi = (int)g;
             }
           if (!G) continue;
+          // time on a bounded sample: a few waves of the persistent grid, in
+          // work per item (the 8x8 variant has four times the items)
+          const int per_wave = ctas * b->nsm;
+          int nsample = std::min(G->r.n, 6 * per_wave * (tile == 8 ? 4 : 1));
+          nsample = std::max(nsample, std::min(G->r.n, per_wave));
           float tot = 0.f;
-          for (int rep = 0; rep < 4; ++rep) {
+          for (int rep = 0; rep < 3; ++rep) {
             cudaMemsetAsync(b->d_ctr + gi, 0, sizeof(unsigned int), st);
             cudaEventRecord(e0, st);
-            fx::launch_hydro_batch(nd, tile, pr, b->d_req, b->d_items + G->r.off, G->r.n,
+            fx::launch_hydro_batch(nd, tile, pr, b->d_req, b->d_items + G->r.off, nsample,
                                    b->d_ctr + gi, ctas, b->nsm, st);
             cudaEventRecord(e1, st);
             cudaEventSynchronize(e1);
@@ -997,13 +1025,15 @@ int fx_batch_tune(fx_batch *b, void *stream, int *report) {
             cudaEventElapsedTime(&ms, e0, e1);
             if (rep > 0) tot += ms;   // first launch warms up
           }
+          // normalise to the whole group: time per item times items
+          const float est = tot / 2.f * (float)G->r.n / (float)nsample;
           if (report && nrep < 64) {
             report[3 * nrep] = tile;
             report[3 * nrep + 1] = ctas;
-            report[3 * nrep + 2] = (int)(tot * 1000.f / 3.f);   // microseconds
+            report[3 * nrep + 2] = std::max(1, (int)(est * 1000.f));   // microseconds
             ++nrep;
           }
-          if (tot < best) { best = tot; bestc.tile = tile; bestc.ctas = ctas; }
+          if (est < best) { best = est; bestc.tile = tile; bestc.ctas = ctas; }
         }
       }
       b->choice[nd - 2][pr] = bestc;
