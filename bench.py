@@ -155,6 +155,71 @@ def oracle_sample(workload: str, target_s: float = 12.0, max_steps: int = 50):
             "kind": "oracle", "sample": f"{desc}; {steps} full steps in {dt:.1f} s"}
 
 
+def measure_variants(args, fx, inputs, mesh, dev, cfl, zones, bs, ws, hbm_peak):
+    """The same workload (i) as one request of a batch -- coarse-fine fill,
+    persistent update and flux correction replayed as one CUDA graph per step,
+    launch choice autotuned -- and (ii) in the other precision, timed the same
+    way (CUDA events on the launching stream, warm-up first)."""
+    import torch
+    out = {}
+    stream = torch.cuda.Stream(device=dev)
+    sptr = stream.cuda_stream
+    # (i) batched + graph
+    ctx = fx.fx_init(1.4, mesh.nxb, mesh.ng)
+    batch = fx.Batch(ctx, 1)
+    slot = batch.add(bs, cfl, args.warmup + args.steps, stream=sptr)
+    tuning = batch.tune(stream=sptr)
+    batch.run(args.warmup, stream=sptr)
+    stream.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    batch.run(args.steps, stream=sptr)
+    b.record(stream)
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3
+    batch.remove(slot, stream=sptr)
+    ok = bs.status() == 0
+    tile, ctas = batch.choice(mesh.ndim, bs.precision)
+    batch.close()
+    fx.fx_finalize(ctx)
+    z, t = aggregate(zones * args.steps, sec, dev)
+    out["batched_graph"] = {"value": z / t, "unit": UNIT, "ms_per_step": 1e3 * t / args.steps,
+                            "tile": tile, "ctas_per_sm": ctas, "tuning_us": tuning, "ok": ok}
+    # (ii) the other precision, plain per-call path
+    other = "f32bulk" if args.precision == "f64" else "f64"
+    prec = fx.FX_F32BULK if other == "f32bulk" else fx.FX_F64
+    mesh2, W, gamma, _ = inputs.workload(args.workload, scale=args.scale)
+    bs2 = fx.BlockSet(mesh2, gamma, precision=prec, device=dev)
+    bs2.set_primitive(W)
+    del W
+    dtp = bs2.dt.data_ptr()
+    for _ in range(args.warmup):
+        fx.fx_step(bs2.ctx, bs2.bs, cfl, dtp, sptr)
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    a.record(stream)
+    for k in range(args.steps):
+        fx.fx_compute_dt(bs2.ctx, bs2.bs, cfl, dtp, sptr)
+        fx.fx_guardcell_fill_amr(bs2.ctx, bs2.bs, sptr)
+        ev[k][0].record(stream)
+        fx.fx_hydro_advance(bs2.ctx, bs2.bs, dtp, sptr)
+        ev[k][1].record(stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3
+    hyd = float(np.mean([x.elapsed_time(y) for x, y in ev])) / 1e3
+    z, t = aggregate(zones * args.steps, sec, dev)
+    bpz = HBM_BYTES_PER_ZONE[other]
+    out[other] = {"value": z / t, "unit": UNIT, "ms_per_step": 1e3 * t / args.steps,
+                  "dtype": "f32" if other == "f32bulk" else "f64", "hydro_ms": hyd * 1e3,
+                  "hydro_hbm_frac": bpz * zones / hyd / (hbm_peak * 1e9),
+                  "step_hbm_frac": bpz * (z / t) / ws / (hbm_peak * 1e9),
+                  "ok": bs2.status() == 0}
+    bs2.close()
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -324,6 +389,9 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if not args.no_variants:
+        line["variants"] = measure_variants(args, fx, inputs, mesh, dev, cfl, zones_per_step, bs,
+                                            ws, hbm_peak)
     if rank == 0 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = oracle_sample(args.workload)
@@ -388,6 +456,8 @@ def main(argv=None):
                     help="blocks per axis (default: the full workload, 16 for kh3d)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the batched-graph and other-precision measurements")
     ap.add_argument("--serve", action="store_true", help="run the serving stream instead")
     ap.add_argument("--serve-requests", type=int, default=160)
     ap.add_argument("--serve-max-blocks", type=int, default=512)
