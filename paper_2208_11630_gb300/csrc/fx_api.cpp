@@ -468,11 +468,12 @@ int fx_guardcell_fill(fx_ctx *ctx, fx_blocks *bs, void *stream) {
   for (int l = bs->lmax; l >= 0; --l)
     FX_CUDA(fx::launch_restrict(bs->dm, U, bs->prec, bs->d_lists + bs->par_off[l], bs->par_cnt[l], s),
             "restrict launch");
-  FX_CUDA(fx::launch_guard_copy(bs->dm, U, bs->prec, bs->d_lists + bs->leaves_off, bs->nleaves, s),
+  FX_CUDA(fx::launch_guard_copy(bs->dm, U, bs->prec, bs->d_lists + bs->leaves_off, bs->nleaves,
+                                bs->ng, s),
           "guard copy launch");
   for (int l = 1; l <= bs->lmax; ++l)
     FX_CUDA(fx::launch_guard_prolong(bs->dm, U, bs->prec, bs->d_lists + bs->pro_off[l],
-                                     bs->pro_cnt[l], s),
+                                     bs->pro_cnt[l], bs->ng, 0, s),
             "guard prolong launch");
   return FX_OK;
 }
@@ -534,11 +535,12 @@ static int fill_for_fused_advance(fx_ctx *ctx, fx_blocks *bs, cudaStream_t s) {
   for (int l = bs->lmax; l >= 0; --l)
     FX_CUDA(fx::launch_restrict(bs->dm, U, bs->prec, bs->d_lists + bs->par_off[l], bs->par_cnt[l], s),
             "restrict launch");
-  FX_CUDA(fx::launch_guard_copy(bs->dm, U, bs->prec, bs->d_lists + bs->src_off, bs->nsrc, s),
+  FX_CUDA(fx::launch_guard_copy(bs->dm, U, bs->prec, bs->d_lists + bs->src_off, bs->nsrc,
+                                fx::kHydroGuardDepth, s),
           "guard copy launch");
   for (int l = 1; l <= bs->lmax; ++l)
     FX_CUDA(fx::launch_guard_prolong(bs->dm, U, bs->prec, bs->d_lists + bs->pro_off[l],
-                                     bs->pro_cnt[l], s),
+                                     bs->pro_cnt[l], fx::kHydroGuardDepth, 1, s),
             "guard prolong launch");
   (void)ctx;
   return FX_OK;

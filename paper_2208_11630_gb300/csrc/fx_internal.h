@@ -68,10 +68,15 @@ cudaError_t launch_prim_to_cons(const DevMesh &m, const double *W, void *U, int 
                                 cudaStream_t s);
 cudaError_t launch_restrict(const DevMesh &m, void *U, int prec, const int *parents, int n,
                             cudaStream_t s);
+// Guard fills touch only guard cells within `depth` (Chebyshev distance) of
+// the interior; prolongation of FP32 state computes in FP32 when
+// state_precision_math is set (else FP64).
 cudaError_t launch_guard_copy(const DevMesh &m, void *U, int prec, const int *leaves, int n,
-                              cudaStream_t s);
+                              int depth, cudaStream_t s);
 cudaError_t launch_guard_prolong(const DevMesh &m, void *U, int prec, const int *leaves, int n,
-                                 cudaStream_t s);
+                                 int depth, int state_precision_math, cudaStream_t s);
+// Guard depth the fused update reads (radius-2 stencil).
+constexpr int kHydroGuardDepth = 2;
 // smax (may be null): receives atomicMax of the bit patterns of the new
 // state's CFL signal speeds (form 0 = sum over directions, 1 = max); cells on
 // the faces flagged in rmask[block] (bit 2d+s) are left to the reflux kernel.

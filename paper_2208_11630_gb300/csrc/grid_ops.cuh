@@ -72,22 +72,30 @@ __device__ __forceinline__ void restrict_cells(const DevMesh &m, S *__restrict__
   }
 }
 
-// Leaf b, padded z-plane k, whole CTA: every guard cell whose slot is a
-// same-level copy reads the source block's interior at the boundary-mapped
-// global position.
+// Chebyshev distance of padded index i outside [lo, hi) (0 inside).
+__device__ __forceinline__ int outside(int i, int lo, int hi) {
+  return i < lo ? lo - i : (i >= hi ? i - hi + 1 : 0);
+}
+
+// Leaf b, padded z-plane k, whole CTA: every guard cell within `depth` of
+// the interior (Chebyshev distance) whose slot is a same-level copy reads the
+// source block's interior at the boundary-mapped global position.
 template <typename S>
 __device__ __forceinline__ void guard_copy_plane(const DevMesh &m, S *__restrict__ U, int b,
-                                                 int k) {
+                                                 int k, int depth) {
   __shared__ int2 sl[27];
   __syncthreads();
   if (threadIdx.x < 27) sl[threadIdx.x] = m.slots[b * 27 + threadIdx.x];
   __syncthreads();
   const int P = m.P, ng = m.ng, n = m.nxb, lev = m.level[b];
+  const int dz = m.ndim == 3 ? outside(k, ng, ng + n) : 0;
+  if (dz > depth) return;
   const int sz = m.ndim == 3 ? slot_of(k, ng, ng + n) : 1;
   const int ox = m.origin[3 * b], oy = m.origin[3 * b + 1], oz = m.origin[3 * b + 2];
   S *Ub = U + (long long)b * m.bstride;
   for (int c = threadIdx.x; c < P * P; c += blockDim.x) {
     const int i = c % P, j = c / P;
+    if (outside(i, ng, ng + n) > depth || outside(j, ng, ng + n) > depth) continue;
     const int sx = slot_of(i, ng, ng + n), sy = slot_of(j, ng, ng + n);
     if (sx == 1 && sy == 1 && sz == 1) continue;
     const int2 s = sl[sx + 3 * sy + 9 * sz];
@@ -108,24 +116,37 @@ __device__ __forceinline__ void guard_copy_plane(const DevMesh &m, S *__restrict
   }
 }
 
-// Leaf b, padded z-plane k, whole CTA: guard cells covered by a coarser leaf
-// get U_c + sum_d s_d MC(U_c - U_{c-e_d}, U_{c+e_d} - U_c), s_d = -1/4 for the
+// MC limiter in the compute precision C (same definition as mc_lim).
+template <typename C>
+__device__ __forceinline__ C mc_lim_c(C a, C b) {
+  if (a * b <= C(0)) return C(0);
+  C s = fmin(fmin(C(2) * fabs(a), C(2) * fabs(b)), C(0.5) * fabs(a + b));
+  return a > C(0) ? s : -s;
+}
+
+// Leaf b, padded z-plane k, whole CTA: guard cells within `depth` of the
+// interior that are covered by a coarser leaf get
+// U_c + sum_d s_d MC(U_c - U_{c-e_d}, U_{c+e_d} - U_c), s_d = -1/4 for the
 // lower fine half of the coarse cell along d and +1/4 for the upper half,
-// summed x, y, z.  The coarse leaf's own guards (depth 1) must be filled.
-template <typename S>
+// summed x, y, z, in precision C.  The coarse leaf's own guards (depth 1)
+// must be filled.
+template <typename S, typename C = double>
 __device__ __forceinline__ void guard_prolong_plane(const DevMesh &m, S *__restrict__ U, int b,
-                                                    int k) {
+                                                    int k, int depth) {
   __shared__ int2 sl[27];
   __syncthreads();
   if (threadIdx.x < 27) sl[threadIdx.x] = m.slots[b * 27 + threadIdx.x];
   __syncthreads();
   const int P = m.P, ng = m.ng, n = m.nxb, lev = m.level[b];
+  const int dz = m.ndim == 3 ? outside(k, ng, ng + n) : 0;
+  if (dz > depth) return;
   const int sz = m.ndim == 3 ? slot_of(k, ng, ng + n) : 1;
   const int ox = m.origin[3 * b], oy = m.origin[3 * b + 1], oz = m.origin[3 * b + 2];
   S *Ub = U + (long long)b * m.bstride;
   const long long sP = P, sPP = (long long)P * P;
   for (int c = threadIdx.x; c < P * P; c += blockDim.x) {
     const int i = c % P, j = c / P;
+    if (outside(i, ng, ng + n) > depth || outside(j, ng, ng + n) > depth) continue;
     const int sx = slot_of(i, ng, ng + n), sy = slot_of(j, ng, ng + n);
     if (sx == 1 && sy == 1 && sz == 1) continue;
     const int2 s = sl[sx + 3 * sy + 9 * sz];
@@ -138,20 +159,20 @@ __device__ __forceinline__ void guard_prolong_plane(const DevMesh &m, S *__restr
     const int cx = (g[0] >> 1) - m.origin[3 * cb] + ng;
     const int cy = (g[1] >> 1) - m.origin[3 * cb + 1] + ng;
     const int cz = m.ndim == 3 ? (g[2] >> 1) - m.origin[3 * cb + 2] + ng : 0;
-    const S *C = U + (long long)cb * m.bstride + (cz * sPP + cy * sP + cx);
+    const S *Cc = U + (long long)cb * m.bstride + (cz * sPP + cy * sP + cx);
     S *Ud = Ub + ((long long)k * P + j) * P + i;
     const long long step[3] = {1, sP, sPP};
     for (int v = 0; v < 5; ++v) {
-      const S *cv = C + v * m.vstride;
-      const double uc = ld(cv);
-      double val = uc;
+      const S *cv = Cc + v * m.vstride;
+      const C uc = C(*cv);
+      C val = uc;
       for (int d = 0; d < m.ndim; ++d) {
-        const double um = ld(cv - step[d]), up = ld(cv + step[d]);
-        const double sig = mc_lim(uc - um, up - uc);
-        const double off = (g[d] & 1) ? 0.25 : -0.25;
+        const C um = C(cv[-step[d]]), up = C(cv[step[d]]);
+        const C sig = mc_lim_c<C>(uc - um, up - uc);
+        const C off = (g[d] & 1) ? C(0.25) : C(-0.25);
         val = val + off * sig;
       }
-      st(Ud + v * m.vstride, val);
+      Ud[v * m.vstride] = S(val);
     }
   }
 }

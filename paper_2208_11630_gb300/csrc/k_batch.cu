@@ -56,7 +56,7 @@ __global__ void k_batch_copy(const BatchReq *__restrict__ reqs, const int4 *__re
   const int4 w = items[blockIdx.x];
   const BatchReq &q = reqs[w.x];
   if (q.steps_left <= 0) return;
-  ops::guard_copy_plane<S>(q.m, static_cast<S *>(q.U[q.cur]), w.y, w.z);
+  ops::guard_copy_plane<S>(q.m, static_cast<S *>(q.U[q.cur]), w.y, w.z, kHydroGuardDepth);
 }
 
 template <typename S>
@@ -64,7 +64,7 @@ __global__ void k_batch_prolong(const BatchReq *__restrict__ reqs, const int4 *_
   const int4 w = items[blockIdx.x];
   const BatchReq &q = reqs[w.x];
   if (q.steps_left <= 0) return;
-  ops::guard_prolong_plane<S>(q.m, static_cast<S *>(q.U[q.cur]), w.y, w.z);
+  ops::guard_prolong_plane<S, S>(q.m, static_cast<S *>(q.U[q.cur]), w.y, w.z, kHydroGuardDepth);
 }
 
 // items: (request, reflux item, chunk, chunks)

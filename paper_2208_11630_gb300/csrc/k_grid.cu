@@ -43,16 +43,19 @@ __global__ void k_restrict(DevMesh m, S *__restrict__ U, const int *__restrict__
   ops::restrict_cells<S>(m, U, parents[blockIdx.x], blockIdx.y);
 }
 
-// One CTA per (leaf, padded z-plane): same-level guard copies.
+// One CTA per (leaf, padded z-plane): same-level guard copies up to `depth`.
 template <typename S>
-__global__ void k_guard_copy(DevMesh m, S *__restrict__ U, const int *__restrict__ leaves) {
-  ops::guard_copy_plane<S>(m, U, leaves[blockIdx.x], blockIdx.y);
+__global__ void k_guard_copy(DevMesh m, S *__restrict__ U, const int *__restrict__ leaves,
+                             int depth) {
+  ops::guard_copy_plane<S>(m, U, leaves[blockIdx.x], blockIdx.y, depth);
 }
 
-// One CTA per (leaf, padded z-plane): prolonged guards.
-template <typename S>
-__global__ void k_guard_prolong(DevMesh m, S *__restrict__ U, const int *__restrict__ leaves) {
-  ops::guard_prolong_plane<S>(m, U, leaves[blockIdx.x], blockIdx.y);
+// One CTA per (leaf, padded z-plane): prolonged guards up to `depth`, in
+// precision C.
+template <typename S, typename C>
+__global__ void k_guard_prolong(DevMesh m, S *__restrict__ U, const int *__restrict__ leaves,
+                                int depth) {
+  ops::guard_prolong_plane<S, C>(m, U, leaves[blockIdx.x], blockIdx.y, depth);
 }
 
 template <typename S>
@@ -84,21 +87,25 @@ cudaError_t launch_restrict(const DevMesh &m, void *U, int prec, const int *pare
 }
 
 cudaError_t launch_guard_copy(const DevMesh &m, void *U, int prec, const int *leaves, int n,
-                              cudaStream_t s) {
+                              int depth, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   dim3 grid(n, m.PZ);
-  if (prec == 0) k_guard_copy<double><<<grid, 256, 0, s>>>(m, static_cast<double *>(U), leaves);
-  else k_guard_copy<float><<<grid, 256, 0, s>>>(m, static_cast<float *>(U), leaves);
+  if (prec == 0) k_guard_copy<double><<<grid, 256, 0, s>>>(m, static_cast<double *>(U), leaves, depth);
+  else k_guard_copy<float><<<grid, 256, 0, s>>>(m, static_cast<float *>(U), leaves, depth);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_guard_prolong(const DevMesh &m, void *U, int prec, const int *leaves, int n,
-                                 cudaStream_t s) {
+                                 int depth, int state_precision_math, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   dim3 grid(n, m.PZ);
-  if (prec == 0) k_guard_prolong<double><<<grid, 256, 0, s>>>(m, static_cast<double *>(U), leaves);
-  else k_guard_prolong<float><<<grid, 256, 0, s>>>(m, static_cast<float *>(U), leaves);
+  if (prec == 0)
+    k_guard_prolong<double, double><<<grid, 256, 0, s>>>(m, static_cast<double *>(U), leaves, depth);
+  else if (state_precision_math)
+    k_guard_prolong<float, float><<<grid, 256, 0, s>>>(m, static_cast<float *>(U), leaves, depth);
+  else
+    k_guard_prolong<float, double><<<grid, 256, 0, s>>>(m, static_cast<float *>(U), leaves, depth);
   count_launch();
   return cudaGetLastError();
 }
