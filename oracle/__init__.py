@@ -63,6 +63,8 @@ def lib():
                                            dp, ctypes.c_int, ip]
             L.or_conserved_totals.argtypes = [ctypes.c_void_p, dp, dp]
             L.or_restrict_parents.argtypes = [ctypes.c_void_p, dp]
+            L.or_hydro_advance_rk2.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_double,
+                                               ctypes.c_int, dp]
             L.or_mc.restype = ctypes.c_double
             L.or_mc.argtypes = [ctypes.c_double, ctypes.c_double]
             L.or_hllc.argtypes = [dp, dp, ctypes.c_int, ctypes.c_double, dp]
@@ -139,9 +141,10 @@ class OracleMesh:
         return float(dt[0])
 
     def hydro_advance(self, U: np.ndarray, dt: float, reflux: bool = True,
-                      want_bflux: bool = False, select=None):
+                      want_bflux: bool = False, select=None, integrator: int = 0):
         """Advance the leaves one step from ``U`` (guards filled).  Returns
-        ``(Unew, status, bflux)``; ``Unew`` starts as a copy of ``U``."""
+        ``(Unew, status, bflux)``; ``Unew`` starts as a copy of ``U``.
+        integrator 0: MUSCL-Hancock; 1: SSP-RK2 (no ``select``)."""
         m = self.mesh
         Unew = U.copy()
         bflux = None
@@ -150,6 +153,9 @@ class OracleMesh:
             nf = m.nxb ** (m.ndim - 1)
             bflux = np.zeros((m.nb, 2 * m.ndim, 5, nf))
             bptr = _dp(bflux)
+        if integrator == 1:
+            st = lib().or_hydro_advance_rk2(self._h, _dp(U), _dp(Unew), float(dt), int(reflux), bptr)
+            return Unew, st, bflux
         if select is not None:
             sel = np.ascontiguousarray(select, dtype=np.int32)
             st = lib().or_hydro_advance(self._h, _dp(U), _dp(Unew), float(dt), int(reflux), bptr,
@@ -168,7 +174,8 @@ class OracleMesh:
         return out
 
     def step(self, U: np.ndarray, cfl: float = 0.8, dt: float | None = None, form: int = 0,
-             reflux: bool = True, t_end: float | None = None, t: float = 0.0):
+             reflux: bool = True, t_end: float | None = None, t: float = 0.0,
+             integrator: int = 0):
         """One full step: dt, guard fill, advance.  Returns ``(Unew, dt)``."""
         U = U.copy()
         if dt is None:
@@ -176,13 +183,14 @@ class OracleMesh:
         if t_end is not None:
             dt = min(dt, t_end - t)
         self.guardcell_fill(U)
-        Unew, st, _ = self.hydro_advance(U, dt, reflux)
+        Unew, st, _ = self.hydro_advance(U, dt, reflux, integrator=integrator)
         if st:
             raise FloatingPointError("unphysical state after step")
         return Unew, dt
 
     def run(self, U: np.ndarray, nsteps: int | None = None, t_end: float | None = None,
-            cfl: float = 0.8, form: int = 0, reflux: bool = True, max_steps: int = 100000):
+            cfl: float = 0.8, form: int = 0, reflux: bool = True, max_steps: int = 100000,
+            integrator: int = 0):
         t = 0.0
         n = 0
         while True:
@@ -192,7 +200,8 @@ class OracleMesh:
                 break
             if n >= max_steps:
                 raise RuntimeError("too many steps")
-            U, dt = self.step(U, cfl=cfl, form=form, reflux=reflux, t_end=t_end, t=t)
+            U, dt = self.step(U, cfl=cfl, form=form, reflux=reflux, t_end=t_end, t=t,
+                              integrator=integrator)
             t += dt
             n += 1
         return U, t, n

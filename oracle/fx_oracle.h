@@ -83,6 +83,17 @@ int or_compute_dt(const or_mesh *m, const double *U, double cfl, int form, doubl
 int or_hydro_advance(const or_mesh *m, const double *U, double *Unew, double dt,
                      int reflux, double *bflux, int nsel, const int *sel);
 
+/* SSP-RK2 variant of the step (method-of-lines, the family of Flash-X's
+ * Spark solver, Section 2.2): plain MC-limited PLM face states (no Hancock
+ * predictor), HLLC, U1 = U + dt L(U), guard fill of U1, then
+ * Unew = (U + (U1 + dt L(U1))) / 2; flux correction with the stage-averaged
+ * fluxes; restriction into parents.  U must have filled guards.  bflux as in
+ * or_hydro_advance (stage-averaged).  Pinned: scalar-advection special case
+ * (textbook Heun + MC-PLM), Sod L1 convergence, linear waves at second order,
+ * conservation (periodic, AMR with correction), uniform state. */
+int or_hydro_advance_rk2(const or_mesh *m, const double *U, double *Unew, double dt, int reflux,
+                         double *bflux);
+
 /* Restriction of every non-leaf block from its children, finest level first:
  * each parent cell is the pairwise mean (x pairs, then y, then z) of the
  * 2^d child cells it covers.  Pinned: uniform state, linear-field exactness

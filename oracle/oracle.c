@@ -432,8 +432,11 @@ static size_t wi(const or_mesh *m, int v, int k, int j, int i) {
   return (((size_t)v * m->PZ + k) * m->P + j) * m->P + i;
 }
 
+/* One leaf: Unew = U + dt L(U), or with Uavg != NULL the second SSP-RK2
+ * stage Unew = (Uavg + (U + dt L(U))) / 2.  predictor = 1: MUSCL-Hancock face
+ * states; 0: plain MC-limited PLM face states (method-of-lines). */
 static int advance_block(const or_mesh *m, const double *U, double *Unew, double dt, int b,
-                         or_work *w, double *bflux) {
+                         or_work *w, double *bflux, int predictor, const double *Uavg) {
   int P = m->P, PZ = m->PZ, ng = m->ng, n = m->nxb, nd = m->ndim;
   size_t per = (size_t)5 * PZ * P * P;
   double gamma = m->gamma;
@@ -479,7 +482,7 @@ static int advance_block(const or_mesh *m, const double *U, double *Unew, double
           a[4] = gamma * p * dW[d][nrm] + un * dW[d][4];
           for (int v = 0; v < 5; v++) acc[v] = acc[v] + a[v] / dx[d];
         }
-        for (int v = 0; v < 5; v++) Wh[v] = W0[v] - 0.5 * dt * acc[v];
+        for (int v = 0; v < 5; v++) Wh[v] = predictor ? W0[v] - 0.5 * dt * acc[v] : W0[v];
         int bad = 0;
         for (int d = 0; d < nd; d++)
           for (int v = 0; v < 5; v++) {
@@ -532,6 +535,7 @@ static int advance_block(const or_mesh *m, const double *U, double *Unew, double
             div = div + (fl - fr) / dx[d];
           }
           un[v] = U[cell_index(m, b, v, k, j, i)] + dt * div;
+          if (Uavg) un[v] = 0.5 * (Uavg[cell_index(m, b, v, k, j, i)] + un[v]);
           Unew[cell_index(m, b, v, k, j, i)] = un[v];
         }
         double q[5];
@@ -669,7 +673,7 @@ int or_hydro_advance(const or_mesh *m, const double *U, double *Unew, double dt,
     for (int t = 0; t < count; t++) {
       int b = sel ? sel[t] : t;
       if (!m->leaf[b]) continue;
-      bad |= advance_block(m, U, Unew, dt, b, &w, flux);
+      bad |= advance_block(m, U, Unew, dt, b, &w, flux, 1, NULL);
     }
     free(w.W); free(w.FSm); free(w.FSp); free(w.F);
   }
@@ -699,6 +703,70 @@ int or_hydro_advance(const or_mesh *m, const double *U, double *Unew, double dt,
     }
   }
   if (own) free(flux);
+  return bad ? -4 : 0;
+}
+
+/* SSP-RK2 (Shu-Osher / Heun) with MC-limited PLM and HLLC, the second-order
+ * method-of-lines family of Flash-X's Spark solver (Section 2.2):
+ *   U1 = U + dt L(U);  guard fill of U1;  U2 = (U + (U1 + dt L(U1))) / 2.
+ * The coarse-fine correction uses the stage-averaged fluxes (F1 + F2) / 2 on
+ * both sides, which is what the two-stage update of a coarse cell used. */
+int or_hydro_advance_rk2(const or_mesh *m, const double *U, double *Unew, double dt, int reflux,
+                         double *bflux) {
+  size_t per = (size_t)5 * m->PZ * m->P * m->P;
+  size_t tot = per * (size_t)m->nb;
+  int nd = m->ndim, n = m->nxb;
+  int nf = nd == 3 ? n * n : n;
+  size_t nfl = (size_t)m->nb * 2 * nd * 5 * nf;
+  double *U1 = (double *)malloc(sizeof(double) * tot);
+  double *f1 = (double *)calloc(nfl, sizeof(double));
+  double *f2 = (double *)calloc(nfl, sizeof(double));
+  memcpy(U1, U, sizeof(double) * tot);
+  int bad = 0;
+  for (int stage = 0; stage < 2; stage++) {
+#pragma omp parallel num_threads(or_get_threads()) reduction(| : bad)
+    {
+      or_work w;
+      w.W = (double *)malloc(sizeof(double) * per);
+      w.FSm = (double *)malloc(sizeof(double) * per * 3);
+      w.FSp = (double *)malloc(sizeof(double) * per * 3);
+      w.F = (double *)malloc(sizeof(double) * per * 3);
+#pragma omp for schedule(dynamic)
+      for (int b = 0; b < m->nb; b++) {
+        if (!m->leaf[b]) continue;
+        if (stage == 0) bad |= advance_block(m, U, U1, dt, b, &w, f1, 0, NULL);
+        else bad |= advance_block(m, U1, Unew, dt, b, &w, f2, 0, U);
+      }
+      free(w.W); free(w.FSm); free(w.FSp); free(w.F);
+    }
+    if (stage == 0) {
+      or_restrict_parents(m, U1);
+      if (or_guardcell_fill(m, U1)) bad = 1;
+    }
+  }
+  for (size_t q = 0; q < nfl; q++) f1[q] = (f1[q] + f2[q]) * 0.5;
+  if (m->lmax > 0) {
+    if (reflux) {
+#pragma omp parallel for schedule(dynamic) num_threads(or_get_threads())
+      for (int b = 0; b < m->nb; b++)
+        if (m->leaf[b]) reflux_block(m, Unew, dt, b, f1);
+    }
+    or_restrict_parents(m, Unew);
+  }
+  int nz = nd == 3 ? n : 1, kz = nd == 3 ? m->ng : 0;
+  for (int b = 0; b < m->nb && !bad; b++) {
+    if (!m->leaf[b]) continue;
+    for (int k = 0; k < nz; k++)
+      for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) {
+          double u[5], q[5];
+          for (int v = 0; v < 5; v++) u[v] = Unew[cell_index(m, b, v, k + kz, j + m->ng, i + m->ng)];
+          prim_from_cons(u, m->gamma, q);
+          if (!(q[0] > 0.0) || !(q[4] > 0.0)) bad = 1;
+        }
+  }
+  if (bflux) memcpy(bflux, f1, sizeof(double) * nfl);
+  free(U1); free(f1); free(f2);
   return bad ? -4 : 0;
 }
 

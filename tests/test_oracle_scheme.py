@@ -24,6 +24,19 @@ def mesh_2level(nblk=4, nxb=8, ng=4, bc=inputs.OUTFLOW, central=None, ndim=3):
     return inputs.refine(base, np.array(flags))
 
 
+def mesh_3level(bc=inputs.OUTFLOW, nxb=8):
+    """4^3 coarse blocks, the central 2^3 refined, and the central 2^3 of the
+    resulting fine blocks refined again (64 blocks per level, 2:1 balanced)."""
+    m2 = mesh_2level(4, nxb, 4, bc)
+    leaf = m2.is_leaf()
+    flags = np.zeros(m2.nb, dtype=bool)
+    for b in range(m2.nb):
+        if m2.level[b] == 1 and leaf[b]:
+            o = m2.origin[b] // nxb
+            flags[b] = all(3 <= o[d] < 5 for d in range(3))
+    return inputs.refine(m2, flags)
+
+
 # ------------------------------------------------------------------ guard fill
 
 @pytest.mark.parametrize("ndim,bc", [(2, inputs.PERIODIC), (2, inputs.OUTFLOW),
@@ -149,7 +162,7 @@ def test_restriction_of_prolongation_is_identity(orc):
 
 # ------------------------------------------------------------------ invariants
 
-@pytest.mark.parametrize("case", ["2d_outflow", "3d_periodic", "3d_outflow", "amr"])
+@pytest.mark.parametrize("case", ["2d_outflow", "3d_periodic", "3d_outflow", "amr", "amr3"])
 def test_uniform_state_bitwise(orc, case):
     if case == "2d_outflow":
         mesh = inputs.uniform_mesh(2, (3, 2), 8, 4, inputs.OUTFLOW)
@@ -157,8 +170,10 @@ def test_uniform_state_bitwise(orc, case):
         mesh = inputs.uniform_mesh(3, (2, 2, 2), 8, 4, inputs.PERIODIC)
     elif case == "3d_outflow":
         mesh = inputs.uniform_mesh(3, (2, 1, 2), 8, 4, inputs.OUTFLOW)
-    else:
+    elif case == "amr":
         mesh = mesh_2level(4, 8, 4)
+    else:
+        mesh = mesh_3level()
     om = orc.OracleMesh(mesh)
     U0 = om.prim_to_cons(inputs.uniform_state(mesh))
     U, t, n = om.run(U0.copy(), nsteps=3)
@@ -190,6 +205,19 @@ def test_conservation_amr_needs_reflux(orc):
     d2 = np.abs(om.conserved_totals(U2) - T0) / A
     assert np.all(d1 <= 1e-13), d1
     assert d2.max() > 1e-8, d2
+
+
+def test_conservation_three_levels(orc):
+    """Three levels, periodic: flux correction at both coarse-fine interfaces
+    keeps the totals to roundoff."""
+    mesh = mesh_3level(inputs.PERIODIC)
+    om = orc.OracleMesh(mesh)
+    U0 = om.prim_to_cons(inputs.random_smooth_state(mesh, seed=14))
+    T0 = om.conserved_totals(U0)
+    U1, _, _ = om.run(U0.copy(), nsteps=10)
+    A = om.conserved_totals(np.abs(U1)) + om.conserved_totals(np.abs(U0))
+    d = np.abs(om.conserved_totals(U1) - T0) / A
+    assert np.all(d <= 1e-13), d
 
 
 def test_reflux_matches_geometric_face_average(orc):
@@ -496,3 +524,93 @@ def test_linear_waves_second_order(orc, kind):
     errs = _wave_errors(orc, kind)
     orders = np.log2(errs[:-1] / errs[1:])
     assert np.all(orders > 1.6), (errs, orders)
+
+
+# ------------------------------------------------------------------ SSP-RK2 variant
+
+def test_rk2_scalar_advection_special_case(orc):
+    """With uniform velocity and pressure the SSP-RK2 mass update is the
+    textbook Heun scheme on MC-limited upwind PLM:
+    L(r)_i = -nu (r_i + s_i/2 - r_{i-1} - s_{i-1}/2),
+    r1 = r + L(r), r_new = (r + r1 + L(r1)) / 2."""
+    mesh = inputs.uniform_mesh(2, (4, 1), 16, 4, inputs.PERIODIC)
+    om = orc.OracleMesh(mesh)
+    W = inputs.uniform_state(mesh, rho=1.0, vel=(0.8, 0.0, 0.0), p=1.0)
+    N = 64
+    rng = np.random.default_rng(13)
+    prof = 1.0 + 0.5 * rng.random(N)
+    for b in range(mesh.nb):
+        o = int(mesh.origin[b, 0])
+        W[b, 0, 0, 4:20, 4:20] = prof[o:o + 16][None, :]
+    U = om.prim_to_cons(W)
+    om.guardcell_fill(U)
+    dt = 0.5 / N
+    nu = 0.8 * dt * N
+
+    def L(r):
+        a, bb = r - np.roll(r, 1), np.roll(r, -1) - r
+        s = np.where(a * bb <= 0, 0.0,
+                     np.sign(a) * np.minimum(np.minimum(2 * np.abs(a), 2 * np.abs(bb)),
+                                             0.5 * np.abs(a + bb)))
+        face = r + 0.5 * s
+        return -nu * (face - np.roll(face, 1))
+
+    r1 = prof + L(prof)
+    want = 0.5 * (prof + (r1 + L(r1)))
+    Un, st, _ = om.hydro_advance(U, dt, integrator=1)
+    assert st == 0
+    np.testing.assert_allclose(assemble(mesh, Un)[0, 0, 0], want, rtol=1e-13)
+
+
+def test_rk2_sod_convergence_and_linear_waves(orc):
+    errs = []
+    for nx in (64, 128, 256):
+        mesh = inputs.uniform_mesh(2, (nx // 16, 1), 16, 4, inputs.OUTFLOW)
+        om = orc.OracleMesh(mesh)
+        U, t, _ = om.run(om.prim_to_cons(inputs.sod_state(mesh)), t_end=0.2, integrator=1)
+        rho = assemble(mesh, U)[0, 0, 0]
+        x = (np.arange(nx) + 0.5) / nx
+        ex = orc.riemann_sample([1, 0, 1], [0.125, 0, 0.1], (x - 0.5) / t)[:, 0]
+        errs.append(np.abs(rho - ex).mean())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 0.75) and np.all(orders < 1.3), (errs, orders)
+    # smooth acoustic wave at second order
+    errs = []
+    eps = 1e-5
+    for nx in (32, 64, 128):
+        mesh = inputs.uniform_mesh(2, (nx // 16, 1), 16, 4, inputs.PERIODIC)
+        om = orc.OracleMesh(mesh)
+        W = inputs.uniform_state(mesh, rho=1.0, vel=(0, 0, 0), p=1.0 / GAMMA)
+        for b in range(mesh.nb):
+            x, _, _ = mesh.cell_centers(b)
+            s = np.sin(2 * np.pi * x)[0]
+            W[b, 0, 0, 4:20, 4:20] = 1.0 + eps * s
+            W[b, 1, 0, 4:20, 4:20] = eps * s
+            W[b, 4, 0, 4:20, 4:20] = 1.0 / GAMMA + eps * s
+        U, t, _ = om.run(om.prim_to_cons(W), t_end=0.25, integrator=1)
+        xg = (np.arange(nx) + 0.5) / nx
+        got = (assemble(mesh, U)[0, 0, 0] - 1.0) / eps
+        errs.append(np.abs(got - np.sin(2 * np.pi * (xg - t))).mean())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 1.6), (errs, orders)
+
+
+def test_rk2_conservation_uniform_and_amr(orc):
+    for mesh, W in ((inputs.uniform_mesh(3, (2, 2, 2), 8, 4, inputs.PERIODIC), None),
+                    (mesh_2level(4, 8, 4, inputs.PERIODIC), None)):
+        W = inputs.random_smooth_state(mesh, seed=18)
+        om = orc.OracleMesh(mesh)
+        U0 = om.prim_to_cons(W)
+        T0 = om.conserved_totals(U0)
+        U1, _, _ = om.run(U0.copy(), nsteps=15, integrator=1)
+        A = om.conserved_totals(np.abs(U0)) + om.conserved_totals(np.abs(U1))
+        d = np.abs(om.conserved_totals(U1) - T0) / A
+        assert np.all(d <= 1e-13), d
+        if mesh.level.max() > 0:       # without the stage-averaged correction it drifts
+            U2, _, _ = om.run(U0.copy(), nsteps=15, integrator=1, reflux=False)
+            assert (np.abs(om.conserved_totals(U2) - T0) / A).max() > 1e-8
+    mesh = mesh_2level(4, 8, 4)
+    om = orc.OracleMesh(mesh)
+    U0 = om.prim_to_cons(inputs.uniform_state(mesh))
+    U, _, _ = om.run(U0.copy(), nsteps=3, integrator=1)
+    assert np.array_equal(leaf_interior(mesh, U), leaf_interior(mesh, U0))

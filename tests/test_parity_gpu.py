@@ -12,7 +12,7 @@ import pytest
 
 from paper_2208_11630_gb300 import inputs
 from tests.helpers import leaf_interior, max_rel_err
-from tests.test_oracle_scheme import mesh_2level
+from tests.test_oracle_scheme import mesh_2level, mesh_3level
 
 pytestmark = pytest.mark.gpu
 
@@ -60,6 +60,13 @@ CASES = {
         mesh_2level(4, 8, 4, inputs.PERIODIC)),
     "amr_2d_blocky": lambda: (lambda m: (m, inputs.random_blocky_state(m, 9)))(
         mesh_2level(4, 16, 4, inputs.OUTFLOW, ndim=2)),
+    "amr_3level_sedov": lambda: (lambda m: (m, inputs.sedov_state(m)))(mesh_3level()),
+    "amr_3level_periodic": lambda: (lambda m: (m, inputs.random_smooth_state(m, 15)))(
+        mesh_3level(inputs.PERIODIC)),
+    "smooth3d_nxb24": lambda: (lambda m: (m, inputs.random_smooth_state(m, 16)))(
+        inputs.uniform_mesh(3, (2, 1, 1), 24, 4, inputs.PERIODIC)),
+    "smooth3d_nxb64": lambda: (lambda m: (m, inputs.random_smooth_state(m, 17)))(
+        inputs.uniform_mesh(3, (1, 1, 1), 64, 4, inputs.PERIODIC)),
 }
 
 
@@ -127,7 +134,9 @@ def test_one_step(orc, fx, case):
 
 @pytest.mark.parametrize("case,nsteps", [("sod2d", 50), ("sod2d", 100), ("kh64", 100),
                                          ("amr_sedov_small", 100), ("amr_smooth_periodic", 100),
-                                         ("amr_2d_blocky", 100), ("smooth3d_nxb32", 100)])
+                                         ("amr_2d_blocky", 100), ("smooth3d_nxb32", 100),
+                                         ("amr_3level_sedov", 100), ("amr_3level_periodic", 100),
+                                         ("smooth3d_nxb24", 100)])
 def test_many_steps(orc, fx, case, nsteps):
     mesh, W = CASES[case]()
     om, U, bs = both_start(orc, fx, mesh, W)
