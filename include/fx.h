@@ -77,7 +77,14 @@ FX_API int fx_finalize(fx_ctx *ctx);
 /* fx_set_option: set a numeric option of the context.
  *   "cfl_form"  0 = dt from the sum over directions of (|u_d|+c)/dx_d
  *               (default), 1 = from the maximum over directions;
- *   "reflux"    1 = apply fine-to-coarse flux correction (default), 0 = off.
+ *   "reflux"    1 = apply fine-to-coarse flux correction (default), 0 = off;
+ *   "integrator" 0 = MUSCL-Hancock (default); 1 = SSP-RK2 with plain
+ *               MC-limited PLM face states and the same HLLC flux (the
+ *               method-of-lines family of the Spark solver, Section 2.2):
+ *               U1 = U + dt L(U), coarse-fine fill of U1,
+ *               U <- (U + (U1 + dt L(U1))) / 2 in the current buffer, flux
+ *               correction with the stage-averaged fluxes.  Batches accept
+ *               only integrator 0.
  * Errors: FX_ERR_ARG for an unknown key or value. */
 FX_API int fx_set_option(fx_ctx *ctx, const char *key, double value);
 

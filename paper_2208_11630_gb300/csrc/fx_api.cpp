@@ -28,6 +28,7 @@ struct fx_ctx {
   int nxb = 16, ng = 4;
   int cfl_form = 0;
   int reflux = 1;
+  int integrator = 0;   // 0 MUSCL-Hancock, 1 SSP-RK2
   int device = 0;
   std::string err;
 };
@@ -157,6 +158,11 @@ int fx_set_option(fx_ctx *ctx, const char *key, double value) {
   if (!strcmp(key, "reflux")) {
     if (value != 0.0 && value != 1.0) return fail(ctx, FX_ERR_ARG, "reflux must be 0 or 1");
     ctx->reflux = (int)value;
+    return FX_OK;
+  }
+  if (!strcmp(key, "integrator")) {
+    if (value != 0.0 && value != 1.0) return fail(ctx, FX_ERR_ARG, "integrator must be 0 or 1");
+    ctx->integrator = (int)value;
     return FX_OK;
   }
   return fail(ctx, FX_ERR_ARG, std::string("unknown option ") + key);
@@ -500,6 +506,8 @@ int fx_blocks_mark_dirty(fx_blocks *bs) {
   return FX_OK;
 }
 
+static int fill_for_fused_advance(fx_ctx *ctx, fx_blocks *bs, cudaStream_t s, void *U);
+
 int fx_hydro_advance(fx_ctx *ctx, fx_blocks *bs, const double *dt_dev, void *stream) {
   if (!ctx || !bs || !dt_dev) return FX_ERR_ARG;
   if (bs->in_batch) return fail(ctx, FX_ERR_STATE, "block set is owned by a batch");
@@ -507,8 +515,39 @@ int fx_hydro_advance(fx_ctx *ctx, fx_blocks *bs, const double *dt_dev, void *str
   void *Uo = bs->U[bs->cur], *Un = bs->U[1 - bs->cur];
   unsigned long long *smax = bs->d_scratch + 2;
   const bool refl = ctx->reflux && bs->nrefl > 0;
+  const int *leaves = bs->d_lists + bs->leaves_off;
+  if (ctx->integrator == 1) {
+    // SSP-RK2: U1 = U + dt L(U) into the other buffer; coarse-fine fill of
+    // U1; U = (U + (U1 + dt L(U1))) / 2 in place; registers hold the stage
+    // average of the fluxes for the correction.
+    fx::HydroStage s1, s2;
+    s1.pred = 0; s1.reg_mode = 1;
+    s2.pred = 0; s2.reg_mode = 2; s2.Uavg = Uo;
+    FX_CUDA(fx::launch_hydro(bs->dm, Uo, Un, bs->prec, leaves, bs->nleaves, dt_dev, bs->d_regs,
+                             bs->d_status, nullptr, nullptr, ctx->cfl_form, s, s1),
+            "hydro stage 1 launch");
+    int rc = fill_for_fused_advance(ctx, bs, s, Un);
+    if (rc) return rc;
+    FX_CUDA(cudaMemsetAsync(smax, 0, sizeof(unsigned long long), s), "signal max reset");
+    FX_CUDA(fx::launch_hydro(bs->dm, Un, Uo, bs->prec, leaves, bs->nleaves, dt_dev, bs->d_regs,
+                             bs->d_status, smax, refl ? bs->d_rmask : nullptr, ctx->cfl_form, s,
+                             s2),
+            "hydro stage 2 launch");
+    if (refl)
+      FX_CUDA(fx::launch_reflux(bs->dm, Uo, bs->prec, bs->d_refl, bs->nrefl, dt_dev, bs->d_regs,
+                                bs->d_status, smax, ctx->cfl_form, s),
+              "reflux launch");
+    for (int l = bs->lmax; l >= 0; --l)
+      FX_CUDA(fx::launch_restrict(bs->dm, Uo, bs->prec, bs->d_lists + bs->par_off[l],
+                                  bs->par_cnt[l], s),
+              "restrict launch");
+    ++bs->epoch;                      // the new state is in the same buffer
+    bs->next_epoch = bs->epoch;
+    bs->next_form = ctx->cfl_form;
+    return FX_OK;
+  }
   FX_CUDA(cudaMemsetAsync(smax, 0, sizeof(unsigned long long), s), "signal max reset");
-  FX_CUDA(fx::launch_hydro(bs->dm, Uo, Un, bs->prec, bs->d_lists + bs->leaves_off, bs->nleaves,
+  FX_CUDA(fx::launch_hydro(bs->dm, Uo, Un, bs->prec, leaves, bs->nleaves,
                            dt_dev, bs->d_regs, bs->d_status, smax, refl ? bs->d_rmask : nullptr,
                            ctx->cfl_form, s),
           "hydro launch");
@@ -530,8 +569,7 @@ int fx_hydro_advance(fx_ctx *ctx, fx_blocks *bs, const double *dt_dev, void *str
 // restricted (they are same-level sources), the guards of coarse leaves that
 // feed a prolongation, and the prolonged guards themselves.  Same-level guards
 // of every other leaf are read by the hydro kernel from the neighbours.
-static int fill_for_fused_advance(fx_ctx *ctx, fx_blocks *bs, cudaStream_t s) {
-  void *U = bs->U[bs->cur];
+static int fill_for_fused_advance(fx_ctx *ctx, fx_blocks *bs, cudaStream_t s, void *U) {
   for (int l = bs->lmax; l >= 0; --l)
     FX_CUDA(fx::launch_restrict(bs->dm, U, bs->prec, bs->d_lists + bs->par_off[l], bs->par_cnt[l], s),
             "restrict launch");
@@ -548,7 +586,7 @@ static int fill_for_fused_advance(fx_ctx *ctx, fx_blocks *bs, cudaStream_t s) {
 
 int fx_guardcell_fill_amr(fx_ctx *ctx, fx_blocks *bs, void *stream) {
   if (!ctx || !bs) return FX_ERR_ARG;
-  return fill_for_fused_advance(ctx, bs, (cudaStream_t)stream);
+  return fill_for_fused_advance(ctx, bs, (cudaStream_t)stream, bs->U[bs->cur]);
 }
 
 int fx_step(fx_ctx *ctx, fx_blocks *bs, double cfl, double *dt_dev, void *stream) {
@@ -867,6 +905,8 @@ int fx_batch_destroy(fx_batch *b) {
 int fx_batch_add(fx_batch *b, fx_blocks *bs, double cfl, int nsteps, void *stream, int *slot_out) {
   if (!b || !bs || !(cfl > 0.0) || nsteps < 1) return FX_ERR_ARG;
   if (bs->in_batch) return fail(b->ctx, FX_ERR_STATE, "block set already in a batch");
+  if (bs->ctx->integrator != 0)
+    return fail(b->ctx, FX_ERR_ARG, "batches step MUSCL-Hancock block sets only");
   int s = -1;
   for (int r = 0; r < b->max_req; ++r)
     if (!b->slot[r]) { s = r; break; }

@@ -77,13 +77,20 @@ cudaError_t launch_guard_prolong(const DevMesh &m, void *U, int prec, const int 
                                  int depth, int state_precision_math, cudaStream_t s);
 // Guard depth the fused update reads (radius-2 stencil).
 constexpr int kHydroGuardDepth = 2;
+// Time-integration stage of one update launch (defaults: MUSCL-Hancock).
+struct HydroStage {
+  int pred = 1;               // 1: Hancock predictor; 0: PLM face states (SSP-RK2)
+  const void *Uavg = nullptr; // SSP-RK2 second stage: average with this state
+  int reg_mode = 0;           // flux registers: 0 store F, 1 store F/2, 2 add F/2
+};
+
 // smax (may be null): receives atomicMax of the bit patterns of the new
 // state's CFL signal speeds (form 0 = sum over directions, 1 = max); cells on
 // the faces flagged in rmask[block] (bit 2d+s) are left to the reflux kernel.
 cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, const int *leaves,
                          int n, const double *dt, double *regs, int *status,
                          unsigned long long *smax, const unsigned char *rmask, int form,
-                         cudaStream_t s);
+                         cudaStream_t s, const HydroStage &st = HydroStage());
 cudaError_t launch_reflux(const DevMesh &m, void *Unew, int prec, const RefluxItem *items, int n,
                           const double *dt, const double *regs, int *status,
                           unsigned long long *smax, int form, cudaStream_t s);

@@ -60,6 +60,15 @@ __device__ __forceinline__ bool positive(float x) {
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 
+// Flux-register write: store F, store F/2, or add F/2 (stage averages).
+template <typename R>
+__device__ __forceinline__ void put_reg(double &r, R f, int mode) {
+  const double v = double(f);
+  if (mode == 0) r = v;
+  else if (mode == 1) r = 0.5 * v;
+  else r = r + 0.5 * v;
+}
+
 // Quotient and reciprocal: IEEE division in FP64; the fast (MUFU-based,
 // ~2 ulp) forms in FP32, whose error is far below the FP32 storage rounding.
 __device__ __forceinline__ double div_r(double a, double b) { return a / b; }
@@ -225,14 +234,20 @@ __device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int 
 // One T x T column tile of leaf block b, marched along z.  Called by the
 // per-block-set kernel (one CTA per tile) and by the batched persistent
 // kernel (each CTA loops over tiles of many block sets).
+//   pred      1: MUSCL-Hancock half step; 0: plain PLM face states (SSP-RK2)
+//   Uavg      null, or the SSP-RK2 second stage: Unew = (Uavg + (U + dt L(U)))/2
+//             (Uavg may be Unew itself: each cell is read before it is written
+//             by the same thread, so neither pointer is declared restrict)
+//   reg_mode  flux registers: 0 store F, 1 store F/2, 2 add F/2
 template <int NDIM, int T, typename S, typename R>
 __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict__ U,
-                                           S *__restrict__ Unew, int b, int tile, int tiles,
+                                           S *Unew, int b, int tile, int tiles,
                                            double dt, double *__restrict__ regs,
                                            int *__restrict__ status,
                                            unsigned long long *__restrict__ smax_out,
                                            const unsigned char *__restrict__ rmask,
-                                           int cfl_form) {
+                                           int cfl_form, int pred = 1, const S *Uavg = nullptr,
+                                           int reg_mode = 0) {
   using SM = Smem<T>;
   constexpr int NT = T * T;
   constexpr int NPL = NDIM == 3 ? 3 : 1;
@@ -250,14 +265,14 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
   const int lev = m.level[b];
   const long long vs = m.vstride;
   const R g = R(m.gamma), gm1 = R(m.gamma - 1.0), igm1 = R(1.0 / (m.gamma - 1.0));
-  const R hdt = R(0.5 * dt);
+  const R hdt = pred ? R(0.5 * dt) : R(0);
   R idx2[3];
   idx2[0] = R(2.0 * m.idx[lev][0]);
   idx2[1] = R(2.0 * m.idx[lev][1]);
   idx2[2] = R(2.0 * m.idx[lev][2]);
   const double didx = m.idx[lev][0], didy = m.idx[lev][1], didz = m.idx[lev][2];
   const S *Ub = U + (long long)b * m.bstride;
-  S *Unb = Unew + (long long)b * m.bstride;
+  S *Unb = Unew + (long long)b * m.bstride;   // may alias Uavg (see above)
   const int ti = tid % T, tj = tid / T;
   const int zoff = NDIM == 3 ? ng : 0;
   const int ridx = m.regidx[b];
@@ -436,8 +451,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
             const int face = a == 0 ? 0 : 1;
             const int t1 = y0 + e, t2 = NDIM == 3 ? zglob : 0;
 #pragma unroll
-            for (int v = 0; v < 5; ++v)
-              reg[(face * 5 + v) * nfc + t2 * n + t1] = double(F[v]);
+            for (int v = 0; v < 5; ++v) put_reg(reg[(face * 5 + v) * nfc + t2 * n + t1], F[v], reg_mode);
           }
         } else {
 #pragma unroll
@@ -452,8 +466,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
             const int face = a == 0 ? 2 : 3;
             const int t1 = x0 + e, t2 = NDIM == 3 ? zglob : 0;
 #pragma unroll
-            for (int v = 0; v < 5; ++v)
-              reg[(face * 5 + v) * nfc + t2 * n + t1] = double(F[v]);
+            for (int v = 0; v < 5; ++v) put_reg(reg[(face * 5 + v) * nfc + t2 * n + t1], F[v], reg_mode);
           }
         }
       }
@@ -464,8 +477,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
       if (reg && (p == 0 || p == n)) {
         const int face = p == 0 ? 4 : 5;
 #pragma unroll
-        for (int v = 0; v < 5; ++v)
-          reg[(face * 5 + v) * nfc + (y0 + tj) * n + (x0 + ti)] = double(Fz[v]);
+        for (int v = 0; v < 5; ++v) put_reg(reg[(face * 5 + v) * nfc + (y0 + tj) * n + (x0 + ti)], Fz[v], reg_mode);
       }
     }
     __syncthreads();
@@ -486,6 +498,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
           const double div = txy[v] + (fzl[v] - Fz[v]) * didz;
           un[v] = double(Ub[o + v * vs]) + dt * div;
         }
+        if (Uavg) un[v] = R(0.5) * (R(Uavg[(long long)b * m.bstride + o + v * vs]) + un[v]);
         Unb[o + v * vs] = S(un[v]);
       }
       if (!(un[0] > R(0)) || !(R(2) * un[4] * un[0] > un[1] * un[1] + un[2] * un[2] + un[3] * un[3]))
@@ -513,6 +526,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
         for (int v = 0; v < 5; ++v) {
           if constexpr (kF32) un[v] = float(Ub[o + v * vs]) + txy[v];
           else un[v] = double(Ub[o + v * vs]) + dt * txy[v];
+          if (Uavg) un[v] = R(0.5) * (R(Uavg[(long long)b * m.bstride + o + v * vs]) + un[v]);
           Unb[o + v * vs] = S(un[v]);
         }
         if (!(un[0] > R(0)) ||
@@ -537,13 +551,14 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
 
 template <int NDIM, int T, typename S, typename R>
 __global__ void __launch_bounds__(T *T, (T == 16 ? (sizeof(R) == 4 ? 4 : 2) : 6))
-k_hydro(DevMesh m, const S *__restrict__ U, S *__restrict__ Unew, const int *__restrict__ leaves,
+k_hydro(DevMesh m, const S *__restrict__ U, S *Unew, const int *__restrict__ leaves,
         int tiles, const double *__restrict__ dtp, double *__restrict__ regs,
         int *__restrict__ status, unsigned long long *__restrict__ smax_out,
-        const unsigned char *__restrict__ rmask, int cfl_form) {
+        const unsigned char *__restrict__ rmask, int cfl_form, int pred, const S *Uavg,
+        int reg_mode) {
   const int tpb = tiles * tiles;
   hydro_tile<NDIM, T, S, R>(m, U, Unew, leaves[blockIdx.x / tpb], blockIdx.x % tpb, tiles, *dtp,
-                            regs, status, smax_out, rmask, cfl_form);
+                            regs, status, smax_out, rmask, cfl_form, pred, Uavg, reg_mode);
 }
 
 // Persistent batched kernel: the CTAs pull (request, leaf, tile) items from a
@@ -573,7 +588,7 @@ k_hydro_batch(const BatchReq *__restrict__ reqs, const int4 *__restrict__ items,
 template <int NDIM, int T, typename S, typename R>
 cudaError_t launch_t(const DevMesh &m, const void *U, void *Unew, const int *leaves, int n,
                      const double *dt, double *regs, int *status, unsigned long long *smax,
-                     const unsigned char *rmask, int form, cudaStream_t s) {
+                     const unsigned char *rmask, int form, const HydroStage &st, cudaStream_t s) {
   const int tiles = m.nxb / T;
   const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(R);
   auto kern = k_hydro<NDIM, T, S, R>;
@@ -585,7 +600,8 @@ cudaError_t launch_t(const DevMesh &m, const void *U, void *Unew, const int *lea
     attr_done = true;
   }
   kern<<<n * tiles * tiles, T * T, smem, s>>>(m, static_cast<const S *>(U), static_cast<S *>(Unew),
-                                              leaves, tiles, dt, regs, status, smax, rmask, form);
+                                              leaves, tiles, dt, regs, status, smax, rmask, form,
+                                              st.pred, static_cast<const S *>(st.Uavg), st.reg_mode);
   count_launch();
   return cudaGetLastError();
 }
@@ -662,21 +678,21 @@ size_t hydro_smem_bytes(int ndim, int tile, int prec) {
 cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, const int *leaves,
                          int n, const double *dt, double *regs, int *status,
                          unsigned long long *smax, const unsigned char *rmask, int form,
-                         cudaStream_t s) {
+                         cudaStream_t s, const HydroStage &st) {
   if (n <= 0) return cudaSuccess;
   const int T = (m.nxb % 16 == 0) ? 16 : 8;
   if (prec == 0) {
     if (m.ndim == 3)
-      return T == 16 ? launch_t<3, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
-                     : launch_t<3, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
-    return T == 16 ? launch_t<2, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
-                   : launch_t<2, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
+      return T == 16 ? launch_t<3, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, st, s)
+                     : launch_t<3, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, st, s);
+    return T == 16 ? launch_t<2, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, st, s)
+                   : launch_t<2, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, st, s);
   }
   if (m.ndim == 3)
-    return T == 16 ? launch_t<3, 16, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
-                   : launch_t<3, 8, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
-  return T == 16 ? launch_t<2, 16, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
-                 : launch_t<2, 8, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
+    return T == 16 ? launch_t<3, 16, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, st, s)
+                   : launch_t<3, 8, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, st, s);
+  return T == 16 ? launch_t<2, 16, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, st, s)
+                 : launch_t<2, 8, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, st, s);
 }
 
 }  // namespace fx

@@ -321,3 +321,38 @@ def test_full_size_sedov_amr(orc, fx):
     a, b = mesh.interior(G)[par], mesh.interior(Uo)[par]
     s = np.maximum(np.abs(b).max(axis=(0, 2, 3, 4), keepdims=True), 1e-300)
     assert (np.abs(a - b) / np.maximum(np.abs(b), s)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("case", ["sod2d", "kh64", "blocky2d_nxb8", "amr_smooth_periodic",
+                                  "amr_sedov_small", "amr_3level_periodic", "smooth3d_nxb32"])
+def test_rk2_variant(orc, fx, case):
+    """SSP-RK2 with PLM and HLLC (integrator option 1) against the oracle's
+    SSP-RK2: one step at 1e-12, thirty more at 1e-10; totals conserved on
+    periodic meshes (stage-averaged flux correction on AMR)."""
+    mesh, W = CASES[case]()
+    om, U, bs = both_start(orc, fx, mesh, W, options={"integrator": 1})
+    bs.set_conserved(U)
+    Uo, dto = om.step(U, integrator=1)
+    bs.step(0.8)
+    assert bs.status() == 0
+    assert float(bs.dt.item()) == pytest.approx(dto, rel=1e-15)
+    assert max_rel_err(mesh, bs.state(), Uo) <= 1e-12
+    Uo2, _, _ = om.run(Uo, nsteps=30, integrator=1)
+    bs.run(30, 0.8)
+    assert bs.status() == 0
+    assert max_rel_err(mesh, bs.state(), Uo2) <= 1e-10
+    if mesh.bc[0][0] == inputs.PERIODIC:
+        A = om.conserved_totals(np.abs(U)) + om.conserved_totals(np.abs(Uo2))
+        assert np.all(np.abs(bs.totals() - om.conserved_totals(U)) / A <= 1e-13)
+
+
+def test_rk2_block_sets_are_not_batched(fx):
+    mesh, W = CASES["kh64"]()
+    bs = fx.BlockSet(mesh, 1.4, options={"integrator": 1})
+    bs.set_primitive(W)
+    ctx = fx.fx_init(1.4, 16, 4)
+    batch = fx.Batch(ctx, 2)
+    with pytest.raises(fx.FxError):
+        batch.add(bs, 0.8, 3)
+    batch.close()
+    fx.fx_finalize(ctx)

@@ -124,3 +124,17 @@ def test_advection_precision_study_64(orc, fx):
     assert e64 <= 1e-10
     assert e32 <= 1e-3
     assert abs(l1s["f32bulk"] - l1s["oracle"]) <= 1e-3 * l1s["oracle"]
+
+
+@pytest.mark.parametrize("case", ["kh64", "amr_sedov_small"])
+def test_f32bulk_rk2_one_step(orc, fx, case):
+    mesh, W = CASES[case]()
+    om = orc.OracleMesh(mesh)
+    U = om.prim_to_cons(W)
+    bs = f32_blockset(fx, mesh, W, options={"integrator": 1})
+    Uo, dto = om.step(U, integrator=1)
+    bs.step(0.8)
+    assert bs.status() == 0
+    err = max_rel_err_vec(mesh, bs.state(), Uo)
+    print(f"\nf32bulk SSP-RK2 one step {case}: max rel err {err:.3e}")
+    assert err <= 1e-5, err
