@@ -34,11 +34,19 @@ namespace {
 // Half of van Leer's MC slope: 0 if a and b differ in sign or one is zero,
 // else sign(a) min(|a|, |b|, |a+b|/4) -- exactly MC(a, b) / 2, since scaling by
 // powers of two is exact.  The sign tests run on the integer pipe.
+//
+// FP64: the minimum of the three non-negative magnitudes is taken on their bit
+// patterns (which order like the values), keeping it off the FP64 pipe.
 __device__ __forceinline__ double mc_half(double a, double b) {
   const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
   const bool same = ((ia ^ ib) >= 0) && (ia << 1) != 0 && (ib << 1) != 0;
-  const double m = fmin(fmin(fabs(a), fabs(b)), 0.25 * fabs(a + b));
-  return same ? copysign(m, a) : 0.0;
+  const long long ma = ia & 0x7fffffffffffffffll, mb = ib & 0x7fffffffffffffffll;
+  const long long mq = __double_as_longlong(0.25 * fabs(a + b));
+  long long m = ma < mb ? ma : mb;
+  m = mq < m ? mq : m;
+  // sign of a on the minimum magnitude
+  const long long r = m | (ia & (long long)0x8000000000000000ull);
+  return same ? __longlong_as_double(r) : 0.0;
 }
 
 __device__ __forceinline__ float mc_half(float a, float b) {
@@ -53,9 +61,19 @@ __device__ __forceinline__ float mc_half(float a, float b) {
 __device__ __forceinline__ bool positive(double x) {
   return (unsigned long long)__double_as_longlong(x) - 1ull < 0x7ff0000000000000ull;
 }
-__device__ __forceinline__ bool positive(float x) {
-  return (unsigned)__float_as_int(x) - 1u < 0x7f800000u;
+// FP32: a plain compare is cheaper than the bit test; +inf is the only
+// value where the two forms differ, and it counts as positive in both.
+__device__ __forceinline__ bool positive(float x) { return x > 0.0f; }
+
+// x >= 0 (true for -0; a NaN with a clear sign bit would count as >= 0, which
+// only matters for states that are already invalid), on the bit pattern.
+__device__ __forceinline__ bool ge0(double x) {
+  const long long i = __double_as_longlong(x);
+  return i >= 0 || (i << 1) == 0;
 }
+__device__ __forceinline__ bool ge0(float x) { return x >= 0.0f; }
+__device__ __forceinline__ bool gt0(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool gt0(float x) { return x > 0.0f; }
 
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
@@ -102,9 +120,9 @@ __device__ __forceinline__ void hllc(const R (&WL)[5], const R (&WR)[5], R g, R 
   const R dL = SL - uL, dR = SR - uR;
   const R Sst = div_r(pR - pL + rL * uL * dL - rR * uR * dR, rL * dL - rR * dR);
   // Branches: S_L >= 0 -> F_L; S* >= 0 -> F*_L; S_R > 0 -> F*_R; else F_R.
-  const bool caseA = SL >= R(0);
-  const bool useL = caseA || Sst >= R(0);
-  const bool star = !caseA && (useL || SR > R(0));
+  const bool caseA = ge0(SL);
+  const bool useL = caseA || ge0(Sst);
+  const bool star = !caseA && (useL || gt0(SR));
   R W[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) W[q] = useL ? WL[q] : WR[q];
