@@ -47,7 +47,7 @@ typedef struct or_mesh or_mesh;
 
 /* Build the oracle's own view of a block set (levels, origins in the block's
  * level lattice, parents).  bc[6] = {x-, x+, y-, y+, z-, z+}, 0 = outflow,
- * 1 = periodic.  Returns NULL on invalid input (message via or_last_error). */
+ * 1 = periodic (both sides of an axis), 2 = reflecting wall.  Returns NULL on invalid input (message via or_last_error). */
 or_mesh *or_mesh_create(int ndim, int nxb, int ng, int nb, const int nroot[3],
                         const int *level, const int64_t *origin, const int *parent,
                         const double lo[3], const double hi[3], const int bc[6],

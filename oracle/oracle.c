@@ -13,6 +13,8 @@
  *   predictor  MUSCL-Hancock half step, primitive quasi-linear form (Toro ch. 14)
  *   flux       HLLC, Davis speeds (Toro, Spruce & Speares 1994; Toro ch. 10)
  *   update     unsplit conservative update, directions summed x, y, z
+ *   walls      outflow (nearest interior cell), periodic (wrap), reflecting
+ *              (mirror image with the wall-normal momentum negated)
  *   AMR        restriction (pairwise mean of children), MC-limited conservative
  *              linear prolongation, fine-to-coarse flux correction
  *              (Berger & Colella 1989)
@@ -270,13 +272,18 @@ static double interior_value(const or_mesh *m, const double *U, int l, const int
 static int guard_value(const or_mesh *m, const double *U, int l, const int64_t gin[3], int v,
                        double *out) {
   int64_t g[3];
+  int flip = 0;                                 /* momentum components to negate */
   for (int d = 0; d < 3; d++) {
     g[d] = gin[d];
     if (d >= m->ndim) { g[d] = 0; continue; }
     int64_t N = m->ncell[l][d];
     if (g[d] < 0 || g[d] >= N) {
-      if (m->bc[d][g[d] < 0 ? 0 : 1] == 1) {
+      int kind = m->bc[d][g[d] < 0 ? 0 : 1];
+      if (kind == 1) {
         g[d] = ((g[d] % N) + N) % N;            /* periodic: wrap */
+      } else if (kind == 2) {
+        g[d] = g[d] < 0 ? -1 - g[d] : 2 * N - 1 - g[d];  /* reflecting: mirror */
+        if (v == 1 + d) flip ^= 1;              /* ... with the normal momentum negated */
       } else {
         g[d] = g[d] < 0 ? 0 : N - 1;            /* outflow: nearest interior cell */
       }
@@ -287,6 +294,7 @@ static int guard_value(const or_mesh *m, const double *U, int l, const int64_t g
   int b = lookup(m, l, bcoord);
   if (b >= 0) {
     *out = interior_value(m, U, l, g, v);
+    if (flip) *out = -*out;
     return 0;
   }
   /* covered by a coarser leaf: conservative MC-limited linear prolongation */
@@ -309,7 +317,7 @@ static int guard_value(const or_mesh *m, const double *U, int l, const int64_t g
     double s = (g[d] % 2 == 0) ? -0.25 : 0.25;
     val = val + s * sigma;
   }
-  *out = val;
+  *out = flip ? -val : val;
   return 0;
 }
 

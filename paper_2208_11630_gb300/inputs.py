@@ -24,6 +24,7 @@ import numpy as np
 
 OUTFLOW = 0
 PERIODIC = 1
+REFLECT = 2
 
 
 @dataclass

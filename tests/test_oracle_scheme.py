@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from paper_2208_11630_gb300 import inputs
-from tests.helpers import assemble, leaf_interior
+from tests.helpers import assemble, leaf_interior, rel_err
 
 GAMMA = 1.4
 
@@ -39,13 +39,18 @@ def mesh_3level(bc=inputs.OUTFLOW, nxb=8):
 
 # ------------------------------------------------------------------ guard fill
 
+R_, O_, P_ = inputs.REFLECT, inputs.OUTFLOW, inputs.PERIODIC
+
+
 @pytest.mark.parametrize("ndim,bc", [(2, inputs.PERIODIC), (2, inputs.OUTFLOW),
                                      (3, inputs.PERIODIC), (3, inputs.OUTFLOW),
-                                     (3, ((inputs.PERIODIC,) * 2, (inputs.OUTFLOW,) * 2,
-                                          (inputs.PERIODIC,) * 2))])
+                                     (3, ((P_, P_), (O_, O_), (P_, P_))),
+                                     (2, inputs.REFLECT),
+                                     (3, ((R_, O_), (P_, P_), (O_, R_)))])
 def test_guard_fill_brute_force(orc, ndim, bc):
     """Guards of a uniform mesh equal global-array indexing with wrap
-    (periodic) or clip (outflow) per axis -- bitwise."""
+    (periodic), clip (outflow) or mirror about the wall with the normal
+    momentum negated (reflecting) per side -- bitwise."""
     nblk = (3, 2, 2)[:ndim]
     mesh = inputs.uniform_mesh(ndim, nblk, 8, 4, bc)
     om = orc.OracleMesh(mesh)
@@ -56,18 +61,29 @@ def test_guard_fill_brute_force(orc, ndim, bc):
     N = mesh.cells_per_axis(0)
     bcs = mesh.bc
     for b in range(mesh.nb):
-        idx = []
+        idx, sign = [], []
         for d in range(3):
             if d >= ndim:
                 idx.append(np.zeros(1, dtype=int))
+                sign.append(np.ones(1))
                 continue
             g = mesh.origin[b, d] + np.arange(mesh.P) - mesh.ng
-            if bcs[d][0] == inputs.PERIODIC:
-                g = np.mod(g, N[d])
-            else:
-                g = np.clip(g, 0, N[d] - 1)
+            sg = np.ones(mesh.P)
+            for side, beyond in ((0, g < 0), (1, g >= N[d])):
+                kind = bcs[d][side]
+                if kind == inputs.PERIODIC:
+                    g = np.where(beyond, np.mod(g, N[d]), g)
+                elif kind == inputs.REFLECT:
+                    g = np.where(beyond, (-1 - g) if side == 0 else (2 * N[d] - 1 - g), g)
+                    sg = np.where(beyond, -1.0, sg)
+                else:
+                    g = np.where(beyond, 0 if side == 0 else N[d] - 1, g)
             idx.append(g)
-        want = G[:, idx[2][:, None, None], idx[1][None, :, None], idx[0][None, None, :]]
+            sign.append(sg)
+        want = G[:, idx[2][:, None, None], idx[1][None, :, None], idx[0][None, None, :]].copy()
+        want[1] *= sign[0][None, None, :]
+        want[2] *= sign[1][None, :, None]
+        want[3] *= sign[2][:, None, None]
         assert np.array_equal(U[b], want)
 
 
@@ -614,3 +630,109 @@ def test_rk2_conservation_uniform_and_amr(orc):
     U0 = om.prim_to_cons(inputs.uniform_state(mesh))
     U, _, _ = om.run(U0.copy(), nsteps=3, integrator=1)
     assert np.array_equal(leaf_interior(mesh, U), leaf_interior(mesh, U0))
+
+
+# ------------------------------------------------------------------ reflecting walls
+
+def _wall_problem(ndim, nblk, nxb, walls, refine_at, seed):
+    """A problem with reflecting walls on both sides of the axes in ``walls``
+    (periodic elsewhere), and its mirror-image extension: the periodic
+    problem on the domain doubled to [-1, 1] along each wall axis, with the
+    initial data mirrored there (density, pressure and the tangential
+    velocities even, the normal velocity odd).  By symmetry the periodic
+    solution restricted to [0, 1] is the walled one.  ``refine_at(c)`` says
+    whether the level-0 block with block coordinates ``c`` of the walled
+    domain is refined once.  The initial data are random per level-0 cell."""
+    bc_r = tuple((R_, R_) if d in walls else (P_, P_) for d in range(3))
+    m_r = inputs.uniform_mesh(ndim, nblk, nxb, 4, bc_r)
+    nb_p = tuple(2 * nblk[d] if d in walls else nblk[d] for d in range(ndim))
+    lo_p = tuple(-1.0 if d in walls else 0.0 for d in range(3))
+    m_p = inputs.uniform_mesh(ndim, nb_p, nxb, 4, P_, lo=lo_p)
+
+    def mirror_coord(c):
+        return tuple((c[d] - nblk[d] if c[d] >= nblk[d] else nblk[d] - 1 - c[d])
+                     if d in walls else c[d] for d in range(ndim))
+
+    f_r = [refine_at(tuple(m_r.origin[b, :ndim] // nxb)) for b in range(m_r.nb)]
+    f_p = [refine_at(mirror_coord(tuple(m_p.origin[b, :ndim] // nxb))) for b in range(m_p.nb)]
+    if any(f_r):
+        m_r, m_p = inputs.refine(m_r, np.array(f_r)), inputs.refine(m_p, np.array(f_p))
+    rng = np.random.default_rng(seed)
+    N = m_r.cells_per_axis(0)
+    Gr = np.empty((5, N[2], N[1], N[0]))
+    Gr[0] = rng.uniform(0.5, 2.0, Gr[0].shape)
+    for d in range(3):
+        Gr[1 + d] = rng.uniform(-1.0, 1.0, Gr[0].shape) if d < ndim else 0.0
+    Gr[4] = rng.uniform(0.5, 2.0, Gr[0].shape)
+    Gp = Gr
+    for d in walls:
+        ax = 3 - d
+        half = np.flip(Gp, axis=ax).copy()
+        half[1 + d] = -half[1 + d]
+        Gp = np.concatenate([half, Gp], axis=ax)
+
+    def fill(mesh, G):
+        W = np.zeros(mesh.shape)
+        for b in range(mesh.nb):
+            gx, gy, gz = mesh.global_index(b)
+            s = int(mesh.level[b])
+            vals = G[:, gz >> s, gy >> s, gx >> s]
+            if ndim == 3:
+                W[b, :, 4:-4, 4:-4, 4:-4] = vals
+            else:
+                W[b, :, 0, 4:-4, 4:-4] = vals[:, 0]
+        return W
+
+    return m_r, fill(m_r, Gr), m_p, fill(m_p, Gp)
+
+
+@pytest.mark.parametrize("case", ["2d_box", "3d_xz", "3d_amr_wall"])
+def test_reflecting_equals_mirrored_periodic(orc, case):
+    """Reflecting walls reproduce the mirror-symmetric periodic solution on
+    the doubled domain (up to roundoff: the periodic run is mirror-symmetric
+    only to rounding), uniform and with refined blocks against a wall."""
+    if case == "2d_box":
+        args = (2, (2, 2), 8, (0, 1), lambda c: False)
+    elif case == "3d_xz":
+        args = (3, (2, 1, 2), 8, (0, 2), lambda c: False)
+    else:
+        args = (3, (2, 2, 2), 8, (0,), lambda c: c[0] == 0 and c[1] == 1)
+    m_r, W_r, m_p, W_p = _wall_problem(*args, seed=21)
+    walls = args[3]
+    o_r, o_p = orc.OracleMesh(m_r), orc.OracleMesh(m_p)
+    U_r, U_p = o_r.prim_to_cons(W_r), o_p.prim_to_cons(W_p)
+    dt = 0.5 * o_r.compute_dt(U_r, 0.8)
+    for _ in range(6):
+        U_r, _ = o_r.step(U_r, dt=dt)
+        U_p, _ = o_p.step(U_p, dt=dt)
+    G_r, G_p = assemble(m_r, U_r), assemble(m_p, U_p)
+    for d in walls:
+        ax = 3 - d
+        n = G_r.shape[ax]
+        G_p = np.take(G_p, np.arange(n, 2 * n), axis=ax)
+    assert not np.isnan(G_r).any()
+    err = rel_err(G_r, G_p, axis_var=0).max()
+    assert err <= 1e-12, err
+    # the walls did something: the state differs from an outflow run
+    bc_o = tuple((O_, O_) if d in walls else (P_, P_) for d in range(3))
+    m_o = inputs.Mesh(**{**m_r.__dict__, "bc": bc_o, "extra": {}})
+    o_o = orc.OracleMesh(m_o)
+    U_o = o_o.prim_to_cons(W_r)
+    for _ in range(6):
+        U_o, _ = o_o.step(U_o, dt=dt)
+    assert rel_err(assemble(m_o, U_o), G_p, axis_var=0).max() > 1e-3
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_closed_box_conserves_mass_and_energy(orc, ndim):
+    """All walls reflecting on a 2-level mesh: no mass or energy crosses a
+    wall, so both totals stay constant to roundoff (momentum does not: the
+    walls push back)."""
+    mesh = mesh_2level(4, 8, 4, inputs.REFLECT, ndim=ndim)
+    om = orc.OracleMesh(mesh)
+    U0 = om.prim_to_cons(inputs.random_smooth_state(mesh, seed=8))
+    T0 = om.conserved_totals(U0)
+    U1, _, _ = om.run(U0.copy(), nsteps=15)
+    A = om.conserved_totals(np.abs(U1)) + om.conserved_totals(np.abs(U0))
+    d = np.abs(om.conserved_totals(U1) - T0) / np.where(A == 0, 1.0, A)
+    assert d[0] <= 1e-13 and d[4] <= 1e-13, d
