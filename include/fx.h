@@ -60,7 +60,7 @@ enum {
 };
 
 enum { FX_F64 = 0, FX_F32BULK = 1 };        /* state element type            */
-enum { FX_BC_OUTFLOW = 0, FX_BC_PERIODIC = 1 };
+enum { FX_BC_OUTFLOW = 0, FX_BC_PERIODIC = 1, FX_BC_REFLECT = 2 };
 
 /* fx_init: create a context for a perfect gas with ratio of specific heats
  * `gamma` (> 1), default block size `nxb` interior cells per axis (a
@@ -105,7 +105,10 @@ FX_API const char *fx_last_error(const fx_ctx *ctx);
  *               is a leaf iff it is nobody's parent; non-leaf blocks hold the
  *               restriction of their children;
  *   lo[3], hi[3] physical domain; bc[6] = {x-, x+, y-, y+, z-, z+}
- *               boundary kinds (FX_BC_*; periodic must be set on both sides);
+ *               boundary kinds (FX_BC_*; periodic must be set on both sides).
+ *               Outflow guards copy the nearest interior cell, periodic ones
+ *               wrap, reflecting ones take the mirror-image cell with the
+ *               wall-normal momentum negated (a solid slip wall);
  *   precision   FX_F64 or FX_F32BULK (element type of the state buffers);
  *   U0, U1      caller-owned device buffers of nblocks*5*PZ*P*P elements,
  *               16-byte aligned.  U0 holds the initial state; U1 receives the

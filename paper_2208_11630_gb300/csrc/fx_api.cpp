@@ -188,7 +188,8 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
   for (int d = 0; d < ndim; ++d) {
     if (nroot[d] < 1 || !(hi[d] > lo[d])) return fail(ctx, FX_ERR_ARG, "bad nroot or domain");
     for (int s = 0; s < 2; ++s)
-      if (bc[2 * d + s] != FX_BC_OUTFLOW && bc[2 * d + s] != FX_BC_PERIODIC)
+      if (bc[2 * d + s] != FX_BC_OUTFLOW && bc[2 * d + s] != FX_BC_PERIODIC &&
+          bc[2 * d + s] != FX_BC_REFLECT)
         return fail(ctx, FX_ERR_ARG, "bad boundary kind");
     if ((bc[2 * d] == FX_BC_PERIODIC) != (bc[2 * d + 1] == FX_BC_PERIODIC))
       return fail(ctx, FX_ERR_ARG, "periodic boundaries must be set on both sides of an axis");
@@ -285,7 +286,9 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
             const long long N = ncell[l][d];
             if (g[d] < 0 || g[d] >= N) {
               const int kind = bc[2 * d + (g[d] < 0 ? 0 : 1)];
-              g[d] = kind == FX_BC_PERIODIC ? ((g[d] % N) + N) % N : (g[d] < 0 ? 0 : N - 1);
+              if (kind == FX_BC_PERIODIC) g[d] = ((g[d] % N) + N) % N;
+              else if (kind == FX_BC_REFLECT) g[d] = g[d] < 0 ? -1 - g[d] : 2 * N - 1 - g[d];
+              else g[d] = g[d] < 0 ? 0 : N - 1;
             }
           }
           long long bcd[3] = {g[0] / n, g[1] / n, g[2] / n};

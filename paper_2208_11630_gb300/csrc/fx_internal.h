@@ -7,6 +7,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "fx.h"
+
 #define FX_MAXLEV 16
 
 namespace fx {

@@ -7,7 +7,7 @@
 // Paper: Flash-X (arXiv 2208.11630), Section 2 -- the Grid reconciles block
 // boundaries across refinement levels between the per-block physics updates.
 // Operators (textbook block-AMR): pairwise-mean restriction, same-level copy
-// with outflow/periodic boundaries, MC-limited conservative linear
+// with outflow/periodic/reflecting boundaries, MC-limited conservative linear
 // prolongation, Berger & Colella (1989) flux correction.
 #pragma once
 
@@ -22,9 +22,20 @@ __device__ __forceinline__ double ld(const S *p) { return static_cast<double>(*p
 template <typename S>
 __device__ __forceinline__ void st(S *p, double v) { *p = static_cast<S>(v); }
 
-__device__ __forceinline__ int apply_bc(int g, int N, int kind_lo, int kind_hi) {
-  if (g < 0) return kind_lo == 1 ? ((g % N) + N) % N : 0;
-  if (g >= N) return kind_hi == 1 ? g % N : N - 1;
+// Level-lattice index g mapped into [0, N) by the boundary kind of the side
+// it lies beyond: periodic wraps, reflecting mirrors about the wall (sets
+// `mirror`, the caller negates the wall-normal momentum), outflow clamps.
+__device__ __forceinline__ int apply_bc(int g, int N, int kind_lo, int kind_hi, bool &mirror) {
+  if (g < 0) {
+    if (kind_lo == FX_BC_PERIODIC) return ((g % N) + N) % N;
+    if (kind_lo == FX_BC_REFLECT) { mirror = true; return -1 - g; }
+    return 0;
+  }
+  if (g >= N) {
+    if (kind_hi == FX_BC_PERIODIC) return g % N;
+    if (kind_hi == FX_BC_REFLECT) { mirror = true; return 2 * N - 1 - g; }
+    return N - 1;
+  }
   return g;
 }
 
@@ -100,19 +111,23 @@ __device__ __forceinline__ void guard_copy_plane(const DevMesh &m, S *__restrict
     if (sx == 1 && sy == 1 && sz == 1) continue;
     const int2 s = sl[sx + 3 * sy + 9 * sz];
     if (s.x != SLOT_COPY) continue;
-    const int gx = apply_bc(ox + i - ng, m.ncell[lev][0], m.bc[0][0], m.bc[0][1]);
-    const int gy = apply_bc(oy + j - ng, m.ncell[lev][1], m.bc[1][0], m.bc[1][1]);
+    bool mir[3] = {false, false, false};
+    const int gx = apply_bc(ox + i - ng, m.ncell[lev][0], m.bc[0][0], m.bc[0][1], mir[0]);
+    const int gy = apply_bc(oy + j - ng, m.ncell[lev][1], m.bc[1][0], m.bc[1][1], mir[1]);
     const int src = s.y;
     const int lx = gx - m.origin[3 * src] + ng, ly = gy - m.origin[3 * src + 1] + ng;
     int lz = 0;
     if (m.ndim == 3) {
-      const int gz = apply_bc(oz + k - ng, m.ncell[lev][2], m.bc[2][0], m.bc[2][1]);
+      const int gz = apply_bc(oz + k - ng, m.ncell[lev][2], m.bc[2][0], m.bc[2][1], mir[2]);
       lz = gz - m.origin[3 * src + 2] + ng;
     }
     const S *Us = U + (long long)src * m.bstride + ((long long)lz * P + ly) * P + lx;
     S *Ud = Ub + ((long long)k * P + j) * P + i;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Ud[v * m.vstride] = Us[v * m.vstride];
+    for (int v = 0; v < 5; ++v) {
+      const S x = Us[v * m.vstride];
+      Ud[v * m.vstride] = (v >= 1 && v <= 3 && mir[v - 1]) ? -x : x;
+    }
   }
 }
 
@@ -152,9 +167,11 @@ __device__ __forceinline__ void guard_prolong_plane(const DevMesh &m, S *__restr
     const int2 s = sl[sx + 3 * sy + 9 * sz];
     if (s.x != SLOT_PROLONG) continue;
     int g[3];
-    g[0] = apply_bc(ox + i - ng, m.ncell[lev][0], m.bc[0][0], m.bc[0][1]);
-    g[1] = apply_bc(oy + j - ng, m.ncell[lev][1], m.bc[1][0], m.bc[1][1]);
-    g[2] = m.ndim == 3 ? apply_bc(oz + k - ng, m.ncell[lev][2], m.bc[2][0], m.bc[2][1]) : 0;
+    bool mir[3] = {false, false, false};
+    g[0] = apply_bc(ox + i - ng, m.ncell[lev][0], m.bc[0][0], m.bc[0][1], mir[0]);
+    g[1] = apply_bc(oy + j - ng, m.ncell[lev][1], m.bc[1][0], m.bc[1][1], mir[1]);
+    g[2] = m.ndim == 3 ? apply_bc(oz + k - ng, m.ncell[lev][2], m.bc[2][0], m.bc[2][1], mir[2])
+                       : 0;
     const int cb = s.y;
     const int cx = (g[0] >> 1) - m.origin[3 * cb] + ng;
     const int cy = (g[1] >> 1) - m.origin[3 * cb + 1] + ng;
@@ -172,6 +189,7 @@ __device__ __forceinline__ void guard_prolong_plane(const DevMesh &m, S *__restr
         const C off = (g[d] & 1) ? C(0.25) : C(-0.25);
         val = val + off * sig;
       }
+      if (v >= 1 && v <= 3 && mir[v - 1]) val = -val;
       Ud[v * m.vstride] = S(val);
     }
   }

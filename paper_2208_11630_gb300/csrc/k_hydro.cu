@@ -315,21 +315,32 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
       const int sx = gx < ng ? 0 : (gx >= ng + n ? 2 : 1);
       const int sy = gy < ng ? 0 : (gy >= ng + n ? 2 : 1);
       const S *src = Ub + ((long long)zpad * P + gy) * P + gx;
+      unsigned flip = 0;                 // velocity components mirrored at a wall
       if (sx != 1 || sy != 1 || sz != 1) {
         const int2 sl = slots[sx + 3 * sy + 9 * sz];
         if (sl.x == SLOT_COPY) {
-          const int N0 = m.ncell[lev][0], N1 = m.ncell[lev][1];
-          int ax = ox + gx - ng, ay = oy + gy - ng;
-          if (ax < 0) ax = m.bc[0][0] == 1 ? ax + N0 : 0;
-          else if (ax >= N0) ax = m.bc[0][1] == 1 ? ax - N0 : N0 - 1;
-          if (ay < 0) ay = m.bc[1][0] == 1 ? ay + N1 : 0;
-          else if (ay >= N1) ay = m.bc[1][1] == 1 ? ay - N1 : N1 - 1;
+          // outflow clamps, periodic wraps, reflecting mirrors (and negates
+          // the wall-normal velocity below)
+          auto map = [&](int a, int N, int d) {
+            if (a < 0) {
+              const int kind = m.bc[d][0];
+              if (kind == FX_BC_PERIODIC) return a + N;
+              if (kind == FX_BC_REFLECT) { flip |= 1u << d; return -1 - a; }
+              return 0;
+            }
+            if (a >= N) {
+              const int kind = m.bc[d][1];
+              if (kind == FX_BC_PERIODIC) return a - N;
+              if (kind == FX_BC_REFLECT) { flip |= 1u << d; return 2 * N - 1 - a; }
+              return N - 1;
+            }
+            return a;
+          };
+          const int ax = map(ox + gx - ng, m.ncell[lev][0], 0);
+          const int ay = map(oy + gy - ng, m.ncell[lev][1], 1);
           int lz = 0;
           if (NDIM == 3) {
-            const int N2 = m.ncell[lev][2];
-            int az = oz + zpad - ng;
-            if (az < 0) az = m.bc[2][0] == 1 ? az + N2 : 0;
-            else if (az >= N2) az = m.bc[2][1] == 1 ? az - N2 : N2 - 1;
+            const int az = map(oz + zpad - ng, m.ncell[lev][2], 2);
             lz = az - m.origin[3 * sl.y + 2] + ng;
           }
           const int lx = ax - m.origin[3 * sl.y] + ng, ly = ay - m.origin[3 * sl.y + 1] + ng;
@@ -338,6 +349,11 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
       }
       R w[6];
       prim<S, R>(src, vs, gm1, w);
+      if (flip) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+          if ((flip >> d) & 1u) w[1 + d] = -w[1 + d];
+      }
 #pragma unroll
       for (int v = 0; v < 6; ++v) dst[v * SM::W4 * SM::W4 + c] = w[v];
     }

@@ -23,6 +23,7 @@ FX_F64 = 0
 FX_F32BULK = 1
 FX_BC_OUTFLOW = 0
 FX_BC_PERIODIC = 1
+FX_BC_REFLECT = 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None

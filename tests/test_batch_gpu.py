@@ -13,7 +13,7 @@ import pytest
 
 from paper_2208_11630_gb300 import inputs
 from tests.helpers import leaf_interior, max_rel_err, max_rel_err_vec
-from tests.test_oracle_scheme import mesh_2level
+from tests.test_oracle_scheme import _wall_problem, mesh_2level
 
 pytestmark = pytest.mark.gpu
 
@@ -36,6 +36,8 @@ def _cases():
     m_sed = mesh_2level(4, 16, 4)
     m_32 = inputs.uniform_mesh(3, (2, 1, 1), 32, 4, inputs.PERIODIC)
     m_8 = inputs.uniform_mesh(3, (3, 3, 2), 8, 4, inputs.OUTFLOW)
+    m_wall, W_wall = _wall_problem(3, (2, 2, 2), 8, (0,), lambda c: c[0] == 0 and c[1] == 1,
+                                   24)[:2]
     return [
         ("kh_f64", m_kh, inputs.kh_state(m_kh), 0, 7),
         ("sod_f64", m_sod, inputs.sod_state(m_sod), 0, 12),
@@ -44,6 +46,8 @@ def _cases():
         ("nxb32_f32", m_32, inputs.random_smooth_state(m_32, 4), 1, 9),
         ("nxb8_f64", m_8, inputs.random_blocky_state(m_8, 5), 0, 4),
         ("kh_f32", m_kh, inputs.kh_state(m_kh), 1, 8),
+        ("reflect_f64", m_wall, W_wall, 0, 6),
+        ("reflect_f32", m_wall, W_wall, 1, 5),
     ]
 
 

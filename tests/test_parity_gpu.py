@@ -12,7 +12,7 @@ import pytest
 
 from paper_2208_11630_gb300 import inputs
 from tests.helpers import leaf_interior, max_rel_err
-from tests.test_oracle_scheme import mesh_2level, mesh_3level
+from tests.test_oracle_scheme import O_, P_, R_, _wall_problem, mesh_2level, mesh_3level
 
 pytestmark = pytest.mark.gpu
 
@@ -67,6 +67,16 @@ CASES = {
         inputs.uniform_mesh(3, (2, 1, 1), 24, 4, inputs.PERIODIC)),
     "smooth3d_nxb64": lambda: (lambda m: (m, inputs.random_smooth_state(m, 17)))(
         inputs.uniform_mesh(3, (1, 1, 1), 64, 4, inputs.PERIODIC)),
+    # reflecting walls: all sides, mixed with outflow and periodic, and with
+    # refined blocks against a wall (mirrored prolonged guards)
+    "reflect2d_blocky": lambda: (lambda m: (m, inputs.random_blocky_state(m, 18)))(
+        inputs.uniform_mesh(2, (4, 3), 16, 4, inputs.REFLECT)),
+    "reflect3d_mixed": lambda: (lambda m: (m, inputs.random_smooth_state(m, 19)))(
+        inputs.uniform_mesh(3, (3, 2, 2), 16, 4, ((R_, O_), (P_, P_), (O_, R_)))),
+    "amr_reflect_wall": lambda: _wall_problem(3, (2, 2, 2), 8, (0,),
+                                              lambda c: c[0] == 0 and c[1] == 1, 22)[:2],
+    "amr_2d_reflect_wall": lambda: _wall_problem(2, (4, 4), 16, (0, 1),
+                                                 lambda c: c[0] == 0 and c[1] in (1, 2), 23)[:2],
 }
 
 
@@ -136,7 +146,9 @@ def test_one_step(orc, fx, case):
                                          ("amr_sedov_small", 100), ("amr_smooth_periodic", 100),
                                          ("amr_2d_blocky", 100), ("smooth3d_nxb32", 100),
                                          ("amr_3level_sedov", 100), ("amr_3level_periodic", 100),
-                                         ("smooth3d_nxb24", 100)])
+                                         ("smooth3d_nxb24", 100), ("reflect2d_blocky", 100),
+                                         ("reflect3d_mixed", 100), ("amr_reflect_wall", 100),
+                                         ("amr_2d_reflect_wall", 100)])
 def test_many_steps(orc, fx, case, nsteps):
     mesh, W = CASES[case]()
     om, U, bs = both_start(orc, fx, mesh, W)
@@ -324,7 +336,8 @@ def test_full_size_sedov_amr(orc, fx):
 
 
 @pytest.mark.parametrize("case", ["sod2d", "kh64", "blocky2d_nxb8", "amr_smooth_periodic",
-                                  "amr_sedov_small", "amr_3level_periodic", "smooth3d_nxb32"])
+                                  "amr_sedov_small", "amr_3level_periodic", "smooth3d_nxb32",
+                                  "amr_reflect_wall"])
 def test_rk2_variant(orc, fx, case):
     """SSP-RK2 with PLM and HLLC (integrator option 1) against the oracle's
     SSP-RK2: one step at 1e-12, thirty more at 1e-10; totals conserved on
