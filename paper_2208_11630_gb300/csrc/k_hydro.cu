@@ -105,7 +105,8 @@ __device__ __forceinline__ float scaled_diff(float a, float b, float c) {
 // HLLC flux along direction D from primitive left/right states.  One
 // reciprocal square root per side gives both the sound speed and 1/rho:
 // r = (gamma p rho)^(-1/2), c = gamma p r, 1/rho = c r.  The star state of the
-// upwind side K needs two divisions: S* and 1/(S_K - S*).
+// upwind side K needs S* and 1/(S_K - S*): one FP64 reciprocal, or two FP32
+// fast divisions.
 template <int D, typename R>
 __device__ __forceinline__ void hllc(const R (&WL)[5], const R (&WR)[5], R g, R igm1,
                                      R (&F)[5]) {
@@ -118,10 +119,24 @@ __device__ __forceinline__ void hllc(const R (&WL)[5], const R (&WR)[5], R g, R 
   const R SL = fmin(uL - cL, uR - cR);
   const R SR = fmax(uL + cL, uR + cR);
   const R dL = SL - uL, dR = SR - uR;
-  const R Sst = div_r(pR - pL + rL * uL * dL - rR * uR * dR, rL * dL - rR * dR);
+  // S* = A / B.  FP64: its sign (A = 0 or A, B of equal sign <=> S* >= 0)
+  // picks the side, and S* and 1/(S_K - S*) both come from one reciprocal
+  // below; FP32: two fast divisions.
+  const R A = pR - pL + rL * uL * dL - rR * uR * dR;
+  const R B = rL * dL - rR * dR;
+  constexpr bool kF64 = std::is_same<R, double>::value;
+  R Sst = R(0);
+  bool sst_ge0;
+  if constexpr (kF64) {
+    const long long ia = __double_as_longlong(A), ib = __double_as_longlong(B);
+    sst_ge0 = (ia << 1) == 0 || (ia ^ ib) >= 0;
+  } else {
+    Sst = div_r(A, B);
+    sst_ge0 = ge0(Sst);
+  }
   // Branches: S_L >= 0 -> F_L; S* >= 0 -> F*_L; S_R > 0 -> F*_R; else F_R.
   const bool caseA = ge0(SL);
-  const bool useL = caseA || ge0(Sst);
+  const bool useL = caseA || sst_ge0;
   const bool star = !caseA && (useL || gt0(SR));
   R W[5];
 #pragma unroll
@@ -140,7 +155,17 @@ __device__ __forceinline__ void hllc(const R (&WL)[5], const R (&WR)[5], R g, R 
   F[4] = uK * (EK + pK);
   if (star) {
     const R dK = SK - uK;
-    const R inv = div_r(R(1), SK - Sst);
+    R inv;
+    if constexpr (kF64) {
+      // S_K - S* = D / B with D = S_K B - A:  r = 1/(B D), S* = A D r,
+      // 1/(S_K - S*) = B B r
+      const R D = SK * B - A;
+      const R r = R(1) / (B * D);
+      Sst = A * D * r;
+      inv = B * B * r;
+    } else {
+      inv = div_r(R(1), SK - Sst);
+    }
     const R fac = rK * dK * inv;                       // rho*_K
     const R ds = Sst - uK;
     R Us[5];
@@ -301,6 +326,13 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
   // neighbour's interior (the value the guard copy would have written); a
   // slot covered by a coarser leaf is read from this block's own guards,
   // which the prolongation pass filled.
+  // Work of one plane beyond one item per thread, spread over disjoint warps
+  // so that no warp carries two extras into a barrier: the halo predictor
+  // (4T cells) runs on threads [0, 4T), the last partial round of x/y faces
+  // on the threads right after them, the last partial round of the plane
+  // load on the highest threads.
+  constexpr int kLoadTail = (SM::W4 * SM::W4) % NT;
+  constexpr int kFaceShift = NT - 4 * T;
   __shared__ int2 slots[27];
   if (tid < 27) slots[tid] = m.slots[b * 27 + tid];
   __syncthreads();
@@ -309,7 +341,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
     R *dst = ring + slot * SM::RING;
     const int zpad = p + zoff;
     const int sz = NDIM == 3 ? (zpad < ng ? 0 : (zpad >= ng + n ? 2 : 1)) : 1;
-    for (int c = tid; c < SM::W4 * SM::W4; c += NT) {
+    for (int c = (tid + kLoadTail) % NT; c < SM::W4 * SM::W4; c += NT) {
       const int ii = c % SM::W4, jj = c / SM::W4;
       const int gx = x0 + ii - 2 + ng, gy = y0 + jj - 2 + ng;
       const int sx = gx < ng ? 0 : (gx >= ng + n ? 2 : 1);
@@ -458,7 +490,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
     // state), z face below the thread's own cell
     const int zglob = p;  // interior z index of this plane
     if (inner) {
-      for (int f = tid; f < 2 * (T + 1) * T; f += NT) {
+      for (int f = (tid + kFaceShift) % NT; f < 2 * (T + 1) * T; f += NT) {
         const int dir = f >= (T + 1) * T;
         const int ff = dir ? f - (T + 1) * T : f;
         // a: face index along the normal (0..T), e: transverse index; the
