@@ -207,6 +207,21 @@ FX_API int fx_status(fx_ctx *ctx, fx_blocks *bs);
 FX_API int fx_run_host(fx_ctx *ctx, fx_blocks *bs, const void *U_host_in, void *U_host_out,
                 int nsteps, double cfl, double *t_host, void *stream);
 
+/* fx_run_host_interior: like fx_run_host, for callers that hold only the
+ * interior cells: W_in and W_out are packed conserved states
+ * [nblocks][5][nz][nxb][nxb] (nz = nxb in 3D, 1 in 2D; x fastest; element
+ * type of the block set's precision), page-locked host memory recommended.
+ * Guard cells never cross the host link (they are rebuilt by the guard fill),
+ * so each direction moves (nxb/(nxb+2 nguard))^ndim of fx_run_host's bytes.
+ * On a single-level block set the last step's update runs in chunks of
+ * blocks whose interiors are downloaded while later chunks compute.  The
+ * first call allocates a device staging buffer of the packed size and two
+ * streams; they live as long as the block set.  Results equal fx_run_host's
+ * bit for bit.  Synchronises.  Errors: FX_ERR_ARG, FX_ERR_STATE (block set
+ * in a batch), FX_ERR_OOM, FX_ERR_CUDA. */
+FX_API int fx_run_host_interior(fx_ctx *ctx, fx_blocks *bs, const void *W_in, void *W_out,
+                                int nsteps, double cfl, double *t_host, void *stream);
+
 /* fx_block_fluxes: device pointer to the flux registers of block `b`
  * ([2*ndim faces x-,x+,y-,y+,z-,z+][5][nxb^(ndim-1)], lower transverse axis
  * fastest) written by the last fx_hydro_advance, or NULL if the block has no

@@ -67,6 +67,11 @@ struct fx_blocks {
   int *d_status = nullptr;
   double *d_dt = nullptr;                   // dt scratch for fx_run_host
   double *d_totals = nullptr;               // [nleaves][5]
+  // fx_run_host_interior: packed interior staging buffer and the streams and
+  // events of the overlapped download (created on first use)
+  void *d_pack = nullptr;
+  cudaStream_t aux[2] = {nullptr, nullptr}, cpy = nullptr;
+  cudaEvent_t ev_ready = nullptr, ev_done = nullptr, ev_chunk[8] = {};
 };
 
 namespace fx {
@@ -107,6 +112,15 @@ void free_blocks(fx_blocks *bs) {
   cudaFree(bs->d_regidx); cudaFree(bs->d_slots); cudaFree(bs->d_lists);
   cudaFree(bs->d_regs); cudaFree(bs->d_refl); cudaFree(bs->d_scratch);
   cudaFree(bs->d_status); cudaFree(bs->d_dt); cudaFree(bs->d_totals); cudaFree(bs->d_rmask);
+  if (bs->cpy) cudaStreamSynchronize(bs->cpy);
+  for (cudaStream_t a : bs->aux)
+    if (a) { cudaStreamSynchronize(a); cudaStreamDestroy(a); }
+  if (bs->cpy) cudaStreamDestroy(bs->cpy);
+  if (bs->ev_ready) cudaEventDestroy(bs->ev_ready);
+  if (bs->ev_done) cudaEventDestroy(bs->ev_done);
+  for (cudaEvent_t e : bs->ev_chunk)
+    if (e) cudaEventDestroy(e);
+  cudaFree(bs->d_pack);
 }
 
 struct Lattice {
@@ -652,6 +666,122 @@ int fx_run_host(fx_ctx *ctx, fx_blocks *bs, const void *U_host_in, void *U_host_
     }
   }
   FX_CUDA(cudaMemcpyAsync(U_host_out, bs->U[bs->cur], bytes, cudaMemcpyDeviceToHost, s), "state download");
+  FX_CUDA(cudaStreamSynchronize(s), "run sync");
+  if (t_host) *t_host = t;
+  return FX_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+constexpr int kPipeChunks = 8;
+
+// Bytes of one block's interior cells (all five variables).
+size_t interior_block_bytes(const fx_blocks *bs) {
+  return 5 * (size_t)bs->nxb * bs->nxb * (bs->ndim == 3 ? bs->nxb : 1) * bs->elsize;
+}
+
+int ensure_pipeline(fx_blocks *bs) {
+  if (bs->d_pack) return FX_OK;
+  // streams and events first; the staging buffer last marks completion
+  for (cudaStream_t &a : bs->aux)
+    if (!a) FX_CUDA(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking), "stream create");
+  if (!bs->cpy) FX_CUDA(cudaStreamCreateWithFlags(&bs->cpy, cudaStreamNonBlocking), "stream create");
+  if (!bs->ev_ready)
+    FX_CUDA(cudaEventCreateWithFlags(&bs->ev_ready, cudaEventDisableTiming), "event create");
+  if (!bs->ev_done)
+    FX_CUDA(cudaEventCreateWithFlags(&bs->ev_done, cudaEventDisableTiming), "event create");
+  for (cudaEvent_t &e : bs->ev_chunk)
+    if (!e) FX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event create");
+  if (cudaMalloc(&bs->d_pack, interior_block_bytes(bs) * bs->nb) != cudaSuccess) {
+    bs->d_pack = nullptr;
+    cudaGetLastError();
+    return fail(bs->ctx, FX_ERR_OOM, "cudaMalloc of the interior staging buffer failed");
+  }
+  return FX_OK;
+}
+
+// Update of a single-level block set whose leaves are all its blocks, in
+// chunks of consecutive blocks on two alternating streams (so that one
+// chunk's last CTAs overlap the next chunk's first); each chunk's interior
+// is gathered and copied to the host as soon as it is done, overlapping the
+// download with the rest of the update.  Same kernels and results as
+// fx_hydro_advance.
+int advance_and_download(fx_ctx *ctx, fx_blocks *bs, cudaStream_t s, void *W_out) {
+  void *Uo = bs->U[bs->cur], *Un = bs->U[1 - bs->cur];
+  unsigned long long *smax = bs->d_scratch + 2;
+  const size_t pb = interior_block_bytes(bs);
+  const int K = bs->nleaves < kPipeChunks ? bs->nleaves : kPipeChunks;
+  FX_CUDA(cudaMemsetAsync(smax, 0, sizeof(unsigned long long), s), "signal max reset");
+  FX_CUDA(cudaEventRecord(bs->ev_ready, s), "event record");
+  for (int c = 0; c < K; ++c) {
+    const int b0 = (int)((long long)bs->nleaves * c / K);
+    const int b1 = (int)((long long)bs->nleaves * (c + 1) / K);
+    cudaStream_t a = bs->aux[c & 1];
+    if (c < 2) FX_CUDA(cudaStreamWaitEvent(a, bs->ev_ready, 0), "stream wait");
+    FX_CUDA(fx::launch_hydro(bs->dm, Uo, Un, bs->prec, bs->d_lists + bs->leaves_off + b0, b1 - b0,
+                             bs->d_dt, bs->d_regs, bs->d_status, smax, nullptr, ctx->cfl_form, a),
+            "hydro launch");
+    char *pk = static_cast<char *>(bs->d_pack) + pb * b0;
+    FX_CUDA(fx::launch_pack(bs->dm, Un, bs->prec, pk, b0, b1 - b0, 1, a), "pack launch");
+    FX_CUDA(cudaEventRecord(bs->ev_chunk[c], a), "event record");
+    FX_CUDA(cudaStreamWaitEvent(bs->cpy, bs->ev_chunk[c], 0), "stream wait");
+    FX_CUDA(cudaMemcpyAsync(static_cast<char *>(W_out) + pb * b0, pk, pb * (b1 - b0),
+                            cudaMemcpyDeviceToHost, bs->cpy),
+            "state download");
+  }
+  FX_CUDA(cudaEventRecord(bs->ev_done, bs->cpy), "event record");
+  FX_CUDA(cudaStreamWaitEvent(s, bs->ev_done, 0), "stream wait");
+  bs->cur = 1 - bs->cur;
+  ++bs->epoch;
+  bs->next_epoch = bs->epoch;
+  bs->next_form = ctx->cfl_form;
+  return FX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fx_run_host_interior(fx_ctx *ctx, fx_blocks *bs, const void *W_in, void *W_out, int nsteps,
+                         double cfl, double *t_host, void *stream) {
+  if (!ctx || !bs || !W_in || !W_out || nsteps < 0 || !(cfl > 0.0)) return FX_ERR_ARG;
+  if (bs->in_batch) return fail(ctx, FX_ERR_STATE, "block set is owned by a batch");
+  int rc = ensure_pipeline(bs);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = interior_block_bytes(bs) * bs->nb;
+  FX_CUDA(cudaMemcpyAsync(bs->d_pack, W_in, bytes, cudaMemcpyHostToDevice, s), "state upload");
+  FX_CUDA(fx::launch_pack(bs->dm, bs->U[bs->cur], bs->prec, bs->d_pack, 0, bs->nb, 0, s),
+          "unpack launch");
+  ++bs->epoch;
+  const bool single_level = bs->lmax == 0 && bs->nrefl == 0 && bs->nleaves == bs->nb &&
+                            ctx->integrator == 0;
+  bool downloaded = false;
+  double t = 0.0;
+  for (int i = 0; i < nsteps; ++i) {
+    if (i == nsteps - 1 && single_level) {
+      rc = fx_compute_dt(ctx, bs, cfl, bs->d_dt, stream);
+      if (!rc) rc = fx_guardcell_fill_amr(ctx, bs, stream);
+      if (!rc) rc = advance_and_download(ctx, bs, s, W_out);
+      downloaded = true;
+    } else {
+      rc = fx_step(ctx, bs, cfl, bs->d_dt, stream);
+    }
+    if (rc) return rc;
+    if (t_host) {
+      double dt = 0.0;
+      FX_CUDA(cudaMemcpyAsync(&dt, bs->d_dt, sizeof(double), cudaMemcpyDeviceToHost, s), "dt copy");
+      FX_CUDA(cudaStreamSynchronize(s), "dt sync");
+      t += dt;
+    }
+  }
+  if (!downloaded) {
+    FX_CUDA(fx::launch_pack(bs->dm, bs->U[bs->cur], bs->prec, bs->d_pack, 0, bs->nb, 1, s),
+            "pack launch");
+    FX_CUDA(cudaMemcpyAsync(W_out, bs->d_pack, bytes, cudaMemcpyDeviceToHost, s), "state download");
+  }
   FX_CUDA(cudaStreamSynchronize(s), "run sync");
   if (t_host) *t_host = t;
   return FX_OK;

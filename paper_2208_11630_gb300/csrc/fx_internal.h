@@ -70,6 +70,11 @@ cudaError_t launch_prim_to_cons(const DevMesh &m, const double *W, void *U, int 
                                 cudaStream_t s);
 cudaError_t launch_restrict(const DevMesh &m, void *U, int prec, const int *parents, int n,
                             cudaStream_t s);
+// Interior cells of blocks [b0, b0 + nblk): dir 0 scatters a packed array
+// [block][var][z][y][x] (relative to b0) into the padded layout, dir 1
+// gathers them into it.
+cudaError_t launch_pack(const DevMesh &m, void *U, int prec, void *packed, int b0, int nblk,
+                        int dir, cudaStream_t s);
 // Guard fills touch only guard cells within `depth` (Chebyshev distance) of
 // the interior; prolongation of FP32 state computes in FP32 when
 // state_precision_math is set (else FP64).

@@ -58,6 +58,30 @@ __global__ void k_guard_prolong(DevMesh m, S *__restrict__ U, const int *__restr
   ops::guard_prolong_plane<S, C>(m, U, leaves[blockIdx.x], blockIdx.y, depth);
 }
 
+// Interior cells of blocks [b0, b0 + nblk) between the padded block layout
+// and a packed array [block][var][z][y][x] of interior cells (packed index
+// relative to block b0).  dir 0: packed -> padded; 1: padded -> packed.
+template <typename S>
+__global__ void k_pack(DevMesh m, S *__restrict__ U, S *__restrict__ Pk, int b0, int nblk,
+                       int dir) {
+  const int n = m.nxb, ng = m.ng, P = m.P;
+  const int nz = m.ndim == 3 ? n : 1, gz = m.ndim == 3 ? ng : 0;
+  const long long per_var = (long long)nz * n * n;
+  const long long total = (long long)nblk * 5 * per_var;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < total;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % n), j = (int)((c / n) % n);
+    const long long r = c / ((long long)n * n);
+    const int k = (int)(r % nz);
+    const long long bv = r / nz;
+    const int v = (int)(bv % 5);
+    const long long b = b0 + bv / 5;
+    S *u = U + b * m.bstride + v * m.vstride + ((long long)(k + gz) * P + (j + ng)) * P + (i + ng);
+    if (dir == 0) *u = Pk[c];
+    else Pk[c] = *u;
+  }
+}
+
 template <typename S>
 cudaError_t prim_to_cons_t(const DevMesh &m, const double *W, void *U, cudaStream_t s) {
   long long total = (long long)m.nb * m.vstride;
@@ -73,6 +97,23 @@ cudaError_t prim_to_cons_t(const DevMesh &m, const double *W, void *U, cudaStrea
 cudaError_t launch_prim_to_cons(const DevMesh &m, const double *W, void *U, int prec,
                                 cudaStream_t s) {
   return prec == 0 ? prim_to_cons_t<double>(m, W, U, s) : prim_to_cons_t<float>(m, W, U, s);
+}
+
+cudaError_t launch_pack(const DevMesh &m, void *U, int prec, void *packed, int b0, int nblk,
+                        int dir, cudaStream_t s) {
+  if (nblk <= 0) return cudaSuccess;
+  const long long total =
+      (long long)nblk * 5 * m.nxb * m.nxb * (m.ndim == 3 ? m.nxb : 1);
+  long long grid = (total + 255) / 256;
+  if (grid > 152 * 16) grid = 152 * 16;
+  if (prec == 0)
+    k_pack<double><<<(int)grid, 256, 0, s>>>(m, static_cast<double *>(U),
+                                             static_cast<double *>(packed), b0, nblk, dir);
+  else
+    k_pack<float><<<(int)grid, 256, 0, s>>>(m, static_cast<float *>(U),
+                                            static_cast<float *>(packed), b0, nblk, dir);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_restrict(const DevMesh &m, void *U, int prec, const int *parents, int n,

@@ -72,6 +72,7 @@ def load(build: bool = True):
             "fx_conserved_totals": (c_int, [vp, vp, dp, vp]),
             "fx_status": (c_int, [vp, vp]),
             "fx_run_host": (c_int, [vp, vp, vp, vp, c_int, c_double, dp, vp]),
+            "fx_run_host_interior": (c_int, [vp, vp, vp, vp, c_int, c_double, dp, vp]),
             "fx_block_fluxes": (vp, [vp, c_int]),
             "fx_kernel_launches": (ctypes.c_longlong, []),
             "fx_batch_create": (c_int, [vp, c_int, ctypes.POINTER(vp)]),
@@ -200,6 +201,17 @@ def fx_run_host(ctx, bs, host_in: np.ndarray, host_out: np.ndarray, nsteps: int,
     _check(ctx, load().fx_run_host(ctx, bs, ctypes.c_void_p(host_in.ctypes.data),
                                    ctypes.c_void_p(host_out.ctypes.data), int(nsteps), float(cfl),
                                    tp, _stream_ptr(stream)))
+    return float(t[0]) if want_time else None
+
+
+def fx_run_host_interior(ctx, bs, host_in: np.ndarray, host_out: np.ndarray, nsteps: int,
+                         cfl: float, stream=None, want_time: bool = False):
+    """``host_in``/``host_out``: packed interior cells ``[nb, 5, nz, n, n]``."""
+    t = np.zeros(1)
+    tp = t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if want_time else None
+    _check(ctx, load().fx_run_host_interior(ctx, bs, ctypes.c_void_p(host_in.ctypes.data),
+                                            ctypes.c_void_p(host_out.ctypes.data), int(nsteps),
+                                            float(cfl), tp, _stream_ptr(stream)))
     return float(t[0]) if want_time else None
 
 
@@ -352,6 +364,23 @@ class BlockSet:
     def run(self, nsteps: int, cfl: float = 0.8, stream=None):
         for _ in range(nsteps):
             self.step(cfl, stream)
+
+    def interior_shape(self) -> tuple:
+        m = self.mesh
+        return (m.nb, 5, m.nxb if m.ndim == 3 else 1, m.nxb, m.nxb)
+
+    def run_host_interior(self, host_in: np.ndarray, host_out: np.ndarray, nsteps: int = 1,
+                          cfl: float = 0.8, stream=None, want_time: bool = False):
+        """fx_run_host_interior with shape and dtype checks: ``host_in`` and
+        ``host_out`` are C-contiguous ``interior_shape()`` arrays of the block
+        set's element type (page-locked memory recommended)."""
+        want = np.dtype(np.float64 if self.precision == FX_F64 else np.float32)
+        for a in (host_in, host_out):
+            if a.shape != self.interior_shape() or a.dtype != want or not a.flags.c_contiguous:
+                raise ValueError(f"expected a C-contiguous {want} array of shape "
+                                 f"{self.interior_shape()}, got {a.dtype} {a.shape}")
+        return fx_run_host_interior(self.ctx, self.bs, host_in, host_out, nsteps, cfl, stream,
+                                    want_time)
 
     def totals(self, stream=None) -> np.ndarray:
         return fx_conserved_totals(self.ctx, self.bs, stream)
