@@ -65,6 +65,8 @@ def lib():
             L.or_restrict_parents.argtypes = [ctypes.c_void_p, dp]
             L.or_hydro_advance_rk2.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_double,
                                                ctypes.c_int, dp]
+            L.or_hydro_advance_rk3.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_double,
+                                               ctypes.c_int, dp]
             L.or_mc.restype = ctypes.c_double
             L.or_mc.argtypes = [ctypes.c_double, ctypes.c_double]
             L.or_hllc.argtypes = [dp, dp, ctypes.c_int, ctypes.c_double, dp]
@@ -144,7 +146,7 @@ class OracleMesh:
                       want_bflux: bool = False, select=None, integrator: int = 0):
         """Advance the leaves one step from ``U`` (guards filled).  Returns
         ``(Unew, status, bflux)``; ``Unew`` starts as a copy of ``U``.
-        integrator 0: MUSCL-Hancock; 1: SSP-RK2 (no ``select``)."""
+        integrator 0: MUSCL-Hancock; 1: SSP-RK2; 2: SSP-RK3 (no ``select``)."""
         m = self.mesh
         Unew = U.copy()
         bflux = None
@@ -155,6 +157,9 @@ class OracleMesh:
             bptr = _dp(bflux)
         if integrator == 1:
             st = lib().or_hydro_advance_rk2(self._h, _dp(U), _dp(Unew), float(dt), int(reflux), bptr)
+            return Unew, st, bflux
+        if integrator == 2:
+            st = lib().or_hydro_advance_rk3(self._h, _dp(U), _dp(Unew), float(dt), int(reflux), bptr)
             return Unew, st, bflux
         if select is not None:
             sel = np.ascontiguousarray(select, dtype=np.int32)

@@ -94,6 +94,16 @@ int or_hydro_advance(const or_mesh *m, const double *U, double *Unew, double dt,
 int or_hydro_advance_rk2(const or_mesh *m, const double *U, double *Unew, double dt, int reflux,
                          double *bflux);
 
+/* SSP-RK3 variant (Shu-Osher three-stage form, the third-order member of the
+ * same family): U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1));
+ * Unew = 1/3 U + 2/3 (U2 + dt L(U2)), guard fills of U1 and U2, flux
+ * correction with the fluxes weighted 1/6, 1/6, 2/3.  Pinned: scalar-advection
+ * special case (textbook SSP-RK3 + MC-PLM), third-order temporal convergence
+ * on smooth data, conservation (periodic, AMR with correction), uniform
+ * state. */
+int or_hydro_advance_rk3(const or_mesh *m, const double *U, double *Unew, double dt, int reflux,
+                         double *bflux);
+
 /* Restriction of every non-leaf block from its children, finest level first:
  * each parent cell is the pairwise mean (x pairs, then y, then z) of the
  * 2^d child cells it covers.  Pinned: uniform state, linear-field exactness

@@ -440,11 +440,12 @@ static size_t wi(const or_mesh *m, int v, int k, int j, int i) {
   return (((size_t)v * m->PZ + k) * m->P + j) * m->P + i;
 }
 
-/* One leaf: Unew = U + dt L(U), or with Uavg != NULL the second SSP-RK2
- * stage Unew = (Uavg + (U + dt L(U))) / 2.  predictor = 1: MUSCL-Hancock face
+/* One leaf: Unew = U + dt L(U), or with Uavg != NULL an SSP-RK stage
+ * Unew = wa Uavg + wb (U + dt L(U)).  predictor = 1: MUSCL-Hancock face
  * states; 0: plain MC-limited PLM face states (method-of-lines). */
 static int advance_block(const or_mesh *m, const double *U, double *Unew, double dt, int b,
-                         or_work *w, double *bflux, int predictor, const double *Uavg) {
+                         or_work *w, double *bflux, int predictor, const double *Uavg,
+                         double wa, double wb) {
   int P = m->P, PZ = m->PZ, ng = m->ng, n = m->nxb, nd = m->ndim;
   size_t per = (size_t)5 * PZ * P * P;
   double gamma = m->gamma;
@@ -543,7 +544,7 @@ static int advance_block(const or_mesh *m, const double *U, double *Unew, double
             div = div + (fl - fr) / dx[d];
           }
           un[v] = U[cell_index(m, b, v, k, j, i)] + dt * div;
-          if (Uavg) un[v] = 0.5 * (Uavg[cell_index(m, b, v, k, j, i)] + un[v]);
+          if (Uavg) un[v] = wa * Uavg[cell_index(m, b, v, k, j, i)] + wb * un[v];
           Unew[cell_index(m, b, v, k, j, i)] = un[v];
         }
         double q[5];
@@ -681,7 +682,7 @@ int or_hydro_advance(const or_mesh *m, const double *U, double *Unew, double dt,
     for (int t = 0; t < count; t++) {
       int b = sel ? sel[t] : t;
       if (!m->leaf[b]) continue;
-      bad |= advance_block(m, U, Unew, dt, b, &w, flux, 1, NULL);
+      bad |= advance_block(m, U, Unew, dt, b, &w, flux, 1, NULL, 0.0, 1.0);
     }
     free(w.W); free(w.FSm); free(w.FSp); free(w.F);
   }
@@ -742,8 +743,8 @@ int or_hydro_advance_rk2(const or_mesh *m, const double *U, double *Unew, double
 #pragma omp for schedule(dynamic)
       for (int b = 0; b < m->nb; b++) {
         if (!m->leaf[b]) continue;
-        if (stage == 0) bad |= advance_block(m, U, U1, dt, b, &w, f1, 0, NULL);
-        else bad |= advance_block(m, U1, Unew, dt, b, &w, f2, 0, U);
+        if (stage == 0) bad |= advance_block(m, U, U1, dt, b, &w, f1, 0, NULL, 0.0, 1.0);
+        else bad |= advance_block(m, U1, Unew, dt, b, &w, f2, 0, U, 0.5, 0.5);
       }
       free(w.W); free(w.FSm); free(w.FSp); free(w.F);
     }
@@ -775,6 +776,87 @@ int or_hydro_advance_rk2(const or_mesh *m, const double *U, double *Unew, double
   }
   if (bflux) memcpy(bflux, f1, sizeof(double) * nfl);
   free(U1); free(f1); free(f2);
+  return bad ? -4 : 0;
+}
+
+/* Positivity of the leaf interiors of U (0 if every cell has rho > 0, p > 0). */
+static int leaves_positive(const or_mesh *m, const double *U) {
+  int nd = m->ndim, n = m->nxb;
+  int nz = nd == 3 ? n : 1, kz = nd == 3 ? m->ng : 0;
+  for (int b = 0; b < m->nb; b++) {
+    if (!m->leaf[b]) continue;
+    for (int k = 0; k < nz; k++)
+      for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) {
+          double u[5], q[5];
+          for (int v = 0; v < 5; v++) u[v] = U[cell_index(m, b, v, k + kz, j + m->ng, i + m->ng)];
+          prim_from_cons(u, m->gamma, q);
+          if (!(q[0] > 0.0) || !(q[4] > 0.0)) return 1;
+        }
+  }
+  return 0;
+}
+
+/* SSP-RK3 of Shu and Osher (1988) with MC-limited PLM and HLLC, the
+ * third-order member of the Spark family (Section 2.2):
+ *   U1 = U + dt L(U)
+ *   U2 = 3/4 U + 1/4 (U1 + dt L(U1))
+ *   Unew = 1/3 U + 2/3 (U2 + dt L(U2)),
+ * with a guard fill of U1 and of U2.  Unrolled, Unew = U + dt (L(U)/6 +
+ * L(U1)/6 + 2 L(U2)/3), so the coarse-fine correction uses the fluxes
+ * weighted 1/6, 1/6, 2/3 on both sides. */
+int or_hydro_advance_rk3(const or_mesh *m, const double *U, double *Unew, double dt, int reflux,
+                         double *bflux) {
+  size_t per = (size_t)5 * m->PZ * m->P * m->P;
+  size_t tot = per * (size_t)m->nb;
+  int nd = m->ndim, n = m->nxb;
+  int nf = nd == 3 ? n * n : n;
+  size_t nfl = (size_t)m->nb * 2 * nd * 5 * nf;
+  double *U1 = (double *)malloc(sizeof(double) * tot);
+  double *U2 = (double *)malloc(sizeof(double) * tot);
+  double *f[3];
+  for (int q = 0; q < 3; q++) f[q] = (double *)calloc(nfl, sizeof(double));
+  memcpy(U1, U, sizeof(double) * tot);
+  memcpy(U2, U, sizeof(double) * tot);
+  const double wa[3] = {0.0, 0.75, 1.0 / 3.0}, wb[3] = {1.0, 0.25, 2.0 / 3.0};
+  const double *src[3] = {U, U1, U2};
+  double *dst[3] = {U1, U2, Unew};
+  int bad = 0;
+  for (int stage = 0; stage < 3; stage++) {
+#pragma omp parallel num_threads(or_get_threads()) reduction(| : bad)
+    {
+      or_work w;
+      w.W = (double *)malloc(sizeof(double) * per);
+      w.FSm = (double *)malloc(sizeof(double) * per * 3);
+      w.FSp = (double *)malloc(sizeof(double) * per * 3);
+      w.F = (double *)malloc(sizeof(double) * per * 3);
+#pragma omp for schedule(dynamic)
+      for (int b = 0; b < m->nb; b++) {
+        if (!m->leaf[b]) continue;
+        bad |= advance_block(m, src[stage], dst[stage], dt, b, &w, f[stage], 0,
+                             stage ? U : NULL, wa[stage], wb[stage]);
+      }
+      free(w.W); free(w.FSm); free(w.FSp); free(w.F);
+    }
+    if (stage < 2) {
+      or_restrict_parents(m, dst[stage]);
+      if (or_guardcell_fill(m, dst[stage])) bad = 1;
+    }
+  }
+  for (size_t q = 0; q < nfl; q++)
+    f[0][q] = (f[0][q] + f[1][q]) * (1.0 / 6.0) + f[2][q] * (2.0 / 3.0);
+  if (m->lmax > 0) {
+    if (reflux) {
+#pragma omp parallel for schedule(dynamic) num_threads(or_get_threads())
+      for (int b = 0; b < m->nb; b++)
+        if (m->leaf[b]) reflux_block(m, Unew, dt, b, f[0]);
+    }
+    or_restrict_parents(m, Unew);
+  }
+  if (!bad) bad = leaves_positive(m, Unew);
+  if (bflux) memcpy(bflux, f[0], sizeof(double) * nfl);
+  free(U1); free(U2);
+  for (int q = 0; q < 3; q++) free(f[q]);
   return bad ? -4 : 0;
 }
 

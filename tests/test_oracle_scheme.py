@@ -632,6 +632,101 @@ def test_rk2_conservation_uniform_and_amr(orc):
     assert np.array_equal(leaf_interior(mesh, U), leaf_interior(mesh, U0))
 
 
+def test_rk3_scalar_advection_special_case(orc):
+    """With uniform velocity and pressure the SSP-RK3 mass update is the
+    textbook Shu-Osher scheme on MC-limited upwind PLM:
+    r1 = r + L(r), r2 = 3/4 r + 1/4 (r1 + L(r1)), r_new = 1/3 r + 2/3 (r2 + L(r2))."""
+    mesh = inputs.uniform_mesh(2, (4, 1), 16, 4, inputs.PERIODIC)
+    om = orc.OracleMesh(mesh)
+    W = inputs.uniform_state(mesh, rho=1.0, vel=(0.8, 0.0, 0.0), p=1.0)
+    N = 64
+    rng = np.random.default_rng(17)
+    prof = 1.0 + 0.5 * rng.random(N)
+    for b in range(mesh.nb):
+        o = int(mesh.origin[b, 0])
+        W[b, 0, 0, 4:20, 4:20] = prof[o:o + 16][None, :]
+    U = om.prim_to_cons(W)
+    om.guardcell_fill(U)
+    dt = 0.5 / N
+    nu = 0.8 * dt * N
+
+    def L(r):
+        a, bb = r - np.roll(r, 1), np.roll(r, -1) - r
+        s = np.where(a * bb <= 0, 0.0,
+                     np.sign(a) * np.minimum(np.minimum(2 * np.abs(a), 2 * np.abs(bb)),
+                                             0.5 * np.abs(a + bb)))
+        face = r + 0.5 * s
+        return -nu * (face - np.roll(face, 1))
+
+    r1 = prof + L(prof)
+    r2 = 0.75 * prof + 0.25 * (r1 + L(r1))
+    want = prof / 3.0 + 2.0 / 3.0 * (r2 + L(r2))
+    Un, st, _ = om.hydro_advance(U, dt, integrator=2)
+    assert st == 0
+    np.testing.assert_allclose(assemble(mesh, Un)[0, 0, 0], want, rtol=1e-13)
+
+
+def _front_errors(orc, integrator, cfls=(0.8, 0.4, 0.2), ref_cfl=0.025, t_end=0.2):
+    """L1 distance of the density at t_end from a run with a much smaller dt,
+    on one mesh (so only the time discretisation differs): a smooth tanh front
+    advected at u = 0.8 through uniform pressure, where the MC limiter takes
+    the central slope and the spatial operator is linear (Fromm)."""
+    nx = 128
+    mesh = inputs.uniform_mesh(2, (nx // 16, 1), 16, 4, inputs.OUTFLOW)
+    om = orc.OracleMesh(mesh)
+    W = inputs.uniform_state(mesh, rho=1.0, vel=(0.8, 0.0, 0.0), p=1.0)
+    for b in range(mesh.nb):
+        x, _, _ = mesh.cell_centers(b)
+        W[b, 0, 0, 4:20, 4:20] = 1.5 + 0.4 * np.tanh((x[0] - 0.3) / 0.08)
+    U0 = om.prim_to_cons(W)
+    dx = 1.0 / nx
+    amax = 0.8 + np.sqrt(GAMMA * 1.0 / 1.1)
+
+    def run(cfl):
+        dt = cfl * dx / amax
+        n = int(round(t_end / dt))
+        U = U0.copy()
+        for _ in range(n):
+            U, _ = om.step(U, dt=t_end / n, integrator=integrator)
+        return assemble(mesh, U)[0, 0, 0]
+
+    ref = run(ref_cfl)
+    return [np.abs(run(c) - ref).mean() for c in cfls]
+
+
+def test_rk3_third_order_in_time(orc):
+    """Halving dt on a fixed mesh cuts the time-discretisation error ~8x for
+    SSP-RK3 (~4x for SSP-RK2, which this test also checks so that it can tell
+    the two apart)."""
+    e3 = _front_errors(orc, 2)
+    o3 = np.log2(np.array(e3[:-1]) / np.array(e3[1:]))
+    assert np.all(o3 > 2.6), (e3, o3)
+    e2 = _front_errors(orc, 1)
+    o2 = np.log2(np.array(e2[:-1]) / np.array(e2[1:]))
+    assert np.all(o2 > 1.7) and np.all(o2 < 2.4), (e2, o2)
+
+
+def test_rk3_conservation_uniform_and_amr(orc):
+    for mesh in (inputs.uniform_mesh(3, (2, 2, 2), 8, 4, inputs.PERIODIC),
+                 mesh_2level(4, 8, 4, inputs.PERIODIC)):
+        W = inputs.random_smooth_state(mesh, seed=19)
+        om = orc.OracleMesh(mesh)
+        U0 = om.prim_to_cons(W)
+        T0 = om.conserved_totals(U0)
+        U1, _, _ = om.run(U0.copy(), nsteps=12, integrator=2)
+        A = om.conserved_totals(np.abs(U0)) + om.conserved_totals(np.abs(U1))
+        d = np.abs(om.conserved_totals(U1) - T0) / A
+        assert np.all(d <= 1e-13), d
+        if mesh.level.max() > 0:       # without the stage-weighted correction it drifts
+            U2, _, _ = om.run(U0.copy(), nsteps=12, integrator=2, reflux=False)
+            assert (np.abs(om.conserved_totals(U2) - T0) / A).max() > 1e-8
+    mesh = mesh_2level(4, 8, 4)
+    om = orc.OracleMesh(mesh)
+    U0 = om.prim_to_cons(inputs.uniform_state(mesh))
+    U, _, _ = om.run(U0.copy(), nsteps=3, integrator=2)
+    assert np.array_equal(leaf_interior(mesh, U), leaf_interior(mesh, U0))
+
+
 # ------------------------------------------------------------------ reflecting walls
 
 def _wall_problem(ndim, nblk, nxb, walls, refine_at, seed):
