@@ -83,8 +83,14 @@ FX_API int fx_finalize(fx_ctx *ctx);
  *               method-of-lines family of the Spark solver, Section 2.2):
  *               U1 = U + dt L(U), coarse-fine fill of U1,
  *               U <- (U + (U1 + dt L(U1))) / 2 in the current buffer, flux
- *               correction with the stage-averaged fluxes.  Batches accept
- *               only integrator 0.
+ *               correction with the stage-averaged fluxes; 2 = SSP-RK3 of
+ *               Shu and Osher with the same face states and flux:
+ *               U2 = 3/4 U + 1/4 (U1 + dt L(U1)) in a third state buffer
+ *               that the library allocates on first use (the size of one
+ *               state buffer, freed with the block set), coarse-fine fill
+ *               of U2, U <- 1/3 U + 2/3 (U2 + dt L(U2)), flux correction with
+ *               the fluxes weighted 1/6, 1/6, 2/3.  Batches accept only
+ *               integrator 0.
  * Errors: FX_ERR_ARG for an unknown key or value. */
 FX_API int fx_set_option(fx_ctx *ctx, const char *key, double value);
 

@@ -36,7 +36,8 @@ def sources():
 def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    deps = (sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
+            + glob.glob(os.path.join(ROOT, "include", "*.h")))
     return max(os.path.getmtime(f) for f in deps) > os.path.getmtime(LIB)
 
 

@@ -28,7 +28,7 @@ struct fx_ctx {
   int nxb = 16, ng = 4;
   int cfl_form = 0;
   int reflux = 1;
-  int integrator = 0;   // 0 MUSCL-Hancock, 1 SSP-RK2
+  int integrator = 0;   // 0 MUSCL-Hancock, 1 SSP-RK2, 2 SSP-RK3
   int device = 0;
   std::string err;
 };
@@ -70,6 +70,7 @@ struct fx_blocks {
   // fx_run_host_interior: packed interior staging buffer and the streams and
   // events of the overlapped download (created on first use)
   void *d_pack = nullptr;
+  void *d_U3 = nullptr;                     // third state buffer of SSP-RK3 (first use)
   cudaStream_t aux[2] = {nullptr, nullptr}, cpy = nullptr;
   cudaEvent_t ev_ready = nullptr, ev_done = nullptr, ev_chunk[8] = {};
 };
@@ -121,6 +122,7 @@ void free_blocks(fx_blocks *bs) {
   for (cudaEvent_t e : bs->ev_chunk)
     if (e) cudaEventDestroy(e);
   cudaFree(bs->d_pack);
+  cudaFree(bs->d_U3);
 }
 
 struct Lattice {
@@ -175,7 +177,8 @@ int fx_set_option(fx_ctx *ctx, const char *key, double value) {
     return FX_OK;
   }
   if (!strcmp(key, "integrator")) {
-    if (value != 0.0 && value != 1.0) return fail(ctx, FX_ERR_ARG, "integrator must be 0 or 1");
+    if (value != 0.0 && value != 1.0 && value != 2.0)
+      return fail(ctx, FX_ERR_ARG, "integrator must be 0, 1 or 2");
     ctx->integrator = (int)value;
     return FX_OK;
   }
@@ -533,23 +536,49 @@ int fx_hydro_advance(fx_ctx *ctx, fx_blocks *bs, const double *dt_dev, void *str
   unsigned long long *smax = bs->d_scratch + 2;
   const bool refl = ctx->reflux && bs->nrefl > 0;
   const int *leaves = bs->d_lists + bs->leaves_off;
-  if (ctx->integrator == 1) {
+  if (ctx->integrator == 1 || ctx->integrator == 2) {
     // SSP-RK2: U1 = U + dt L(U) into the other buffer; coarse-fine fill of
     // U1; U = (U + (U1 + dt L(U1))) / 2 in place; registers hold the stage
     // average of the fluxes for the correction.
-    fx::HydroStage s1, s2;
-    s1.pred = 0; s1.reg_mode = 1;
-    s2.pred = 0; s2.reg_mode = 2; s2.Uavg = Uo;
+    // SSP-RK3: U1 as above; U2 = 3/4 U + 1/4 (U1 + dt L(U1)) into a third
+    // buffer; U = 1/3 U + 2/3 (U2 + dt L(U2)) in place; register weights
+    // 1/6, 1/6, 2/3.
+    const bool rk3 = ctx->integrator == 2;
+    if (rk3 && !bs->d_U3) {
+      const size_t bytes = (size_t)bs->nb * bs->dm.bstride * bs->elsize;
+      if (cudaMalloc(&bs->d_U3, bytes) != cudaSuccess) {
+        bs->d_U3 = nullptr;
+        cudaGetLastError();
+        return fail(ctx, FX_ERR_OOM, "cudaMalloc of the SSP-RK3 stage buffer failed");
+      }
+      FX_CUDA(cudaMemsetAsync(bs->d_U3, 0, bytes, s), "stage buffer clear");
+    }
+    fx::HydroStage s1, s2, s3;
+    s1.pred = 0; s1.reg_w = rk3 ? 1.0 / 6.0 : 0.5;
+    s2.pred = 0; s2.Uavg = Uo; s2.reg_add = 1;
+    if (rk3) { s2.wa = 0.75; s2.wb = 0.25; s2.reg_w = 1.0 / 6.0; }
+    else { s2.wa = 0.5; s2.wb = 0.5; s2.reg_w = 0.5; }
+    s3.pred = 0; s3.Uavg = Uo; s3.reg_add = 1;
+    s3.wa = 1.0 / 3.0; s3.wb = 2.0 / 3.0; s3.reg_w = 2.0 / 3.0;
     FX_CUDA(fx::launch_hydro(bs->dm, Uo, Un, bs->prec, leaves, bs->nleaves, dt_dev, bs->d_regs,
                              bs->d_status, nullptr, nullptr, ctx->cfl_form, s, s1),
             "hydro stage 1 launch");
     int rc = fill_for_fused_advance(ctx, bs, s, Un);
     if (rc) return rc;
+    void *Ulast = Un;
+    if (rk3) {
+      FX_CUDA(fx::launch_hydro(bs->dm, Un, bs->d_U3, bs->prec, leaves, bs->nleaves, dt_dev,
+                               bs->d_regs, bs->d_status, nullptr, nullptr, ctx->cfl_form, s, s2),
+              "hydro stage 2 launch");
+      rc = fill_for_fused_advance(ctx, bs, s, bs->d_U3);
+      if (rc) return rc;
+      Ulast = bs->d_U3;
+    }
     FX_CUDA(cudaMemsetAsync(smax, 0, sizeof(unsigned long long), s), "signal max reset");
-    FX_CUDA(fx::launch_hydro(bs->dm, Un, Uo, bs->prec, leaves, bs->nleaves, dt_dev, bs->d_regs,
+    FX_CUDA(fx::launch_hydro(bs->dm, Ulast, Uo, bs->prec, leaves, bs->nleaves, dt_dev, bs->d_regs,
                              bs->d_status, smax, refl ? bs->d_rmask : nullptr, ctx->cfl_form, s,
-                             s2),
-            "hydro stage 2 launch");
+                             rk3 ? s3 : s2),
+            "hydro final stage launch");
     if (refl)
       FX_CUDA(fx::launch_reflux(bs->dm, Uo, bs->prec, bs->d_refl, bs->nrefl, dt_dev, bs->d_regs,
                                 bs->d_status, smax, ctx->cfl_form, s),

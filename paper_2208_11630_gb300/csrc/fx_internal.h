@@ -85,10 +85,15 @@ cudaError_t launch_guard_prolong(const DevMesh &m, void *U, int prec, const int 
 // Guard depth the fused update reads (radius-2 stencil).
 constexpr int kHydroGuardDepth = 2;
 // Time-integration stage of one update launch (defaults: MUSCL-Hancock).
+// Unew = wa Uavg + wb (U + dt L(U)) when Uavg is set (an SSP Runge-Kutta
+// stage), else U + dt L(U); flux registers receive reg_w F, stored or (reg_add)
+// added.
 struct HydroStage {
-  int pred = 1;               // 1: Hancock predictor; 0: PLM face states (SSP-RK2)
-  const void *Uavg = nullptr; // SSP-RK2 second stage: average with this state
-  int reg_mode = 0;           // flux registers: 0 store F, 1 store F/2, 2 add F/2
+  int pred = 1;               // 1: Hancock predictor; 0: PLM face states (SSP-RK)
+  const void *Uavg = nullptr; // state blended into the stage result (or null)
+  double wa = 0.5, wb = 0.5;  // blend weights
+  double reg_w = 1.0;         // weight of the fluxes in the registers
+  int reg_add = 0;            // 0 store, 1 add to the registers
 };
 
 // smax (may be null): receives atomicMax of the bit patterns of the new
@@ -98,6 +103,11 @@ cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, 
                          int n, const double *dt, double *regs, int *status,
                          unsigned long long *smax, const unsigned char *rmask, int form,
                          cudaStream_t s, const HydroStage &st = HydroStage());
+// The SSP Runge-Kutta stage kernels behind launch_hydro (st.pred == 0).
+cudaError_t launch_hydro_rk(const DevMesh &m, const void *U, void *Unew, int prec,
+                            const int *leaves, int n, const double *dt, double *regs, int *status,
+                            unsigned long long *smax, const unsigned char *rmask, int form,
+                            cudaStream_t s, const HydroStage &st);
 cudaError_t launch_reflux(const DevMesh &m, void *Unew, int prec, const RefluxItem *items, int n,
                           const double *dt, const double *regs, int *status,
                           unsigned long long *smax, int form, cudaStream_t s);

@@ -1,0 +1,639 @@
+// hydro_tile.cuh -- device body of the fused unsplit update of one T x T column
+// tile of a leaf block, shared by the MUSCL-Hancock kernels (k_hydro.cu) and
+// the SSP Runge-Kutta stage kernels (k_hydro_rk.cu).
+//
+// Paper: Flash-X (arXiv 2208.11630), Section 2.2 -- an unsplit compressible
+// hydro solver of predictor-corrector type, applied one block at a time
+// (Section 2).  Concrete scheme (textbook): primitive variables, MC-
+// limited slopes (van Leer 1977), Hancock half-step predictor in primitive
+// form (Toro ch. 14), HLLC flux with Davis speeds (Toro, Spruce & Speares
+// 1994), conservative update summed over x, y, z.  A cell whose predicted face
+// states are not all positive in density and pressure falls back to first
+// order (zero slopes, no predictor).
+//
+// GB300 design.  One CTA owns a T x T column tile of one block and marches it
+// along z.  Guard cells of same-level neighbours are read directly from the
+// neighbour's interior while the tile is loaded (the guard copy is fused
+// away); only guards covered by a coarser leaf come from the padded array.  Shared memory holds a ring of three primitive planes (radius-2
+// halo in x and y) and the x/y face states of the current plane; each face
+// flux is computed once by one thread and written over the face state it
+// consumed.  The thread owning column (i, j) keeps its z face states and z
+// fluxes in registers, so no z data touches shared memory.  Per plane: load
+// + primitives, predictor, fluxes, update, three barriers.
+//
+// Precision variants: FP64 state and arithmetic; or FP32-bulk -- FP32 state,
+// FP32 reconstruction and Riemann solver, and an update that adds to U the
+// exactly differenced fluxes (TwoSum) scaled by dt/dx with a single final
+// rounding, which matches an FP64 accumulation up to a fraction of an FP32
+// ulp at a tiny fraction of the cost of FP64 arithmetic on this GPU.
+#pragma once
+
+#include "fx_internal.h"
+
+#include <type_traits>
+
+namespace fx {
+namespace {
+
+// Half of van Leer's MC slope: 0 if a and b differ in sign or one is zero,
+// else sign(a) min(|a|, |b|, |a+b|/4) -- exactly MC(a, b) / 2, since scaling by
+// powers of two is exact.  The sign tests run on the integer pipe.
+//
+// FP64: the minimum of the three non-negative magnitudes is taken on their bit
+// patterns (which order like the values), keeping it off the FP64 pipe.
+__device__ __forceinline__ double mc_half(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  const bool same = ((ia ^ ib) >= 0) && (ia << 1) != 0 && (ib << 1) != 0;
+  const long long ma = ia & 0x7fffffffffffffffll, mb = ib & 0x7fffffffffffffffll;
+  const long long mq = __double_as_longlong(0.25 * fabs(a + b));
+  long long m = ma < mb ? ma : mb;
+  m = mq < m ? mq : m;
+  // sign of a on the minimum magnitude
+  const long long r = m | (ia & (long long)0x8000000000000000ull);
+  return same ? __longlong_as_double(r) : 0.0;
+}
+
+// FP32: (sign(a)/2 + sign(b)/2) min(|a|, |b|, |a+b|/4), where the signed
+// halves are +-1/2 (exact sums +-1 or 0): equal signs give +-m, opposite
+// signs 0, and a zero argument makes m zero -- the same values as the FP64
+// form, without compares or selects (only the sign of a zero result can
+// differ, which no later sum or product turns into a nonzero value).
+__device__ __forceinline__ float mc_half(float a, float b) {
+  const float m = fminf(fminf(fabsf(a), fabsf(b)), 0.25f * fabsf(a + b));
+  return (copysignf(0.5f, a) + copysignf(0.5f, b)) * m;
+}
+
+// x > 0 (false for zero, negative and NaN; +inf counts as positive), tested on
+// the bit pattern.
+__device__ __forceinline__ bool positive(double x) {
+  return (unsigned long long)__double_as_longlong(x) - 1ull < 0x7ff0000000000000ull;
+}
+// FP32: a plain compare is cheaper than the bit test; +inf is the only
+// value where the two forms differ, and it counts as positive in both.
+__device__ __forceinline__ bool positive(float x) { return x > 0.0f; }
+
+// x >= 0 (true for -0; a NaN with a clear sign bit would count as >= 0, which
+// only matters for states that are already invalid), on the bit pattern.
+__device__ __forceinline__ bool ge0(double x) {
+  const long long i = __double_as_longlong(x);
+  return i >= 0 || (i << 1) == 0;
+}
+__device__ __forceinline__ bool ge0(float x) { return x >= 0.0f; }
+__device__ __forceinline__ bool gt0(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool gt0(float x) { return x > 0.0f; }
+
+__device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+
+// Flux-register write: MUSCL-Hancock stores F; an SSP-RK stage stores or
+// adds st.reg_w F (stage-weighted sums).
+template <bool RK, typename R>
+__device__ __forceinline__ void put_reg(double &r, R f, const HydroStage &st) {
+  const double v = double(f);
+  if constexpr (RK) r = st.reg_add ? fma(st.reg_w, v, r) : st.reg_w * v;
+  else r = v;
+}
+
+// Quotient and reciprocal: IEEE division in FP64; the fast (MUFU-based,
+// ~2 ulp) forms in FP32, whose error is far below the FP32 storage rounding.
+__device__ __forceinline__ double div_r(double a, double b) { return a / b; }
+__device__ __forceinline__ float div_r(float a, float b) { return __fdividef(a, b); }
+
+// c * (a - b) with the difference a - b taken exactly (Knuth's TwoSum error
+// term), so that nearly equal face fluxes lose no digits before scaling.
+__device__ __forceinline__ float scaled_diff(float a, float b, float c) {
+  const float nb = -b;
+  const float s = a + nb;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (nb - bb);
+  return fmaf(c, s, c * e);
+}
+
+// HLLC flux along direction D from primitive left/right states.  One
+// reciprocal square root per side gives both the sound speed and 1/rho:
+// r = (gamma p rho)^(-1/2), c = gamma p r, 1/rho = c r.  The star state of the
+// upwind side K needs S* and 1/(S_K - S*): one FP64 reciprocal, or two FP32
+// fast divisions.
+template <int D, typename R>
+__device__ __forceinline__ void hllc(const R (&WL)[5], const R (&WR)[5], R g, R igm1,
+                                     R (&F)[5]) {
+  constexpr int N = 1 + D;
+  const R rL = WL[0], uL = WL[N], pL = WL[4];
+  const R rR = WR[0], uR = WR[N], pR = WR[4];
+  const R gpL = g * pL, gpR = g * pR;
+  const R qL = rsqrt_r(gpL * rL), qR = rsqrt_r(gpR * rR);
+  const R cL = gpL * qL, cR = gpR * qR;
+  const R SL = fmin(uL - cL, uR - cR);
+  const R SR = fmax(uL + cL, uR + cR);
+  const R dL = SL - uL, dR = SR - uR;
+  // S* = A / B.  FP64: its sign (A = 0 or A, B of equal sign <=> S* >= 0)
+  // picks the side, and S* and 1/(S_K - S*) both come from one reciprocal
+  // below; FP32: two fast divisions.
+  const R A = pR - pL + rL * uL * dL - rR * uR * dR;
+  const R B = rL * dL - rR * dR;
+  constexpr bool kF64 = std::is_same<R, double>::value;
+  R Sst = R(0);
+  bool sst_ge0;
+  if constexpr (kF64) {
+    const long long ia = __double_as_longlong(A), ib = __double_as_longlong(B);
+    sst_ge0 = (ia << 1) == 0 || (ia ^ ib) >= 0;
+  } else {
+    Sst = div_r(A, B);
+    sst_ge0 = ge0(Sst);
+  }
+  // Branches: S_L >= 0 -> F_L; S* >= 0 -> F*_L; S_R > 0 -> F*_R; else F_R.
+  const bool caseA = ge0(SL);
+  const bool useL = caseA || sst_ge0;
+  const bool star = !caseA && (useL || gt0(SR));
+  R W[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) W[q] = useL ? WL[q] : WR[q];
+  const R SK = useL ? SL : SR;
+  const R irK = useL ? cL * qL : cR * qR;
+  const R rK = W[0], uK = W[N], pK = W[4];
+  const R ke = R(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+  const R EK = pK * igm1 + rK * ke;          // total energy of side K
+  const R eK = pK * igm1 * irK + ke;         // E_K / rho_K
+  const R mK = rK * uK;
+  F[0] = mK;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) F[1 + t] = mK * W[1 + t];
+  F[N] += pK;
+  F[4] = uK * (EK + pK);
+  if (star) {
+    const R dK = SK - uK;
+    R inv;
+    if constexpr (kF64) {
+      // S_K - S* = D / B with D = S_K B - A:  r = 1/(B D), S* = A D r,
+      // 1/(S_K - S*) = B B r
+      const R D = SK * B - A;
+      const R r = R(1) / (B * D);
+      Sst = A * D * r;
+      inv = B * B * r;
+    } else {
+      inv = div_r(R(1), SK - Sst);
+    }
+    const R fac = rK * dK * inv;                       // rho*_K
+    const R ds = Sst - uK;
+    R Us[5];
+    Us[0] = fac;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) Us[1 + t] = fac * W[1 + t];
+    Us[N] = fac * Sst;
+    Us[4] = fac * (eK + ds * Sst) + ds * pK * inv;     // rho*_K e*_K
+    F[0] = F[0] + SK * (Us[0] - rK);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) F[1 + t] = F[1 + t] + SK * (Us[1 + t] - rK * W[1 + t]);
+    F[4] = F[4] + SK * (Us[4] - EK);
+  }
+}
+
+// Primitives (rho, u, v, w, p) and 1/rho of one cell.
+template <typename S, typename R>
+__device__ __forceinline__ void prim(const S *u, long long vs, R gm1, R (&w)[6]) {
+  const R r = R(u[0]), mx = R(u[vs]), my = R(u[2 * vs]), mz = R(u[3 * vs]), E = R(u[4 * vs]);
+  const R ir = div_r(R(1), r);
+  w[0] = r;
+  w[1] = mx * ir;
+  w[2] = my * ir;
+  w[3] = mz * ir;
+  w[4] = gm1 * (E - R(0.5) * (mx * mx + my * my + mz * mz) * ir);
+  w[5] = ir;
+}
+
+// Shared-memory map, in elements of R.
+template <int T>
+struct Smem {
+  static constexpr int W4 = T + 4;          // ring plane width (radius-2 halo)
+  static constexpr int W2 = T + 2;          // face-state row width (radius-1)
+  static constexpr int NV = 6;              // rho, u, v, w, p, 1/rho
+  static constexpr int RING = NV * W4 * W4; // one primitive plane
+  static constexpr int FX = 5 * T * W2;     // x face states [v][j][i+1]
+  static constexpr int FY = 5 * W2 * T;     // y face states [v][j+1][i]
+  static constexpr int total(int nplanes) { return nplanes * RING + 2 * FX + 2 * FY; }
+};
+
+// Slopes, Hancock predictor and face states of the cell at tile-local (i, j)
+// of the plane in ring slot s0 (neighbour planes in sm, sp).  Works with half
+// slopes h = dW/2 throughout: the predictor is linear in the slopes, so
+// A(W) h (2/dx) is exactly A(W) dW / dx, and the face states are W* -+ h.
+// Returns the lower/upper face states per direction in fm/fp.
+template <int NDIM, int T, typename R, bool PRED = true>
+__device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int s0, int sp, int i,
+                                        int j, R hdt, const R (&idx2)[3], R g,
+                                        R (&fm)[3][5], R (&fp)[3][5]) {
+  using SM = Smem<T>;
+  constexpr int PL = SM::W4 * SM::W4;
+  const int c = (j + 2) * SM::W4 + (i + 2);
+  const R *p0 = ring + s0 * SM::RING;
+  R W0[5], h[3][5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) W0[v] = p0[v * PL + c];
+  const R ir = p0[5 * PL + c];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const R *q = p0 + v * PL + c;
+    h[0][v] = mc_half(W0[v] - q[-1], q[1] - W0[v]);
+    h[1][v] = mc_half(W0[v] - q[-SM::W4], q[SM::W4] - W0[v]);
+    if (NDIM == 3) {
+      const R wm = ring[sm * SM::RING + v * PL + c];
+      const R wp = ring[sp * SM::RING + v * PL + c];
+      h[2][v] = mc_half(W0[v] - wm, wp - W0[v]);
+    } else {
+      h[2][v] = R(0);
+    }
+  }
+  R Wh[5];
+  if constexpr (PRED) {
+    // primitive quasi-linear form: sum_d A_d(W) dW_d / dx_d
+    R acc[5] = {R(0), R(0), R(0), R(0), R(0)};
+    const R r = W0[0], gp = g * W0[4];
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+      const int n = 1 + d;
+      const R un = W0[n];
+      R a[5];
+      a[0] = un * h[d][0] + r * h[d][n];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) a[1 + t] = un * h[d][1 + t];
+      a[n] = a[n] + h[d][4] * ir;
+      a[4] = gp * h[d][n] + un * h[d][4];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) acc[v] = acc[v] + a[v] * idx2[d];
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Wh[v] = W0[v] - hdt * acc[v];
+  } else {
+    // plain PLM face states: no half step
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Wh[v] = W0[v];
+  }
+  bool ok = true;
+#pragma unroll
+  for (int d = 0; d < NDIM; ++d) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      fm[d][v] = Wh[v] - h[d][v];
+      fp[d][v] = Wh[v] + h[d][v];
+    }
+    ok = ok && positive(fm[d][0]) && positive(fm[d][4]) && positive(fp[d][0]) &&
+         positive(fp[d][4]);
+  }
+  if (!ok) {
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) { fm[d][v] = W0[v]; fp[d][v] = W0[v]; }
+  }
+}
+
+// One T x T column tile of leaf block b, marched along z.  Called by the
+// per-block-set kernel (one CTA per tile) and by the batched persistent
+// kernel (each CTA loops over tiles of many block sets).
+//   RK false  MUSCL-Hancock: Hancock half step, registers store F (st unused)
+//   RK true   an SSP Runge-Kutta stage: plain PLM face states; st.Uavg null,
+//             or Unew = st.wa Uavg + st.wb (U + dt L(U)) (Uavg may be Unew
+//             itself: each cell is read before it is written by the same
+//             thread, so neither pointer is declared restrict); registers
+//             store or (st.reg_add) add st.reg_w F
+template <int NDIM, int T, typename S, typename R, bool RK = false>
+__device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict__ U,
+                                           S *Unew, int b, int tile, int tiles,
+                                           double dt, double *__restrict__ regs,
+                                           int *__restrict__ status,
+                                           unsigned long long *__restrict__ smax_out,
+                                           const unsigned char *__restrict__ rmask,
+                                           int cfl_form, const HydroStage &st = HydroStage()) {
+  const S *Uavg = RK ? static_cast<const S *>(st.Uavg) : nullptr;
+  using SM = Smem<T>;
+  constexpr int NT = T * T;
+  constexpr int NPL = NDIM == 3 ? 3 : 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *ring = reinterpret_cast<R *>(smem_raw);
+  R *fxm = ring + NPL * SM::RING;   // x lower-face states, then x fluxes
+  R *fxp = fxm + SM::FX;
+  R *fym = fxp + SM::FX;            // y lower-face states, then y fluxes
+  R *fyp = fym + SM::FY;
+
+  const int tid = threadIdx.x;
+  __syncthreads();   // the previous tile of this CTA is done with shared memory
+  const int x0 = (tile % tiles) * T, y0 = (tile / tiles) * T;
+  const int n = m.nxb, ng = m.ng, P = m.P;
+  const int lev = m.level[b];
+  const long long vs = m.vstride;
+  const R g = R(m.gamma), gm1 = R(m.gamma - 1.0), igm1 = R(1.0 / (m.gamma - 1.0));
+  const R hdt = R(0.5 * dt);
+  R idx2[3];
+  idx2[0] = R(2.0 * m.idx[lev][0]);
+  idx2[1] = R(2.0 * m.idx[lev][1]);
+  idx2[2] = R(2.0 * m.idx[lev][2]);
+  const double didx = m.idx[lev][0], didy = m.idx[lev][1], didz = m.idx[lev][2];
+  const S *Ub = U + (long long)b * m.bstride;
+  S *Unb = Unew + (long long)b * m.bstride;   // may alias Uavg (see above)
+  const int ti = tid % T, tj = tid / T;
+  const int zoff = NDIM == 3 ? ng : 0;
+  const int ridx = m.regidx[b];
+  double *reg = ridx >= 0 ? regs + (long long)ridx * m.nfaces * 5 * m.nface_cells : nullptr;
+  const int nfc = m.nface_cells;
+
+  // Guard sources of this block: a same-level slot is read straight from the
+  // neighbour's interior (the value the guard copy would have written); a
+  // slot covered by a coarser leaf is read from this block's own guards,
+  // which the prolongation pass filled.
+  // Work of one plane beyond one item per thread, spread over disjoint warps
+  // so that no warp carries two extras into a barrier: the halo predictor
+  // (4T cells) runs on threads [0, 4T), the last partial round of x/y faces
+  // on the threads right after them, the last partial round of the plane
+  // load on the highest threads.
+  constexpr int kLoadTail = (SM::W4 * SM::W4) % NT;
+  constexpr int kFaceShift = NT - 4 * T;
+  __shared__ int2 slots[27];
+  if (tid < 27) slots[tid] = m.slots[b * 27 + tid];
+  __syncthreads();
+  const int ox = m.origin[3 * b], oy = m.origin[3 * b + 1], oz = m.origin[3 * b + 2];
+  auto load_plane = [&](int p, int slot) {
+    R *dst = ring + slot * SM::RING;
+    const int zpad = p + zoff;
+    const int sz = NDIM == 3 ? (zpad < ng ? 0 : (zpad >= ng + n ? 2 : 1)) : 1;
+    for (int c = (tid + kLoadTail) % NT; c < SM::W4 * SM::W4; c += NT) {
+      const int ii = c % SM::W4, jj = c / SM::W4;
+      const int gx = x0 + ii - 2 + ng, gy = y0 + jj - 2 + ng;
+      const int sx = gx < ng ? 0 : (gx >= ng + n ? 2 : 1);
+      const int sy = gy < ng ? 0 : (gy >= ng + n ? 2 : 1);
+      const S *src = Ub + ((long long)zpad * P + gy) * P + gx;
+      unsigned flip = 0;                 // velocity components mirrored at a wall
+      if (sx != 1 || sy != 1 || sz != 1) {
+        const int2 sl = slots[sx + 3 * sy + 9 * sz];
+        if (sl.x == SLOT_COPY) {
+          // outflow clamps, periodic wraps, reflecting mirrors (and negates
+          // the wall-normal velocity below)
+          auto map = [&](int a, int N, int d) {
+            if (a < 0) {
+              const int kind = m.bc[d][0];
+              if (kind == FX_BC_PERIODIC) return a + N;
+              if (kind == FX_BC_REFLECT) { flip |= 1u << d; return -1 - a; }
+              return 0;
+            }
+            if (a >= N) {
+              const int kind = m.bc[d][1];
+              if (kind == FX_BC_PERIODIC) return a - N;
+              if (kind == FX_BC_REFLECT) { flip |= 1u << d; return 2 * N - 1 - a; }
+              return N - 1;
+            }
+            return a;
+          };
+          const int ax = map(ox + gx - ng, m.ncell[lev][0], 0);
+          const int ay = map(oy + gy - ng, m.ncell[lev][1], 1);
+          int lz = 0;
+          if (NDIM == 3) {
+            const int az = map(oz + zpad - ng, m.ncell[lev][2], 2);
+            lz = az - m.origin[3 * sl.y + 2] + ng;
+          }
+          const int lx = ax - m.origin[3 * sl.y] + ng, ly = ay - m.origin[3 * sl.y + 1] + ng;
+          src = U + (long long)sl.y * m.bstride + ((long long)lz * P + ly) * P + lx;
+        }
+      }
+      R w[6];
+      prim<S, R>(src, vs, gm1, w);
+      if (flip) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+          if ((flip >> d) & 1u) w[1 + d] = -w[1 + d];
+      }
+#pragma unroll
+      for (int v = 0; v < 6; ++v) dst[v * SM::W4 * SM::W4 + c] = w[v];
+    }
+  };
+  auto slot_of = [&](int p) { return NDIM == 3 ? ((p % 3) + 3) % 3 : 0; };
+
+  // register state of the thread's column: pending update of the cell below
+  // (x+y part of its flux divergence, flux through its lower z face)
+  constexpr bool kF32 = std::is_same<R, float>::value;
+  R txy[5], fzl[5];
+  R zprev[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) { txy[v] = R(0); fzl[v] = R(0); zprev[v] = R(0); }
+  // FP32 path: dt/dx per direction; FP64 path: 1/dx and dt separately
+  const float cx = float(dt * m.idx[lev][0]), cy = float(dt * m.idx[lev][1]),
+              cz = float(dt * m.idx[lev][2]);
+  (void)cx; (void)cy; (void)cz;
+  // Signal speed of the new state, for the next step's CFL dt (same formula
+  // and precision as the standalone reduction).  Cells that the flux
+  // correction will still change (on a face in rmask) are left to it.
+  const unsigned fmask = rmask ? rmask[b] : 0u;
+  const R sidx[3] = {R(m.idx[lev][0]), R(m.idx[lev][1]), R(m.idx[lev][2])};
+  R smax_t = R(0);
+  auto signal = [&](const R (&u)[5], int ci, int cj, int ck) {
+    if (fmask) {
+      const int cc[3] = {ci, cj, ck};
+      for (int d = 0; d < NDIM; ++d) {
+        if (((fmask >> (2 * d)) & 1u) && cc[d] == 0) return;
+        if (((fmask >> (2 * d + 1)) & 1u) && cc[d] == n - 1) return;
+      }
+    }
+    const R ir = R(1) / u[0];
+    const R pr = gm1 * (u[4] - R(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * ir);
+    const R cs = sqrt(g * pr * ir);
+    R sg = R(0);
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+      const R sd = (fabs(u[1 + d] * ir) + cs) * sidx[d];
+      sg = cfl_form == 0 ? sg + sd : fmax(sg, sd);
+    }
+    if (!(sg <= smax_t)) smax_t = sg;   // keeps a NaN
+  };
+
+  const int pstart = NDIM == 3 ? -1 : 0;
+  const int pend = NDIM == 3 ? n : 0;   // inclusive
+  if (NDIM == 3) {
+    load_plane(-2, slot_of(-2));
+    load_plane(-1, slot_of(-1));
+  }
+  for (int p = pstart; p <= pend; ++p) {
+    const bool inner = p >= 0 && p < (NDIM == 3 ? n : 1);
+    const int s0 = slot_of(p), sm = slot_of(p - 1), sp = slot_of(p + 1);
+    if (NDIM == 3) load_plane(p + 1, sp);
+    else load_plane(0, 0);
+    __syncthreads();
+
+    // ---- predictor: own column cell, then (inner planes) the radius-1 ring
+    R zm[5], zp[5];
+    {
+      R fm[3][5], fp[3][5];
+      predict<NDIM, T, R, !RK>(ring, sm, s0, sp, ti, tj, hdt, idx2, g, fm, fp);
+      if (inner) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          fxm[v * T * SM::W2 + tj * SM::W2 + ti + 1] = fm[0][v];
+          fxp[v * T * SM::W2 + tj * SM::W2 + ti + 1] = fp[0][v];
+          fym[v * SM::W2 * T + (tj + 1) * T + ti] = fm[1][v];
+          fyp[v * SM::W2 * T + (tj + 1) * T + ti] = fp[1][v];
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) { zm[v] = fm[2][v]; zp[v] = fp[2][v]; }
+    }
+    if (inner) {
+      for (int c = tid; c < 4 * T; c += NT) {
+        const int side = c / T, e = c % T;
+        int i, j;
+        if (side == 0) { i = -1; j = e; }
+        else if (side == 1) { i = T; j = e; }
+        else if (side == 2) { i = e; j = -1; }
+        else { i = e; j = T; }
+        R fm[3][5], fp[3][5];
+        predict<NDIM, T, R, !RK>(ring, sm, s0, sp, i, j, hdt, idx2, g, fm, fp);
+        if (side < 2) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            fxm[v * T * SM::W2 + j * SM::W2 + i + 1] = fm[0][v];
+            fxp[v * T * SM::W2 + j * SM::W2 + i + 1] = fp[0][v];
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            fym[v * SM::W2 * T + (j + 1) * T + i] = fm[1][v];
+            fyp[v * SM::W2 * T + (j + 1) * T + i] = fp[1][v];
+          }
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- fluxes: x and y faces of inner planes (in place over the lower-face
+    // state), z face below the thread's own cell
+    const int zglob = p;  // interior z index of this plane
+    if (inner) {
+      for (int f = (tid + kFaceShift) % NT; f < 2 * (T + 1) * T; f += NT) {
+        const int dir = f >= (T + 1) * T;
+        const int ff = dir ? f - (T + 1) * T : f;
+        // a: face index along the normal (0..T), e: transverse index; the
+        // lanes of a warp take consecutive x so shared-memory rows stay
+        // contiguous for both directions
+        int a, e;
+        if (ff < T * T) {
+          if (!dir) { a = ff % T; e = ff / T; }
+          else { a = ff / T; e = ff % T; }
+        } else {
+          a = T; e = ff - T * T;
+        }
+        R WL[5], WR[5], F[5];
+        if (!dir) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            WL[v] = fxp[v * T * SM::W2 + e * SM::W2 + a];
+            WR[v] = fxm[v * T * SM::W2 + e * SM::W2 + a + 1];
+          }
+          hllc<0, R>(WL, WR, g, igm1, F);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) fxm[v * T * SM::W2 + e * SM::W2 + a + 1] = F[v];
+          if (reg && ((a == 0 && x0 == 0) || (a == T && x0 + T == n))) {
+            const int face = a == 0 ? 0 : 1;
+            const int t1 = y0 + e, t2 = NDIM == 3 ? zglob : 0;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) put_reg<RK>(reg[(face * 5 + v) * nfc + t2 * n + t1], F[v], st);
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            WL[v] = fyp[v * SM::W2 * T + a * T + e];
+            WR[v] = fym[v * SM::W2 * T + (a + 1) * T + e];
+          }
+          hllc<1, R>(WL, WR, g, igm1, F);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) fym[v * SM::W2 * T + (a + 1) * T + e] = F[v];
+          if (reg && ((a == 0 && y0 == 0) || (a == T && y0 + T == n))) {
+            const int face = a == 0 ? 2 : 3;
+            const int t1 = x0 + e, t2 = NDIM == 3 ? zglob : 0;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) put_reg<RK>(reg[(face * 5 + v) * nfc + t2 * n + t1], F[v], st);
+          }
+        }
+      }
+    }
+    R Fz[5];
+    if (NDIM == 3 && p >= 0) {
+      hllc<2, R>(zprev, zm, g, igm1, Fz);
+      if (reg && (p == 0 || p == n)) {
+        const int face = p == 0 ? 4 : 5;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) put_reg<RK>(reg[(face * 5 + v) * nfc + (y0 + tj) * n + (x0 + ti)], Fz[v], st);
+      }
+    }
+    __syncthreads();
+
+    // ---- update: finish the cell below (3D), start this plane's cell.
+    // FP64: U + dt ((Fx- - Fx+)/dx + (Fy- - Fy+)/dy + (Fz- - Fz+)/dz).
+    // FP32 storage: exact flux differences scaled by dt/dx, summed, one
+    // rounding when added to U.
+    if (NDIM == 3 && p >= 1) {
+      const long long o = ((long long)(p - 1 + ng) * P + (y0 + tj + ng)) * P + (x0 + ti + ng);
+      R un[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        if constexpr (kF32) {
+          const float d = txy[v] + scaled_diff(fzl[v], Fz[v], cz);
+          un[v] = float(Ub[o + v * vs]) + d;
+        } else {
+          const double div = txy[v] + (fzl[v] - Fz[v]) * didz;
+          un[v] = double(Ub[o + v * vs]) + dt * div;
+        }
+        if constexpr (RK) {
+          if (Uavg)
+            un[v] = fma(R(st.wa), R(Uavg[(long long)b * m.bstride + o + v * vs]), R(st.wb) * un[v]);
+        }
+        Unb[o + v * vs] = S(un[v]);
+      }
+      if (!(un[0] > R(0)) || !(R(2) * un[4] * un[0] > un[1] * un[1] + un[2] * un[2] + un[3] * un[3]))
+        atomicOr(status, 1);
+      if (smax_out) signal(un, x0 + ti, y0 + tj, p - 1);
+    }
+    if (inner) {
+      const R *Fx = fxm + tj * SM::W2 + ti + 1;
+      const R *Fy = fym + (tj + 1) * T + ti;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const R fxl = Fx[v * T * SM::W2], fxr = Fx[v * T * SM::W2 + 1];
+        const R fyl = Fy[v * SM::W2 * T], fyr = Fy[v * SM::W2 * T + T];
+        if constexpr (kF32) {
+          txy[v] = scaled_diff(fxl, fxr, cx) + scaled_diff(fyl, fyr, cy);
+        } else {
+          txy[v] = (fxl - fxr) * didx + (fyl - fyr) * didy;
+        }
+        if (NDIM == 3) fzl[v] = Fz[v];
+      }
+      if (NDIM == 2) {
+        const long long o = (long long)(y0 + tj + ng) * P + (x0 + ti + ng);
+        R un[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          if constexpr (kF32) un[v] = float(Ub[o + v * vs]) + txy[v];
+          else un[v] = double(Ub[o + v * vs]) + dt * txy[v];
+          if constexpr (RK) {
+            if (Uavg)
+              un[v] = fma(R(st.wa), R(Uavg[(long long)b * m.bstride + o + v * vs]), R(st.wb) * un[v]);
+          }
+          Unb[o + v * vs] = S(un[v]);
+        }
+        if (!(un[0] > R(0)) ||
+            !(R(2) * un[4] * un[0] > un[1] * un[1] + un[2] * un[2] + un[3] * un[3]))
+          atomicOr(status, 1);
+        if (smax_out) signal(un, x0 + ti, y0 + tj, 0);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) zprev[v] = zp[v];
+  }
+  if (smax_out) {
+    // maximum over the CTA on the bit patterns of non-negative doubles
+    unsigned long long bits = __double_as_longlong(double(smax_t));
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long other = __shfl_down_sync(0xffffffffu, bits, o);
+      bits = other > bits ? other : bits;
+    }
+    if ((tid & 31) == 0) atomicMax(smax_out, bits);
+  }
+}
+
+}  // namespace
+}  // namespace fx

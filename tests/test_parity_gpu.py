@@ -372,22 +372,23 @@ def test_full_size_sedov_amr(orc, fx):
     assert (np.abs(a - b) / np.maximum(np.abs(b), s)).max() <= 1e-12
 
 
+@pytest.mark.parametrize("integrator", [1, 2])
 @pytest.mark.parametrize("case", ["sod2d", "kh64", "blocky2d_nxb8", "amr_smooth_periodic",
                                   "amr_sedov_small", "amr_3level_periodic", "smooth3d_nxb32",
                                   "amr_reflect_wall"])
-def test_rk2_variant(orc, fx, case):
-    """SSP-RK2 with PLM and HLLC (integrator option 1) against the oracle's
-    SSP-RK2: one step at 1e-12, thirty more at 1e-10; totals conserved on
-    periodic meshes (stage-averaged flux correction on AMR)."""
+def test_rk2_variant(orc, fx, case, integrator):
+    """SSP-RK2 and SSP-RK3 with PLM and HLLC (integrator options 1 and 2)
+    against the oracle's: one step at 1e-12, thirty more at 1e-10; totals
+    conserved on periodic meshes (stage-weighted flux correction on AMR)."""
     mesh, W = CASES[case]()
-    om, U, bs = both_start(orc, fx, mesh, W, options={"integrator": 1})
+    om, U, bs = both_start(orc, fx, mesh, W, options={"integrator": integrator})
     bs.set_conserved(U)
-    Uo, dto = om.step(U, integrator=1)
+    Uo, dto = om.step(U, integrator=integrator)
     bs.step(0.8)
     assert bs.status() == 0
     assert float(bs.dt.item()) == pytest.approx(dto, rel=1e-15)
     assert max_rel_err(mesh, bs.state(), Uo) <= 1e-12
-    Uo2, _, _ = om.run(Uo, nsteps=30, integrator=1)
+    Uo2, _, _ = om.run(Uo, nsteps=30, integrator=integrator)
     bs.run(30, 0.8)
     assert bs.status() == 0
     assert max_rel_err(mesh, bs.state(), Uo2) <= 1e-10
@@ -397,9 +398,10 @@ def test_rk2_variant(orc, fx, case):
         assert np.all(np.abs(bs.totals() - om.conserved_totals(U)) / A <= 1e-13)
 
 
-def test_rk2_block_sets_are_not_batched(fx):
+@pytest.mark.parametrize("integrator", [1, 2])
+def test_rk2_block_sets_are_not_batched(fx, integrator):
     mesh, W = CASES["kh64"]()
-    bs = fx.BlockSet(mesh, 1.4, options={"integrator": 1})
+    bs = fx.BlockSet(mesh, 1.4, options={"integrator": integrator})
     bs.set_primitive(W)
     ctx = fx.fx_init(1.4, 16, 4)
     batch = fx.Batch(ctx, 2)
@@ -407,3 +409,18 @@ def test_rk2_block_sets_are_not_batched(fx):
         batch.add(bs, 0.8, 3)
     batch.close()
     fx.fx_finalize(ctx)
+
+
+def test_rk3_interior_host_round_trip(fx):
+    """SSP-RK3 through the interior-only host path (not chunked: three
+    stages) equals stepping on the device, bit for bit."""
+    mesh, W = CASES["kh64"]()
+    bs = fx.BlockSet(mesh, 1.4, options={"integrator": 2})
+    bs.set_primitive(W)
+    ref = fx.BlockSet(mesh, 1.4, options={"integrator": 2})
+    ref.set_primitive(W)
+    host_in = torch.from_numpy(np.ascontiguousarray(mesh.interior(bs.state()))).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    bs.run_host_interior(host_in.numpy(), host_out.numpy(), 2, 0.8)
+    ref.run(2, 0.8)
+    assert np.array_equal(host_out.numpy(), mesh.interior(ref.state()))

@@ -126,13 +126,15 @@ def test_advection_precision_study_64(orc, fx):
     assert abs(l1s["f32bulk"] - l1s["oracle"]) <= 1e-3 * l1s["oracle"]
 
 
+@pytest.mark.parametrize("integrator", [1, 2])
 @pytest.mark.parametrize("case", ["kh64", "amr_sedov_weak"])
-def test_f32bulk_rk2_one_step(orc, fx, case):
-    """FP32-bulk SSP-RK2.  The AMR case uses a blast 100x weaker than the Sedov
-    configuration: with the full blast the pressure ratio (5e8) exceeds the
-    24-bit resolution of FP32, and the forward-Euler first stage leaves cells
-    whose pressure is a difference of nearly equal FP32 energies; the
-    Hancock path is unaffected there (see test_f32bulk_one_step)."""
+def test_f32bulk_rk2_one_step(orc, fx, case, integrator):
+    """FP32-bulk SSP-RK2 and SSP-RK3.  The AMR case uses a blast 100x weaker
+    than the Sedov configuration: with the full blast the pressure ratio (5e8)
+    exceeds the 24-bit resolution of FP32, and the forward-Euler first stage
+    leaves cells whose pressure is a difference of nearly equal FP32
+    energies; the Hancock path is unaffected there (see
+    test_f32bulk_one_step)."""
     if case == "amr_sedov_weak":
         mesh = mesh_2level(4, 16, 4)
         W = inputs.sedov_state(mesh, e_blast=0.01)
@@ -140,10 +142,10 @@ def test_f32bulk_rk2_one_step(orc, fx, case):
         mesh, W = CASES[case]()
     om = orc.OracleMesh(mesh)
     U = om.prim_to_cons(W)
-    bs = f32_blockset(fx, mesh, W, options={"integrator": 1})
-    Uo, dto = om.step(U, integrator=1)
+    bs = f32_blockset(fx, mesh, W, options={"integrator": integrator})
+    Uo, dto = om.step(U, integrator=integrator)
     bs.step(0.8)
     assert bs.status() == 0
     err = max_rel_err_vec(mesh, bs.state(), Uo)
-    print(f"\nf32bulk SSP-RK2 one step {case}: max rel err {err:.3e}")
+    print(f"\nf32bulk SSP-RK{integrator + 1} one step {case}: max rel err {err:.3e}")
     assert err <= 1e-5, err
