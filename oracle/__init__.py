@@ -67,6 +67,12 @@ def lib():
                                                ctypes.c_int, dp]
             L.or_hydro_advance_rk3.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_double,
                                                ctypes.c_int, dp]
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            L.or_regrid_errors.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, dp]
+            L.or_regrid_plan.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_int, ctypes.c_int, ip, i64p, ip, ip, ip, ip]
+            L.or_regrid_transfer.argtypes = [ctypes.c_void_p, dp, ctypes.c_void_p, ip, ip, ip,
+                                             dp]
             L.or_mc.restype = ctypes.c_double
             L.or_mc.argtypes = [ctypes.c_double, ctypes.c_double]
             L.or_hllc.argtypes = [dp, dp, ctypes.c_int, ctypes.c_double, dp]
@@ -169,6 +175,49 @@ class OracleMesh:
             st = lib().or_hydro_advance(self._h, _dp(U), _dp(Unew), float(dt), int(reflux), bptr,
                                         0, None)
         return Unew, st, bflux
+
+    def regrid_errors(self, U: np.ndarray, eps: float = 0.01) -> np.ndarray:
+        """Loehner indicator per block (U guard-filled; -1 for parents)."""
+        err = np.zeros(self.mesh.nb)
+        lib().or_regrid_errors(self._h, _dp(U), float(eps), _dp(err))
+        return err
+
+    def regrid(self, U: np.ndarray, refine_cutoff: float = 0.8, derefine_cutoff: float = 0.2,
+               eps: float = 0.01, max_level: int | None = None):
+        """One regrid of state ``U``: restriction into parents, full guard
+        fill, error estimate, marking with 2:1 balance, new mesh, data
+        transfer, restriction into the new parents.  Returns
+        ``(OracleMesh of the new mesh, new state, errors, (kind, src, oct))``."""
+        import dataclasses
+        m = self.mesh
+        max_level = int(m.level.max()) + 1 if max_level is None else int(max_level)
+        U = U.copy()
+        self.restrict_parents(U)
+        self.guardcell_fill(U)
+        err = self.regrid_errors(U, eps)
+        cap = m.nb * (1 + 2 ** m.ndim)
+        level = np.zeros(cap, dtype=np.int32)
+        origin = np.zeros((cap, 3), dtype=np.int64)
+        parent = np.zeros(cap, dtype=np.int32)
+        kind = np.zeros(cap, dtype=np.int32)
+        src = np.zeros(cap, dtype=np.int32)
+        octs = np.zeros(cap, dtype=np.int32)
+        nn = lib().or_regrid_plan(self._h, _dp(err), float(refine_cutoff), float(derefine_cutoff),
+                                  max_level, cap, _ip(level),
+                                  origin.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  _ip(parent), _ip(kind), _ip(src), _ip(octs))
+        if nn < 0:
+            raise RuntimeError(lib().or_last_error().decode())
+        new_mesh = dataclasses.replace(m, level=level[:nn].copy(), origin=origin[:nn].copy(),
+                                       parent=parent[:nn].copy(), extra={})
+        om = OracleMesh(new_mesh, self.gamma)
+        Unew = np.zeros(new_mesh.shape)
+        maps = (np.ascontiguousarray(kind[:nn]), np.ascontiguousarray(src[:nn]),
+                np.ascontiguousarray(octs[:nn]))
+        lib().or_regrid_transfer(self._h, _dp(U), om._h, _ip(maps[0]), _ip(maps[1]),
+                                 _ip(maps[2]), _dp(Unew))
+        om.restrict_parents(Unew)
+        return om, Unew, err, maps
 
     def restrict_parents(self, U: np.ndarray) -> None:
         lib().or_restrict_parents(self._h, _dp(U))

@@ -114,6 +114,32 @@ void or_restrict_parents(const or_mesh *m, double *U);
  * order).  Pinned by conservation tests. */
 void or_conserved_totals(const or_mesh *m, const double *U, double out[5]);
 
+/* Regridding (dynamic refinement of the PARAMESH-style octree, Section 2).
+ * or_regrid_errors: per block, the maximum over interior cells and over
+ * density and pressure of Loehner's (1987) normalised second-derivative
+ * indicator with filter eps (-1 for non-leaf blocks).  U must have filled
+ * guards.  Pinned: zero on linear fields, closed forms on a quadratic and a
+ * step.
+ * or_regrid_plan: leaves with error > rc (and level < max_level) are
+ * refined; a parent whose children are all leaves with error < dc (none
+ * refined) is coarsened; then, until nothing changes, any leaf region two or
+ * more levels coarser than a touching region (faces, edges, corners;
+ * periodic wrap) is refined, or its coarsening cancelled.  Writes the new
+ * mesh sorted by (level, z, y, x of the origin) with parents, and per new
+ * block kind 0 = kept (src = old block) or 1 = new child (src = old parent,
+ * oct = octant).  Returns the new block count, or -1 (capacity / error).
+ * or_regrid_transfer: kept blocks copy their interior, new children take
+ * the conservative MC-limited linear prolongation of the parent (the guard
+ * prolongation's formula; Uold guards filled).  Parents of the new mesh are
+ * left to or_restrict_parents.  Pinned: conservation, uniform state, linear
+ * fields, 2:1 balance and requests honoured (brute force). */
+int or_regrid_errors(const or_mesh *m, const double *U, double eps, double *err);
+int or_regrid_plan(const or_mesh *m, const double *err, double rc, double dc, int max_level,
+                   int cap, int *level_out, int64_t *origin_out, int *parent_out, int *kind_out,
+                   int *src_out, int *oct_out);
+int or_regrid_transfer(const or_mesh *om, const double *Uold, const or_mesh *nm, const int *kind,
+                       const int *src, const int *oct, double *Unew);
+
 /* Point functions for unit pins. */
 double or_mc(double a, double b);
 void or_hllc(const double WL[5], const double WR[5], int dir, double gamma, double F[5]);

@@ -861,6 +861,274 @@ int or_hydro_advance_rk3(const or_mesh *m, const double *U, double *Unew, double
 }
 
 /* ------------------------------------------------------------------------ */
+/* regridding                                                                */
+/* ------------------------------------------------------------------------ */
+
+/* Loehner's (1987) normalised second-derivative indicator of one interior
+ * cell (i, j, k) of a scalar field q given on a block's padded array
+ * [PZ][P][P] (guards filled at depth 1, edges and corners included):
+ *   E = sqrt( sum_{a,b} (N_ab / (dx_a dx_b))^2 / sum_{a,b} (D_ab / (dx_a dx_b))^2 )
+ * over ordered direction pairs, with
+ *   a = b:  N = (q+ - q0) - (q0 - q-),
+ *           D = |q+ - q0| + |q0 - q-| + eps (|q+| + 2|q0| + |q-|)
+ *   a != b: N = ((q++ - q-+) - (q+- - q--)) / 4,
+ *           D = (|q++ - q-+| + |q+- - q--|) / 4 + eps (|q++| + |q-+| + |q+-| + |q--|) / 4
+ * (first sign: direction a, second: direction b); E = 0 where the
+ * denominator vanishes. */
+static double loehner_cell(const or_mesh *m, const double *q, int lev, int k, int j, int i,
+                           double eps) {
+  int P = m->P, nd = m->ndim;
+  double num = 0.0, den = 0.0;
+  for (int a = 0; a < nd; a++)
+    for (int b = 0; b < nd; b++) {
+      double nu, de;
+      if (a == b) {
+        int p[3] = {i, j, k}, q_[3] = {i, j, k};
+        p[a] += 1;
+        q_[a] -= 1;
+        double up = q[((size_t)p[2] * P + p[1]) * P + p[0]];
+        double u0 = q[((size_t)k * P + j) * P + i];
+        double um = q[((size_t)q_[2] * P + q_[1]) * P + q_[0]];
+        nu = (up - u0) - (u0 - um);
+        de = fabs(up - u0) + fabs(u0 - um) + eps * (fabs(up) + 2.0 * fabs(u0) + fabs(um));
+      } else {
+        double u[2][2];
+        for (int sa = 0; sa < 2; sa++)
+          for (int sb = 0; sb < 2; sb++) {
+            int c[3] = {i, j, k};
+            c[a] += sa ? 1 : -1;
+            c[b] += sb ? 1 : -1;
+            u[sa][sb] = q[((size_t)c[2] * P + c[1]) * P + c[0]];
+          }
+        nu = ((u[1][1] - u[0][1]) - (u[1][0] - u[0][0])) * 0.25;
+        de = (fabs(u[1][1] - u[0][1]) + fabs(u[1][0] - u[0][0])) * 0.25 +
+             eps * (fabs(u[1][1]) + fabs(u[0][1]) + fabs(u[1][0]) + fabs(u[0][0])) * 0.25;
+      }
+      double sc = 1.0 / (m->dx[lev][a] * m->dx[lev][b]);
+      nu = nu * sc;
+      de = de * sc;
+      num = num + nu * nu;
+      den = den + de * de;
+    }
+  return den > 0.0 ? sqrt(num / den) : 0.0;
+}
+
+int or_regrid_errors(const or_mesh *m, const double *U, double eps, double *err) {
+  int P = m->P, PZ = m->PZ, ng = m->ng, n = m->nxb, nd = m->ndim;
+  size_t plane = (size_t)PZ * P * P;
+#pragma omp parallel num_threads(or_get_threads())
+  {
+    double *rho = (double *)malloc(sizeof(double) * plane);
+    double *pre = (double *)malloc(sizeof(double) * plane);
+#pragma omp for schedule(dynamic)
+    for (int b = 0; b < m->nb; b++) {
+      if (!m->leaf[b]) { err[b] = -1.0; continue; }
+      for (size_t c = 0; c < plane; c++) {
+        double u[5], w[5];
+        for (int v = 0; v < 5; v++) u[v] = U[((size_t)b * 5 + v) * plane + c];
+        prim_from_cons(u, m->gamma, w);
+        rho[c] = w[0];
+        pre[c] = w[4];
+      }
+      double e = 0.0;
+      int k0 = nd == 3 ? ng : 0, k1 = nd == 3 ? ng + n : 1;
+      for (int k = k0; k < k1; k++)
+        for (int j = ng; j < ng + n; j++)
+          for (int i = ng; i < ng + n; i++) {
+            double a = loehner_cell(m, rho, m->level[b], k, j, i, eps);
+            double c2 = loehner_cell(m, pre, m->level[b], k, j, i, eps);
+            if (a > e) e = a;
+            if (c2 > e) e = c2;
+          }
+      err[b] = e;
+    }
+    free(rho);
+    free(pre);
+  }
+  return 0;
+}
+
+typedef struct {
+  int level;
+  int64_t o[3];
+  int kind, src, oct;
+} rg_entry;
+
+static int rg_cmp(const void *x, const void *y) {
+  const rg_entry *a = (const rg_entry *)x, *b = (const rg_entry *)y;
+  if (a->level != b->level) return a->level < b->level ? -1 : 1;
+  for (int d = 2; d >= 0; d--)
+    if (a->o[d] != b->o[d]) return a->o[d] < b->o[d] ? -1 : 1;
+  return 0;
+}
+
+int or_regrid_plan(const or_mesh *m, const double *err, double rc, double dc, int max_level,
+                   int cap, int *level_out, int64_t *origin_out, int *parent_out, int *kind_out,
+                   int *src_out, int *oct_out) {
+  int nb = m->nb, nd = m->ndim, n = m->nxb;
+  int *ref = (int *)calloc(nb, sizeof(int));
+  int *der = (int *)calloc(nb, sizeof(int));
+  /* requests */
+  for (int b = 0; b < nb; b++)
+    if (m->leaf[b] && err[b] > rc && m->level[b] < max_level) ref[b] = 1;
+  for (int p = 0; p < nb; p++) {
+    if (m->leaf[p]) continue;
+    int ok = 1;
+    for (int c = 0; c < (1 << nd); c++) {
+      int ch = m->child[p * 8 + c];
+      if (!m->leaf[ch] || !(err[ch] < dc) || ref[ch]) ok = 0;
+    }
+    der[p] = ok;
+  }
+  /* 2:1 balance on a lattice of blocks one level finer than the finest */
+  int Lf = m->lmax + 1;
+  int64_t gn[3];
+  size_t tot = 1;
+  for (int d = 0; d < 3; d++) {
+    gn[d] = d < nd ? ((int64_t)m->nroot[d] << Lf) : 1;
+    tot *= (size_t)gn[d];
+  }
+  int *LV = (int *)malloc(sizeof(int) * tot);
+  int *OW = (int *)malloc(sizeof(int) * tot);
+  int stuck = 0;
+  for (int changed = 1; changed;) {
+    changed = 0;
+    for (int b = 0; b < nb; b++) {
+      if (!m->leaf[b]) continue;
+      int X = b, lvl = m->level[b] + ref[b];
+      if (m->parent[b] >= 0 && der[m->parent[b]]) { X = m->parent[b]; lvl = m->level[X]; }
+      int sh = Lf - m->level[X];
+      int64_t lo[3], hi[3];
+      for (int d = 0; d < 3; d++) {
+        if (d < nd) { lo[d] = (m->origin[X * 3 + d] / n) << sh; hi[d] = lo[d] + ((int64_t)1 << sh); }
+        else { lo[d] = 0; hi[d] = 1; }
+      }
+      for (int64_t z = lo[2]; z < hi[2]; z++)
+        for (int64_t y = lo[1]; y < hi[1]; y++)
+          for (int64_t x = lo[0]; x < hi[0]; x++) {
+            size_t g = ((size_t)z * gn[1] + y) * gn[0] + x;
+            LV[g] = lvl;
+            OW[g] = X;
+          }
+    }
+    for (int64_t z = 0; z < gn[2]; z++)
+      for (int64_t y = 0; y < gn[1]; y++)
+        for (int64_t x = 0; x < gn[0]; x++) {
+          size_t g = ((size_t)z * gn[1] + y) * gn[0] + x;
+          int X = OW[g];
+          int need = 0;
+          for (int dz = (nd == 3 ? -1 : 0); dz <= (nd == 3 ? 1 : 0) && !need; dz++)
+            for (int dy = -1; dy <= 1 && !need; dy++)
+              for (int dx = -1; dx <= 1 && !need; dx++) {
+                int64_t h[3] = {x + dx, y + dy, z + dz};
+                int skip = 0;
+                for (int d = 0; d < nd; d++) {
+                  if (h[d] < 0 || h[d] >= gn[d]) {
+                    if (m->bc[d][h[d] < 0 ? 0 : 1] == 1) h[d] = (h[d] + gn[d]) % gn[d];
+                    else skip = 1;
+                  }
+                }
+                if (skip) continue;
+                size_t gh = ((size_t)h[2] * gn[1] + h[1]) * gn[0] + h[0];
+                if (LV[gh] > LV[g] + 1) need = 1;
+              }
+          if (!need) continue;
+          if (!m->leaf[X]) {                  /* a coarsening that would unbalance */
+            if (der[X]) { der[X] = 0; changed = 1; }
+          } else if (!ref[X]) {               /* a leaf too coarse next to finer ones */
+            ref[X] = 1;
+            changed = 1;
+          } else if (LV[g] == m->level[X] + 1) {
+            stuck = 1;                        /* refined already: not reachable from a
+                                                 balanced mesh */
+          }
+        }
+    if (stuck) break;
+  }
+  free(LV);
+  free(OW);
+  if (stuck) { free(ref); free(der); set_err("regrid: mesh not 2:1 balanced"); return -1; }
+  /* the new block list */
+  rg_entry *e = (rg_entry *)malloc(sizeof(rg_entry) * ((size_t)nb * (1 + (1 << nd))));
+  int ne = 0;
+  for (int b = 0; b < nb; b++) {
+    if (m->parent[b] >= 0 && der[m->parent[b]]) continue;
+    e[ne].level = m->level[b];
+    for (int d = 0; d < 3; d++) e[ne].o[d] = m->origin[b * 3 + d];
+    e[ne].kind = 0; e[ne].src = b; e[ne].oct = 0;
+    ne++;
+    if (m->leaf[b] && ref[b])
+      for (int c = 0; c < (1 << nd); c++) {
+        e[ne].level = m->level[b] + 1;
+        for (int d = 0; d < 3; d++)
+          e[ne].o[d] = d < nd ? 2 * m->origin[b * 3 + d] + (((c >> d) & 1) ? n : 0) : 0;
+        e[ne].kind = 1; e[ne].src = b; e[ne].oct = c;
+        ne++;
+      }
+  }
+  free(ref);
+  free(der);
+  if (ne > cap) { free(e); set_err("regrid: output capacity too small"); return -1; }
+  qsort(e, ne, sizeof(rg_entry), rg_cmp);
+  for (int i = 0; i < ne; i++) {
+    level_out[i] = e[i].level;
+    for (int d = 0; d < 3; d++) origin_out[i * 3 + d] = e[i].o[d];
+    kind_out[i] = e[i].kind; src_out[i] = e[i].src; oct_out[i] = e[i].oct;
+    parent_out[i] = -1;
+    if (e[i].level == 0) continue;
+    rg_entry key;
+    key.level = e[i].level - 1;
+    for (int d = 0; d < 3; d++) key.o[d] = d < nd ? ((e[i].o[d] / n) / 2) * n : 0;
+    rg_entry *f = (rg_entry *)bsearch(&key, e, ne, sizeof(rg_entry), rg_cmp);
+    if (!f) { free(e); set_err("regrid: block without parent"); return -1; }
+    parent_out[i] = (int)(f - e);
+  }
+  free(e);
+  return ne;
+}
+
+int or_regrid_transfer(const or_mesh *om, const double *Uold, const or_mesh *nm, const int *kind,
+                       const int *src, const int *oct, double *Unew) {
+  int n = nm->nxb, ng = nm->ng, nd = nm->ndim;
+  int nz = nd == 3 ? n : 1, kz = nd == 3 ? ng : 0;
+#pragma omp parallel for schedule(dynamic) num_threads(or_get_threads())
+  for (int b = 0; b < nm->nb; b++) {
+    int s = src[b];
+    for (int v = 0; v < 5; v++)
+      for (int k = 0; k < nz; k++)
+        for (int j = 0; j < n; j++)
+          for (int i = 0; i < n; i++) {
+            double val;
+            if (kind[b] == 0) {
+              val = Uold[cell_index(om, s, v, k + kz, j + ng, i + ng)];
+            } else {
+              /* conservative MC-limited linear prolongation from the parent */
+              int f[3] = {i, j, k}, pc[3];
+              for (int d = 0; d < 3; d++) {
+                int fine = d < nd ? ((oct[b] >> d) & 1) * n + f[d] : 0;
+                pc[d] = d < nd ? fine / 2 + ng : 0;
+                f[d] = fine;
+              }
+              double uc = Uold[cell_index(om, s, v, pc[2], pc[1], pc[0])];
+              val = uc;
+              for (int d = 0; d < nd; d++) {
+                int lm[3] = {pc[0], pc[1], pc[2]}, lp[3] = {pc[0], pc[1], pc[2]};
+                lm[d] -= 1;
+                lp[d] += 1;
+                double um = Uold[cell_index(om, s, v, lm[2], lm[1], lm[0])];
+                double up = Uold[cell_index(om, s, v, lp[2], lp[1], lp[0])];
+                double sigma = or_mc(uc - um, up - uc);
+                double sg = (f[d] % 2 == 0) ? -0.25 : 0.25;
+                val = val + sg * sigma;
+              }
+            }
+            Unew[cell_index(nm, b, v, k + kz, j + ng, i + ng)] = val;
+          }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* conserved totals                                                          */
 /* ------------------------------------------------------------------------ */
 
