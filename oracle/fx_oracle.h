@@ -130,7 +130,9 @@ void or_conserved_totals(const or_mesh *m, const double *U, double out[5]);
  * oct = octant).  Returns the new block count, or -1 (capacity / error).
  * or_regrid_transfer: kept blocks copy their interior, new children take
  * the conservative MC-limited linear prolongation of the parent (the guard
- * prolongation's formula; Uold guards filled).  Parents of the new mesh are
+ * prolongation's formula; Uold guards filled) -- per coarse cell, unless that
+ * would leave a non-positive density or pressure in one of its children, in
+ * which case all of them take the coarse value.  Parents of the new mesh are
  * left to or_restrict_parents.  Pinned: conservation, uniform state, linear
  * fields, 2:1 balance and requests honoured (brute force). */
 int or_regrid_errors(const or_mesh *m, const double *U, double eps, double *err);

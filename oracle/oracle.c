@@ -1087,6 +1087,27 @@ int or_regrid_plan(const or_mesh *m, const double *err, double rc, double dc, in
   return ne;
 }
 
+/* Conservative MC-limited linear prolongation of variable v of parent
+ * block s, coarse cell pc (padded indices), to the fine cell whose fine
+ * parities along x, y, z are par[] (0 lower half, 1 upper half). */
+static double prolong_value(const or_mesh *om, const double *Uold, int s, int v, const int pc[3],
+                            const int par[3]) {
+  int nd = om->ndim;
+  double uc = Uold[cell_index(om, s, v, pc[2], pc[1], pc[0])];
+  double val = uc;
+  for (int d = 0; d < nd; d++) {
+    int lm[3] = {pc[0], pc[1], pc[2]}, lp[3] = {pc[0], pc[1], pc[2]};
+    lm[d] -= 1;
+    lp[d] += 1;
+    double um = Uold[cell_index(om, s, v, lm[2], lm[1], lm[0])];
+    double up = Uold[cell_index(om, s, v, lp[2], lp[1], lp[0])];
+    double sigma = or_mc(uc - um, up - uc);
+    double sg = par[d] ? 0.25 : -0.25;
+    val = val + sg * sigma;
+  }
+  return val;
+}
+
 int or_regrid_transfer(const or_mesh *om, const double *Uold, const or_mesh *nm, const int *kind,
                        const int *src, const int *oct, double *Unew) {
   int n = nm->nxb, ng = nm->ng, nd = nm->ndim;
@@ -1094,36 +1115,37 @@ int or_regrid_transfer(const or_mesh *om, const double *Uold, const or_mesh *nm,
 #pragma omp parallel for schedule(dynamic) num_threads(or_get_threads())
   for (int b = 0; b < nm->nb; b++) {
     int s = src[b];
-    for (int v = 0; v < 5; v++)
-      for (int k = 0; k < nz; k++)
-        for (int j = 0; j < n; j++)
-          for (int i = 0; i < n; i++) {
-            double val;
-            if (kind[b] == 0) {
-              val = Uold[cell_index(om, s, v, k + kz, j + ng, i + ng)];
-            } else {
-              /* conservative MC-limited linear prolongation from the parent */
-              int f[3] = {i, j, k}, pc[3];
-              for (int d = 0; d < 3; d++) {
-                int fine = d < nd ? ((oct[b] >> d) & 1) * n + f[d] : 0;
-                pc[d] = d < nd ? fine / 2 + ng : 0;
-                f[d] = fine;
-              }
-              double uc = Uold[cell_index(om, s, v, pc[2], pc[1], pc[0])];
-              val = uc;
-              for (int d = 0; d < nd; d++) {
-                int lm[3] = {pc[0], pc[1], pc[2]}, lp[3] = {pc[0], pc[1], pc[2]};
-                lm[d] -= 1;
-                lp[d] += 1;
-                double um = Uold[cell_index(om, s, v, lm[2], lm[1], lm[0])];
-                double up = Uold[cell_index(om, s, v, lp[2], lp[1], lp[0])];
-                double sigma = or_mc(uc - um, up - uc);
-                double sg = (f[d] % 2 == 0) ? -0.25 : 0.25;
-                val = val + sg * sigma;
-              }
+    for (int k = 0; k < nz; k++)
+      for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) {
+          double out[5];
+          if (kind[b] == 0) {
+            for (int v = 0; v < 5; v++) out[v] = Uold[cell_index(om, s, v, k + kz, j + ng, i + ng)];
+          } else {
+            /* new child: the parent's coarse cell and this cell's parities */
+            int f[3] = {i, j, k}, pc[3], par[3];
+            for (int d = 0; d < 3; d++) {
+              int fine = d < nd ? ((oct[b] >> d) & 1) * n + f[d] : 0;
+              pc[d] = d < nd ? fine / 2 + ng : 0;
+              par[d] = fine % 2;
             }
-            Unew[cell_index(nm, b, v, k + kz, j + ng, i + ng)] = val;
+            /* linear prolongation, unless it leaves a non-positive density
+             * or pressure in any of the coarse cell's 2^d children: then
+             * all of them take the coarse value (still conservative) */
+            int ok = 1;
+            for (int c = 0; c < (1 << nd) && ok; c++) {
+              int pq[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+              double u[5], w[5];
+              for (int v = 0; v < 5; v++) u[v] = prolong_value(om, Uold, s, v, pc, pq);
+              prim_from_cons(u, om->gamma, w);
+              if (!(w[0] > 0.0) || !(w[4] > 0.0)) ok = 0;
+            }
+            for (int v = 0; v < 5; v++)
+              out[v] = ok ? prolong_value(om, Uold, s, v, pc, par)
+                          : Uold[cell_index(om, s, v, pc[2], pc[1], pc[0])];
           }
+          for (int v = 0; v < 5; v++) Unew[cell_index(nm, b, v, k + kz, j + ng, i + ng)] = out[v];
+        }
   }
   return 0;
 }

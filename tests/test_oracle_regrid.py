@@ -348,3 +348,45 @@ def test_transfer_linear_field_exact_and_uniform_bitwise(orc):
     Li = leaf_interior(om3.mesh, U3)
     ref = leaf_interior(mesh, om.prim_to_cons(Wu))[0, :, 0, 0, 0]
     assert np.all(Li == ref[None, :, None, None, None])
+
+
+def test_transfer_injects_where_linear_prolongation_is_not_positive(orc):
+    """Density 1, momentum m = 2x (coarse cells ..., -2, 0, 2, ...), energy
+    kinetic + 100, except kinetic + 1e-3 in the column where m = 0: there the
+    MC slope of E vanishes (E has a minimum) while the momentum slope does
+    not, so the linear children would carry m = +-1/2 with the coarse energy
+    and a negative pressure.  They take the coarse value instead; elsewhere
+    the prolongation stays linear; totals are conserved exactly."""
+    mesh = inputs.uniform_mesh(2, (2, 2), 8, 4, O_)
+    om = orc.OracleMesh(mesh)
+    U = np.zeros(mesh.shape)
+    tiny = 1e-3
+    for b in range(mesh.nb):
+        X, Y, _ = mesh.global_index(b)
+        X, Y = np.broadcast_arrays(X, Y)
+        m = 2.0 * (X[0] - 7)
+        U[b, 0, 0, 4:12, 4:12] = 1.0
+        U[b, 1, 0, 4:12, 4:12] = m
+        U[b, 4, 0, 4:12, 4:12] = 0.5 * m * m + np.where(X[0] == 7, tiny, 100.0)
+    om2, U2, err, (kind, src, octs) = om.regrid(U, refine_cutoff=-1.0, derefine_cutoff=-1.0,
+                                                max_level=1)
+    m2 = om2.mesh
+    W2 = om2.cons_to_prim(U2)
+    leaf = m2.is_leaf().astype(bool)
+    assert np.all(m2.interior(W2)[leaf][:, 4] > 0.0)
+    # the children of coarse column x = 7 (m = 0) carry exactly the coarse state
+    for b in range(m2.nb):
+        if not leaf[b]:
+            continue
+        X, Y, _ = m2.global_index(b)
+        X = np.broadcast_to(X, (1, 8, 8))[0]
+        cols = (X // 2 == 7)
+        if cols.any():
+            assert np.all(m2.interior(U2)[b, 1, 0][cols] == 0.0)
+            assert np.all(m2.interior(U2)[b, 4, 0][cols] == tiny)
+        far = (X // 2 == 3)
+        if far.any():              # a linear profile: children split the slope
+            got = m2.interior(U2)[b, 1, 0][far]
+            assert set(np.unique(got)) == {-8.5, -7.5}
+    T0, T1 = om.conserved_totals(U), om2.conserved_totals(U2)
+    assert np.all(T1 == T0)
