@@ -228,6 +228,44 @@ FX_API int fx_run_host(fx_ctx *ctx, fx_blocks *bs, const void *U_host_in, void *
 FX_API int fx_run_host_interior(fx_ctx *ctx, fx_blocks *bs, const void *W_in, void *W_out,
                                 int nsteps, double cfl, double *t_host, void *stream);
 
+/* ---- regridding (dynamic refinement) ----------------------------------
+ * Paper: the Grid unit's octree adapts to the solution (PARAMESH, Section 2).
+ * The criterion is Loehner's (1987) normalised second derivative, evaluated
+ * per cell on density and pressure (the FLASH-family default refinement
+ * variables), maximised over each leaf.  Two calls change the mesh, so that
+ * the caller can allocate the new state buffers in between:
+ *
+ * fx_regrid_plan: restricts the parents and fills every guard layer of the
+ *   current state (leaf interiors unchanged), computes the indicator with
+ *   filter `filter` (0.01 typical), and plans the new mesh: leaves above
+ *   `refine_cutoff` are split (up to level `max_level`), sibling leaves all
+ *   below `derefine_cutoff` merge into their parent, then splits are added
+ *   and merges cancelled until touching leaf regions (faces, edges, corners,
+ *   periodic wrap) differ by at most one level.  *nblocks_new receives the
+ *   new block count.  Synchronises `stream`.  Errors: FX_ERR_ARG,
+ *   FX_ERR_STATE (in a batch), FX_ERR_OOM, FX_ERR_CUDA, FX_ERR_MESH.
+ * fx_regrid_errors: the indicator per block of the current mesh from the
+ *   last plan (-1 for parents); err_host holds nblocks doubles.
+ * fx_regrid_mesh: the planned mesh (nblocks_new entries, sorted by level,
+ *   then z, y, x of the origin): level, origin [n][3] in the block's level
+ *   lattice, parent (-1 at level 0).
+ * fx_regrid_apply: moves the state onto the planned mesh in the new
+ *   caller-owned buffers U0_new, U1_new (nblocks_new * 5 * PZ * P * P
+ *   elements, 16-byte aligned; U0_new becomes current): kept blocks copy
+ *   their interior, new children take the conservative MC-limited linear
+ *   prolongation of their parent, parents are restricted.  The handle then
+ *   describes the new mesh (tables rebuilt, old buffers no longer used: the
+ *   caller may free them after this call returns).  Totals are conserved to
+ *   rounding.  Synchronises.  Errors: FX_ERR_STATE (no plan / in a batch),
+ *   FX_ERR_ARG, FX_ERR_OOM, FX_ERR_CUDA, FX_ERR_MESH. */
+FX_API int fx_regrid_plan(fx_ctx *ctx, fx_blocks *bs, double refine_cutoff,
+                          double derefine_cutoff, double filter, int max_level, void *stream,
+                          int *nblocks_new);
+FX_API int fx_regrid_errors(const fx_blocks *bs, double *err_host);
+FX_API int fx_regrid_mesh(const fx_blocks *bs, int *level, int64_t *origin, int *parent);
+FX_API int fx_regrid_apply(fx_ctx *ctx, fx_blocks *bs, void *U0_new, void *U1_new,
+                           void *stream);
+
 /* fx_block_fluxes: device pointer to the flux registers of block `b`
  * ([2*ndim faces x-,x+,y-,y+,z-,z+][5][nxb^(ndim-1)], lower transverse axis
  * fastest) written by the last fx_hydro_advance, or NULL if the block has no

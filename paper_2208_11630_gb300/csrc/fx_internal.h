@@ -6,6 +6,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
+#include <vector>
 
 #include "fx.h"
 
@@ -103,6 +105,14 @@ cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, 
                          int n, const double *dt, double *regs, int *status,
                          unsigned long long *smax, const unsigned char *rmask, int form,
                          cudaStream_t s, const HydroStage &st = HydroStage());
+// Regridding: per-leaf maximum of the Loehner indicator on density and
+// pressure (filter eps) into err_bits[i] for leaves[i] (bit patterns, zeroed
+// by the caller; guards filled); and the state transfer onto a new mesh,
+// map[j] = (kind 0 copy / 1 prolong, old block, octant, -) per new block.
+cudaError_t launch_regrid_err(const DevMesh &m, const void *U, int prec, const int *leaves, int n,
+                              double eps, unsigned long long *err_bits, cudaStream_t s);
+cudaError_t launch_regrid_transfer(const DevMesh &mo, const void *Uold, const DevMesh &mn,
+                                   void *Unew, int prec, const int4 *map, cudaStream_t s);
 // The SSP Runge-Kutta stage kernels behind launch_hydro (st.pred == 0).
 cudaError_t launch_hydro_rk(const DevMesh &m, const void *U, void *Unew, int prec,
                             const int *leaves, int n, const double *dt, double *regs, int *status,
@@ -146,6 +156,19 @@ cudaError_t hydro_batch_fit(int ndim, int tile, int prec, int *fit);
 cudaError_t launch_hydro_batch(int ndim, int tile, int prec, const BatchReq *reqs,
                                const int4 *items, int nitems, unsigned int *counter,
                                int ctas_per_sm, int nsm, cudaStream_t s);
+
+// Host plan of a regrid (regrid.cpp): the new mesh sorted by (level, z, y,
+// x) and, per new block, (kind 0 keep / 1 new child, old block or old
+// parent, octant, 0).  Returns FX_OK or FX_ERR_MESH with *msg set.
+struct RegridPlan {
+  std::vector<int> level, parent;
+  std::vector<long long> origin;   // [n][3]
+  std::vector<int4> map;
+};
+int regrid_plan(int ndim, int nxb, const int nroot[3], const int bc[6], int nb,
+                const std::vector<int> &level, const std::vector<int> &origin,
+                const std::vector<int> &parent, const std::vector<double> &err, double rc,
+                double dc, int max_level, RegridPlan *out, std::string *msg);
 
 // Process-wide count of kernels launched by the library.
 void count_launch(int n = 1);

@@ -1,0 +1,185 @@
+// k_regrid.cu -- device side of regridding (dynamic refinement of the
+// octree): the per-leaf error indicator and the transfer of the state onto a
+// new mesh.
+//
+// Paper: Flash-X (arXiv 2208.11630), Section 2 -- AMR with an octree of blocks
+// (PARAMESH).  Indicator: Loehner's (1987) normalised second derivative,
+// evaluated on density and pressure; transfer: kept blocks copy their
+// interior, new children take the conservative MC-limited linear
+// prolongation of their parent (the coarse-fine guard operator), with
+// injection where that would not be positive.
+#include "grid_ops.cuh"
+
+namespace fx {
+namespace {
+
+// Density (v = 0) or pressure (v = 4) of the cell at padded offset o.
+template <typename S>
+__device__ __forceinline__ double rho_or_p(const S *Ub, long long vs, long long o, int v,
+                                           double gm1) {
+  const double r = double(Ub[o]);
+  if (v == 0) return r;
+  const double mx = double(Ub[o + vs]), my = double(Ub[o + 2 * vs]), mz = double(Ub[o + 3 * vs]);
+  return gm1 * (double(Ub[o + 4 * vs]) - 0.5 * (mx * mx + my * my + mz * mz) / r);
+}
+
+// Indicator of one cell for one field: sqrt(sum N^2 / sum D^2) over ordered
+// direction pairs (a, b), each term scaled by 1/(dx_a dx_b); diagonal pairs
+// use the second difference over its first-difference magnitudes plus the
+// filter eps times |q+| + 2|q0| + |q-|; off-diagonal pairs the mixed
+// difference / 4 over the two a-differences at b -+ 1 / 4 plus eps times the
+// four corner magnitudes / 4.  Zero where the denominator vanishes.
+template <typename S>
+__device__ double loehner(const DevMesh &m, const S *Ub, int lev, int i, int j, int k, int v,
+                          double eps) {
+  const long long vs = m.vstride, P = m.P;
+  const long long step[3] = {1, P, P * P};
+  const long long o0 = ((long long)k * P + j) * P + i;
+  const double gm1 = m.gamma - 1.0;
+  double num = 0.0, den = 0.0;
+  for (int a = 0; a < m.ndim; ++a)
+    for (int b = 0; b < m.ndim; ++b) {
+      double nu, de;
+      if (a == b) {
+        const double up = rho_or_p(Ub, vs, o0 + step[a], v, gm1);
+        const double u0 = rho_or_p(Ub, vs, o0, v, gm1);
+        const double um = rho_or_p(Ub, vs, o0 - step[a], v, gm1);
+        nu = (up - u0) - (u0 - um);
+        de = fabs(up - u0) + fabs(u0 - um) + eps * (fabs(up) + 2.0 * fabs(u0) + fabs(um));
+      } else {
+        const double upp = rho_or_p(Ub, vs, o0 + step[a] + step[b], v, gm1);
+        const double ump = rho_or_p(Ub, vs, o0 - step[a] + step[b], v, gm1);
+        const double upm = rho_or_p(Ub, vs, o0 + step[a] - step[b], v, gm1);
+        const double umm = rho_or_p(Ub, vs, o0 - step[a] - step[b], v, gm1);
+        nu = ((upp - ump) - (upm - umm)) * 0.25;
+        de = (fabs(upp - ump) + fabs(upm - umm)) * 0.25 +
+             eps * (fabs(upp) + fabs(ump) + fabs(upm) + fabs(umm)) * 0.25;
+      }
+      const double sc = 1.0 / (m.dx[lev][a] * m.dx[lev][b]);
+      nu = nu * sc;
+      de = de * sc;
+      num = num + nu * nu;
+      den = den + de * de;
+    }
+  return den > 0.0 ? sqrt(num / den) : 0.0;
+}
+
+// One CTA per leaf: maximum over interior cells and over density and
+// pressure, into err_bits[leaf index] (bit pattern of a non-negative double;
+// zeroed by the caller).  Guards must be filled at depth 1.
+template <typename S>
+__global__ void k_regrid_err(DevMesh m, const S *__restrict__ U, const int *__restrict__ leaves,
+                             double eps, unsigned long long *__restrict__ err_bits) {
+  const int b = leaves[blockIdx.x];
+  const int n = m.nxb, ng = m.ng;
+  const int nz = m.ndim == 3 ? n : 1, kz = m.ndim == 3 ? ng : 0;
+  const S *Ub = U + (long long)b * m.bstride;
+  const int lev = m.level[b];
+  double e = 0.0;
+  for (int c = threadIdx.x; c < n * n * nz; c += blockDim.x) {
+    const int i = c % n + ng, j = (c / n) % n + ng, k = c / (n * n) + kz;
+    const double er = loehner(m, Ub, lev, i, j, k, 0, eps);
+    const double ep = loehner(m, Ub, lev, i, j, k, 4, eps);
+    e = fmax(e, fmax(er, ep));
+  }
+  unsigned long long bits = __double_as_longlong(e);
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_down_sync(0xffffffffu, bits, o);
+    bits = other > bits ? other : bits;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(err_bits + blockIdx.x, bits);
+}
+
+// New block j, padded z-plane blockIdx.y of its interior: kind 0 copies the
+// interior of old block src, kind 1 prolongs from old parent src (octant
+// oct; its guards filled at depth 1), in FP64, rounding once to S -- per
+// coarse cell, with the coarse value injected into all its children when
+// the linear form would leave one of them non-positive in density or
+// pressure.
+template <typename S>
+__global__ void k_regrid_transfer(DevMesh mo, const S *__restrict__ Uold, DevMesh mn,
+                                  S *__restrict__ Unew, const int4 *__restrict__ map) {
+  const int j = blockIdx.x;
+  const int4 w = map[j];            // (kind, src, oct, -)
+  const int n = mn.nxb, ng = mn.ng, P = mn.P;
+  const int kz = mn.ndim == 3 ? ng : 0;
+  const int k = blockIdx.y;         // interior plane
+  const S *Us = Uold + (long long)w.y * mo.bstride;
+  S *Ud = Unew + (long long)j * mn.bstride;
+  const long long sP = P, sPP = (long long)P * P;
+  const long long step[3] = {1, sP, sPP};
+  for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+    const int i = c % n, jj = c / n;
+    const long long od = ((long long)(k + kz) * P + (jj + ng)) * P + (i + ng);
+    if (w.x == 0) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Ud[od + v * mn.vstride] = Us[od + v * mo.vstride];
+      continue;
+    }
+    const int f[3] = {((w.z >> 0) & 1) * n + i, ((w.z >> 1) & 1) * n + jj,
+                      mn.ndim == 3 ? ((w.z >> 2) & 1) * n + k : 0};
+    const long long oc = ((long long)(mn.ndim == 3 ? f[2] / 2 + ng : 0) * P + (f[1] / 2 + ng)) * P +
+                         (f[0] / 2 + ng);
+    // conserved variables of the fine cell with parities q of coarse cell oc
+    auto prolong = [&](const int (&q)[3], double (&u)[5]) {
+      for (int v = 0; v < 5; ++v) {
+        const S *cv = Us + v * mo.vstride + oc;
+        const double uc = double(*cv);
+        double val = uc;
+        for (int d = 0; d < mn.ndim; ++d) {
+          const double um = double(cv[-step[d]]), up = double(cv[step[d]]);
+          const double sig = ops::mc_lim(uc - um, up - uc);
+          val = val + (q[d] ? 0.25 : -0.25) * sig;
+        }
+        u[v] = val;
+      }
+    };
+    // linear prolongation unless one of the coarse cell's 2^d children would
+    // get a non-positive density or pressure: then all take the coarse value
+    bool ok = true;
+    for (int c = 0; c < (1 << mn.ndim) && ok; ++c) {
+      const int q[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+      double u[5];
+      prolong(q, u);
+      const double pr = (mn.gamma - 1.0) * (u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0]);
+      if (!(u[0] > 0.0) || !(pr > 0.0)) ok = false;
+    }
+    double u[5];
+    if (ok) {
+      const int q[3] = {f[0] & 1, f[1] & 1, f[2] & 1};
+      prolong(q, u);
+    } else {
+      for (int v = 0; v < 5; ++v) u[v] = double(Us[v * mo.vstride + oc]);
+    }
+    for (int v = 0; v < 5; ++v) Ud[od + v * mn.vstride] = S(u[v]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_regrid_err(const DevMesh &m, const void *U, int prec, const int *leaves, int n,
+                              double eps, unsigned long long *err_bits, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (prec == 0)
+    k_regrid_err<double><<<n, 256, 0, s>>>(m, static_cast<const double *>(U), leaves, eps, err_bits);
+  else
+    k_regrid_err<float><<<n, 256, 0, s>>>(m, static_cast<const float *>(U), leaves, eps, err_bits);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_regrid_transfer(const DevMesh &mo, const void *Uold, const DevMesh &mn,
+                                   void *Unew, int prec, const int4 *map, cudaStream_t s) {
+  if (mn.nb <= 0) return cudaSuccess;
+  dim3 grid(mn.nb, mn.ndim == 3 ? mn.nxb : 1);
+  if (prec == 0)
+    k_regrid_transfer<double><<<grid, 256, 0, s>>>(mo, static_cast<const double *>(Uold), mn,
+                                                   static_cast<double *>(Unew), map);
+  else
+    k_regrid_transfer<float><<<grid, 256, 0, s>>>(mo, static_cast<const float *>(Uold), mn,
+                                                  static_cast<float *>(Unew), map);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace fx

@@ -73,6 +73,10 @@ def load(build: bool = True):
             "fx_status": (c_int, [vp, vp]),
             "fx_run_host": (c_int, [vp, vp, vp, vp, c_int, c_double, dp, vp]),
             "fx_run_host_interior": (c_int, [vp, vp, vp, vp, c_int, c_double, dp, vp]),
+            "fx_regrid_plan": (c_int, [vp, vp, c_double, c_double, c_double, c_int, vp, ip]),
+            "fx_regrid_errors": (c_int, [vp, dp]),
+            "fx_regrid_mesh": (c_int, [vp, ip, i64p, ip]),
+            "fx_regrid_apply": (c_int, [vp, vp, vp, vp, vp]),
             "fx_block_fluxes": (vp, [vp, c_int]),
             "fx_kernel_launches": (ctypes.c_longlong, []),
             "fx_batch_create": (c_int, [vp, c_int, ctypes.POINTER(vp)]),
@@ -381,6 +385,44 @@ class BlockSet:
                                  f"{self.interior_shape()}, got {a.dtype} {a.shape}")
         return fx_run_host_interior(self.ctx, self.bs, host_in, host_out, nsteps, cfl, stream,
                                     want_time)
+
+    def regrid(self, refine_cutoff: float = 0.8, derefine_cutoff: float = 0.2,
+               filt: float = 0.01, max_level: int | None = None, stream=None) -> bool:
+        """Adapt the mesh to the current state (fx_regrid_plan, new state
+        buffers, fx_regrid_apply).  ``self.mesh`` and the buffers follow.
+        Returns whether the mesh changed; the indicator of the old mesh's
+        blocks is kept in ``self.last_errors``."""
+        import dataclasses
+        import torch
+        L = load()
+        m = self.mesh
+        max_level = int(m.level.max()) + 1 if max_level is None else int(max_level)
+        nn = ctypes.c_int(0)
+        _check(self.ctx, L.fx_regrid_plan(self.ctx, self.bs, float(refine_cutoff),
+                                          float(derefine_cutoff), float(filt), max_level,
+                                          _stream_ptr(stream), ctypes.byref(nn)))
+        err = np.zeros(m.nb)
+        _check(self.ctx, L.fx_regrid_errors(self.bs, err.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_double))))
+        self.last_errors = err
+        n = nn.value
+        level = np.zeros(n, dtype=np.int32)
+        origin = np.zeros((n, 3), dtype=np.int64)
+        parent = np.zeros(n, dtype=np.int32)
+        _check(self.ctx, L.fx_regrid_mesh(self.bs, level.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                          origin.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                          parent.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        changed = not (n == m.nb and np.array_equal(level, m.level)
+                       and np.array_equal(origin, m.origin) and np.array_equal(parent, m.parent))
+        new_mesh = dataclasses.replace(m, level=level, origin=origin, parent=parent, extra={})
+        dev = self.U[0].device
+        U = [torch.zeros(new_mesh.shape, dtype=self.dtype, device=dev) for _ in range(2)]
+        _check(self.ctx, L.fx_regrid_apply(self.ctx, self.bs, ctypes.c_void_p(U[0].data_ptr()),
+                                           ctypes.c_void_p(U[1].data_ptr()),
+                                           _stream_ptr(stream)))
+        self.U = U
+        self.mesh = new_mesh
+        return changed
 
     def totals(self, stream=None) -> np.ndarray:
         return fx_conserved_totals(self.ctx, self.bs, stream)
