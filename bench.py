@@ -217,6 +217,36 @@ def measure_variants(args, fx, inputs, mesh, dev, cfl, zones, bs, ws, hbm_peak):
                   "step_hbm_frac": bpz * (z / t) / ws / (hbm_peak * 1e9),
                   "ok": bs2.status() == 0}
     bs2.close()
+    # (iii) dynamic AMR: the Sedov blast on its 2-level mesh, regridded every
+    # 4 steps (Loehner indicator on density and pressure, up to level 2);
+    # wall-clock time between synchronisations, since the plan runs on the host
+    meshs, Ws, gammas, _ = inputs.workload("sedov_amr", scale=None)
+    bs3 = fx.BlockSet(meshs, gammas, precision=fx.FX_F64, device=dev)
+    bs3.set_primitive(Ws)
+    del Ws
+    nsteps = max(8, args.steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    zones_done, regrid_s, nregrid = 0, 0.0, 0
+    for k in range(nsteps):
+        if k % 4 == 0:
+            torch.cuda.synchronize()
+            r0 = time.perf_counter()
+            bs3.regrid(refine_cutoff=0.8, derefine_cutoff=0.2, filt=0.01, max_level=2,
+                       stream=sptr)
+            regrid_s += time.perf_counter() - r0
+            nregrid += 1
+        fx.fx_step(bs3.ctx, bs3.bs, cfl, bs3.dt.data_ptr(), sptr)
+        zones_done += bs3.mesh.leaf_zones()
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    z, t = aggregate(zones_done, sec, dev)
+    out["dynamic_amr_sedov"] = {
+        "value": z / t, "unit": UNIT, "steps": nsteps, "regrid_every": 4,
+        "regrid_ms": 1e3 * regrid_s / nregrid, "blocks": int(bs3.mesh.nb),
+        "levels": np.bincount(bs3.mesh.level).tolist(), "timing": "wall clock",
+        "ok": bs3.status() == 0}
+    bs3.close()
     return out
 
 
