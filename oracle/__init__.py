@@ -68,6 +68,10 @@ def lib():
             L.or_hydro_advance_rk3.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_double,
                                                ctypes.c_int, dp]
             i64p = ctypes.POINTER(ctypes.c_int64)
+            L.or_mesh_set_species.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, dp]
+            L.or_riemann_star2.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp]
+            L.or_riemann_sample2.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, dp]
             L.or_regrid_errors.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, dp]
             L.or_regrid_plan.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_int, ctypes.c_int, ip, i64p, ip, ip, ip, ip]
@@ -120,6 +124,12 @@ class OracleMesh:
                                    _ip(self._parent), _dp(lo), _dp(hi), _ip(bc), self.gamma)
         if not self._h:
             raise ValueError(L.or_last_error().decode())
+        ns = int(getattr(mesh, "nspec", 0))
+        if ns:
+            g = np.array([sp[0] for sp in mesh.species], dtype=np.float64)
+            a = np.array([sp[1] for sp in mesh.species], dtype=np.float64)
+            if L.or_mesh_set_species(self._h, ns, _dp(g), _dp(a)):
+                raise ValueError(L.or_last_error().decode())
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -159,7 +169,7 @@ class OracleMesh:
         bptr = None
         if want_bflux:
             nf = m.nxb ** (m.ndim - 1)
-            bflux = np.zeros((m.nb, 2 * m.ndim, 5, nf))
+            bflux = np.zeros((m.nb, 2 * m.ndim, 5 + int(getattr(m, "nspec", 0)), nf))
             bptr = _dp(bflux)
         if integrator == 1:
             st = lib().or_hydro_advance_rk2(self._h, _dp(U), _dp(Unew), float(dt), int(reflux), bptr)
@@ -223,7 +233,7 @@ class OracleMesh:
         lib().or_restrict_parents(self._h, _dp(U))
 
     def conserved_totals(self, U: np.ndarray) -> np.ndarray:
-        out = np.zeros(5)
+        out = np.zeros(5 + int(getattr(self.mesh, "nspec", 0)))
         lib().or_conserved_totals(self._h, _dp(U), _dp(out))
         return out
 
@@ -279,6 +289,21 @@ def riemann_star(WL, WR, gamma: float = 1.4) -> np.ndarray:
     out = np.zeros(4)
     if lib().or_riemann_star(_dp(WL), _dp(WR), float(gamma), _dp(out)):
         raise ValueError("vacuum")
+    return out
+
+
+def riemann_sample2(WL, WR, xi, gL: float, gR: float) -> np.ndarray:
+    """Exact solution of a two-gas Riemann problem ({rho, u, p} per side,
+    gamma gL left of the contact, gR right) sampled at xi = x/t (array)."""
+    xi = np.atleast_1d(np.asarray(xi, dtype=np.float64))
+    out = np.zeros((xi.size, 3))
+    wl = np.ascontiguousarray(WL, dtype=np.float64)
+    wr = np.ascontiguousarray(WR, dtype=np.float64)
+    o = np.zeros(3)
+    for i, x in enumerate(xi):
+        if lib().or_riemann_sample2(_dp(wl), _dp(wr), float(gL), float(gR), float(x), _dp(o)):
+            raise ValueError("vacuum")
+        out[i] = o
     return out
 
 

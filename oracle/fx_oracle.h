@@ -53,6 +53,18 @@ or_mesh *or_mesh_create(int ndim, int nxb, int ng, int nb, const int nroot[3],
                         const double lo[3], const double hi[3], const int bc[6],
                         double gamma);
 void or_mesh_destroy(or_mesh *m);
+/* Multispecies perfect gas (Section 2.2 names a multispecies variant of the
+ * perfect-gas EOS): nspec (<= 4) species with ratios of specific heats
+ * gamma_k and molar masses A_k; the state then carries 5 + nspec variables
+ * per cell, the last nspec being rho X_k (mass fractions X_k, advected with
+ * the flow; HLLC keeps each side's X through the star region), and a cell's
+ * gamma follows the ideal-gas mixture rule
+ * gamma - 1 = (sum X_k / A_k) / (sum X_k / (A_k (gamma_k - 1))).
+ * Call before any use of the mesh.  Pinned: one species equal to the single
+ * gas, two identical species equal to one gas with exact species transport,
+ * the scalar-advection special case for X, the EOS mixture closed form, and
+ * L1 convergence to the exact two-gas Riemann solution. */
+int or_mesh_set_species(or_mesh *m, int nspec, const double *gamma_k, const double *A_k);
 const char *or_last_error(void);
 void or_set_threads(int n);
 int or_get_threads(void);
@@ -110,9 +122,9 @@ int or_hydro_advance_rk3(const or_mesh *m, const double *U, double *Unew, double
  * via prolongation, conservation with flux correction. */
 void or_restrict_parents(const or_mesh *m, double *U);
 
-/* Sum over leaf interior cells of U dV per variable (compensated sums, fixed
- * order).  Pinned by conservation tests. */
-void or_conserved_totals(const or_mesh *m, const double *U, double out[5]);
+/* Sum over leaf interior cells of U dV per variable (out: 5 + nspec values;
+ * compensated sums, fixed order).  Pinned by conservation tests. */
+void or_conserved_totals(const or_mesh *m, const double *U, double *out);
 
 /* Regridding (dynamic refinement of the PARAMESH-style octree, Section 2).
  * or_regrid_errors: per block, the maximum over interior cells and over
@@ -152,6 +164,11 @@ int or_riemann_star(const double WL[3], const double WR[3], double gamma, double
 /* Sample the self-similar solution at xi = x / t: out = {rho, u, p}. */
 int or_riemann_sample(const double WL[3], const double WR[3], double gamma, double xi,
                       double out[3]);
+/* The same for two gases: gamma gL left of the contact, gR right of it. */
+int or_riemann_star2(const double WL[3], const double WR[3], double gL, double gR,
+                     double star[4]);
+int or_riemann_sample2(const double WL[3], const double WR[3], double gL, double gR, double xi,
+                       double out[3]);
 
 #ifdef __cplusplus
 }

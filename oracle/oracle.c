@@ -39,6 +39,8 @@
 #endif
 
 #define OR_MAXLEV 16
+#define OR_MAXSP 4                /* species of the multispecies perfect gas */
+#define OR_MAXV (5 + OR_MAXSP)    /* conserved variables per cell, at most */
 
 struct or_mesh {
   int ndim, nxb, ng, nb, P, PZ, lmax;
@@ -51,6 +53,8 @@ struct or_mesh {
   int64_t nblk[OR_MAXLEV][3];         /* blocks per axis at each level */
   double dx[OR_MAXLEV][3];
   int *lut[OR_MAXLEV];                /* dense block lookup per level */
+  int nspec, nv;                      /* species; variables per cell = 5 + nspec */
+  double spa[OR_MAXSP], spb[OR_MAXSP]; /* 1 / A_k and 1 / (A_k (gamma_k - 1)) */
 };
 
 static char g_err[256];
@@ -75,7 +79,7 @@ static void set_err(const char *s) { snprintf(g_err, sizeof g_err, "%s", s); }
 /* ------------------------------------------------------------------------ */
 
 static size_t cell_index(const or_mesh *m, int b, int v, int k, int j, int i) {
-  return ((((size_t)b * 5 + v) * m->PZ + k) * m->P + j) * m->P + i;
+  return ((((size_t)b * m->nv + v) * m->PZ + k) * m->P + j) * m->P + i;
 }
 
 static int lookup(const or_mesh *m, int l, const int64_t bcoord[3]) {
@@ -107,6 +111,7 @@ or_mesh *or_mesh_create(int ndim, int nxb, int ng, int nb, const int nroot[3],
   }
   or_mesh *m = (or_mesh *)calloc(1, sizeof *m);
   m->ndim = ndim; m->nxb = nxb; m->ng = ng; m->nb = nb;
+  m->nspec = 0; m->nv = 5;
   m->P = nxb + 2 * ng; m->PZ = ndim == 3 ? m->P : 1;
   m->gamma = gamma;
   for (int d = 0; d < 3; d++) {
@@ -183,22 +188,58 @@ or_mesh *or_mesh_create(int ndim, int nxb, int ng, int nb, const int nroot[3],
 /* EOS                                                                       */
 /* ------------------------------------------------------------------------ */
 
-static void prim_from_cons(const double U[5], double gamma, double W[5]) {
-  double rho = U[0];
-  W[0] = rho;
-  W[1] = U[1] / rho;
-  W[2] = U[2] / rho;
-  W[3] = U[3] / rho;
-  W[4] = (gamma - 1.0) * (U[4] - 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / rho);
+/* Ratio of specific heats of a cell from its primitive state W (mass
+ * fractions in W[5..]): the mesh's gamma for a single gas; for the
+ * multispecies perfect gas the mixture of ideal gases,
+ * gamma - 1 = (sum_k X_k / A_k) / (sum_k X_k / (A_k (gamma_k - 1))),
+ * i.e. the ratio of the mass-weighted heat capacities. */
+static double cell_gamma(const or_mesh *m, const double *W) {
+  if (m->nspec == 0) return m->gamma;
+  double q1 = 0.0, q2 = 0.0;
+  for (int k = 0; k < m->nspec; k++) {
+    q1 = q1 + W[5 + k] * m->spa[k];
+    q2 = q2 + W[5 + k] * m->spb[k];
+  }
+  return 1.0 + q1 / q2;
 }
 
-static void cons_from_prim(const double W[5], double gamma, double U[5]) {
+/* Conserved from primitive with a given gamma (species: rho X_k). */
+static void cons_g(const double *W, int nv, double gamma, double *U) {
   double rho = W[0];
   U[0] = rho;
   U[1] = rho * W[1];
   U[2] = rho * W[2];
   U[3] = rho * W[3];
   U[4] = W[4] / (gamma - 1.0) + 0.5 * rho * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+  for (int v = 5; v < nv; v++) U[v] = rho * W[v];
+}
+
+static void prim_from_cons(const or_mesh *m, const double *U, double *W) {
+  double rho = U[0];
+  W[0] = rho;
+  W[1] = U[1] / rho;
+  W[2] = U[2] / rho;
+  W[3] = U[3] / rho;
+  for (int v = 5; v < m->nv; v++) W[v] = U[v] / rho;
+  double gamma = cell_gamma(m, W);
+  W[4] = (gamma - 1.0) * (U[4] - 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / rho);
+}
+
+static void cons_from_prim(const or_mesh *m, const double *W, double *U) {
+  cons_g(W, m->nv, cell_gamma(m, W), U);
+}
+
+int or_mesh_set_species(or_mesh *m, int nspec, const double *gamma_k, const double *A_k) {
+  if (nspec < 0 || nspec > OR_MAXSP) { set_err("nspec out of range"); return -1; }
+  for (int k = 0; k < nspec; k++)
+    if (!(gamma_k[k] > 1.0) || !(A_k[k] > 0.0)) { set_err("bad species constants"); return -1; }
+  m->nspec = nspec;
+  m->nv = 5 + nspec;
+  for (int k = 0; k < nspec; k++) {
+    m->spa[k] = 1.0 / A_k[k];
+    m->spb[k] = 1.0 / (A_k[k] * (gamma_k[k] - 1.0));
+  }
+  return 0;
 }
 
 static size_t ncells_total(const or_mesh *m) {
@@ -207,24 +248,26 @@ static size_t ncells_total(const or_mesh *m) {
 
 void or_prim_to_cons(const or_mesh *m, const double *W, double *U) {
   size_t per = (size_t)m->PZ * m->P * m->P;
+  int nv = m->nv;
   for (int b = 0; b < m->nb; b++)
     for (size_t c = 0; c < per; c++) {
-      double w[5], u[5];
-      for (int v = 0; v < 5; v++) w[v] = W[((size_t)b * 5 + v) * per + c];
-      cons_from_prim(w, m->gamma, u);
-      for (int v = 0; v < 5; v++) U[((size_t)b * 5 + v) * per + c] = u[v];
+      double w[OR_MAXV], u[OR_MAXV];
+      for (int v = 0; v < nv; v++) w[v] = W[((size_t)b * nv + v) * per + c];
+      cons_from_prim(m, w, u);
+      for (int v = 0; v < nv; v++) U[((size_t)b * nv + v) * per + c] = u[v];
     }
   (void)ncells_total;
 }
 
 void or_cons_to_prim(const or_mesh *m, const double *U, double *W) {
   size_t per = (size_t)m->PZ * m->P * m->P;
+  int nv = m->nv;
   for (int b = 0; b < m->nb; b++)
     for (size_t c = 0; c < per; c++) {
-      double w[5], u[5];
-      for (int v = 0; v < 5; v++) u[v] = U[((size_t)b * 5 + v) * per + c];
-      prim_from_cons(u, m->gamma, w);
-      for (int v = 0; v < 5; v++) W[((size_t)b * 5 + v) * per + c] = w[v];
+      double w[OR_MAXV], u[OR_MAXV];
+      for (int v = 0; v < nv; v++) u[v] = U[((size_t)b * nv + v) * per + c];
+      prim_from_cons(m, u, w);
+      for (int v = 0; v < nv; v++) W[((size_t)b * nv + v) * per + c] = w[v];
     }
 }
 
@@ -338,7 +381,7 @@ int or_guardcell_fill(const or_mesh *m, double *U) {
             g[0] = m->origin[b * 3 + 0] + (i - ng);
             g[1] = m->origin[b * 3 + 1] + (j - ng);
             g[2] = m->ndim == 3 ? m->origin[b * 3 + 2] + (k - ng) : 0;
-            for (int v = 0; v < 5; v++) {
+            for (int v = 0; v < m->nv; v++) {
               double val;
               if (guard_value(m, U, l, g, v, &val)) { fail |= 1; val = NAN; }
               U[cell_index(m, b, v, k, j, i)] = val;
@@ -365,10 +408,10 @@ int or_compute_dt(const or_mesh *m, const double *U, double cfl, int form, doubl
     for (int k = 0; k < nz; k++)
       for (int j = 0; j < n; j++)
         for (int i = 0; i < n; i++) {
-          double u[5], w[5];
-          for (int v = 0; v < 5; v++) u[v] = U[cell_index(m, b, v, k + kz, j + ng, i + ng)];
-          prim_from_cons(u, m->gamma, w);
-          double c = sqrt(m->gamma * w[4] / w[0]);
+          double u[OR_MAXV], w[OR_MAXV];
+          for (int v = 0; v < m->nv; v++) u[v] = U[cell_index(m, b, v, k + kz, j + ng, i + ng)];
+          prim_from_cons(m, u, w);
+          double c = sqrt(cell_gamma(m, w) * w[4] / w[0]);
           double s = 0.0;
           for (int d = 0; d < m->ndim; d++) {
             double sd = (fabs(w[1 + d]) + c) / dx[d];
@@ -386,43 +429,52 @@ int or_compute_dt(const or_mesh *m, const double *U, double cfl, int form, doubl
 /* HLLC flux (Toro, Spruce & Speares 1994)                                   */
 /* ------------------------------------------------------------------------ */
 
-static void phys_flux(const double W[5], const double Uc[5], int d, double F[5]) {
+static void phys_flux(const double *W, const double *Uc, int nv, int d, double *F) {
   int nrm = 1 + d;
   double un = W[nrm];
   F[0] = W[0] * un;
   for (int k = 0; k < 3; k++) F[1 + k] = W[0] * un * W[1 + k];
   F[nrm] += W[4];
   F[4] = un * (Uc[4] + W[4]);
+  for (int v = 5; v < nv; v++) F[v] = W[0] * un * W[v];
 }
 
-void or_hllc(const double WL[5], const double WR[5], int d, double gamma, double F[5]) {
+/* HLLC with the ratio of specific heats of each side (gL, gR); passive
+ * species keep their side's mass fraction through the star region. */
+static void hllc_core(const double *WL, const double *WR, int nv, int d, double gL, double gR,
+                      double *F) {
   int nrm = 1 + d;
   double rL = WL[0], pL = WL[4], uL = WL[nrm];
   double rR = WR[0], pR = WR[4], uR = WR[nrm];
-  double cL = sqrt(gamma * pL / rL), cR = sqrt(gamma * pR / rR);
+  double cL = sqrt(gL * pL / rL), cR = sqrt(gR * pR / rR);
   double SL = fmin(uL - cL, uR - cR);
   double SR = fmax(uL + cL, uR + cR);
-  double UL[5], UR[5], FL[5], FR[5];
-  cons_from_prim(WL, gamma, UL);
-  cons_from_prim(WR, gamma, UR);
-  phys_flux(WL, UL, d, FL);
-  phys_flux(WR, UR, d, FR);
+  double UL[OR_MAXV], UR[OR_MAXV], FL[OR_MAXV], FR[OR_MAXV];
+  cons_g(WL, nv, gL, UL);
+  cons_g(WR, nv, gR, UR);
+  phys_flux(WL, UL, nv, d, FL);
+  phys_flux(WR, UR, nv, d, FR);
   double Sst = (pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) /
                (rL * (SL - uL) - rR * (SR - uR));
   const double *WK, *UK, *FK;
   double SK;
-  if (SL >= 0.0) { for (int q = 0; q < 5; q++) F[q] = FL[q]; return; }
+  if (SL >= 0.0) { for (int q = 0; q < nv; q++) F[q] = FL[q]; return; }
   if (Sst >= 0.0) { WK = WL; UK = UL; FK = FL; SK = SL; }
   else if (SR > 0.0) { WK = WR; UK = UR; FK = FR; SK = SR; }
-  else { for (int q = 0; q < 5; q++) F[q] = FR[q]; return; }
+  else { for (int q = 0; q < nv; q++) F[q] = FR[q]; return; }
   double rK = WK[0], uK = WK[nrm], pK = WK[4];
   double fac = rK * (SK - uK) / (SK - Sst);
-  double Us[5];
+  double Us[OR_MAXV];
   Us[0] = fac;
   for (int k = 0; k < 3; k++) Us[1 + k] = fac * WK[1 + k];
   Us[nrm] = fac * Sst;
   Us[4] = fac * (UK[4] / rK + (Sst - uK) * (Sst + pK / (rK * (SK - uK))));
-  for (int q = 0; q < 5; q++) F[q] = FK[q] + SK * (Us[q] - UK[q]);
+  for (int q = 5; q < nv; q++) Us[q] = fac * WK[q];
+  for (int q = 0; q < nv; q++) F[q] = FK[q] + SK * (Us[q] - UK[q]);
+}
+
+void or_hllc(const double WL[5], const double WR[5], int d, double gamma, double F[5]) {
+  hllc_core(WL, WR, 5, d, gamma, gamma, F);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -430,10 +482,10 @@ void or_hllc(const double WL[5], const double WR[5], int d, double gamma, double
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-  double *W;    /* [5][PZ][P][P] primitives */
-  double *FSm;  /* [3][5][PZ][P][P] face state at the lower face of a cell, per direction */
-  double *FSp;  /* [3][5][PZ][P][P] face state at the upper face */
-  double *F;    /* [3][5][PZ][P][P] flux through the lower face of a cell */
+  double *W;    /* [nv][PZ][P][P] primitives */
+  double *FSm;  /* [3][nv][PZ][P][P] face state at the lower face of a cell, per direction */
+  double *FSp;  /* [3][nv][PZ][P][P] face state at the upper face */
+  double *F;    /* [3][nv][PZ][P][P] flux through the lower face of a cell */
 } or_work;
 
 static size_t wi(const or_mesh *m, int v, int k, int j, int i) {
@@ -447,8 +499,8 @@ static int advance_block(const or_mesh *m, const double *U, double *Unew, double
                          or_work *w, double *bflux, int predictor, const double *Uavg,
                          double wa, double wb) {
   int P = m->P, PZ = m->PZ, ng = m->ng, n = m->nxb, nd = m->ndim;
-  size_t per = (size_t)5 * PZ * P * P;
-  double gamma = m->gamma;
+  int nv = m->nv;
+  size_t per = (size_t)nv * PZ * P * P;
   const double *dx = m->dx[m->level[b]];
   int lo[3], hi[3];  /* padded index range of the interior, per axis */
   for (int d = 0; d < 3; d++) {
@@ -459,42 +511,44 @@ static int advance_block(const or_mesh *m, const double *U, double *Unew, double
   for (int k = 0; k < PZ; k++)
     for (int j = 0; j < P; j++)
       for (int i = 0; i < P; i++) {
-        double u[5], q[5];
-        for (int v = 0; v < 5; v++) u[v] = U[cell_index(m, b, v, k, j, i)];
-        prim_from_cons(u, gamma, q);
-        for (int v = 0; v < 5; v++) w->W[wi(m, v, k, j, i)] = q[v];
+        double u[OR_MAXV], q[OR_MAXV];
+        for (int v = 0; v < nv; v++) u[v] = U[cell_index(m, b, v, k, j, i)];
+        prim_from_cons(m, u, q);
+        for (int v = 0; v < nv; v++) w->W[wi(m, v, k, j, i)] = q[v];
       }
   /* 2. slopes, Hancock predictor and face states on the interior grown by one */
   for (int k = lo[2] - (nd == 3); k < hi[2] + (nd == 3); k++)
     for (int j = lo[1] - 1; j < hi[1] + 1; j++)
       for (int i = lo[0] - 1; i < hi[0] + 1; i++) {
-        double W0[5], dW[3][5] = {{0}}, Wh[5], fm[3][5], fp[3][5];
-        for (int v = 0; v < 5; v++) W0[v] = w->W[wi(m, v, k, j, i)];
+        double W0[OR_MAXV], dW[3][OR_MAXV] = {{0}}, Wh[OR_MAXV], fm[3][OR_MAXV], fp[3][OR_MAXV];
+        for (int v = 0; v < nv; v++) W0[v] = w->W[wi(m, v, k, j, i)];
         for (int d = 0; d < nd; d++) {
           int om[3] = {i, j, k}, op[3] = {i, j, k};
           om[d] -= 1; op[d] += 1;
-          for (int v = 0; v < 5; v++) {
+          for (int v = 0; v < nv; v++) {
             double wm = w->W[wi(m, v, om[2], om[1], om[0])];
             double wp = w->W[wi(m, v, op[2], op[1], op[0])];
             dW[d][v] = or_mc(W0[v] - wm, wp - W0[v]);
           }
         }
         /* primitive quasi-linear form: A_d(W) dW_d for each direction */
-        double acc[5] = {0, 0, 0, 0, 0};
+        double acc[OR_MAXV] = {0};
+        double gamma = cell_gamma(m, W0);
         for (int d = 0; d < nd; d++) {
           int nrm = 1 + d;
           double un = W0[nrm], r = W0[0], p = W0[4];
-          double a[5];
+          double a[OR_MAXV];
           a[0] = un * dW[d][0] + r * dW[d][nrm];
           for (int t = 0; t < 3; t++) a[1 + t] = un * dW[d][1 + t];
           a[nrm] = a[nrm] + dW[d][4] / r;
           a[4] = gamma * p * dW[d][nrm] + un * dW[d][4];
-          for (int v = 0; v < 5; v++) acc[v] = acc[v] + a[v] / dx[d];
+          for (int v = 5; v < nv; v++) a[v] = un * dW[d][v];   /* advected mass fractions */
+          for (int v = 0; v < nv; v++) acc[v] = acc[v] + a[v] / dx[d];
         }
-        for (int v = 0; v < 5; v++) Wh[v] = predictor ? W0[v] - 0.5 * dt * acc[v] : W0[v];
+        for (int v = 0; v < nv; v++) Wh[v] = predictor ? W0[v] - 0.5 * dt * acc[v] : W0[v];
         int bad = 0;
         for (int d = 0; d < nd; d++)
-          for (int v = 0; v < 5; v++) {
+          for (int v = 0; v < nv; v++) {
             fm[d][v] = Wh[v] - 0.5 * dW[d][v];
             fp[d][v] = Wh[v] + 0.5 * dW[d][v];
           }
@@ -503,9 +557,9 @@ static int advance_block(const or_mesh *m, const double *U, double *Unew, double
             bad = 1;
         if (bad) /* positivity fallback: first order for this cell */
           for (int d = 0; d < nd; d++)
-            for (int v = 0; v < 5; v++) { fm[d][v] = W0[v]; fp[d][v] = W0[v]; }
+            for (int v = 0; v < nv; v++) { fm[d][v] = W0[v]; fp[d][v] = W0[v]; }
         for (int d = 0; d < nd; d++)
-          for (int v = 0; v < 5; v++) {
+          for (int v = 0; v < nv; v++) {
             w->FSm[d * per + wi(m, v, k, j, i)] = fm[d][v];
             w->FSp[d * per + wi(m, v, k, j, i)] = fp[d][v];
           }
@@ -519,13 +573,13 @@ static int advance_block(const or_mesh *m, const double *U, double *Unew, double
         for (int i = lo[0]; i < hii; i++) {
           int o[3] = {i, j, k};
           o[d] -= 1;
-          double WL[5], WR[5], F[5];
-          for (int v = 0; v < 5; v++) {
+          double WL[OR_MAXV], WR[OR_MAXV], F[OR_MAXV];
+          for (int v = 0; v < nv; v++) {
             WL[v] = w->FSp[d * per + wi(m, v, o[2], o[1], o[0])];
             WR[v] = w->FSm[d * per + wi(m, v, k, j, i)];
           }
-          or_hllc(WL, WR, d, gamma, F);
-          for (int v = 0; v < 5; v++) w->F[d * per + wi(m, v, k, j, i)] = F[v];
+          hllc_core(WL, WR, nv, d, cell_gamma(m, WL), cell_gamma(m, WR), F);
+          for (int v = 0; v < nv; v++) w->F[d * per + wi(m, v, k, j, i)] = F[v];
         }
   }
   /* 4. conservative update of the interior, directions summed x, y, z */
@@ -533,8 +587,8 @@ static int advance_block(const or_mesh *m, const double *U, double *Unew, double
   for (int k = lo[2]; k < hi[2]; k++)
     for (int j = lo[1]; j < hi[1]; j++)
       for (int i = lo[0]; i < hi[0]; i++) {
-        double un[5];
-        for (int v = 0; v < 5; v++) {
+        double un[OR_MAXV];
+        for (int v = 0; v < nv; v++) {
           double div = 0.0;
           for (int d = 0; d < nd; d++) {
             int o[3] = {i, j, k};
@@ -547,8 +601,8 @@ static int advance_block(const or_mesh *m, const double *U, double *Unew, double
           if (Uavg) un[v] = wa * Uavg[cell_index(m, b, v, k, j, i)] + wb * un[v];
           Unew[cell_index(m, b, v, k, j, i)] = un[v];
         }
-        double q[5];
-        prim_from_cons(un, gamma, q);
+        double q[OR_MAXV];
+        prim_from_cons(m, un, q);
         if (!(q[0] > 0.0) || !(q[4] > 0.0)) bad = 1;
       }
   /* 5. block-boundary fluxes for flux correction */
@@ -556,9 +610,9 @@ static int advance_block(const or_mesh *m, const double *U, double *Unew, double
     int nf = nd == 3 ? n * n : n;
     for (int d = 0; d < nd; d++)
       for (int s = 0; s < 2; s++) {
-        double *dst = bflux + (((size_t)b * 2 * nd + 2 * d + s) * 5) * nf;
+        double *dst = bflux + (((size_t)b * 2 * nd + 2 * d + s) * nv) * nf;
         int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2; /* transverse axes, lower first */
-        for (int v = 0; v < 5; v++)
+        for (int v = 0; v < m->nv; v++)
           for (int t2 = 0; t2 < (nd == 3 ? n : 1); t2++)
             for (int t1 = 0; t1 < n; t1++) {
               int c[3];
@@ -595,10 +649,10 @@ static void reflux_block(const or_mesh *m, double *Unew, double dt, int c, const
       int64_t gfd = s ? 2 * (m->origin[c * 3 + d] + n) : 2 * m->origin[c * 3 + d] - 1;
       gfd = ((gfd % NF) + NF) % NF;
       int fine_face = s ? 0 : 1; /* the fine block's lower (s=+) or upper face */
-      const double *Fc = bflux + (((size_t)c * 2 * nd + 2 * d + s) * 5) * nf;
+      const double *Fc = bflux + (((size_t)c * 2 * nd + 2 * d + s) * m->nv) * nf;
       for (int t2 = 0; t2 < (nd == 3 ? n : 1); t2++)
         for (int t1 = 0; t1 < n; t1++)
-          for (int v = 0; v < 5; v++) {
+          for (int v = 0; v < m->nv; v++) {
             double f[4];
             int cnt = 0;
             for (int b2 = 0; b2 < (nd == 3 ? 2 : 1); b2++)
@@ -612,7 +666,7 @@ static void reflux_block(const or_mesh *m, double *Unew, double dt, int c, const
                 int fblk = lookup(m, l + 1, fb);
                 int u1 = (int)(gf[a1] - m->origin[fblk * 3 + a1]);
                 int u2 = nd == 3 ? (int)(gf[a2] - m->origin[fblk * 3 + a2]) : 0;
-                const double *Ff = bflux + (((size_t)fblk * 2 * nd + 2 * d + fine_face) * 5) * nf;
+                const double *Ff = bflux + (((size_t)fblk * 2 * nd + 2 * d + fine_face) * m->nv) * nf;
                 f[cnt++] = Ff[(size_t)v * nf + (size_t)u2 * n + u1];
               }
             double fbar = nd == 3 ? ((f[0] + f[1]) + (f[2] + f[3])) * 0.25 : (f[0] + f[1]) * 0.5;
@@ -632,7 +686,7 @@ static void reflux_block(const or_mesh *m, double *Unew, double dt, int c, const
 static void restrict_block(const or_mesh *m, double *U, int p) {
   int nd = m->ndim, n = m->nxb, ng = m->ng;
   int nz = nd == 3 ? n : 1, kz = nd == 3 ? ng : 0;
-  for (int v = 0; v < 5; v++)
+  for (int v = 0; v < m->nv; v++)
     for (int k = 0; k < nz; k++)
       for (int j = 0; j < n; j++)
         for (int i = 0; i < n; i++) {
@@ -660,13 +714,13 @@ void or_restrict_parents(const or_mesh *m, double *U) {
 
 int or_hydro_advance(const or_mesh *m, const double *U, double *Unew, double dt, int reflux,
                      double *bflux, int nsel, const int *sel) {
-  size_t per = (size_t)5 * m->PZ * m->P * m->P;
+  size_t per = (size_t)m->nv * m->PZ * m->P * m->P;
   int nd = m->ndim, n = m->nxb;
   int nf = nd == 3 ? n * n : n;
   double *flux = bflux;
   int own = 0;
   if (!flux && !sel && m->lmax > 0) {
-    flux = (double *)calloc((size_t)m->nb * 2 * nd * 5 * nf, sizeof(double));
+    flux = (double *)calloc((size_t)m->nb * 2 * nd * m->nv * nf, sizeof(double));
     own = 1;
   }
   int count = sel ? nsel : m->nb;
@@ -704,9 +758,9 @@ int or_hydro_advance(const or_mesh *m, const double *U, double *Unew, double dt,
       for (int k = 0; k < nz; k++)
         for (int j = 0; j < n; j++)
           for (int i = 0; i < n; i++) {
-            double u[5], q[5];
-            for (int v = 0; v < 5; v++) u[v] = Unew[cell_index(m, b, v, k + kz, j + m->ng, i + m->ng)];
-            prim_from_cons(u, m->gamma, q);
+            double u[OR_MAXV], q[OR_MAXV];
+            for (int v = 0; v < m->nv; v++) u[v] = Unew[cell_index(m, b, v, k + kz, j + m->ng, i + m->ng)];
+            prim_from_cons(m, u, q);
             if (!(q[0] > 0.0) || !(q[4] > 0.0)) bad = 1;
           }
     }
@@ -722,11 +776,11 @@ int or_hydro_advance(const or_mesh *m, const double *U, double *Unew, double dt,
  * both sides, which is what the two-stage update of a coarse cell used. */
 int or_hydro_advance_rk2(const or_mesh *m, const double *U, double *Unew, double dt, int reflux,
                          double *bflux) {
-  size_t per = (size_t)5 * m->PZ * m->P * m->P;
+  size_t per = (size_t)m->nv * m->PZ * m->P * m->P;
   size_t tot = per * (size_t)m->nb;
   int nd = m->ndim, n = m->nxb;
   int nf = nd == 3 ? n * n : n;
-  size_t nfl = (size_t)m->nb * 2 * nd * 5 * nf;
+  size_t nfl = (size_t)m->nb * 2 * nd * m->nv * nf;
   double *U1 = (double *)malloc(sizeof(double) * tot);
   double *f1 = (double *)calloc(nfl, sizeof(double));
   double *f2 = (double *)calloc(nfl, sizeof(double));
@@ -768,9 +822,9 @@ int or_hydro_advance_rk2(const or_mesh *m, const double *U, double *Unew, double
     for (int k = 0; k < nz; k++)
       for (int j = 0; j < n; j++)
         for (int i = 0; i < n; i++) {
-          double u[5], q[5];
-          for (int v = 0; v < 5; v++) u[v] = Unew[cell_index(m, b, v, k + kz, j + m->ng, i + m->ng)];
-          prim_from_cons(u, m->gamma, q);
+          double u[OR_MAXV], q[OR_MAXV];
+          for (int v = 0; v < m->nv; v++) u[v] = Unew[cell_index(m, b, v, k + kz, j + m->ng, i + m->ng)];
+          prim_from_cons(m, u, q);
           if (!(q[0] > 0.0) || !(q[4] > 0.0)) bad = 1;
         }
   }
@@ -788,9 +842,9 @@ static int leaves_positive(const or_mesh *m, const double *U) {
     for (int k = 0; k < nz; k++)
       for (int j = 0; j < n; j++)
         for (int i = 0; i < n; i++) {
-          double u[5], q[5];
-          for (int v = 0; v < 5; v++) u[v] = U[cell_index(m, b, v, k + kz, j + m->ng, i + m->ng)];
-          prim_from_cons(u, m->gamma, q);
+          double u[OR_MAXV], q[OR_MAXV];
+          for (int v = 0; v < m->nv; v++) u[v] = U[cell_index(m, b, v, k + kz, j + m->ng, i + m->ng)];
+          prim_from_cons(m, u, q);
           if (!(q[0] > 0.0) || !(q[4] > 0.0)) return 1;
         }
   }
@@ -807,11 +861,11 @@ static int leaves_positive(const or_mesh *m, const double *U) {
  * weighted 1/6, 1/6, 2/3 on both sides. */
 int or_hydro_advance_rk3(const or_mesh *m, const double *U, double *Unew, double dt, int reflux,
                          double *bflux) {
-  size_t per = (size_t)5 * m->PZ * m->P * m->P;
+  size_t per = (size_t)m->nv * m->PZ * m->P * m->P;
   size_t tot = per * (size_t)m->nb;
   int nd = m->ndim, n = m->nxb;
   int nf = nd == 3 ? n * n : n;
-  size_t nfl = (size_t)m->nb * 2 * nd * 5 * nf;
+  size_t nfl = (size_t)m->nb * 2 * nd * m->nv * nf;
   double *U1 = (double *)malloc(sizeof(double) * tot);
   double *U2 = (double *)malloc(sizeof(double) * tot);
   double *f[3];
@@ -924,9 +978,9 @@ int or_regrid_errors(const or_mesh *m, const double *U, double eps, double *err)
     for (int b = 0; b < m->nb; b++) {
       if (!m->leaf[b]) { err[b] = -1.0; continue; }
       for (size_t c = 0; c < plane; c++) {
-        double u[5], w[5];
-        for (int v = 0; v < 5; v++) u[v] = U[((size_t)b * 5 + v) * plane + c];
-        prim_from_cons(u, m->gamma, w);
+        double u[OR_MAXV], w[OR_MAXV];
+        for (int v = 0; v < m->nv; v++) u[v] = U[((size_t)b * m->nv + v) * plane + c];
+        prim_from_cons(m, u, w);
         rho[c] = w[0];
         pre[c] = w[4];
       }
@@ -1118,9 +1172,9 @@ int or_regrid_transfer(const or_mesh *om, const double *Uold, const or_mesh *nm,
     for (int k = 0; k < nz; k++)
       for (int j = 0; j < n; j++)
         for (int i = 0; i < n; i++) {
-          double out[5];
+          double out[OR_MAXV];
           if (kind[b] == 0) {
-            for (int v = 0; v < 5; v++) out[v] = Uold[cell_index(om, s, v, k + kz, j + ng, i + ng)];
+            for (int v = 0; v < nm->nv; v++) out[v] = Uold[cell_index(om, s, v, k + kz, j + ng, i + ng)];
           } else {
             /* new child: the parent's coarse cell and this cell's parities */
             int f[3] = {i, j, k}, pc[3], par[3];
@@ -1135,16 +1189,16 @@ int or_regrid_transfer(const or_mesh *om, const double *Uold, const or_mesh *nm,
             int ok = 1;
             for (int c = 0; c < (1 << nd) && ok; c++) {
               int pq[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
-              double u[5], w[5];
-              for (int v = 0; v < 5; v++) u[v] = prolong_value(om, Uold, s, v, pc, pq);
-              prim_from_cons(u, om->gamma, w);
+              double u[OR_MAXV], w[OR_MAXV];
+              for (int v = 0; v < om->nv; v++) u[v] = prolong_value(om, Uold, s, v, pc, pq);
+              prim_from_cons(om, u, w);
               if (!(w[0] > 0.0) || !(w[4] > 0.0)) ok = 0;
             }
-            for (int v = 0; v < 5; v++)
+            for (int v = 0; v < nm->nv; v++)
               out[v] = ok ? prolong_value(om, Uold, s, v, pc, par)
                           : Uold[cell_index(om, s, v, pc[2], pc[1], pc[0])];
           }
-          for (int v = 0; v < 5; v++) Unew[cell_index(nm, b, v, k + kz, j + ng, i + ng)] = out[v];
+          for (int v = 0; v < nm->nv; v++) Unew[cell_index(nm, b, v, k + kz, j + ng, i + ng)] = out[v];
         }
   }
   return 0;
@@ -1154,10 +1208,10 @@ int or_regrid_transfer(const or_mesh *om, const double *Uold, const or_mesh *nm,
 /* conserved totals                                                          */
 /* ------------------------------------------------------------------------ */
 
-void or_conserved_totals(const or_mesh *m, const double *U, double out[5]) {
+void or_conserved_totals(const or_mesh *m, const double *U, double *out) {
   int n = m->nxb, ng = m->ng, nd = m->ndim;
   int nz = nd == 3 ? n : 1, kz = nd == 3 ? ng : 0;
-  for (int v = 0; v < 5; v++) {
+  for (int v = 0; v < m->nv; v++) {
     double sum = 0.0, comp = 0.0;
     for (int b = 0; b < m->nb; b++) {
       if (!m->leaf[b]) continue;

@@ -43,10 +43,20 @@ class Mesh:
     bc: tuple = ((OUTFLOW, OUTFLOW),) * 3
     name: str = ""
     extra: dict = field(default_factory=dict)
+    species: tuple = ()    # multispecies perfect gas: ((gamma_k, A_k), ...)
 
     @property
     def nb(self) -> int:
         return int(self.level.shape[0])
+
+    @property
+    def nspec(self) -> int:
+        return len(self.species)
+
+    @property
+    def nvar(self) -> int:
+        """Variables per cell: rho, rho u, rho v, rho w, E, then rho X_k."""
+        return 5 + len(self.species)
 
     @property
     def P(self) -> int:
@@ -58,8 +68,8 @@ class Mesh:
 
     @property
     def shape(self) -> tuple:
-        """Shape of one state buffer ``[nb, 5, PZ, P, P]``."""
-        return (self.nb, 5, self.PZ, self.P, self.P)
+        """Shape of one state buffer ``[nb, nvar, PZ, P, P]``."""
+        return (self.nb, self.nvar, self.PZ, self.P, self.P)
 
     def is_leaf(self) -> np.ndarray:
         leaf = np.ones(self.nb, dtype=np.int32)
@@ -122,7 +132,7 @@ class Mesh:
 
 def uniform_mesh(ndim: int, nblk: tuple, nxb: int = 16, ng: int = 4,
                  bc: int | tuple = OUTFLOW, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
-                 name: str = "") -> Mesh:
+                 name: str = "", species: tuple = ()) -> Mesh:
     """One level of ``nblk[0] x nblk[1] (x nblk[2])`` blocks, x fastest."""
     nb3 = [nblk[d] if d < ndim else 1 for d in range(3)]
     origin = []
@@ -137,7 +147,7 @@ def uniform_mesh(ndim: int, nblk: tuple, nxb: int = 16, ng: int = 4,
                 level=np.zeros(nb, dtype=np.int32),
                 origin=np.array(origin, dtype=np.int64).reshape(nb, 3),
                 parent=-np.ones(nb, dtype=np.int32), lo=tuple(lo), hi=tuple(hi),
-                bc=tuple(tuple(x) for x in bc), name=name)
+                bc=tuple(tuple(x) for x in bc), name=name, species=tuple(species))
 
 
 def refine(mesh: Mesh, refine_flags: np.ndarray, name: str = "") -> Mesh:
@@ -168,7 +178,7 @@ def refine(mesh: Mesh, refine_flags: np.ndarray, name: str = "") -> Mesh:
                 level=np.array(level, dtype=np.int32),
                 origin=np.array(origin, dtype=np.int64).reshape(nb, 3),
                 parent=np.array(parent, dtype=np.int32), lo=mesh.lo, hi=mesh.hi,
-                bc=mesh.bc, name=name or mesh.name)
+                bc=mesh.bc, name=name or mesh.name, species=mesh.species)
 
 
 def sedov_refine_flags(nblk: int) -> np.ndarray:
@@ -207,7 +217,7 @@ def _empty(mesh: Mesh) -> np.ndarray:
 
 def _fill(mesh: Mesh, W: np.ndarray, b: int, fields) -> None:
     g, n = mesh.ng, mesh.nxb
-    for v in range(5):
+    for v in range(len(fields)):
         val = np.broadcast_to(fields[v], (n if mesh.ndim == 3 else 1, n, n))
         if mesh.ndim == 3:
             W[b, v, g:g + n, g:g + n, g:g + n] = val

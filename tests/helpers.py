@@ -16,7 +16,7 @@ def assemble(mesh, U, level=None, leaves_only=True):
     level = lmax if level is None else level
     n = mesh.nxb
     N = mesh.cells_per_axis(level)
-    G = np.full((5, N[2], N[1], N[0]), np.nan)
+    G = np.full((U.shape[1], N[2], N[1], N[0]), np.nan)
     leaf = mesh.is_leaf()
     for b in range(mesh.nb):
         lb = int(mesh.level[b])
@@ -43,8 +43,9 @@ def rel_err(a, b, axis_var=1):
     largest |b| of that variable over the compared cells."""
     a = np.asarray(a)
     b = np.asarray(b)
-    moved_a = np.moveaxis(a, axis_var, 0).reshape(5, -1)
-    moved_b = np.moveaxis(b, axis_var, 0).reshape(5, -1)
+    nv = a.shape[axis_var]
+    moved_a = np.moveaxis(a, axis_var, 0).reshape(nv, -1)
+    moved_b = np.moveaxis(b, axis_var, 0).reshape(nv, -1)
     s = np.abs(moved_b).max(axis=1, keepdims=True)
     s = np.where(s == 0, 1.0, s)
     den = np.maximum(np.abs(moved_b), s)
@@ -71,8 +72,9 @@ def max_rel_err_vec(mesh, a, b):
     step), so that its absolute roundoff is judged against the flow's
     momentum rather than against its own vanishing maximum."""
     leaf = mesh.is_leaf().astype(bool)
-    ia = np.moveaxis(mesh.interior(a)[leaf], 1, 0).reshape(5, -1)
-    ib = np.moveaxis(mesh.interior(b)[leaf], 1, 0).reshape(5, -1)
+    nv = a.shape[1]
+    ia = np.moveaxis(mesh.interior(a)[leaf], 1, 0).reshape(nv, -1)
+    ib = np.moveaxis(mesh.interior(b)[leaf], 1, 0).reshape(nv, -1)
     s = np.abs(ib).max(axis=1)
     s[1:4] = np.sqrt((ib[1:4] ** 2).sum(axis=0)).max()
     s = np.where(s == 0, 1.0, s)[:, None]
