@@ -286,7 +286,7 @@ def workload_config(args, name, mesh=None):
     if mesh is None:
         return {"workload": name, "blocks": 64, "nxb": 16, "nguard": 4, "cells": 64 ** 3,
                 "bc": "periodic", "cfl": 0.8, "precision": args.precision}
-    state_bytes = mesh.nb * 5 * mesh.PZ * mesh.P * mesh.P * (8 if args.precision == "f64" else 4)
+    state_bytes = mesh.nb * mesh.nvar * mesh.PZ * mesh.P * mesh.P * (8 if args.precision == "f64" else 4)
     bc = "periodic" if mesh.bc[0][0] == 1 else "outflow"
     return {"workload": name, "blocks": mesh.nb, "leaf_blocks": int(mesh.is_leaf().sum()),
             "nxb": mesh.nxb, "nguard": mesh.ng, "cells": mesh.leaf_zones(), "bc": bc, "cfl": 0.8,

@@ -94,6 +94,22 @@ FX_API int fx_finalize(fx_ctx *ctx);
  * Errors: FX_ERR_ARG for an unknown key or value. */
 FX_API int fx_set_option(fx_ctx *ctx, const char *key, double value);
 
+/* fx_set_species: make block sets created afterwards with this context a
+ * multispecies perfect gas (Section 2.2: the perfect-gas EOS has a
+ * multispecies variant) of `nspec` (0..4; 0 = the single gas of fx_init)
+ * species with ratios of specific heats gamma_k[k] (> 1) and molar masses
+ * A_k[k] (> 0).  Such block sets carry nvar = 5 + nspec variables per cell
+ * (state buffers of nblocks * nvar * PZ * P * P elements; the last nspec
+ * variables are rho X_k, the partial densities of mass fractions X_k, and
+ * the primitive input of fx_prim_to_cons carries X_k there); a cell's gamma
+ * follows the ideal-gas mixture rule
+ *   gamma - 1 = (sum_k X_k / A_k) / (sum_k X_k / (A_k (gamma_k - 1))).
+ * The mass fractions are reconstructed and predicted like a transverse
+ * velocity and HLLC carries each side's fractions through the star region.
+ * Multispecies block sets are stepped with integrator 0 and outside batches.
+ * Errors: FX_ERR_ARG. */
+FX_API int fx_set_species(fx_ctx *ctx, int nspec, const double *gamma_k, const double *A_k);
+
 /* fx_last_error: NUL-terminated text of the last error of `ctx` (owned by
  * the context, valid until its next call). */
 FX_API const char *fx_last_error(const fx_ctx *ctx);
@@ -116,7 +132,8 @@ FX_API const char *fx_last_error(const fx_ctx *ctx);
  *               wrap, reflecting ones take the mirror-image cell with the
  *               wall-normal momentum negated (a solid slip wall);
  *   precision   FX_F64 or FX_F32BULK (element type of the state buffers);
- *   U0, U1      caller-owned device buffers of nblocks*5*PZ*P*P elements,
+ *   U0, U1      caller-owned device buffers of nblocks*nvar*PZ*P*P elements
+ *               (nvar = 5, or 5 + nspec after fx_set_species),
  *               16-byte aligned.  U0 holds the initial state; U1 receives the
  *               first update; they alternate afterwards (fx_blocks_current).
  * The mesh must be 2:1 balanced (every guard region is covered by a block of
@@ -197,9 +214,10 @@ FX_API int fx_hydro_advance(fx_ctx *ctx, fx_blocks *bs, const double *dt_dev, vo
 FX_API int fx_step(fx_ctx *ctx, fx_blocks *bs, double cfl, double *dt_dev, void *stream);
 
 /* fx_conserved_totals: out_host[v] = sum over leaf interior cells of U_v dV
- * for the current buffer, summed per block in a fixed order on the device
- * and over blocks with compensated summation on the host.  Synchronises. */
-FX_API int fx_conserved_totals(fx_ctx *ctx, fx_blocks *bs, double out_host[5], void *stream);
+ * for the current buffer (v < nvar: 5, or 5 + nspec for a multispecies
+ * block set), summed per block in a fixed order on the device and over
+ * blocks with compensated summation on the host.  Synchronises. */
+FX_API int fx_conserved_totals(fx_ctx *ctx, fx_blocks *bs, double *out_host, void *stream);
 
 /* fx_status: synchronise the device and report the latched device status of
  * the block set (FX_OK or FX_ERR_UNPHYSICAL); clears the latch. */
@@ -215,7 +233,7 @@ FX_API int fx_run_host(fx_ctx *ctx, fx_blocks *bs, const void *U_host_in, void *
 
 /* fx_run_host_interior: like fx_run_host, for callers that hold only the
  * interior cells: W_in and W_out are packed conserved states
- * [nblocks][5][nz][nxb][nxb] (nz = nxb in 3D, 1 in 2D; x fastest; element
+ * [nblocks][nvar][nz][nxb][nxb] (nz = nxb in 3D, 1 in 2D; x fastest; element
  * type of the block set's precision), page-locked host memory recommended.
  * Guard cells never cross the host link (they are rebuilt by the guard fill),
  * so each direction moves (nxb/(nxb+2 nguard))^ndim of fx_run_host's bytes.
@@ -250,7 +268,7 @@ FX_API int fx_run_host_interior(fx_ctx *ctx, fx_blocks *bs, const void *W_in, vo
  *   then z, y, x of the origin): level, origin [n][3] in the block's level
  *   lattice, parent (-1 at level 0).
  * fx_regrid_apply: moves the state onto the planned mesh in the new
- *   caller-owned buffers U0_new, U1_new (nblocks_new * 5 * PZ * P * P
+ *   caller-owned buffers U0_new, U1_new (nblocks_new * nvar * PZ * P * P
  *   elements, 16-byte aligned; U0_new becomes current): kept blocks copy
  *   their interior, new children take the conservative MC-limited linear
  *   prolongation of their parent, parents are restricted.  The handle then
@@ -267,7 +285,7 @@ FX_API int fx_regrid_apply(fx_ctx *ctx, fx_blocks *bs, void *U0_new, void *U1_ne
                            void *stream);
 
 /* fx_block_fluxes: device pointer to the flux registers of block `b`
- * ([2*ndim faces x-,x+,y-,y+,z-,z+][5][nxb^(ndim-1)], lower transverse axis
+ * ([2*ndim faces x-,x+,y-,y+,z-,z+][nvar][nxb^(ndim-1)], lower transverse axis
  * fastest) written by the last fx_hydro_advance, or NULL if the block has no
  * coarse-fine face.  For diagnostics and tests. */
 FX_API const double *fx_block_fluxes(const fx_blocks *bs, int b);

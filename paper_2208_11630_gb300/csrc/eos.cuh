@@ -1,0 +1,54 @@
+// eos.cuh -- perfect-gas equation of state shared by the device code: one gas
+// of ratio of specific heats gamma, or the multispecies perfect gas
+// (Section 2.2 of Flash-X, arXiv 2208.11630, names a multispecies variant of
+// the perfect-gas EOS) whose cell gamma follows the ideal-gas mixture rule
+//   gamma - 1 = (sum_k X_k / A_k) / (sum_k X_k / (A_k (gamma_k - 1)))
+// over the mass fractions X_k = (rho X_k) / rho.
+#pragma once
+
+#include "fx_internal.h"
+
+namespace fx {
+
+// gamma and gamma - 1 of a cell in precision R from its mass fractions
+// X[0..ns) (ns = 0: the mesh's gamma).
+template <typename R>
+__device__ __forceinline__ void mix_gamma(const DevMesh &m, const R *X, int ns, R &g, R &gm1) {
+  if (ns == 0) {
+    g = R(m.gamma);
+    gm1 = R(m.gamma - 1.0);
+    return;
+  }
+  R q1 = R(0), q2 = R(0);
+  for (int k = 0; k < ns; ++k) {
+    q1 = q1 + X[k] * R(m.spa[k]);
+    q2 = q2 + X[k] * R(m.spb[k]);
+  }
+  g = R(1) + q1 / q2;
+  gm1 = g - R(1);
+}
+
+// CFL signal speed of one cell from its conserved variables u[0..5+ns) in
+// precision R: sum over directions (form 0) or maximum (form 1) of
+// (|u_d| + c) / dx_d, c = sqrt(gamma p / rho).  The fused epilogue of the
+// update, the flux correction and the standalone reduction all use it, so
+// that they agree bit for bit.
+template <typename R>
+__device__ __forceinline__ R cell_signal(const DevMesh &m, const R *u, int ns, int lev,
+                                         int form) {
+  const R ir = R(1) / u[0];
+  R X[FX_MAXSPEC];
+  for (int k = 0; k < ns; ++k) X[k] = u[5 + k] * ir;
+  R g, gm1;
+  mix_gamma<R>(m, X, ns, g, gm1);
+  const R pr = gm1 * (u[4] - R(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * ir);
+  const R cs = sqrt(g * pr * ir);
+  R sg = R(0);
+  for (int d = 0; d < m.ndim; ++d) {
+    const R sd = (fabs(u[1 + d] * ir) + cs) * R(m.idx[lev][d]);
+    sg = form == 0 ? sg + sd : fmax(sg, sd);
+  }
+  return sg;
+}
+
+}  // namespace fx

@@ -29,6 +29,8 @@ struct fx_ctx {
   int cfl_form = 0;
   int reflux = 1;
   int integrator = 0;   // 0 MUSCL-Hancock, 1 SSP-RK2, 2 SSP-RK3
+  int nspec = 0;        // multispecies perfect gas: species and their constants
+  double spa[FX_MAXSPEC] = {0, 0, 0, 0}, spb[FX_MAXSPEC] = {0, 0, 0, 0};
   int device = 0;
   std::string err;
 };
@@ -36,6 +38,7 @@ struct fx_ctx {
 struct fx_blocks {
   fx_ctx *ctx = nullptr;
   int ndim = 3, nb = 0, nxb = 16, ng = 4, P = 24, PZ = 24, lmax = 0, prec = 0;
+  int nvar = 5;                             // variables per cell (5 + species)
   size_t elsize = 8;
   void *U[2] = {nullptr, nullptr};
   int cur = 0;
@@ -66,7 +69,7 @@ struct fx_blocks {
   int next_form = 0;
   int *d_status = nullptr;
   double *d_dt = nullptr;                   // dt scratch for fx_run_host
-  double *d_totals = nullptr;               // [nleaves][5]
+  double *d_totals = nullptr;               // [nleaves][nvar]
   // fx_run_host_interior: packed interior staging buffer and the streams and
   // events of the overlapped download (created on first use)
   void *d_pack = nullptr;
@@ -171,6 +174,20 @@ int fx_finalize(fx_ctx *ctx) {
   return FX_OK;
 }
 
+int fx_set_species(fx_ctx *ctx, int nspec, const double *gamma_k, const double *A_k) {
+  if (!ctx || nspec < 0 || nspec > FX_MAXSPEC || (nspec && (!gamma_k || !A_k)))
+    return FX_ERR_ARG;
+  for (int k = 0; k < nspec; ++k)
+    if (!(gamma_k[k] > 1.0) || !(A_k[k] > 0.0))
+      return fail(ctx, FX_ERR_ARG, "species need gamma_k > 1 and A_k > 0");
+  ctx->nspec = nspec;
+  for (int k = 0; k < FX_MAXSPEC; ++k) {
+    ctx->spa[k] = k < nspec ? 1.0 / A_k[k] : 0.0;
+    ctx->spb[k] = k < nspec ? 1.0 / (A_k[k] * (gamma_k[k] - 1.0)) : 0.0;
+  }
+  return FX_OK;
+}
+
 int fx_set_option(fx_ctx *ctx, const char *key, double value) {
   if (!ctx || !key) return FX_ERR_ARG;
   if (!strcmp(key, "cfl_form")) {
@@ -229,6 +246,7 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
   bs->PZ = ndim == 3 ? bs->P : 1;
   bs->prec = precision;
   bs->elsize = precision == FX_F64 ? 8 : 4;
+  bs->nvar = 5 + ctx->nspec;
   bs->U[0] = U0;
   bs->U[1] = U1;
   for (int d = 0; d < 3; ++d) {
@@ -441,13 +459,13 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
   if (bs->nrefl > 0 && (rc = upload(bs, &bs->d_rmask, rmask))) return bail(rc, ctx->err);
   const int nfc = ndim == 3 ? n * n : n;
   if (bs->nreg > 0) {
-    if (cudaMalloc(&bs->d_regs, sizeof(double) * (size_t)bs->nreg * 2 * ndim * 5 * nfc) != cudaSuccess)
+    if (cudaMalloc(&bs->d_regs, sizeof(double) * (size_t)bs->nreg * 2 * ndim * bs->nvar * nfc) != cudaSuccess)
       return bail(FX_ERR_OOM, "cudaMalloc of flux registers failed");
   }
   if (cudaMalloc(&bs->d_scratch, 3 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&bs->d_status, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&bs->d_dt, sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&bs->d_totals, sizeof(double) * 5 * (size_t)bs->nleaves) != cudaSuccess)
+      cudaMalloc(&bs->d_totals, sizeof(double) * bs->nvar * (size_t)bs->nleaves) != cudaSuccess)
     return bail(FX_ERR_OOM, "cudaMalloc of scratch failed");
   if (cudaMemset(bs->d_scratch, 0, 3 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemset(bs->d_status, 0, sizeof(int)) != cudaSuccess)
@@ -456,7 +474,13 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
   DevMesh &m = bs->dm;
   m.ndim = ndim; m.nxb = n; m.ng = bs->ng; m.P = bs->P; m.PZ = bs->PZ; m.nb = nb; m.lmax = lmax;
   m.vstride = (long long)bs->PZ * bs->P * bs->P;
-  m.bstride = 5 * m.vstride;
+  m.bstride = (long long)bs->nvar * m.vstride;
+  m.nvar = bs->nvar;
+  m.nspec = bs->nvar - 5;
+  for (int k = 0; k < FX_MAXSPEC; ++k) {
+    m.spa[k] = ctx->spa[k];
+    m.spb[k] = ctx->spb[k];
+  }
   for (int d = 0; d < 3; ++d)
     for (int s = 0; s < 2; ++s) m.bc[d][s] = d < ndim ? bc[2 * d + s] : FX_BC_OUTFLOW;
   for (int l = 0; l < FX_MAXLEV; ++l)
@@ -549,6 +573,8 @@ int fx_hydro_advance(fx_ctx *ctx, fx_blocks *bs, const double *dt_dev, void *str
   unsigned long long *smax = bs->d_scratch + 2;
   const bool refl = ctx->reflux && bs->nrefl > 0;
   const int *leaves = bs->d_lists + bs->leaves_off;
+  if ((ctx->integrator == 1 || ctx->integrator == 2) && bs->nvar > 5)
+    return fail(ctx, FX_ERR_ARG, "the SSP-RK integrators step a single gas only");
   if (ctx->integrator == 1 || ctx->integrator == 2) {
     // SSP-RK2: U1 = U + dt L(U) into the other buffer; coarse-fine fill of
     // U1; U = (U + (U1 + dt L(U1))) / 2 in place; registers hold the stage
@@ -656,20 +682,21 @@ int fx_step(fx_ctx *ctx, fx_blocks *bs, double cfl, double *dt_dev, void *stream
   return fx_hydro_advance(ctx, bs, dt_dev, stream);
 }
 
-int fx_conserved_totals(fx_ctx *ctx, fx_blocks *bs, double out_host[5], void *stream) {
+int fx_conserved_totals(fx_ctx *ctx, fx_blocks *bs, double *out_host, void *stream) {
   if (!ctx || !bs || !out_host) return FX_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   FX_CUDA(fx::launch_totals(bs->dm, bs->U[bs->cur], bs->prec, bs->d_lists + bs->leaves_off,
                             bs->nleaves, bs->d_totals, s),
           "totals launch");
-  std::vector<double> h(5 * (size_t)bs->nleaves);
+  const int nv = bs->nvar;
+  std::vector<double> h(nv * (size_t)bs->nleaves);
   FX_CUDA(cudaMemcpyAsync(h.data(), bs->d_totals, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s),
           "totals copy");
   FX_CUDA(cudaStreamSynchronize(s), "totals sync");
-  for (int v = 0; v < 5; ++v) {
+  for (int v = 0; v < nv; ++v) {
     double sum = 0.0, comp = 0.0;
     for (int i = 0; i < bs->nleaves; ++i) {
-      double y = h[5 * (size_t)i + v] - comp;
+      double y = h[nv * (size_t)i + v] - comp;
       double t = sum + y;
       comp = (t - sum) - y;
       sum = t;
@@ -721,7 +748,7 @@ constexpr int kPipeChunks = 8;
 
 // Bytes of one block's interior cells (all five variables).
 size_t interior_block_bytes(const fx_blocks *bs) {
-  return 5 * (size_t)bs->nxb * bs->nxb * (bs->ndim == 3 ? bs->nxb : 1) * bs->elsize;
+  return (size_t)bs->nvar * bs->nxb * bs->nxb * (bs->ndim == 3 ? bs->nxb : 1) * bs->elsize;
 }
 
 int ensure_pipeline(fx_blocks *bs) {
@@ -895,6 +922,8 @@ int fx_regrid_apply(fx_ctx *ctx, fx_blocks *bs, void *U0_new, void *U1_new, void
   if (!ctx || !bs || !U0_new || !U1_new) return FX_ERR_ARG;
   if (bs->in_batch) return fail(ctx, FX_ERR_STATE, "block set is owned by a batch");
   if (!bs->plan_valid) return fail(ctx, FX_ERR_STATE, "no regrid plan");
+  if (5 + ctx->nspec != bs->nvar)
+    return fail(ctx, FX_ERR_STATE, "the context's species changed since the block set was made");
   cudaStream_t s = (cudaStream_t)stream;
   const int n = (int)bs->plan.level.size();
   fx_blocks *nbs = nullptr;
@@ -1177,6 +1206,7 @@ int fx_batch_add(fx_batch *b, fx_blocks *bs, double cfl, int nsteps, void *strea
   if (bs->in_batch) return fail(b->ctx, FX_ERR_STATE, "block set already in a batch");
   if (bs->ctx->integrator != 0)
     return fail(b->ctx, FX_ERR_ARG, "batches step MUSCL-Hancock block sets only");
+  if (bs->nvar != 5) return fail(b->ctx, FX_ERR_ARG, "batches step single-gas block sets only");
   int s = -1;
   for (int r = 0; r < b->max_req; ++r)
     if (!b->slot[r]) { s = r; break; }
@@ -1375,7 +1405,7 @@ extern "C" {
 const double *fx_block_fluxes(const fx_blocks *bs, int b) {
   if (!bs || b < 0 || b >= bs->nb || bs->regidx[b] < 0 || !bs->d_regs) return nullptr;
   const int nfc = bs->ndim == 3 ? bs->nxb * bs->nxb : bs->nxb;
-  return bs->d_regs + (size_t)bs->regidx[b] * 2 * bs->ndim * 5 * nfc;
+  return bs->d_regs + (size_t)bs->regidx[b] * 2 * bs->ndim * bs->nvar * nfc;
 }
 
 }  // extern "C"

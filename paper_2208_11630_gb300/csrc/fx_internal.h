@@ -12,6 +12,8 @@
 #include "fx.h"
 
 #define FX_MAXLEV 16
+#define FX_MAXSPEC 4                 // species of the multispecies perfect gas
+#define FX_MAXVAR (5 + FX_MAXSPEC)   // conserved variables per cell, at most
 
 namespace fx {
 
@@ -23,7 +25,10 @@ enum SlotKind : int { SLOT_NONE = -1, SLOT_COPY = 0, SLOT_PROLONG = 1 };
 struct DevMesh {
   int ndim, nxb, ng, P, PZ, nb, lmax;
   long long vstride;             // elements of one variable of one block: PZ*P*P
-  long long bstride;             // elements of one block: 5*vstride
+  long long bstride;             // elements of one block: nvar*vstride
+  int nvar, nspec;               // variables per cell (5 + nspec); species
+  double spa[FX_MAXSPEC];        // 1 / A_k
+  double spb[FX_MAXSPEC];        // 1 / (A_k (gamma_k - 1))
   int bc[3][2];                  // FX_BC_* per axis and side
   int ncell[FX_MAXLEV][3];       // cells per axis at each level
   double dx[FX_MAXLEV][3];       // cell widths at each level
@@ -113,6 +118,11 @@ cudaError_t launch_regrid_err(const DevMesh &m, const void *U, int prec, const i
                               double eps, unsigned long long *err_bits, cudaStream_t s);
 cudaError_t launch_regrid_transfer(const DevMesh &mo, const void *Uold, const DevMesh &mn,
                                    void *Unew, int prec, const int4 *map, cudaStream_t s);
+// The multispecies MUSCL-Hancock kernels behind launch_hydro (m.nspec > 0).
+cudaError_t launch_hydro_species(const DevMesh &m, const void *U, void *Unew, int prec,
+                                 const int *leaves, int n, const double *dt, double *regs,
+                                 int *status, unsigned long long *smax,
+                                 const unsigned char *rmask, int form, cudaStream_t s);
 // The SSP Runge-Kutta stage kernels behind launch_hydro (st.pred == 0).
 cudaError_t launch_hydro_rk(const DevMesh &m, const void *U, void *Unew, int prec,
                             const int *leaves, int n, const double *dt, double *regs, int *status,

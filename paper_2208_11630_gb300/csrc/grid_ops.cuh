@@ -11,10 +11,19 @@
 // prolongation, Berger & Colella (1989) flux correction.
 #pragma once
 
-#include "fx_internal.h"
+#include "eos.cuh"
 
 namespace fx {
 namespace ops {
+
+// Pressure from conserved variables u[0..nvar) (FP64).
+__device__ __forceinline__ double cons_pressure(const DevMesh &m, const double *u) {
+  double X[FX_MAXSPEC];
+  for (int k = 0; k < m.nspec; ++k) X[k] = u[5 + k] / u[0];
+  double g, gm1;
+  mix_gamma<double>(m, X, m.nspec, g, gm1);
+  return gm1 * (u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0]);
+}
 
 template <typename S>
 __device__ __forceinline__ double ld(const S *p) { return static_cast<double>(*p); }
@@ -69,7 +78,7 @@ __device__ __forceinline__ void restrict_cells(const DevMesh &m, S *__restrict__
   const S *F = U + (long long)ch * m.bstride;
   S *D = U + (long long)p * m.bstride;
   const int dk = m.ndim == 3 ? k + ng : 0;
-  for (int v = 0; v < 5; ++v) {
+  for (int v = 0; v < m.nvar; ++v) {
     const S *f = F + v * m.vstride + ((long long)fk * P + fj) * P + fi;
     double r;
     if (m.ndim == 2) {
@@ -123,8 +132,7 @@ __device__ __forceinline__ void guard_copy_plane(const DevMesh &m, S *__restrict
     }
     const S *Us = U + (long long)src * m.bstride + ((long long)lz * P + ly) * P + lx;
     S *Ud = Ub + ((long long)k * P + j) * P + i;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
+    for (int v = 0; v < m.nvar; ++v) {
       const S x = Us[v * m.vstride];
       Ud[v * m.vstride] = (v >= 1 && v <= 3 && mir[v - 1]) ? -x : x;
     }
@@ -179,7 +187,7 @@ __device__ __forceinline__ void guard_prolong_plane(const DevMesh &m, S *__restr
     const S *Cc = U + (long long)cb * m.bstride + (cz * sPP + cy * sP + cx);
     S *Ud = Ub + ((long long)k * P + j) * P + i;
     const long long step[3] = {1, sP, sPP};
-    for (int v = 0; v < 5; ++v) {
+    for (int v = 0; v < m.nvar; ++v) {
       const S *cv = Cc + v * m.vstride;
       const C uc = C(*cv);
       C val = uc;
@@ -212,7 +220,8 @@ __device__ __forceinline__ void reflux_cells(const DevMesh &m, S *__restrict__ U
   const int nz = nd == 3 ? n : 1;
   const int lev = m.level[c];
   const int nfc = m.nface_cells;
-  const long long rstride = (long long)m.nfaces * 5 * nfc;
+  const int nv = m.nvar;
+  const long long rstride = (long long)m.nfaces * nv * nfc;
   const double *Fc = regs + (long long)m.regidx[c] * rstride;
   S *Uc = Unew + (long long)c * m.bstride;
   const int ncell = n * n * nz;
@@ -222,7 +231,7 @@ __device__ __forceinline__ void reflux_cells(const DevMesh &m, S *__restrict__ U
     for (int d = 0; d < nd; ++d) surf |= (ci[d] == 0 || ci[d] == n - 1);
     if (!surf) continue;
     const long long o = ((long long)(nd == 3 ? ci[2] + ng : 0) * P + (ci[1] + ng)) * P + (ci[0] + ng);
-    double u[5];
+    double u[FX_MAXVAR];
     bool touched = false;
     for (int d = 0; d < nd; ++d) {
       const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
@@ -231,7 +240,7 @@ __device__ __forceinline__ void reflux_cells(const DevMesh &m, S *__restrict__ U
         if (it.fine[f][0] < 0) continue;
         if (ci[d] != (s ? n - 1 : 0)) continue;
         if (!touched) {
-          for (int v = 0; v < 5; ++v) u[v] = double(Uc[o + v * m.vstride]);
+          for (int v = 0; v < nv; ++v) u[v] = double(Uc[o + v * m.vstride]);
           touched = true;
         }
         const int t1 = ci[a1], t2 = nd == 3 ? ci[a2] : 0;
@@ -239,8 +248,8 @@ __device__ __forceinline__ void reflux_cells(const DevMesh &m, S *__restrict__ U
         const double *Ff = regs + (long long)it.fine[f][h1 + 2 * h2] * rstride;
         const int ff = 2 * d + (s ? 0 : 1);
         const int u1 = 2 * t1 - h1 * n, u2 = nd == 3 ? 2 * t2 - h2 * n : 0;
-        for (int v = 0; v < 5; ++v) {
-          const double *fv = Ff + (long long)(ff * 5 + v) * nfc;
+        for (int v = 0; v < nv; ++v) {
+          const double *fv = Ff + (long long)(ff * nv + v) * nfc;
           double fbar;
           if (nd == 3) {
             fbar = ((fv[u2 * n + u1] + fv[u2 * n + u1 + 1]) +
@@ -248,28 +257,20 @@ __device__ __forceinline__ void reflux_cells(const DevMesh &m, S *__restrict__ U
           } else {
             fbar = (fv[u1] + fv[u1 + 1]) * 0.5;
           }
-          const double fc = Fc[(long long)(f * 5 + v) * nfc + t2 * n + t1];
+          const double fc = Fc[(long long)(f * nv + v) * nfc + t2 * n + t1];
           const double corr = dt * (fc - fbar) * m.idx[lev][d];
           u[v] = s ? u[v] + corr : u[v] - corr;
         }
       }
     }
     if (touched) {
-      S us[5];
-      for (int v = 0; v < 5; ++v) { us[v] = S(u[v]); Uc[o + v * m.vstride] = us[v]; }
+      S us[FX_MAXVAR];
+      for (int v = 0; v < nv; ++v) { us[v] = S(u[v]); Uc[o + v * m.vstride] = us[v]; }
       if (!(u[0] > 0.0) || !(2.0 * u[4] * u[0] > u[1] * u[1] + u[2] * u[2] + u[3] * u[3]))
         atomicOr(status, 1);
       if (smax) {
         // CFL signal speed of the corrected cell, in the state's precision
-        const S ir = S(1) / us[0];
-        const S pr = S(m.gamma - 1.0) *
-                     (us[4] - S(0.5) * (us[1] * us[1] + us[2] * us[2] + us[3] * us[3]) * ir);
-        const S cs = sqrt(S(m.gamma) * pr * ir);
-        S sg = S(0);
-        for (int d = 0; d < nd; ++d) {
-          const S sd = (fabs(us[1 + d] * ir) + cs) * S(m.idx[lev][d]);
-          sg = form == 0 ? sg + sd : fmax(sg, sd);
-        }
+        const S sg = cell_signal<S>(m, us, m.nspec, lev, form);
         atomicMax(smax, (unsigned long long)__double_as_longlong(double(sg)));
       }
     }

@@ -28,7 +28,7 @@
 // ulp at a tiny fraction of the cost of FP64 arithmetic on this GPU.
 #pragma once
 
-#include "fx_internal.h"
+#include "eos.cuh"
 
 #include <type_traits>
 
@@ -114,13 +114,26 @@ __device__ __forceinline__ float scaled_diff(float a, float b, float c) {
 // r = (gamma p rho)^(-1/2), c = gamma p r, 1/rho = c r.  The star state of the
 // upwind side K needs S* and 1/(S_K - S*): one FP64 reciprocal, or two FP32
 // fast divisions.
-template <int D, typename R>
-__device__ __forceinline__ void hllc(const R (&WL)[5], const R (&WR)[5], R g, R igm1,
-                                     R (&F)[5]) {
+//
+// Multispecies (NS > 0): each side's gamma follows from its mass fractions
+// WL[5..], WR[5..], and the species fluxes are the mass flux times the
+// upwind side's mass fractions (they pass unchanged through the star region).
+template <int D, typename R, int NS = 0>
+__device__ __forceinline__ void hllc(const R (&WL)[5 + NS], const R (&WR)[5 + NS], R g, R igm1,
+                                     const DevMesh &m, R (&F)[5 + NS]) {
   constexpr int N = 1 + D;
   const R rL = WL[0], uL = WL[N], pL = WL[4];
   const R rR = WR[0], uR = WR[N], pR = WR[4];
-  const R gpL = g * pL, gpR = g * pR;
+  R gL = g, gR = g, igL = igm1, igR = igm1;
+  if constexpr (NS > 0) {
+    R gm1L, gm1R;
+    mix_gamma<R>(m, WL + 5, NS, gL, gm1L);
+    mix_gamma<R>(m, WR + 5, NS, gR, gm1R);
+    igL = div_r(R(1), gm1L);
+    igR = div_r(R(1), gm1R);
+  }
+  (void)m;
+  const R gpL = gL * pL, gpR = gR * pR;
   const R qL = rsqrt_r(gpL * rL), qR = rsqrt_r(gpR * rR);
   const R cL = gpL * qL, cR = gpR * qR;
   const R SL = fmin(uL - cL, uR - cR);
@@ -145,15 +158,16 @@ __device__ __forceinline__ void hllc(const R (&WL)[5], const R (&WR)[5], R g, R 
   const bool caseA = ge0(SL);
   const bool useL = caseA || sst_ge0;
   const bool star = !caseA && (useL || gt0(SR));
-  R W[5];
+  R W[5 + NS];
 #pragma unroll
-  for (int q = 0; q < 5; ++q) W[q] = useL ? WL[q] : WR[q];
+  for (int q = 0; q < 5 + NS; ++q) W[q] = useL ? WL[q] : WR[q];
   const R SK = useL ? SL : SR;
   const R irK = useL ? cL * qL : cR * qR;
+  const R igK = useL ? igL : igR;
   const R rK = W[0], uK = W[N], pK = W[4];
   const R ke = R(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
-  const R EK = pK * igm1 + rK * ke;          // total energy of side K
-  const R eK = pK * igm1 * irK + ke;         // E_K / rho_K
+  const R EK = pK * igK + rK * ke;           // total energy of side K
+  const R eK = pK * igK * irK + ke;          // E_K / rho_K
   const R mK = rK * uK;
   F[0] = mK;
 #pragma unroll
@@ -186,93 +200,120 @@ __device__ __forceinline__ void hllc(const R (&WL)[5], const R (&WR)[5], R g, R 
     for (int t = 0; t < 3; ++t) F[1 + t] = F[1 + t] + SK * (Us[1 + t] - rK * W[1 + t]);
     F[4] = F[4] + SK * (Us[4] - EK);
   }
+#pragma unroll
+  for (int k = 0; k < NS; ++k) F[5 + k] = F[0] * W[5 + k];
 }
 
-// Primitives (rho, u, v, w, p) and 1/rho of one cell.
-template <typename S, typename R>
-__device__ __forceinline__ void prim(const S *u, long long vs, R gm1, R (&w)[6]) {
+// Primitives (rho, u, v, w, p) and 1/rho of one cell; with NS species also
+// the mass fractions (w[6..6+NS)) and the cell's gamma (w[6+NS]).
+template <typename S, typename R, int NS = 0>
+__device__ __forceinline__ void prim(const S *u, long long vs, R gm1, const DevMesh &m,
+                                     R (&w)[6 + NS + (NS > 0)]) {
   const R r = R(u[0]), mx = R(u[vs]), my = R(u[2 * vs]), mz = R(u[3 * vs]), E = R(u[4 * vs]);
   const R ir = div_r(R(1), r);
   w[0] = r;
   w[1] = mx * ir;
   w[2] = my * ir;
   w[3] = mz * ir;
-  w[4] = gm1 * (E - R(0.5) * (mx * mx + my * my + mz * mz) * ir);
+  R gmc = gm1;
+  if constexpr (NS > 0) {
+    R X[NS], gc;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      X[k] = R(u[(5 + k) * vs]) * ir;
+      w[6 + k] = X[k];
+    }
+    mix_gamma<R>(m, X, NS, gc, gmc);
+    w[6 + NS] = gc;
+  }
+  (void)m;
+  w[4] = gmc * (E - R(0.5) * (mx * mx + my * my + mz * mz) * ir);
   w[5] = ir;
 }
 
 // Shared-memory map, in elements of R.
-template <int T>
+template <int T, int NS = 0>
 struct Smem {
   static constexpr int W4 = T + 4;          // ring plane width (radius-2 halo)
   static constexpr int W2 = T + 2;          // face-state row width (radius-1)
-  static constexpr int NV = 6;              // rho, u, v, w, p, 1/rho
+  static constexpr int NV = 6 + NS + (NS > 0);  // rho, u, v, w, p, 1/rho (, X_k, gamma)
+  static constexpr int NF = 5 + NS;         // face-state / flux components
   static constexpr int RING = NV * W4 * W4; // one primitive plane
-  static constexpr int FX = 5 * T * W2;     // x face states [v][j][i+1]
-  static constexpr int FY = 5 * W2 * T;     // y face states [v][j+1][i]
+  static constexpr int FX = NF * T * W2;    // x face states [v][j][i+1]
+  static constexpr int FY = NF * W2 * T;    // y face states [v][j+1][i]
   static constexpr int total(int nplanes) { return nplanes * RING + 2 * FX + 2 * FY; }
 };
+
+// Ring component of primitive variable v (the ring stores 1/rho at 5).
+__host__ __device__ constexpr int ring_comp(int v) { return v < 5 ? v : v + 1; }
 
 // Slopes, Hancock predictor and face states of the cell at tile-local (i, j)
 // of the plane in ring slot s0 (neighbour planes in sm, sp).  Works with half
 // slopes h = dW/2 throughout: the predictor is linear in the slopes, so
 // A(W) h (2/dx) is exactly A(W) dW / dx, and the face states are W* -+ h.
 // Returns the lower/upper face states per direction in fm/fp.
-template <int NDIM, int T, typename R, bool PRED = true>
+template <int NDIM, int T, typename R, bool PRED = true, int NS = 0>
 __device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int s0, int sp, int i,
                                         int j, R hdt, const R (&idx2)[3], R g,
-                                        R (&fm)[3][5], R (&fp)[3][5]) {
-  using SM = Smem<T>;
+                                        R (&fm)[3][5 + NS], R (&fp)[3][5 + NS]) {
+  using SM = Smem<T, NS>;
+  constexpr int NF = 5 + NS;
   constexpr int PL = SM::W4 * SM::W4;
   const int c = (j + 2) * SM::W4 + (i + 2);
   const R *p0 = ring + s0 * SM::RING;
-  R W0[5], h[3][5];
+  R W0[NF], h[3][NF];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) W0[v] = p0[v * PL + c];
+  for (int v = 0; v < NF; ++v) W0[v] = p0[ring_comp(v) * PL + c];
   const R ir = p0[5 * PL + c];
+  // the cell's gamma: the mesh's, or its mixture gamma (species)
+  const R gc = NS > 0 ? p0[(6 + NS) * PL + c] : g;
 #pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    const R *q = p0 + v * PL + c;
+  for (int v = 0; v < NF; ++v) {
+    const R *q = p0 + ring_comp(v) * PL + c;
     h[0][v] = mc_half(W0[v] - q[-1], q[1] - W0[v]);
     h[1][v] = mc_half(W0[v] - q[-SM::W4], q[SM::W4] - W0[v]);
     if (NDIM == 3) {
-      const R wm = ring[sm * SM::RING + v * PL + c];
-      const R wp = ring[sp * SM::RING + v * PL + c];
+      const R wm = ring[sm * SM::RING + ring_comp(v) * PL + c];
+      const R wp = ring[sp * SM::RING + ring_comp(v) * PL + c];
       h[2][v] = mc_half(W0[v] - wm, wp - W0[v]);
     } else {
       h[2][v] = R(0);
     }
   }
-  R Wh[5];
+  R Wh[NF];
   if constexpr (PRED) {
     // primitive quasi-linear form: sum_d A_d(W) dW_d / dx_d
-    R acc[5] = {R(0), R(0), R(0), R(0), R(0)};
-    const R r = W0[0], gp = g * W0[4];
+    R acc[NF];
+#pragma unroll
+    for (int v = 0; v < NF; ++v) acc[v] = R(0);
+    const R r = W0[0], gp = gc * W0[4];
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
       const int n = 1 + d;
       const R un = W0[n];
-      R a[5];
+      R a[NF];
       a[0] = un * h[d][0] + r * h[d][n];
 #pragma unroll
       for (int t = 0; t < 3; ++t) a[1 + t] = un * h[d][1 + t];
       a[n] = a[n] + h[d][4] * ir;
       a[4] = gp * h[d][n] + un * h[d][4];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) acc[v] = acc[v] + a[v] * idx2[d];
+      for (int k = 0; k < NS; ++k) a[5 + k] = un * h[d][5 + k];   // advected X_k
+#pragma unroll
+      for (int v = 0; v < NF; ++v) acc[v] = acc[v] + a[v] * idx2[d];
     }
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Wh[v] = W0[v] - hdt * acc[v];
+    for (int v = 0; v < NF; ++v) Wh[v] = W0[v] - hdt * acc[v];
   } else {
     // plain PLM face states: no half step
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Wh[v] = W0[v];
+    for (int v = 0; v < NF; ++v) Wh[v] = W0[v];
   }
   bool ok = true;
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
+    for (int v = 0; v < NF; ++v) {
       fm[d][v] = Wh[v] - h[d][v];
       fp[d][v] = Wh[v] + h[d][v];
     }
@@ -283,7 +324,7 @@ __device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int 
 #pragma unroll
     for (int d = 0; d < NDIM; ++d)
 #pragma unroll
-      for (int v = 0; v < 5; ++v) { fm[d][v] = W0[v]; fp[d][v] = W0[v]; }
+      for (int v = 0; v < NF; ++v) { fm[d][v] = W0[v]; fp[d][v] = W0[v]; }
   }
 }
 
@@ -296,7 +337,7 @@ __device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int 
 //             itself: each cell is read before it is written by the same
 //             thread, so neither pointer is declared restrict); registers
 //             store or (st.reg_add) add st.reg_w F
-template <int NDIM, int T, typename S, typename R, bool RK = false>
+template <int NDIM, int T, typename S, typename R, bool RK = false, int NS = 0>
 __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict__ U,
                                            S *Unew, int b, int tile, int tiles,
                                            double dt, double *__restrict__ regs,
@@ -305,7 +346,8 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
                                            const unsigned char *__restrict__ rmask,
                                            int cfl_form, const HydroStage &st = HydroStage()) {
   const S *Uavg = RK ? static_cast<const S *>(st.Uavg) : nullptr;
-  using SM = Smem<T>;
+  using SM = Smem<T, NS>;
+  constexpr int NF = 5 + NS;         // conserved variables, face-state components
   constexpr int NT = T * T;
   constexpr int NPL = NDIM == 3 ? 3 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -333,7 +375,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
   const int ti = tid % T, tj = tid / T;
   const int zoff = NDIM == 3 ? ng : 0;
   const int ridx = m.regidx[b];
-  double *reg = ridx >= 0 ? regs + (long long)ridx * m.nfaces * 5 * m.nface_cells : nullptr;
+  double *reg = ridx >= 0 ? regs + (long long)ridx * m.nfaces * NF * m.nface_cells : nullptr;
   const int nfc = m.nface_cells;
 
   // Guard sources of this block: a same-level slot is read straight from the
@@ -393,15 +435,15 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
           src = U + (long long)sl.y * m.bstride + ((long long)lz * P + ly) * P + lx;
         }
       }
-      R w[6];
-      prim<S, R>(src, vs, gm1, w);
+      R w[SM::NV];
+      prim<S, R, NS>(src, vs, gm1, m, w);
       if (flip) {
 #pragma unroll
         for (int d = 0; d < 3; ++d)
           if ((flip >> d) & 1u) w[1 + d] = -w[1 + d];
       }
 #pragma unroll
-      for (int v = 0; v < 6; ++v) dst[v * SM::W4 * SM::W4 + c] = w[v];
+      for (int v = 0; v < SM::NV; ++v) dst[v * SM::W4 * SM::W4 + c] = w[v];
     }
   };
   auto slot_of = [&](int p) { return NDIM == 3 ? ((p % 3) + 3) % 3 : 0; };
@@ -409,10 +451,10 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
   // register state of the thread's column: pending update of the cell below
   // (x+y part of its flux divergence, flux through its lower z face)
   constexpr bool kF32 = std::is_same<R, float>::value;
-  R txy[5], fzl[5];
-  R zprev[5];
+  R txy[NF], fzl[NF];
+  R zprev[NF];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) { txy[v] = R(0); fzl[v] = R(0); zprev[v] = R(0); }
+  for (int v = 0; v < NF; ++v) { txy[v] = R(0); fzl[v] = R(0); zprev[v] = R(0); }
   // FP32 path: dt/dx per direction; FP64 path: 1/dx and dt separately
   const float cx = float(dt * m.idx[lev][0]), cy = float(dt * m.idx[lev][1]),
               cz = float(dt * m.idx[lev][2]);
@@ -421,9 +463,8 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
   // and precision as the standalone reduction).  Cells that the flux
   // correction will still change (on a face in rmask) are left to it.
   const unsigned fmask = rmask ? rmask[b] : 0u;
-  const R sidx[3] = {R(m.idx[lev][0]), R(m.idx[lev][1]), R(m.idx[lev][2])};
   R smax_t = R(0);
-  auto signal = [&](const R (&u)[5], int ci, int cj, int ck) {
+  auto signal = [&](const R (&u)[NF], int ci, int cj, int ck) {
     if (fmask) {
       const int cc[3] = {ci, cj, ck};
       for (int d = 0; d < NDIM; ++d) {
@@ -431,17 +472,10 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
         if (((fmask >> (2 * d + 1)) & 1u) && cc[d] == n - 1) return;
       }
     }
-    const R ir = R(1) / u[0];
-    const R pr = gm1 * (u[4] - R(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * ir);
-    const R cs = sqrt(g * pr * ir);
-    R sg = R(0);
-#pragma unroll
-    for (int d = 0; d < NDIM; ++d) {
-      const R sd = (fabs(u[1 + d] * ir) + cs) * sidx[d];
-      sg = cfl_form == 0 ? sg + sd : fmax(sg, sd);
-    }
+    const R sg = cell_signal<R>(m, u, NS, lev, cfl_form);
     if (!(sg <= smax_t)) smax_t = sg;   // keeps a NaN
   };
+
 
   const int pstart = NDIM == 3 ? -1 : 0;
   const int pend = NDIM == 3 ? n : 0;   // inclusive
@@ -457,13 +491,13 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
     __syncthreads();
 
     // ---- predictor: own column cell, then (inner planes) the radius-1 ring
-    R zm[5], zp[5];
+    R zm[NF], zp[NF];
     {
-      R fm[3][5], fp[3][5];
-      predict<NDIM, T, R, !RK>(ring, sm, s0, sp, ti, tj, hdt, idx2, g, fm, fp);
+      R fm[3][NF], fp[3][NF];
+      predict<NDIM, T, R, !RK, NS>(ring, sm, s0, sp, ti, tj, hdt, idx2, g, fm, fp);
       if (inner) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
+        for (int v = 0; v < NF; ++v) {
           fxm[v * T * SM::W2 + tj * SM::W2 + ti + 1] = fm[0][v];
           fxp[v * T * SM::W2 + tj * SM::W2 + ti + 1] = fp[0][v];
           fym[v * SM::W2 * T + (tj + 1) * T + ti] = fm[1][v];
@@ -471,7 +505,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
         }
       }
 #pragma unroll
-      for (int v = 0; v < 5; ++v) { zm[v] = fm[2][v]; zp[v] = fp[2][v]; }
+      for (int v = 0; v < NF; ++v) { zm[v] = fm[2][v]; zp[v] = fp[2][v]; }
     }
     if (inner) {
       for (int c = tid; c < 4 * T; c += NT) {
@@ -481,17 +515,17 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
         else if (side == 1) { i = T; j = e; }
         else if (side == 2) { i = e; j = -1; }
         else { i = e; j = T; }
-        R fm[3][5], fp[3][5];
-        predict<NDIM, T, R, !RK>(ring, sm, s0, sp, i, j, hdt, idx2, g, fm, fp);
+        R fm[3][NF], fp[3][NF];
+        predict<NDIM, T, R, !RK, NS>(ring, sm, s0, sp, i, j, hdt, idx2, g, fm, fp);
         if (side < 2) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) {
+          for (int v = 0; v < NF; ++v) {
             fxm[v * T * SM::W2 + j * SM::W2 + i + 1] = fm[0][v];
             fxp[v * T * SM::W2 + j * SM::W2 + i + 1] = fp[0][v];
           }
         } else {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) {
+          for (int v = 0; v < NF; ++v) {
             fym[v * SM::W2 * T + (j + 1) * T + i] = fm[1][v];
             fyp[v * SM::W2 * T + (j + 1) * T + i] = fp[1][v];
           }
@@ -517,47 +551,47 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
         } else {
           a = T; e = ff - T * T;
         }
-        R WL[5], WR[5], F[5];
+        R WL[NF], WR[NF], F[NF];
         if (!dir) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) {
+          for (int v = 0; v < NF; ++v) {
             WL[v] = fxp[v * T * SM::W2 + e * SM::W2 + a];
             WR[v] = fxm[v * T * SM::W2 + e * SM::W2 + a + 1];
           }
-          hllc<0, R>(WL, WR, g, igm1, F);
+          hllc<0, R, NS>(WL, WR, g, igm1, m, F);
 #pragma unroll
-          for (int v = 0; v < 5; ++v) fxm[v * T * SM::W2 + e * SM::W2 + a + 1] = F[v];
+          for (int v = 0; v < NF; ++v) fxm[v * T * SM::W2 + e * SM::W2 + a + 1] = F[v];
           if (reg && ((a == 0 && x0 == 0) || (a == T && x0 + T == n))) {
             const int face = a == 0 ? 0 : 1;
             const int t1 = y0 + e, t2 = NDIM == 3 ? zglob : 0;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) put_reg<RK>(reg[(face * 5 + v) * nfc + t2 * n + t1], F[v], st);
+            for (int v = 0; v < NF; ++v) put_reg<RK>(reg[(face * NF + v) * nfc + t2 * n + t1], F[v], st);
           }
         } else {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) {
+          for (int v = 0; v < NF; ++v) {
             WL[v] = fyp[v * SM::W2 * T + a * T + e];
             WR[v] = fym[v * SM::W2 * T + (a + 1) * T + e];
           }
-          hllc<1, R>(WL, WR, g, igm1, F);
+          hllc<1, R, NS>(WL, WR, g, igm1, m, F);
 #pragma unroll
-          for (int v = 0; v < 5; ++v) fym[v * SM::W2 * T + (a + 1) * T + e] = F[v];
+          for (int v = 0; v < NF; ++v) fym[v * SM::W2 * T + (a + 1) * T + e] = F[v];
           if (reg && ((a == 0 && y0 == 0) || (a == T && y0 + T == n))) {
             const int face = a == 0 ? 2 : 3;
             const int t1 = x0 + e, t2 = NDIM == 3 ? zglob : 0;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) put_reg<RK>(reg[(face * 5 + v) * nfc + t2 * n + t1], F[v], st);
+            for (int v = 0; v < NF; ++v) put_reg<RK>(reg[(face * NF + v) * nfc + t2 * n + t1], F[v], st);
           }
         }
       }
     }
-    R Fz[5];
+    R Fz[NF];
     if (NDIM == 3 && p >= 0) {
-      hllc<2, R>(zprev, zm, g, igm1, Fz);
+      hllc<2, R, NS>(zprev, zm, g, igm1, m, Fz);
       if (reg && (p == 0 || p == n)) {
         const int face = p == 0 ? 4 : 5;
 #pragma unroll
-        for (int v = 0; v < 5; ++v) put_reg<RK>(reg[(face * 5 + v) * nfc + (y0 + tj) * n + (x0 + ti)], Fz[v], st);
+        for (int v = 0; v < NF; ++v) put_reg<RK>(reg[(face * NF + v) * nfc + (y0 + tj) * n + (x0 + ti)], Fz[v], st);
       }
     }
     __syncthreads();
@@ -568,9 +602,9 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
     // rounding when added to U.
     if (NDIM == 3 && p >= 1) {
       const long long o = ((long long)(p - 1 + ng) * P + (y0 + tj + ng)) * P + (x0 + ti + ng);
-      R un[5];
+      R un[NF];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
+      for (int v = 0; v < NF; ++v) {
         if constexpr (kF32) {
           const float d = txy[v] + scaled_diff(fzl[v], Fz[v], cz);
           un[v] = float(Ub[o + v * vs]) + d;
@@ -592,7 +626,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
       const R *Fx = fxm + tj * SM::W2 + ti + 1;
       const R *Fy = fym + (tj + 1) * T + ti;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
+      for (int v = 0; v < NF; ++v) {
         const R fxl = Fx[v * T * SM::W2], fxr = Fx[v * T * SM::W2 + 1];
         const R fyl = Fy[v * SM::W2 * T], fyr = Fy[v * SM::W2 * T + T];
         if constexpr (kF32) {
@@ -604,9 +638,9 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
       }
       if (NDIM == 2) {
         const long long o = (long long)(y0 + tj + ng) * P + (x0 + ti + ng);
-        R un[5];
+        R un[NF];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
+        for (int v = 0; v < NF; ++v) {
           if constexpr (kF32) un[v] = float(Ub[o + v * vs]) + txy[v];
           else un[v] = double(Ub[o + v * vs]) + dt * txy[v];
           if constexpr (RK) {
@@ -622,7 +656,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
       }
     }
 #pragma unroll
-    for (int v = 0; v < 5; ++v) zprev[v] = zp[v];
+    for (int v = 0; v < NF; ++v) zprev[v] = zp[v];
   }
   if (smax_out) {
     // maximum over the CTA on the bit patterns of non-negative doubles

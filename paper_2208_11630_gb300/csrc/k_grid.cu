@@ -29,11 +29,21 @@ __global__ void k_prim_to_cons(DevMesh m, const double *__restrict__ W, S *__res
     const double *w = W + b * m.bstride + o;
     S *u = U + b * m.bstride + o;
     double r = w[0], vx = w[per], vy = w[2 * per], vz = w[3 * per], p = w[4 * per];
+    double ig = igm1;
+    if (m.nspec) {          // mass fractions follow; the cell's mixture gamma
+      double X[FX_MAXSPEC], g, gm1;
+      for (int k = 0; k < m.nspec; ++k) {
+        X[k] = w[(5 + k) * per];
+        st(u + (5 + k) * per, r * X[k]);
+      }
+      mix_gamma<double>(m, X, m.nspec, g, gm1);
+      ig = 1.0 / gm1;
+    }
     st(u, r);
     st(u + per, r * vx);
     st(u + 2 * per, r * vy);
     st(u + 3 * per, r * vz);
-    st(u + 4 * per, p * igm1 + 0.5 * r * (vx * vx + vy * vy + vz * vz));
+    st(u + 4 * per, p * ig + 0.5 * r * (vx * vx + vy * vy + vz * vz));
   }
 }
 
@@ -59,7 +69,7 @@ __global__ void k_guard_prolong(DevMesh m, S *__restrict__ U, const int *__restr
 }
 
 // Interior cells of blocks [b0, b0 + nblk) between the padded block layout
-// and a packed array [block][var][z][y][x] of interior cells (packed index
+// and a packed array [block][var][z][y][x] of interior cells (nvar variables) (packed index
 // relative to block b0).  dir 0: packed -> padded; 1: padded -> packed.
 template <typename S>
 __global__ void k_pack(DevMesh m, S *__restrict__ U, S *__restrict__ Pk, int b0, int nblk,
@@ -67,15 +77,16 @@ __global__ void k_pack(DevMesh m, S *__restrict__ U, S *__restrict__ Pk, int b0,
   const int n = m.nxb, ng = m.ng, P = m.P;
   const int nz = m.ndim == 3 ? n : 1, gz = m.ndim == 3 ? ng : 0;
   const long long per_var = (long long)nz * n * n;
-  const long long total = (long long)nblk * 5 * per_var;
+  const int nv = m.nvar;
+  const long long total = (long long)nblk * nv * per_var;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < total;
        c += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(c % n), j = (int)((c / n) % n);
     const long long r = c / ((long long)n * n);
     const int k = (int)(r % nz);
     const long long bv = r / nz;
-    const int v = (int)(bv % 5);
-    const long long b = b0 + bv / 5;
+    const int v = (int)(bv % nv);
+    const long long b = b0 + bv / nv;
     S *u = U + b * m.bstride + v * m.vstride + ((long long)(k + gz) * P + (j + ng)) * P + (i + ng);
     if (dir == 0) *u = Pk[c];
     else Pk[c] = *u;
@@ -103,7 +114,7 @@ cudaError_t launch_pack(const DevMesh &m, void *U, int prec, void *packed, int b
                         int dir, cudaStream_t s) {
   if (nblk <= 0) return cudaSuccess;
   const long long total =
-      (long long)nblk * 5 * m.nxb * m.nxb * (m.ndim == 3 ? m.nxb : 1);
+      (long long)nblk * m.nvar * m.nxb * m.nxb * (m.ndim == 3 ? m.nxb : 1);
   long long grid = (total + 255) / 256;
   if (grid > 152 * 16) grid = 152 * 16;
   if (prec == 0)

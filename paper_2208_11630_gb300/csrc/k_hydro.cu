@@ -139,6 +139,11 @@ cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, 
                          unsigned long long *smax, const unsigned char *rmask, int form,
                          cudaStream_t s, const HydroStage &st) {
   if (n <= 0) return cudaSuccess;
+  if (m.nspec > 0) {   // multispecies gas (k_hydro_sp.cu): MUSCL-Hancock only
+    if (!st.pred || st.Uavg || st.reg_add || st.reg_w != 1.0) return cudaErrorInvalidValue;
+    return launch_hydro_species(m, U, Unew, prec, leaves, n, dt, regs, status, smax, rmask, form,
+                                s);
+  }
   if (!st.pred)     // an SSP Runge-Kutta stage (k_hydro_rk.cu)
     return launch_hydro_rk(m, U, Unew, prec, leaves, n, dt, regs, status, smax, rmask, form, s, st);
   if (st.Uavg || st.reg_add || st.reg_w != 1.0) return cudaErrorInvalidValue;

@@ -7,7 +7,7 @@
 // (Section 2.2).  The maximum of non-negative doubles is taken on their bit
 // patterns with atomicMax, which is exact and independent of order; the last
 // CTA to finish writes dt and re-arms the two scratch words.
-#include "fx_internal.h"
+#include "eos.cuh"
 
 namespace fx {
 namespace {
@@ -23,7 +23,6 @@ __global__ void k_dt(DevMesh m, const S *__restrict__ U, const int *__restrict__
   const long long total = ncell * nleaves;
   // the signal speed is computed in the state's precision
   using C = S;
-  const C g = C(m.gamma), gm1 = C(m.gamma - 1.0);
   C smax = C(0);
   for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total;
        w += (long long)gridDim.x * blockDim.x) {
@@ -33,17 +32,9 @@ __global__ void k_dt(DevMesh m, const S *__restrict__ U, const int *__restrict__
     const S *u = U + (long long)b * m.bstride +
                  ((long long)(nd == 3 ? k + ng : 0) * P + (j + ng)) * P + (i + ng);
     const long long vs = m.vstride;
-    const C r = u[0], mx = u[vs], my = u[2 * vs], mz = u[3 * vs], E = u[4 * vs];
-    const C ir = C(1) / r;
-    const C p = gm1 * (E - C(0.5) * (mx * mx + my * my + mz * mz) * ir);
-    const C cs = sqrt(g * p * ir);
-    const int lev = m.level[b];
-    const C vel[3] = {mx * ir, my * ir, mz * ir};
-    C s = C(0);
-    for (int d = 0; d < nd; ++d) {
-      const C sd = (fabs(vel[d]) + cs) * C(m.idx[lev][d]);
-      s = form == 0 ? s + sd : fmax(s, sd);
-    }
+    C uc[FX_MAXVAR];
+    for (int v = 0; v < m.nvar; ++v) uc[v] = u[v * vs];
+    const C s = cell_signal<C>(m, uc, m.nspec, m.level[b], form);
     if (!(s <= smax)) smax = s;   // keeps a NaN
   }
   // warp and CTA maximum on the bit patterns (non-negative doubles and NaN
@@ -88,25 +79,26 @@ __global__ void k_totals(DevMesh m, const S *__restrict__ U, const int *__restri
   const int n = m.nxb, ng = m.ng, P = m.P, nd = m.ndim;
   const int nz = nd == 3 ? n : 1;
   const int ncell = n * n * nz;
-  __shared__ double red[5][256];
-  double acc[5] = {0, 0, 0, 0, 0};
+  __shared__ double red[FX_MAXVAR][256];
+  double acc[FX_MAXVAR] = {0};
+  const int nv = m.nvar;
   const S *Ub = U + (long long)b * m.bstride;
   for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
     const int i = c % n, j = (c / n) % n, k = c / (n * n);
     const long long o = ((long long)(nd == 3 ? k + ng : 0) * P + (j + ng)) * P + (i + ng);
-    for (int v = 0; v < 5; ++v) acc[v] += double(Ub[o + v * m.vstride]);
+    for (int v = 0; v < nv; ++v) acc[v] += double(Ub[o + v * m.vstride]);
   }
-  for (int v = 0; v < 5; ++v) red[v][threadIdx.x] = acc[v];
+  for (int v = 0; v < nv; ++v) red[v][threadIdx.x] = acc[v];
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s)
-      for (int v = 0; v < 5; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + s];
+      for (int v = 0; v < nv; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x < 5) {
+  if (threadIdx.x < nv) {
     const int lev = m.level[b];
     const double dV = m.dx[lev][0] * m.dx[lev][1] * (nd == 3 ? m.dx[lev][2] : 1.0);
-    out[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0] * dV;
+    out[blockIdx.x * nv + threadIdx.x] = red[threadIdx.x][0] * dV;
   }
 }
 

@@ -15,12 +15,12 @@ namespace {
 
 // Density (v = 0) or pressure (v = 4) of the cell at padded offset o.
 template <typename S>
-__device__ __forceinline__ double rho_or_p(const S *Ub, long long vs, long long o, int v,
-                                           double gm1) {
-  const double r = double(Ub[o]);
-  if (v == 0) return r;
-  const double mx = double(Ub[o + vs]), my = double(Ub[o + 2 * vs]), mz = double(Ub[o + 3 * vs]);
-  return gm1 * (double(Ub[o + 4 * vs]) - 0.5 * (mx * mx + my * my + mz * mz) / r);
+__device__ __forceinline__ double rho_or_p(const DevMesh &m, const S *Ub, long long vs,
+                                           long long o, int v) {
+  if (v == 0) return double(Ub[o]);
+  double u[FX_MAXVAR];
+  for (int q = 0; q < m.nvar; ++q) u[q] = double(Ub[o + q * vs]);
+  return ops::cons_pressure(m, u);
 }
 
 // Indicator of one cell for one field: sqrt(sum N^2 / sum D^2) over ordered
@@ -35,22 +35,21 @@ __device__ double loehner(const DevMesh &m, const S *Ub, int lev, int i, int j, 
   const long long vs = m.vstride, P = m.P;
   const long long step[3] = {1, P, P * P};
   const long long o0 = ((long long)k * P + j) * P + i;
-  const double gm1 = m.gamma - 1.0;
   double num = 0.0, den = 0.0;
   for (int a = 0; a < m.ndim; ++a)
     for (int b = 0; b < m.ndim; ++b) {
       double nu, de;
       if (a == b) {
-        const double up = rho_or_p(Ub, vs, o0 + step[a], v, gm1);
-        const double u0 = rho_or_p(Ub, vs, o0, v, gm1);
-        const double um = rho_or_p(Ub, vs, o0 - step[a], v, gm1);
+        const double up = rho_or_p(m, Ub, vs, o0 + step[a], v);
+        const double u0 = rho_or_p(m, Ub, vs, o0, v);
+        const double um = rho_or_p(m, Ub, vs, o0 - step[a], v);
         nu = (up - u0) - (u0 - um);
         de = fabs(up - u0) + fabs(u0 - um) + eps * (fabs(up) + 2.0 * fabs(u0) + fabs(um));
       } else {
-        const double upp = rho_or_p(Ub, vs, o0 + step[a] + step[b], v, gm1);
-        const double ump = rho_or_p(Ub, vs, o0 - step[a] + step[b], v, gm1);
-        const double upm = rho_or_p(Ub, vs, o0 + step[a] - step[b], v, gm1);
-        const double umm = rho_or_p(Ub, vs, o0 - step[a] - step[b], v, gm1);
+        const double upp = rho_or_p(m, Ub, vs, o0 + step[a] + step[b], v);
+        const double ump = rho_or_p(m, Ub, vs, o0 - step[a] + step[b], v);
+        const double upm = rho_or_p(m, Ub, vs, o0 + step[a] - step[b], v);
+        const double umm = rho_or_p(m, Ub, vs, o0 - step[a] - step[b], v);
         nu = ((upp - ump) - (upm - umm)) * 0.25;
         de = (fabs(upp - ump) + fabs(upm - umm)) * 0.25 +
              eps * (fabs(upp) + fabs(ump) + fabs(upm) + fabs(umm)) * 0.25;
@@ -112,8 +111,7 @@ __global__ void k_regrid_transfer(DevMesh mo, const S *__restrict__ Uold, DevMes
     const int i = c % n, jj = c / n;
     const long long od = ((long long)(k + kz) * P + (jj + ng)) * P + (i + ng);
     if (w.x == 0) {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) Ud[od + v * mn.vstride] = Us[od + v * mo.vstride];
+      for (int v = 0; v < mn.nvar; ++v) Ud[od + v * mn.vstride] = Us[od + v * mo.vstride];
       continue;
     }
     const int f[3] = {((w.z >> 0) & 1) * n + i, ((w.z >> 1) & 1) * n + jj,
@@ -121,8 +119,8 @@ __global__ void k_regrid_transfer(DevMesh mo, const S *__restrict__ Uold, DevMes
     const long long oc = ((long long)(mn.ndim == 3 ? f[2] / 2 + ng : 0) * P + (f[1] / 2 + ng)) * P +
                          (f[0] / 2 + ng);
     // conserved variables of the fine cell with parities q of coarse cell oc
-    auto prolong = [&](const int (&q)[3], double (&u)[5]) {
-      for (int v = 0; v < 5; ++v) {
+    auto prolong = [&](const int (&q)[3], double (&u)[FX_MAXVAR]) {
+      for (int v = 0; v < mn.nvar; ++v) {
         const S *cv = Us + v * mo.vstride + oc;
         const double uc = double(*cv);
         double val = uc;
@@ -139,19 +137,18 @@ __global__ void k_regrid_transfer(DevMesh mo, const S *__restrict__ Uold, DevMes
     bool ok = true;
     for (int c = 0; c < (1 << mn.ndim) && ok; ++c) {
       const int q[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
-      double u[5];
+      double u[FX_MAXVAR];
       prolong(q, u);
-      const double pr = (mn.gamma - 1.0) * (u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0]);
-      if (!(u[0] > 0.0) || !(pr > 0.0)) ok = false;
+      if (!(u[0] > 0.0) || !(ops::cons_pressure(mn, u) > 0.0)) ok = false;
     }
-    double u[5];
+    double u[FX_MAXVAR];
     if (ok) {
       const int q[3] = {f[0] & 1, f[1] & 1, f[2] & 1};
       prolong(q, u);
     } else {
-      for (int v = 0; v < 5; ++v) u[v] = double(Us[v * mo.vstride + oc]);
+      for (int v = 0; v < mn.nvar; ++v) u[v] = double(Us[v * mo.vstride + oc]);
     }
-    for (int v = 0; v < 5; ++v) Ud[od + v * mn.vstride] = S(u[v]);
+    for (int v = 0; v < mn.nvar; ++v) Ud[od + v * mn.vstride] = S(u[v]);
   }
 }
 

@@ -24,6 +24,7 @@ FX_F32BULK = 1
 FX_BC_OUTFLOW = 0
 FX_BC_PERIODIC = 1
 FX_BC_REFLECT = 2
+FX_MAXVAR = 9          # 5 + at most 4 species
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None
@@ -57,6 +58,7 @@ def load(build: bool = True):
             "fx_init": (c_int, [c_double, c_int, c_int, ctypes.POINTER(vp)]),
             "fx_finalize": (c_int, [vp]),
             "fx_set_option": (c_int, [vp, ctypes.c_char_p, c_double]),
+            "fx_set_species": (c_int, [vp, c_int, dp, dp]),
             "fx_last_error": (ctypes.c_char_p, [vp]),
             "fx_blocks_create": (c_int, [vp, c_int, c_int, c_int, ip, ip, i64p, ip, dp, dp, ip,
                                          c_int, vp, vp, ctypes.POINTER(vp)]),
@@ -128,6 +130,16 @@ def fx_finalize(ctx):
     _check(None, load().fx_finalize(ctx))
 
 
+def fx_set_species(ctx, species) -> None:
+    """Multispecies perfect gas for block sets created afterwards:
+    ``species`` = ((gamma_k, A_k), ...) (empty: the single gas)."""
+    g = np.array([sp[0] for sp in species], dtype=np.float64)
+    a = np.array([sp[1] for sp in species], dtype=np.float64)
+    pd = ctypes.POINTER(ctypes.c_double)
+    _check(ctx, load().fx_set_species(ctx, len(species), g.ctypes.data_as(pd) if len(g) else None,
+                                      a.ctypes.data_as(pd) if len(a) else None))
+
+
 def fx_set_option(ctx, key: str, value: float):
     _check(ctx, load().fx_set_option(ctx, key.encode(), float(value)))
 
@@ -187,11 +199,13 @@ def fx_step(ctx, bs, cfl: float, dt_ptr: int, stream=None):
     _check(ctx, load().fx_step(ctx, bs, float(cfl), ctypes.c_void_p(dt_ptr), _stream_ptr(stream)))
 
 
-def fx_conserved_totals(ctx, bs, stream=None) -> np.ndarray:
-    out = np.zeros(5)
+def fx_conserved_totals(ctx, bs, stream=None, nvar: int = 5) -> np.ndarray:
+    """Totals of the first ``nvar`` variables (room for every variable the
+    library may write is always provided)."""
+    out = np.zeros(FX_MAXVAR)
     _check(ctx, load().fx_conserved_totals(ctx, bs, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                            _stream_ptr(stream)))
-    return out
+    return out[:nvar]
 
 
 def fx_status(ctx, bs) -> int:
@@ -210,7 +224,7 @@ def fx_run_host(ctx, bs, host_in: np.ndarray, host_out: np.ndarray, nsteps: int,
 
 def fx_run_host_interior(ctx, bs, host_in: np.ndarray, host_out: np.ndarray, nsteps: int,
                          cfl: float, stream=None, want_time: bool = False):
-    """``host_in``/``host_out``: packed interior cells ``[nb, 5, nz, n, n]``."""
+    """``host_in``/``host_out``: packed interior cells ``[nb, nvar, nz, n, n]``."""
     t = np.zeros(1)
     tp = t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if want_time else None
     _check(ctx, load().fx_run_host_interior(ctx, bs, ctypes.c_void_p(host_in.ctypes.data),
@@ -314,6 +328,8 @@ class BlockSet:
         self.dtype = torch.float64 if precision == FX_F64 else torch.float32
         self.own_ctx = ctx is None
         self.ctx = ctx if ctx is not None else fx_init(gamma, mesh.nxb, mesh.ng)
+        if getattr(mesh, "species", ()) or ctx is None:
+            fx_set_species(self.ctx, getattr(mesh, "species", ()))
         for k, v in (options or {}).items():
             fx_set_option(self.ctx, k, v)
         self.U = [torch.zeros(mesh.shape, dtype=self.dtype, device=device) for _ in range(2)]
@@ -371,7 +387,7 @@ class BlockSet:
 
     def interior_shape(self) -> tuple:
         m = self.mesh
-        return (m.nb, 5, m.nxb if m.ndim == 3 else 1, m.nxb, m.nxb)
+        return (m.nb, m.nvar, m.nxb if m.ndim == 3 else 1, m.nxb, m.nxb)
 
     def run_host_interior(self, host_in: np.ndarray, host_out: np.ndarray, nsteps: int = 1,
                           cfl: float = 0.8, stream=None, want_time: bool = False):
@@ -425,7 +441,7 @@ class BlockSet:
         return changed
 
     def totals(self, stream=None) -> np.ndarray:
-        return fx_conserved_totals(self.ctx, self.bs, stream)
+        return fx_conserved_totals(self.ctx, self.bs, stream, self.mesh.nvar)
 
     def status(self) -> int:
         return fx_status(self.ctx, self.bs)

@@ -124,7 +124,7 @@ def request_problem(req: Request):
 
 def state_bytes(mesh, precision: int) -> int:
     el = 8 if precision == fx.FX_F64 else 4
-    return 2 * mesh.nb * 5 * mesh.PZ * mesh.P * mesh.P * el
+    return 2 * mesh.nb * mesh.nvar * mesh.PZ * mesh.P * mesh.P * el
 
 
 def prepare(reqs):
