@@ -1350,13 +1350,15 @@ int fx_batch_tune(fx_batch *b, void *stream, int *report) {
               gi = (int)g;
             }
           if (!G) continue;
-          // time on a bounded sample: a few waves of the persistent grid, in
-          // work per item (the 8x8 variant has four times the items)
+          // time on a bounded sample: a dozen waves of the persistent grid,
+          // in work per item (the 8x8 variant has four times the items); the
+          // fastest of four launches after a warm-up one, so that a single
+          // disturbed launch cannot decide the choice
           const int per_wave = ctas * b->nsm;
-          int nsample = std::min(G->r.n, 6 * per_wave * (tile == 8 ? 4 : 1));
+          int nsample = std::min(G->r.n, 12 * per_wave * (tile == 8 ? 4 : 1));
           nsample = std::max(nsample, std::min(G->r.n, per_wave));
-          float tot = 0.f;
-          for (int rep = 0; rep < 3; ++rep) {
+          float best_ms = 1e30f;
+          for (int rep = 0; rep < 5; ++rep) {
             cudaMemsetAsync(b->d_ctr + gi, 0, sizeof(unsigned int), st);
             cudaEventRecord(e0, st);
             fx::launch_hydro_batch(nd, tile, pr, b->d_req, b->d_items + G->r.off, nsample,
@@ -1365,10 +1367,10 @@ int fx_batch_tune(fx_batch *b, void *stream, int *report) {
             cudaEventSynchronize(e1);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) tot += ms;   // first launch warms up
+            if (rep > 0 && ms < best_ms) best_ms = ms;   // first launch warms up
           }
           // normalise to the whole group: time per item times items
-          const float est = tot / 2.f * (float)G->r.n / (float)nsample;
+          const float est = best_ms * (float)G->r.n / (float)nsample;
           if (report && nrep < 64) {
             report[3 * nrep] = tile;
             report[3 * nrep + 1] = ctas;

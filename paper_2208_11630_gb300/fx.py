@@ -355,9 +355,14 @@ class BlockSet:
     def current(self):
         return self.U[fx_blocks_current(self.bs)]
 
-    def set_primitive(self, W: np.ndarray, stream=None):
+    def set_primitive(self, W, stream=None):
+        """Primitive state ``W`` [nb, nvar, PZ, P, P] (numpy array, or a torch
+        tensor -- page-locked host memory is copied asynchronously)."""
         import torch
-        Wd = torch.as_tensor(np.ascontiguousarray(W, dtype=np.float64), device=self.U[0].device)
+        if isinstance(W, torch.Tensor):
+            Wd = W.to(device=self.U[0].device, dtype=torch.float64, non_blocking=True)
+        else:
+            Wd = torch.as_tensor(np.ascontiguousarray(W, dtype=np.float64), device=self.U[0].device)
         fx_prim_to_cons(self.ctx, self.bs, Wd.data_ptr(), stream)
         torch.cuda.current_stream().synchronize()
 

@@ -127,10 +127,19 @@ def state_bytes(mesh, precision: int) -> int:
     return 2 * mesh.nb * mesh.nvar * mesh.PZ * mesh.P * mesh.P * el
 
 
-def prepare(reqs):
+def prepare(reqs, pinned: bool = True):
     """Build every request's mesh and initial state on the host (the client's
-    side of the protocol), before the clock starts."""
-    return {r.rid: request_problem(r) for r in reqs}
+    side of the protocol), before the clock starts.  With ``pinned`` the
+    states are held in page-locked host memory, so that admitting a request
+    is an asynchronous copy rather than a staged one."""
+    out = {}
+    for r in reqs:
+        mesh, W = request_problem(r)
+        if pinned:
+            import torch
+            W = torch.from_numpy(np.ascontiguousarray(W, dtype=np.float64)).pin_memory()
+        out[r.rid] = (mesh, W)
+    return out
 
 
 def _percentiles(reqs):
@@ -198,6 +207,8 @@ def serve(reqs, problems, budget_bytes: float = 120e9, max_slots: int = 256, cfl
                 used -= need
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        choices = {f"{nd}d_{'f64' if pr == 0 else 'f32bulk'}": batch.choice(nd, pr)
+                   for nd in (2, 3) for pr in (0, 1)}
     finally:
         batch.close()
         fx.fx_finalize(ctx)
@@ -206,7 +217,7 @@ def serve(reqs, problems, budget_bytes: float = 120e9, max_slots: int = 256, cfl
     return {"requests": len(reqs), "wall_s": wall, "batched_steps": steps,
             "zone_updates_per_s": zones / wall, "requests_per_s": len(reqs) / wall,
             "p50_s": p50, "p99_s": p99, "max_s": pmax, "max_used_bytes": max_used,
-            "max_concurrent": max_active,
+            "max_concurrent": max_active, "launch_choices": choices,
             "failed": int(sum(1 for r in reqs if r.status != 0))}
 
 
