@@ -8,6 +8,8 @@
 
 #include "fx_internal.h"
 
+#include <type_traits>
+
 namespace fx {
 
 // gamma and gamma - 1 of a cell in precision R from its mass fractions
@@ -28,25 +30,63 @@ __device__ __forceinline__ void mix_gamma(const DevMesh &m, const R *X, int ns, 
   gm1 = g - R(1);
 }
 
+// Per-block constants of cell_signal in precision R, formed once outside
+// the cell loops: the single gas's gamma and gamma - 1, and 1/dx per axis
+// (FP32: converted once; FP64: see the specialisation below).
+template <typename R>
+struct SignalConsts {
+  R g, gm1, idx[3];
+  __device__ __forceinline__ SignalConsts(const DevMesh &m, int lev)
+      : g(R(m.gamma)), gm1(R(m.gamma - 1.0)),
+        idx{R(m.idx[lev][0]), R(m.idx[lev][1]), R(m.idx[lev][2])} {}
+};
+
+// FP64: the constants are read from the mesh where they are used (no
+// conversion to make, no registers held across the cell loops).
+template <>
+struct SignalConsts<double> {
+  int lev;
+  __device__ __forceinline__ SignalConsts(const DevMesh &, int l) : lev(l) {}
+};
+
 // CFL signal speed of one cell from its conserved variables u[0..5+ns) in
 // precision R: sum over directions (form 0) or maximum (form 1) of
 // (|u_d| + c) / dx_d, c = sqrt(gamma p / rho).  The fused epilogue of the
 // update, the flux correction and the standalone reduction all use it, so
 // that they agree bit for bit.
-template <typename R>
-__device__ __forceinline__ R cell_signal(const DevMesh &m, const R *u, int ns, int lev,
-                                         int form) {
+//   NDIM > 0: the dimension is known at compile time (the direction loop unrolls).
+template <typename R, int NDIM = 0>
+__device__ __forceinline__ R cell_signal(const DevMesh &m, const R *u, int ns,
+                                         const SignalConsts<R> &k0, int form) {
   const R ir = R(1) / u[0];
-  R X[FX_MAXSPEC];
-  for (int k = 0; k < ns; ++k) X[k] = u[5 + k] * ir;
   R g, gm1;
-  mix_gamma<R>(m, X, ns, g, gm1);
+  if constexpr (std::is_same<R, double>::value) {
+    g = m.gamma;
+    gm1 = m.gamma - 1.0;
+  } else {
+    g = k0.g;
+    gm1 = k0.gm1;
+  }
+  if (ns > 0) {
+    R X[FX_MAXSPEC];
+    for (int k = 0; k < ns; ++k) X[k] = u[5 + k] * ir;
+    mix_gamma<R>(m, X, ns, g, gm1);
+  }
   const R pr = gm1 * (u[4] - R(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * ir);
   const R cs = sqrt(g * pr * ir);
   R sg = R(0);
-  for (int d = 0; d < m.ndim; ++d) {
-    const R sd = (fabs(u[1 + d] * ir) + cs) * R(m.idx[lev][d]);
+  auto term = [&](int d) {
+    R idx_d;
+    if constexpr (std::is_same<R, double>::value) idx_d = m.idx[k0.lev][d];
+    else idx_d = k0.idx[d];
+    const R sd = (fabs(u[1 + d] * ir) + cs) * idx_d;
     sg = form == 0 ? sg + sd : fmax(sg, sd);
+  };
+  if constexpr (NDIM > 0) {
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) term(d);
+  } else {
+    for (int d = 0; d < m.ndim; ++d) term(d);
   }
   return sg;
 }

@@ -270,7 +270,8 @@ __device__ __forceinline__ void reflux_cells(const DevMesh &m, S *__restrict__ U
         atomicOr(status, 1);
       if (smax) {
         // CFL signal speed of the corrected cell, in the state's precision
-        const S sg = cell_signal<S>(m, us, m.nspec, lev, form);
+        const SignalConsts<S> k0(m, lev);
+        const S sg = cell_signal<S>(m, us, m.nspec, k0, form);
         atomicMax(smax, (unsigned long long)__double_as_longlong(double(sg)));
       }
     }

@@ -464,6 +464,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
   // correction will still change (on a face in rmask) are left to it.
   const unsigned fmask = rmask ? rmask[b] : 0u;
   R smax_t = R(0);
+  const SignalConsts<R> sconst(m, lev);
   auto signal = [&](const R (&u)[NF], int ci, int cj, int ck) {
     if (fmask) {
       const int cc[3] = {ci, cj, ck};
@@ -472,7 +473,10 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
         if (((fmask >> (2 * d + 1)) & 1u) && cc[d] == n - 1) return;
       }
     }
-    const R sg = cell_signal<R>(m, u, NS, lev, cfl_form);
+    // FP32: the direction loop unrolled; FP64 (at its register limit) keeps
+    // it rolled, which measured faster there
+    constexpr int kSigDim = std::is_same<R, float>::value ? NDIM : 0;
+    const R sg = cell_signal<R, kSigDim>(m, u, NS, sconst, cfl_form);
     if (!(sg <= smax_t)) smax_t = sg;   // keeps a NaN
   };
 

@@ -34,7 +34,8 @@ __global__ void k_dt(DevMesh m, const S *__restrict__ U, const int *__restrict__
     const long long vs = m.vstride;
     C uc[FX_MAXVAR];
     for (int v = 0; v < m.nvar; ++v) uc[v] = u[v * vs];
-    const C s = cell_signal<C>(m, uc, m.nspec, m.level[b], form);
+    const SignalConsts<C> k0(m, m.level[b]);
+    const C s = cell_signal<C>(m, uc, m.nspec, k0, form);
     if (!(s <= smax)) smax = s;   // keeps a NaN
   }
   // warp and CTA maximum on the bit patterns (non-negative doubles and NaN
