@@ -52,6 +52,9 @@ struct fx_blocks {
   int leaves_off = 0, nleaves = 0;
   std::vector<int> par_off, par_cnt;        // parents per level
   std::vector<int> pro_off, pro_cnt;        // leaves with prolongation slots per level
+  int2 *d_pslots = nullptr;                 // (leaf, slot) items covered by a coarser leaf
+  std::vector<int> pslot_off, pslot_cnt;    // per level
+  std::vector<int2> h_pslots;
   int src_off = 0, nsrc = 0;                // coarse leaves that feed a prolongation
   double *d_regs = nullptr;
   int nreg = 0;
@@ -123,6 +126,7 @@ void free_blocks(fx_blocks *bs) {
   cudaFree(bs->d_regidx); cudaFree(bs->d_slots); cudaFree(bs->d_lists);
   cudaFree(bs->d_regs); cudaFree(bs->d_refl); cudaFree(bs->d_scratch);
   cudaFree(bs->d_status); cudaFree(bs->d_dt); cudaFree(bs->d_totals); cudaFree(bs->d_rmask);
+  cudaFree(bs->d_pslots);
   if (bs->cpy) cudaStreamSynchronize(bs->cpy);
   for (cudaStream_t a : bs->aux)
     if (a) { cudaStreamSynchronize(a); cudaStreamDestroy(a); }
@@ -318,6 +322,7 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
   // ---- guard slots of every leaf
   std::vector<int2> slots(27 * nb, make_int2(fx::SLOT_NONE, -1));
   std::vector<std::vector<int>> pro_by_level(lmax + 1);
+  std::vector<std::vector<int2>> pslots_by_level(lmax + 1);
   for (int b = 0; b < nb; ++b) {
     if (!bs->leaf[b]) continue;
     const int l = level[b];
@@ -353,6 +358,7 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
                                            "leaf (mesh not 2:1 balanced)");
             sl = make_int2(fx::SLOT_PROLONG, c);
             has_pro = true;
+            pslots_by_level[l].push_back(make_int2(b, (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1)));
           }
           slots[27 * b + (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1)] = sl;
         }
@@ -454,6 +460,15 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
   if ((rc = upload(bs, &bs->d_slots, slots))) return bail(rc, ctx->err);
   if ((rc = upload(bs, &bs->d_lists, lists))) return bail(rc, ctx->err);
   bs->h_lists = lists;
+  bs->pslot_off.assign(lmax + 1, 0);
+  bs->pslot_cnt.assign(lmax + 1, 0);
+  bs->h_pslots.clear();
+  for (int l = 0; l <= lmax; ++l) {
+    bs->pslot_off[l] = (int)bs->h_pslots.size();
+    bs->h_pslots.insert(bs->h_pslots.end(), pslots_by_level[l].begin(), pslots_by_level[l].end());
+    bs->pslot_cnt[l] = (int)bs->h_pslots.size() - bs->pslot_off[l];
+  }
+  if ((rc = upload(bs, &bs->d_pslots, bs->h_pslots))) return bail(rc, ctx->err);
   bs->h_refl = refl;
   if ((rc = upload(bs, &bs->d_refl, refl))) return bail(rc, ctx->err);
   if (bs->nrefl > 0 && (rc = upload(bs, &bs->d_rmask, rmask))) return bail(rc, ctx->err);
@@ -535,8 +550,8 @@ int fx_guardcell_fill(fx_ctx *ctx, fx_blocks *bs, void *stream) {
                                 bs->ng, s),
           "guard copy launch");
   for (int l = 1; l <= bs->lmax; ++l)
-    FX_CUDA(fx::launch_guard_prolong(bs->dm, U, bs->prec, bs->d_lists + bs->pro_off[l],
-                                     bs->pro_cnt[l], bs->ng, 0, s),
+    FX_CUDA(fx::launch_guard_prolong_slots(bs->dm, U, bs->prec, bs->d_pslots + bs->pslot_off[l],
+                                           bs->pslot_cnt[l], bs->ng, 0, s),
             "guard prolong launch");
   return FX_OK;
 }
@@ -662,8 +677,9 @@ static int fill_for_fused_advance(fx_ctx *ctx, fx_blocks *bs, cudaStream_t s, vo
                                 fx::kHydroGuardDepth, s),
           "guard copy launch");
   for (int l = 1; l <= bs->lmax; ++l)
-    FX_CUDA(fx::launch_guard_prolong(bs->dm, U, bs->prec, bs->d_lists + bs->pro_off[l],
-                                     bs->pro_cnt[l], fx::kHydroGuardDepth, 1, s),
+    FX_CUDA(fx::launch_guard_prolong_slots(bs->dm, U, bs->prec,
+                                           bs->d_pslots + bs->pslot_off[l], bs->pslot_cnt[l],
+                                           fx::kHydroGuardDepth, 1, s),
             "guard prolong launch");
   (void)ctx;
   return FX_OK;
@@ -1027,8 +1043,10 @@ int build_lists(fx_batch *b, const Choice (&ch)[2][2]) {
     for (int l = 0; l <= bs->lmax; ++l) {
       for (int q = 0; q < bs->par_cnt[l]; ++q)
         for (int c = 0; c < chunks; ++c) rst[pr][l].push_back(make_int4(r, L[bs->par_off[l] + q], c, 0));
-      for (int q = 0; q < bs->pro_cnt[l]; ++q)
-        for (int k = 0; k < bs->PZ; ++k) pro[pr][l].push_back(make_int4(r, L[bs->pro_off[l] + q], k, 0));
+      for (int q = 0; q < bs->pslot_cnt[l]; ++q) {
+        const int2 it = bs->h_pslots[bs->pslot_off[l] + q];
+        pro[pr][l].push_back(make_int4(r, it.x, it.y, 0));
+      }
     }
     for (int q = 0; q < bs->nsrc; ++q)
       for (int k = 0; k < bs->PZ; ++k) cpy[pr].push_back(make_int4(r, L[bs->src_off + q], k, 0));

@@ -89,6 +89,11 @@ cudaError_t launch_guard_copy(const DevMesh &m, void *U, int prec, const int *le
                               int depth, cudaStream_t s);
 cudaError_t launch_guard_prolong(const DevMesh &m, void *U, int prec, const int *leaves, int n,
                                  int depth, int state_precision_math, cudaStream_t s);
+// The same over (leaf, slot) items of slots covered by a coarser leaf: the
+// work is proportional to the prolonged cells.
+cudaError_t launch_guard_prolong_slots(const DevMesh &m, void *U, int prec, const int2 *items,
+                                       int n, int depth, int state_precision_math,
+                                       cudaStream_t s);
 // Guard depth the fused update reads (radius-2 stencil).
 constexpr int kHydroGuardDepth = 2;
 // Time-integration stage of one update launch (defaults: MUSCL-Hancock).

@@ -203,6 +203,68 @@ __device__ __forceinline__ void guard_prolong_plane(const DevMesh &m, S *__restr
   }
 }
 
+// Guard cell (i, j, k) (padded indices) of leaf b covered by coarse leaf cb:
+// U_c + sum_d s_d MC(U_c - U_{c-e_d}, U_{c+e_d} - U_c) per variable, s_d =
+// -1/4 for the lower fine half of the coarse cell along d and +1/4 for the
+// upper half, summed x, y, z, in precision C; mirrored (and the wall-normal
+// momentum negated) beyond a reflecting wall.
+template <typename S, typename C>
+__device__ __forceinline__ void prolong_guard_cell(const DevMesh &m, S *__restrict__ U, int b,
+                                                   int cb, int i, int j, int k) {
+  const int P = m.P, ng = m.ng, lev = m.level[b];
+  const long long sP = P, sPP = (long long)P * P;
+  int g[3];
+  bool mir[3] = {false, false, false};
+  g[0] = apply_bc(m.origin[3 * b] + i - ng, m.ncell[lev][0], m.bc[0][0], m.bc[0][1], mir[0]);
+  g[1] = apply_bc(m.origin[3 * b + 1] + j - ng, m.ncell[lev][1], m.bc[1][0], m.bc[1][1], mir[1]);
+  g[2] = m.ndim == 3 ? apply_bc(m.origin[3 * b + 2] + k - ng, m.ncell[lev][2], m.bc[2][0],
+                                m.bc[2][1], mir[2])
+                     : 0;
+  const int cx = (g[0] >> 1) - m.origin[3 * cb] + ng;
+  const int cy = (g[1] >> 1) - m.origin[3 * cb + 1] + ng;
+  const int cz = m.ndim == 3 ? (g[2] >> 1) - m.origin[3 * cb + 2] + ng : 0;
+  const S *Cc = U + (long long)cb * m.bstride + (cz * sPP + cy * sP + cx);
+  S *Ud = U + (long long)b * m.bstride + ((long long)k * P + j) * P + i;
+  const long long step[3] = {1, sP, sPP};
+  for (int v = 0; v < m.nvar; ++v) {
+    const S *cv = Cc + v * m.vstride;
+    const C uc = C(*cv);
+    C val = uc;
+    for (int d = 0; d < m.ndim; ++d) {
+      const C um = C(cv[-step[d]]), up = C(cv[step[d]]);
+      const C sig = mc_lim_c<C>(uc - um, up - uc);
+      const C off = (g[d] & 1) ? C(0.25) : C(-0.25);
+      val = val + off * sig;
+    }
+    if (v >= 1 && v <= 3 && mir[v - 1]) val = -val;
+    Ud[v * m.vstride] = S(val);
+  }
+}
+
+// Leaf b, neighbour slot `slot` ((sx+1) + 3 (sy+1) + 9 (sz+1)) covered by a
+// coarser leaf: every guard cell of that slot within `depth` of the
+// interior, cells [first, ...) strided by `stride`.  The work is the slot's
+// own cells (depth x n x n for a face slot, depth^2 x n for an edge, depth^3
+// for a corner), not the whole padded block.
+template <typename S, typename C = double>
+__device__ __forceinline__ void guard_prolong_slot(const DevMesh &m, S *__restrict__ U, int b,
+                                                   int slot, int depth, int first, int stride) {
+  const int n = m.nxb, ng = m.ng;
+  const int2 sl = m.slots[b * 27 + slot];
+  const int s3[3] = {slot % 3, (slot / 3) % 3, slot / 9};
+  int lo[3], w[3];
+  for (int d = 0; d < 3; ++d) {
+    if (d >= m.ndim) { lo[d] = 0; w[d] = 1; continue; }
+    lo[d] = s3[d] == 0 ? ng - depth : (s3[d] == 1 ? ng : ng + n);
+    w[d] = s3[d] == 1 ? n : depth;
+  }
+  const int ncell = w[0] * w[1] * w[2];
+  for (int c = first; c < ncell; c += stride) {
+    const int i = lo[0] + c % w[0], j = lo[1] + (c / w[0]) % w[1], k = lo[2] + c / (w[0] * w[1]);
+    prolong_guard_cell<S, C>(m, U, b, sl.y, i, j, k);
+  }
+}
+
 // Coarse leaf it.block, cells [first, ncell) strided by `stride`: replace the
 // coarse face flux F_c by the pairwise mean F_bar of the fine face fluxes,
 //   upper face: U_c += dt/dx (F_c - F_bar); lower face: U_c -= dt/dx (F_c - F_bar),

@@ -8,7 +8,8 @@
 //   begin     dt = cfl / (signal-speed maximum of the current state)
 //   restrict  parents from children, finest level first      (current buffer)
 //   copy      same-level guards of coarse leaves feeding a prolongation
-//   prolong   guards of leaves next to a coarser leaf, level by level
+//   prolong   guards of leaves next to a coarser leaf, level by level, one
+//             CTA per (leaf, slot covered by the coarser leaf)
 //   hydro     fused MUSCL-Hancock/HLLC update (k_hydro_batch, persistent)
 //   reflux    fine-to-coarse flux correction                  (new buffer)
 //   restrict  parents of the new state
@@ -64,7 +65,8 @@ __global__ void k_batch_prolong(const BatchReq *__restrict__ reqs, const int4 *_
   const int4 w = items[blockIdx.x];
   const BatchReq &q = reqs[w.x];
   if (q.steps_left <= 0) return;
-  ops::guard_prolong_plane<S, S>(q.m, static_cast<S *>(q.U[q.cur]), w.y, w.z, kHydroGuardDepth);
+  ops::guard_prolong_slot<S, S>(q.m, static_cast<S *>(q.U[q.cur]), w.y, w.z, kHydroGuardDepth,
+                                threadIdx.x, blockDim.x);
 }
 
 // items: (request, reflux item, chunk, chunks)
@@ -113,8 +115,8 @@ cudaError_t launch_batch_phase(int phase, int prec, const BatchReq *reqs, const 
       else k_batch_copy<double><<<n, 256, 0, s>>>(reqs, items);
       break;
     case BATCH_PROLONG:
-      if (f) k_batch_prolong<float><<<n, 256, 0, s>>>(reqs, items);
-      else k_batch_prolong<double><<<n, 256, 0, s>>>(reqs, items);
+      if (f) k_batch_prolong<float><<<n, 128, 0, s>>>(reqs, items);
+      else k_batch_prolong<double><<<n, 128, 0, s>>>(reqs, items);
       break;
     case BATCH_REFLUX:
       if (f) k_batch_reflux<float><<<n, 256, 0, s>>>(reqs, items);

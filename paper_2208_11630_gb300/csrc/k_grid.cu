@@ -93,6 +93,15 @@ __global__ void k_pack(DevMesh m, S *__restrict__ U, S *__restrict__ Pk, int b0,
   }
 }
 
+// One CTA per (leaf, slot covered by a coarser leaf): the prolonged guards
+// of that slot within `depth`, in precision C.
+template <typename S, typename C>
+__global__ void k_guard_prolong_slots(DevMesh m, S *__restrict__ U, const int2 *__restrict__ items,
+                                      int depth) {
+  const int2 it = items[blockIdx.x];
+  ops::guard_prolong_slot<S, C>(m, U, it.x, it.y, depth, threadIdx.x, blockDim.x);
+}
+
 template <typename S>
 cudaError_t prim_to_cons_t(const DevMesh &m, const double *W, void *U, cudaStream_t s) {
   long long total = (long long)m.nb * m.vstride;
@@ -144,6 +153,20 @@ cudaError_t launch_guard_copy(const DevMesh &m, void *U, int prec, const int *le
   dim3 grid(n, m.PZ);
   if (prec == 0) k_guard_copy<double><<<grid, 256, 0, s>>>(m, static_cast<double *>(U), leaves, depth);
   else k_guard_copy<float><<<grid, 256, 0, s>>>(m, static_cast<float *>(U), leaves, depth);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_guard_prolong_slots(const DevMesh &m, void *U, int prec, const int2 *items,
+                                       int n, int depth, int state_precision_math,
+                                       cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (prec == 0)
+    k_guard_prolong_slots<double, double><<<n, 128, 0, s>>>(m, static_cast<double *>(U), items, depth);
+  else if (state_precision_math)
+    k_guard_prolong_slots<float, float><<<n, 128, 0, s>>>(m, static_cast<float *>(U), items, depth);
+  else
+    k_guard_prolong_slots<float, double><<<n, 128, 0, s>>>(m, static_cast<float *>(U), items, depth);
   count_launch();
   return cudaGetLastError();
 }
