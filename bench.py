@@ -38,6 +38,11 @@ HBM_BYTES_PER_ZONE = {"f64": 80.0, "f32bulk": 40.0}
 ALGO_FLOPS_PER_ZONE = 603.0
 # FP64 peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz.
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
+# DRAM bytes (read + written) per zone of the update kernel, from one ncu
+# capture of the 128^3 KH case (dram__bytes_read.sum + dram__bytes_write.sum
+# over 2,097,152 zones); the full launch's traffic scales with its zones.
+# Valid for the kernel build those counters were taken on.
+TRAFFIC_BYTES_PER_ZONE = {"f64": 102.3, "f32bulk": 67.6}
 
 
 def load_peaks():
@@ -441,13 +446,18 @@ def run_ours(args):
     if args.precision == "f64":
         roof = {"bound": "alu", "kernel": kname,
                 "achieved": achieved_flops / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
-                "unit": "TFLOP/s", "frac": achieved_flops / FP64_PEAK_FLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved_flops / FP64_PEAK_FLOPS,
+                "traffic": TRAFFIC_BYTES_PER_ZONE["f64"] * zones_per_step
+                if args.workload == "kh3d" else None,
                 "peak_kind": "derived FP64 DFMA rate (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "traffic_note": "bytes per launch: ncu DRAM read+write of the 128^3 case scaled by zones",
                 "algorithmic_flops_per_zone": ALGO_FLOPS_PER_ZONE}
     else:
         gbs = bpz * zones_per_step / hydro_s / 1e9
         roof = {"bound": "hbm", "kernel": kname, "achieved": gbs,
-                "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak, "traffic": None,
+                "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "traffic": TRAFFIC_BYTES_PER_ZONE["f32bulk"] * zones_per_step
+                if args.workload == "kh3d" else None,
                 "peak_kind": peak_kind, "algorithmic_bytes_per_zone": bpz}
     roof.update({"hydro_ms": hydro_s * 1e3,
                  "hbm_frac_of_step": (bpz * value / ws) / (hbm_peak * 1e9),
