@@ -425,7 +425,7 @@ def run_ours(args):
     if not args.no_e2e:
         host_in = torch.from_numpy(np.ascontiguousarray(mesh.interior(U0))).to(bs.dtype).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
-        e2e_steps = max(3, min(args.steps, 10))
+        e2e_steps = max(10, min(args.steps, 30))
         bs.run_host_interior(host_in.numpy(), host_out.numpy(), 1, cfl, stream=sptr)
         if ws > 1:
             dist.barrier()

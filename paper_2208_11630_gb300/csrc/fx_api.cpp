@@ -85,7 +85,7 @@ struct fx_blocks {
   fx::RegridPlan plan;
   std::vector<double> plan_err;             // indicator per block (-1: parent)
   cudaStream_t aux[2] = {nullptr, nullptr}, cpy = nullptr;
-  cudaEvent_t ev_ready = nullptr, ev_done = nullptr, ev_chunk[8] = {};
+  cudaEvent_t ev_ready = nullptr, ev_done = nullptr, ev_chunk[8] = {}, ev_up[8] = {};
 };
 
 namespace fx {
@@ -134,6 +134,8 @@ void free_blocks(fx_blocks *bs) {
   if (bs->ev_ready) cudaEventDestroy(bs->ev_ready);
   if (bs->ev_done) cudaEventDestroy(bs->ev_done);
   for (cudaEvent_t e : bs->ev_chunk)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : bs->ev_up)
     if (e) cudaEventDestroy(e);
   cudaFree(bs->d_pack);
   cudaFree(bs->d_U3);
@@ -779,6 +781,8 @@ int ensure_pipeline(fx_blocks *bs) {
     FX_CUDA(cudaEventCreateWithFlags(&bs->ev_done, cudaEventDisableTiming), "event create");
   for (cudaEvent_t &e : bs->ev_chunk)
     if (!e) FX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event create");
+  for (cudaEvent_t &e : bs->ev_up)
+    if (!e) FX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event create");
   if (cudaMalloc(&bs->d_pack, interior_block_bytes(bs) * bs->nb) != cudaSuccess) {
     bs->d_pack = nullptr;
     cudaGetLastError();
@@ -825,6 +829,38 @@ int advance_and_download(fx_ctx *ctx, fx_blocks *bs, cudaStream_t s, void *W_out
   return FX_OK;
 }
 
+// Upload of a single-level block set's packed interiors in chunks of
+// consecutive blocks on the copy stream; each chunk is scattered into the
+// padded layout and its CFL signal maximum reduced on `s` as soon as it
+// lands, so the dt reduction overlaps the rest of the upload.  Leaves
+// dt = cfl / max in bs->d_dt.
+int upload_and_reduce(fx_ctx *ctx, fx_blocks *bs, cudaStream_t s, const void *W_in, double cfl) {
+  const size_t pb = interior_block_bytes(bs);
+  const int K = bs->nb < kPipeChunks ? bs->nb : kPipeChunks;
+  unsigned long long *smax = bs->d_scratch + 2;
+  FX_CUDA(cudaMemsetAsync(smax, 0, sizeof(unsigned long long), s), "signal max reset");
+  FX_CUDA(cudaEventRecord(bs->ev_ready, s), "event record");
+  FX_CUDA(cudaStreamWaitEvent(bs->cpy, bs->ev_ready, 0), "stream wait");
+  for (int c = 0; c < K; ++c) {
+    const int b0 = (int)((long long)bs->nb * c / K), b1 = (int)((long long)bs->nb * (c + 1) / K);
+    char *pk = static_cast<char *>(bs->d_pack) + pb * b0;
+    FX_CUDA(cudaMemcpyAsync(pk, static_cast<const char *>(W_in) + pb * b0, pb * (b1 - b0),
+                            cudaMemcpyHostToDevice, bs->cpy),
+            "state upload");
+    FX_CUDA(cudaEventRecord(bs->ev_up[c], bs->cpy), "event record");
+    FX_CUDA(cudaStreamWaitEvent(s, bs->ev_up[c], 0), "stream wait");
+    FX_CUDA(fx::launch_pack(bs->dm, bs->U[bs->cur], bs->prec, pk, b0, b1 - b0, 0, s),
+            "unpack launch");
+    FX_CUDA(fx::launch_signal_max(bs->dm, bs->U[bs->cur], bs->prec,
+                                  bs->d_lists + bs->leaves_off + b0, b1 - b0, ctx->cfl_form, smax,
+                                  bs->d_scratch, s, 1),
+            "signal max launch");
+  }
+  FX_CUDA(fx::launch_dt_finalize(smax, cfl, bs->d_dt, s), "dt finalize launch");
+  ++bs->epoch;
+  return FX_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -837,16 +873,33 @@ int fx_run_host_interior(fx_ctx *ctx, fx_blocks *bs, const void *W_in, void *W_o
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = interior_block_bytes(bs) * bs->nb;
-  FX_CUDA(cudaMemcpyAsync(bs->d_pack, W_in, bytes, cudaMemcpyHostToDevice, s), "state upload");
-  FX_CUDA(fx::launch_pack(bs->dm, bs->U[bs->cur], bs->prec, bs->d_pack, 0, bs->nb, 0, s),
-          "unpack launch");
-  ++bs->epoch;
   const bool single_level = bs->lmax == 0 && bs->nrefl == 0 && bs->nleaves == bs->nb &&
                             ctx->integrator == 0;
+  bool have_dt = false;
+  if (single_level && nsteps > 0) {
+    rc = upload_and_reduce(ctx, bs, s, W_in, cfl);   // dt of the uploaded state in d_dt
+    if (rc) return rc;
+    have_dt = true;
+  } else {
+    FX_CUDA(cudaMemcpyAsync(bs->d_pack, W_in, bytes, cudaMemcpyHostToDevice, s), "state upload");
+    FX_CUDA(fx::launch_pack(bs->dm, bs->U[bs->cur], bs->prec, bs->d_pack, 0, bs->nb, 0, s),
+            "unpack launch");
+    ++bs->epoch;
+  }
   bool downloaded = false;
   double t = 0.0;
   for (int i = 0; i < nsteps; ++i) {
-    if (i == nsteps - 1 && single_level) {
+    if (i == 0 && have_dt) {
+      rc = fx_guardcell_fill_amr(ctx, bs, stream);
+      if (!rc) {
+        if (i == nsteps - 1) {
+          rc = advance_and_download(ctx, bs, s, W_out);
+          downloaded = true;
+        } else {
+          rc = fx_hydro_advance(ctx, bs, bs->d_dt, stream);
+        }
+      }
+    } else if (i == nsteps - 1 && single_level) {
       rc = fx_compute_dt(ctx, bs, cfl, bs->d_dt, stream);
       if (!rc) rc = fx_guardcell_fill_amr(ctx, bs, stream);
       if (!rc) rc = advance_and_download(ctx, bs, s, W_out);

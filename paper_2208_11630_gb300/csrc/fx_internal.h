@@ -159,9 +159,10 @@ cudaError_t launch_batch_phase(int phase, int prec, const BatchReq *reqs, const 
                                cudaStream_t s);
 // Signal-speed maximum of a state (bit pattern) into *max_out, without
 // forming dt; scratch as for launch_dt.
+// accumulate: atomicMax into *max_out instead of storing (several ranges).
 cudaError_t launch_signal_max(const DevMesh &m, const void *U, int prec, const int *leaves, int n,
                               int form, unsigned long long *max_out, unsigned long long *scratch,
-                              cudaStream_t s);
+                              cudaStream_t s, int accumulate = 0);
 // Occupancy of the batched hydro kernel (CTAs per SM), setting its shared
 // memory attribute on first use.
 cudaError_t hydro_batch_fit(int ndim, int tile, int prec, int *fit);

@@ -16,7 +16,7 @@ template <typename S>
 __global__ void k_dt(DevMesh m, const S *__restrict__ U, const int *__restrict__ leaves, int nleaves,
                      double cfl, int form, double *__restrict__ dt_out,
                      unsigned long long *__restrict__ scratch,
-                     unsigned long long *__restrict__ max_out) {
+                     unsigned long long *__restrict__ max_out, int accumulate) {
   const int n = m.nxb, ng = m.ng, P = m.P, nd = m.ndim;
   const int nz = nd == 3 ? n : 1;
   const long long ncell = (long long)n * n * nz;
@@ -62,8 +62,12 @@ __global__ void k_dt(DevMesh m, const S *__restrict__ U, const int *__restrict__
       if (done == gridDim.x - 1) {
         __threadfence();
         const unsigned long long mb = atomicAdd(&scratch[0], 0ull);
-        if (max_out) *max_out = mb;
-        else *dt_out = cfl / __longlong_as_double(mb);
+        if (max_out) {
+          if (accumulate) atomicMax(max_out, mb);
+          else *max_out = mb;
+        } else {
+          *dt_out = cfl / __longlong_as_double(mb);
+        }
         scratch[0] = 0ull;
         scratch[1] = 0ull;
       }
@@ -127,27 +131,27 @@ cudaError_t launch_dt(const DevMesh &m, const void *U, int prec, const int *leav
   if (grid > 152 * 8) grid = 152 * 8;
   if (prec == 0)
     k_dt<double><<<(int)grid, 256, 0, s>>>(m, static_cast<const double *>(U), leaves, n, cfl, form,
-                                           dt_out, scratch, nullptr);
+                                           dt_out, scratch, nullptr, 0);
   else
     k_dt<float><<<(int)grid, 256, 0, s>>>(m, static_cast<const float *>(U), leaves, n, cfl, form,
-                                          dt_out, scratch, nullptr);
+                                          dt_out, scratch, nullptr, 0);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_signal_max(const DevMesh &m, const void *U, int prec, const int *leaves, int n,
                               int form, unsigned long long *max_out, unsigned long long *scratch,
-                              cudaStream_t s) {
+                              cudaStream_t s, int accumulate) {
   if (n <= 0) return cudaErrorInvalidValue;
   const long long total = (long long)n * m.nxb * m.nxb * (m.ndim == 3 ? m.nxb : 1);
   long long grid = (total + 255) / 256;
   if (grid > 152 * 8) grid = 152 * 8;
   if (prec == 0)
     k_dt<double><<<(int)grid, 256, 0, s>>>(m, static_cast<const double *>(U), leaves, n, 1.0, form,
-                                           nullptr, scratch, max_out);
+                                           nullptr, scratch, max_out, accumulate);
   else
     k_dt<float><<<(int)grid, 256, 0, s>>>(m, static_cast<const float *>(U), leaves, n, 1.0, form,
-                                          nullptr, scratch, max_out);
+                                          nullptr, scratch, max_out, accumulate);
   count_launch();
   return cudaGetLastError();
 }
