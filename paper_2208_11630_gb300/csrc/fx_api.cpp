@@ -51,7 +51,6 @@ struct fx_blocks {
   int *d_lists = nullptr;     // concatenated work lists
   int leaves_off = 0, nleaves = 0;
   std::vector<int> par_off, par_cnt;        // parents per level
-  std::vector<int> pro_off, pro_cnt;        // leaves with prolongation slots per level
   int2 *d_pslots = nullptr;                 // (leaf, slot) items covered by a coarser leaf
   std::vector<int> pslot_off, pslot_cnt;    // per level
   std::vector<int2> h_pslots;
@@ -323,12 +322,10 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
 
   // ---- guard slots of every leaf
   std::vector<int2> slots(27 * nb, make_int2(fx::SLOT_NONE, -1));
-  std::vector<std::vector<int>> pro_by_level(lmax + 1);
   std::vector<std::vector<int2>> pslots_by_level(lmax + 1);
   for (int b = 0; b < nb; ++b) {
     if (!bs->leaf[b]) continue;
     const int l = level[b];
-    bool has_pro = false;
     for (int sz = (ndim == 3 ? -1 : 0); sz <= (ndim == 3 ? 1 : 0); ++sz)
       for (int sy = -1; sy <= 1; ++sy)
         for (int sx = -1; sx <= 1; ++sx) {
@@ -359,12 +356,10 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
                                            " not covered by a same-level block or a coarser "
                                            "leaf (mesh not 2:1 balanced)");
             sl = make_int2(fx::SLOT_PROLONG, c);
-            has_pro = true;
             pslots_by_level[l].push_back(make_int2(b, (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1)));
           }
           slots[27 * b + (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1)] = sl;
         }
-    if (has_pro) pro_by_level[l].push_back(b);
   }
 
   // ---- flux correction: coarse leaf faces on a refined same-level block
@@ -421,7 +416,7 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
     for (int f = 0; f < 6; ++f)
       if (it.fine[f][0] >= 0) rmask[it.block] |= (unsigned char)(1u << f);
 
-  // ---- work lists: leaves | parents per level | prolong leaves per level
+  // ---- work lists: leaves | parents per level | coarse leaves feeding prolongation
   std::vector<int> lists;
   for (int b = 0; b < nb; ++b)
     if (bs->leaf[b]) lists.push_back(b);
@@ -429,18 +424,11 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
   bs->nleaves = (int)lists.size();
   bs->par_off.assign(lmax + 1, 0);
   bs->par_cnt.assign(lmax + 1, 0);
-  bs->pro_off.assign(lmax + 1, 0);
-  bs->pro_cnt.assign(lmax + 1, 0);
   for (int l = 0; l <= lmax; ++l) {
     bs->par_off[l] = (int)lists.size();
     for (int b = 0; b < nb; ++b)
       if (!bs->leaf[b] && level[b] == l) lists.push_back(b);
     bs->par_cnt[l] = (int)lists.size() - bs->par_off[l];
-  }
-  for (int l = 0; l <= lmax; ++l) {
-    bs->pro_off[l] = (int)lists.size();
-    for (int b : pro_by_level[l]) lists.push_back(b);
-    bs->pro_cnt[l] = (int)lists.size() - bs->pro_off[l];
   }
   {
     std::vector<char> is_src(nb, 0);

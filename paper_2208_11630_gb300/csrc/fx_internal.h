@@ -87,10 +87,8 @@ cudaError_t launch_pack(const DevMesh &m, void *U, int prec, void *packed, int b
 // state_precision_math is set (else FP64).
 cudaError_t launch_guard_copy(const DevMesh &m, void *U, int prec, const int *leaves, int n,
                               int depth, cudaStream_t s);
-cudaError_t launch_guard_prolong(const DevMesh &m, void *U, int prec, const int *leaves, int n,
-                                 int depth, int state_precision_math, cudaStream_t s);
-// The same over (leaf, slot) items of slots covered by a coarser leaf: the
-// work is proportional to the prolonged cells.
+// Prolonged guards of (leaf, slot) items -- slots covered by a coarser leaf
+// -- within `depth`; the work is proportional to the prolonged cells.
 cudaError_t launch_guard_prolong_slots(const DevMesh &m, void *U, int prec, const int2 *items,
                                        int n, int depth, int state_precision_math,
                                        cudaStream_t s);

@@ -147,62 +147,6 @@ __device__ __forceinline__ C mc_lim_c(C a, C b) {
   return a > C(0) ? s : -s;
 }
 
-// Leaf b, padded z-plane k, whole CTA: guard cells within `depth` of the
-// interior that are covered by a coarser leaf get
-// U_c + sum_d s_d MC(U_c - U_{c-e_d}, U_{c+e_d} - U_c), s_d = -1/4 for the
-// lower fine half of the coarse cell along d and +1/4 for the upper half,
-// summed x, y, z, in precision C.  The coarse leaf's own guards (depth 1)
-// must be filled.
-template <typename S, typename C = double>
-__device__ __forceinline__ void guard_prolong_plane(const DevMesh &m, S *__restrict__ U, int b,
-                                                    int k, int depth) {
-  __shared__ int2 sl[27];
-  __syncthreads();
-  if (threadIdx.x < 27) sl[threadIdx.x] = m.slots[b * 27 + threadIdx.x];
-  __syncthreads();
-  const int P = m.P, ng = m.ng, n = m.nxb, lev = m.level[b];
-  const int dz = m.ndim == 3 ? outside(k, ng, ng + n) : 0;
-  if (dz > depth) return;
-  const int sz = m.ndim == 3 ? slot_of(k, ng, ng + n) : 1;
-  const int ox = m.origin[3 * b], oy = m.origin[3 * b + 1], oz = m.origin[3 * b + 2];
-  S *Ub = U + (long long)b * m.bstride;
-  const long long sP = P, sPP = (long long)P * P;
-  for (int c = threadIdx.x; c < P * P; c += blockDim.x) {
-    const int i = c % P, j = c / P;
-    if (outside(i, ng, ng + n) > depth || outside(j, ng, ng + n) > depth) continue;
-    const int sx = slot_of(i, ng, ng + n), sy = slot_of(j, ng, ng + n);
-    if (sx == 1 && sy == 1 && sz == 1) continue;
-    const int2 s = sl[sx + 3 * sy + 9 * sz];
-    if (s.x != SLOT_PROLONG) continue;
-    int g[3];
-    bool mir[3] = {false, false, false};
-    g[0] = apply_bc(ox + i - ng, m.ncell[lev][0], m.bc[0][0], m.bc[0][1], mir[0]);
-    g[1] = apply_bc(oy + j - ng, m.ncell[lev][1], m.bc[1][0], m.bc[1][1], mir[1]);
-    g[2] = m.ndim == 3 ? apply_bc(oz + k - ng, m.ncell[lev][2], m.bc[2][0], m.bc[2][1], mir[2])
-                       : 0;
-    const int cb = s.y;
-    const int cx = (g[0] >> 1) - m.origin[3 * cb] + ng;
-    const int cy = (g[1] >> 1) - m.origin[3 * cb + 1] + ng;
-    const int cz = m.ndim == 3 ? (g[2] >> 1) - m.origin[3 * cb + 2] + ng : 0;
-    const S *Cc = U + (long long)cb * m.bstride + (cz * sPP + cy * sP + cx);
-    S *Ud = Ub + ((long long)k * P + j) * P + i;
-    const long long step[3] = {1, sP, sPP};
-    for (int v = 0; v < m.nvar; ++v) {
-      const S *cv = Cc + v * m.vstride;
-      const C uc = C(*cv);
-      C val = uc;
-      for (int d = 0; d < m.ndim; ++d) {
-        const C um = C(cv[-step[d]]), up = C(cv[step[d]]);
-        const C sig = mc_lim_c<C>(uc - um, up - uc);
-        const C off = (g[d] & 1) ? C(0.25) : C(-0.25);
-        val = val + off * sig;
-      }
-      if (v >= 1 && v <= 3 && mir[v - 1]) val = -val;
-      Ud[v * m.vstride] = S(val);
-    }
-  }
-}
-
 // Guard cell (i, j, k) (padded indices) of leaf b covered by coarse leaf cb:
 // U_c + sum_d s_d MC(U_c - U_{c-e_d}, U_{c+e_d} - U_c) per variable, s_d =
 // -1/4 for the lower fine half of the coarse cell along d and +1/4 for the

@@ -60,14 +60,6 @@ __global__ void k_guard_copy(DevMesh m, S *__restrict__ U, const int *__restrict
   ops::guard_copy_plane<S>(m, U, leaves[blockIdx.x], blockIdx.y, depth);
 }
 
-// One CTA per (leaf, padded z-plane): prolonged guards up to `depth`, in
-// precision C.
-template <typename S, typename C>
-__global__ void k_guard_prolong(DevMesh m, S *__restrict__ U, const int *__restrict__ leaves,
-                                int depth) {
-  ops::guard_prolong_plane<S, C>(m, U, leaves[blockIdx.x], blockIdx.y, depth);
-}
-
 // Interior cells of blocks [b0, b0 + nblk) between the padded block layout
 // and a packed array [block][var][z][y][x] of interior cells (nvar variables) (packed index
 // relative to block b0).  dir 0: packed -> padded; 1: padded -> packed.
@@ -167,20 +159,6 @@ cudaError_t launch_guard_prolong_slots(const DevMesh &m, void *U, int prec, cons
     k_guard_prolong_slots<float, float><<<n, 128, 0, s>>>(m, static_cast<float *>(U), items, depth);
   else
     k_guard_prolong_slots<float, double><<<n, 128, 0, s>>>(m, static_cast<float *>(U), items, depth);
-  count_launch();
-  return cudaGetLastError();
-}
-
-cudaError_t launch_guard_prolong(const DevMesh &m, void *U, int prec, const int *leaves, int n,
-                                 int depth, int state_precision_math, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  dim3 grid(n, m.PZ);
-  if (prec == 0)
-    k_guard_prolong<double, double><<<grid, 256, 0, s>>>(m, static_cast<double *>(U), leaves, depth);
-  else if (state_precision_math)
-    k_guard_prolong<float, float><<<grid, 256, 0, s>>>(m, static_cast<float *>(U), leaves, depth);
-  else
-    k_guard_prolong<float, double><<<grid, 256, 0, s>>>(m, static_cast<float *>(U), leaves, depth);
   count_launch();
   return cudaGetLastError();
 }
