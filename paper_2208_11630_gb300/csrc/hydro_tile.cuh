@@ -178,11 +178,11 @@ __device__ __forceinline__ void hllc(const R (&WL)[5 + NS], const R (&WR)[5 + NS
     const R dK = SK - uK;
     R inv;
     if constexpr (kF64) {
-      // S_K - S* = D / B with D = S_K B - A:  r = 1/(B D), S* = A D r,
+      // S_K - S* = Q / B with Q = S_K B - A:  r = 1/(B Q), S* = A Q r,
       // 1/(S_K - S*) = B B r
-      const R D = SK * B - A;
-      const R r = R(1) / (B * D);
-      Sst = A * D * r;
+      const R Q = SK * B - A;
+      const R r = R(1) / (B * Q);
+      Sst = A * Q * r;
       inv = B * B * r;
     } else {
       inv = div_r(R(1), SK - Sst);
