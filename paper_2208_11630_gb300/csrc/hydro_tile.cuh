@@ -328,6 +328,53 @@ __device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int 
   }
 }
 
+// Where the guard cells of slot q (= sx + 3 sy + 9 sz, with 1 = the block's
+// own range on that axis) of block b come from, as a map that is linear in the
+// padded cell coordinates (gx, gy, gz) of b: the cell's first variable sits at
+// element off + gx c.x + gy c.y + gz c.z of the state array, and bit d of c.w
+// says that the d velocity component is mirrored.  A same-level slot reads
+// the neighbour's interior (per axis a shift, the periodic wrap included); at
+// a physical boundary an outflow axis clamps to the edge cell (coefficient 0)
+// and a reflecting axis mirrors (coefficient -1, velocity negated).  Slots
+// covered by a coarser leaf, and the block's own cells, map to the block's
+// own padded array.
+__device__ __forceinline__ void guard_source(const DevMesh &m, int b, int q, long long &off,
+                                             int4 &c) {
+  const int2 sl = m.slots[b * 27 + q];
+  const int P = m.P, ng = m.ng, n = m.nxb, lev = m.level[b];
+  const bool copy = q != 13 && sl.x == SLOT_COPY;
+  const int src = copy ? sl.y : b;
+  int coef[3] = {1, 1, 1}, k[3] = {0, 0, 0};
+  unsigned flip = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (!copy || d >= m.ndim) continue;
+    const int sd = d == 0 ? q % 3 : (d == 1 ? (q / 3) % 3 : q / 9);
+    const int o = m.origin[3 * b + d], os = m.origin[3 * src + d], N = m.ncell[lev][d];
+    // padded index in the source = index in the level lattice - os + ng;
+    // the block's own cell gx sits at lattice index o + gx - ng
+    k[d] = o - os;
+    if (sd == 1) continue;
+    const bool lo = sd == 0;
+    if (lo ? o != 0 : o + n < N) continue;   // inside the domain
+    const int kind = m.bc[d][lo ? 0 : 1];
+    if (kind == FX_BC_PERIODIC) {
+      k[d] = lo ? o + N - os : o - N - os;
+    } else if (kind == FX_BC_REFLECT) {
+      // lattice index -1 - a (low side) or 2N - 1 - a (high side)
+      coef[d] = -1;
+      flip |= 1u << d;
+      k[d] = (lo ? -1 : 2 * N - 1) - o + 2 * ng - os;
+    } else {
+      // outflow: the edge cell, 0 or N - 1
+      coef[d] = 0;
+      k[d] = (lo ? 0 : N - 1) + ng - os;
+    }
+  }
+  off = (long long)src * m.bstride + ((long long)k[2] * P + k[1]) * P + k[0];
+  c = make_int4(coef[0], coef[1] * P, coef[2] * P * P, (int)flip);
+}
+
 // One T x T column tile of leaf block b, marched along z.  Called by the
 // per-block-set kernel (one CTA per tile) and by the batched persistent
 // kernel (each CTA loops over tiles of many block sets).
@@ -389,10 +436,10 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
   // load on the highest threads.
   constexpr int kLoadTail = (SM::W4 * SM::W4) % NT;
   constexpr int kFaceShift = NT - 4 * T;
-  __shared__ int2 slots[27];
-  if (tid < 27) slots[tid] = m.slots[b * 27 + tid];
+  __shared__ long long src_off[27];
+  __shared__ int4 src_map[27];
+  if (tid < 27) guard_source(m, b, tid, src_off[tid], src_map[tid]);
   __syncthreads();
-  const int ox = m.origin[3 * b], oy = m.origin[3 * b + 1], oz = m.origin[3 * b + 2];
   auto load_plane = [&](int p, int slot) {
     R *dst = ring + slot * SM::RING;
     const int zpad = p + zoff;
@@ -402,39 +449,10 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
       const int gx = x0 + ii - 2 + ng, gy = y0 + jj - 2 + ng;
       const int sx = gx < ng ? 0 : (gx >= ng + n ? 2 : 1);
       const int sy = gy < ng ? 0 : (gy >= ng + n ? 2 : 1);
-      const S *src = Ub + ((long long)zpad * P + gy) * P + gx;
-      unsigned flip = 0;                 // velocity components mirrored at a wall
-      if (sx != 1 || sy != 1 || sz != 1) {
-        const int2 sl = slots[sx + 3 * sy + 9 * sz];
-        if (sl.x == SLOT_COPY) {
-          // outflow clamps, periodic wraps, reflecting mirrors (and negates
-          // the wall-normal velocity below)
-          auto map = [&](int a, int N, int d) {
-            if (a < 0) {
-              const int kind = m.bc[d][0];
-              if (kind == FX_BC_PERIODIC) return a + N;
-              if (kind == FX_BC_REFLECT) { flip |= 1u << d; return -1 - a; }
-              return 0;
-            }
-            if (a >= N) {
-              const int kind = m.bc[d][1];
-              if (kind == FX_BC_PERIODIC) return a - N;
-              if (kind == FX_BC_REFLECT) { flip |= 1u << d; return 2 * N - 1 - a; }
-              return N - 1;
-            }
-            return a;
-          };
-          const int ax = map(ox + gx - ng, m.ncell[lev][0], 0);
-          const int ay = map(oy + gy - ng, m.ncell[lev][1], 1);
-          int lz = 0;
-          if (NDIM == 3) {
-            const int az = map(oz + zpad - ng, m.ncell[lev][2], 2);
-            lz = az - m.origin[3 * sl.y + 2] + ng;
-          }
-          const int lx = ax - m.origin[3 * sl.y] + ng, ly = ay - m.origin[3 * sl.y + 1] + ng;
-          src = U + (long long)sl.y * m.bstride + ((long long)lz * P + ly) * P + lx;
-        }
-      }
+      const int q = sx + 3 * sy + 9 * sz;
+      const int4 mq = src_map[q];
+      const S *src = U + (src_off[q] + (gx * mq.x + gy * mq.y + zpad * mq.z));
+      const unsigned flip = (unsigned)mq.w;   // velocity components mirrored at a wall
       R w[SM::NV];
       prim<S, R, NS>(src, vs, gm1, m, w);
       if (flip) {
