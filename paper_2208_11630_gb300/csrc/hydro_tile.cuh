@@ -40,12 +40,17 @@ namespace {
 // powers of two is exact.  The sign tests run on the integer pipe.
 //
 // FP64: the minimum of the three non-negative magnitudes is taken on their bit
-// patterns (which order like the values), keeping it off the FP64 pipe.
+// patterns (which order like the values), keeping it off the FP64 pipe; so is
+// the quarter of |a + b|, by lowering its biased exponent by 2 -- exact for
+// every normal result; a sum below 2^-1020, whose quarter would not be a
+// normal number, gives 0 (a slope 300 orders of magnitude below any state).
 __device__ __forceinline__ double mc_half(double a, double b) {
   const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
   const bool same = ((ia ^ ib) >= 0) && (ia << 1) != 0 && (ib << 1) != 0;
   const long long ma = ia & 0x7fffffffffffffffll, mb = ib & 0x7fffffffffffffffll;
-  const long long mq = __double_as_longlong(0.25 * fabs(a + b));
+  constexpr long long kQuarter = 2ll << 52, kMinNormal = 1ll << 52;
+  long long mq = (__double_as_longlong(a + b) & 0x7fffffffffffffffll) - kQuarter;
+  mq = mq < kMinNormal ? 0 : mq;
   long long m = ma < mb ? ma : mb;
   m = mq < m ? mq : m;
   // sign of a on the minimum magnitude
@@ -189,16 +194,17 @@ __device__ __forceinline__ void hllc(const R (&WL)[5 + NS], const R (&WR)[5 + NS
     }
     const R fac = rK * dK * inv;                       // rho*_K
     const R ds = Sst - uK;
-    R Us[5];
-    Us[0] = fac;
+    // F*_K = F_K + S_K (U*_K - U_K).  Mass and momenta: U*_K - U_K is
+    // (rho*_K - rho_K)(1, u, v, w) plus rho*_K (S* - u_K) in the normal
+    // momentum, since the star velocity keeps the tangential components and
+    // takes S* as the normal one.
+    const R fr = SK * (fac - rK);
+    const R Ue = fac * (eK + ds * Sst) + ds * pK * inv;  // rho*_K e*_K
+    F[0] = F[0] + fr;
 #pragma unroll
-    for (int t = 0; t < 3; ++t) Us[1 + t] = fac * W[1 + t];
-    Us[N] = fac * Sst;
-    Us[4] = fac * (eK + ds * Sst) + ds * pK * inv;     // rho*_K e*_K
-    F[0] = F[0] + SK * (Us[0] - rK);
-#pragma unroll
-    for (int t = 0; t < 3; ++t) F[1 + t] = F[1 + t] + SK * (Us[1 + t] - rK * W[1 + t]);
-    F[4] = F[4] + SK * (Us[4] - EK);
+    for (int t = 0; t < 3; ++t) F[1 + t] = F[1 + t] + fr * W[1 + t];
+    F[N] = F[N] + (SK * fac) * ds;
+    F[4] = F[4] + SK * (Ue - EK);
   }
 #pragma unroll
   for (int k = 0; k < NS; ++k) F[5 + k] = F[0] * W[5 + k];
@@ -227,7 +233,8 @@ __device__ __forceinline__ void prim(const S *u, long long vs, R gm1, const DevM
     w[6 + NS] = gc;
   }
   (void)m;
-  w[4] = gmc * (E - R(0.5) * (mx * mx + my * my + mz * mz) * ir);
+  // kinetic energy density from u.m (= |m|^2 / rho)
+  w[4] = gmc * fma(R(-0.5), w[1] * mx + w[2] * my + w[3] * mz, E);
   w[5] = ir;
 }
 
