@@ -63,7 +63,7 @@ struct fx_blocks {
   int next_form = 0;
   int *d_status = nullptr;
   double *d_dt = nullptr;                   // dt scratch for fx_run_host
-  double *d_totals = nullptr;               // [nleaves][nvar]
+  double *d_totals = nullptr;               // [nleaves][nvar]; also the regrid indicator words
   // fx_run_host_interior: packed interior staging buffer and the streams and
   // events of the overlapped download (created on first use)
   void *d_pack = nullptr;

@@ -13,11 +13,11 @@
 
 #include <atomic>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
-#include <map>
 #include <string>
-#include <tuple>
+#include <unordered_map>
 #include <vector>
 
 
@@ -76,10 +76,23 @@ void free_blocks(fx_blocks *bs) {
 }
 
 struct Lattice {
-  // (level, bx, by, bz) -> block
-  std::map<std::tuple<int, long long, long long, long long>, int> map;
+  // (level, bx, by, bz) -> block; block indices are below 2^30 per axis
+  struct Key {
+    int l, x, y, z;
+    bool operator==(const Key &o) const { return l == o.l && x == o.x && y == o.y && z == o.z; }
+  };
+  struct Hash {
+    size_t operator()(const Key &k) const {
+      uint64_t h = (uint64_t)(uint32_t)k.x * 0x9E3779B97F4A7C15ull;
+      h ^= ((uint64_t)(uint32_t)k.y + ((uint64_t)(uint32_t)k.l << 40)) * 0xC2B2AE3D27D4EB4Full;
+      h ^= (uint64_t)(uint32_t)k.z * 0x165667B19E3779F9ull;
+      return (size_t)(h ^ (h >> 29));
+    }
+  };
+  std::unordered_map<Key, int, Hash> map;
+  static Key key(int l, const long long bc[3]) { return Key{l, (int)bc[0], (int)bc[1], (int)bc[2]}; }
   int find(int l, const long long bc[3]) const {
-    auto it = map.find(std::make_tuple(l, bc[0], bc[1], bc[2]));
+    auto it = map.find(key(l, bc));
     return it == map.end() ? -1 : it->second;
   }
 };
@@ -220,6 +233,7 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
   if (ncell[lmax][0] > (1LL << 30) || ncell[lmax][1] > (1LL << 30) || ncell[lmax][2] > (1LL << 30))
     return bail(FX_ERR_MESH, "lattice too large");
   Lattice lat;
+  lat.map.reserve(2 * (size_t)nb);
   for (int b = 0; b < nb; ++b) {
     long long bcd[3];
     for (int d = 0; d < 3; ++d) {
@@ -229,9 +243,8 @@ int fx_blocks_create(fx_ctx *ctx, int ndim, int nblocks, int nxb, const int nroo
       bs->origin[3 * b + d] = (int)o;
       bcd[d] = o / n;
     }
-    auto key = std::make_tuple(level[b], bcd[0], bcd[1], bcd[2]);
-    if (lat.map.count(key)) return bail(FX_ERR_MESH, "two blocks at the same position");
-    lat.map[key] = b;
+    if (!lat.map.emplace(Lattice::key(level[b], bcd), b).second)
+      return bail(FX_ERR_MESH, "two blocks at the same position");
   }
   for (int b = 0; b < nb; ++b) {
     int p = parent[b];

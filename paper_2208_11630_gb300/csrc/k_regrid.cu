@@ -13,43 +13,31 @@
 namespace fx {
 namespace {
 
-// Density (v = 0) or pressure (v = 4) of the cell at padded offset o.
-template <typename S>
-__device__ __forceinline__ double rho_or_p(const DevMesh &m, const S *Ub, long long vs,
-                                           long long o, int v) {
-  if (v == 0) return double(Ub[o]);
-  double u[FX_MAXVAR];
-  for (int q = 0; q < m.nvar; ++q) u[q] = double(Ub[o + q * vs]);
-  return ops::cons_pressure(m, u);
-}
-
-// Indicator of one cell for one field: sqrt(sum N^2 / sum D^2) over ordered
+// Indicator of one cell for one field, from a window q of that field around
+// the cell at index c0, whose neighbours along axis d sit at offsets lo[d]
+// (minus side) and hi[d] (plus side): sqrt(sum N^2 / sum D^2) over ordered
 // direction pairs (a, b), each term scaled by 1/(dx_a dx_b); diagonal pairs
 // use the second difference over its first-difference magnitudes plus the
 // filter eps times |q+| + 2|q0| + |q-|; off-diagonal pairs the mixed
 // difference / 4 over the two a-differences at b -+ 1 / 4 plus eps times the
 // four corner magnitudes / 4.  Zero where the denominator vanishes.
-template <typename S>
-__device__ double loehner(const DevMesh &m, const S *Ub, int lev, int i, int j, int k, int v,
-                          double eps) {
-  const long long vs = m.vstride, P = m.P;
-  const long long step[3] = {1, P, P * P};
-  const long long o0 = ((long long)k * P + j) * P + i;
+__device__ double loehner(const DevMesh &m, const double *q, const int (&lo)[3],
+                          const int (&hi)[3], int c0, int lev, double eps) {
   double num = 0.0, den = 0.0;
   for (int a = 0; a < m.ndim; ++a)
     for (int b = 0; b < m.ndim; ++b) {
       double nu, de;
       if (a == b) {
-        const double up = rho_or_p(m, Ub, vs, o0 + step[a], v);
-        const double u0 = rho_or_p(m, Ub, vs, o0, v);
-        const double um = rho_or_p(m, Ub, vs, o0 - step[a], v);
+        const double up = q[c0 + hi[a]];
+        const double u0 = q[c0];
+        const double um = q[c0 + lo[a]];
         nu = (up - u0) - (u0 - um);
         de = fabs(up - u0) + fabs(u0 - um) + eps * (fabs(up) + 2.0 * fabs(u0) + fabs(um));
       } else {
-        const double upp = rho_or_p(m, Ub, vs, o0 + step[a] + step[b], v);
-        const double ump = rho_or_p(m, Ub, vs, o0 - step[a] + step[b], v);
-        const double upm = rho_or_p(m, Ub, vs, o0 + step[a] - step[b], v);
-        const double umm = rho_or_p(m, Ub, vs, o0 - step[a] - step[b], v);
+        const double upp = q[c0 + hi[a] + hi[b]];
+        const double ump = q[c0 + lo[a] + hi[b]];
+        const double upm = q[c0 + hi[a] + lo[b]];
+        const double umm = q[c0 + lo[a] + lo[b]];
         nu = ((upp - ump) - (upm - umm)) * 0.25;
         de = (fabs(upp - ump) + fabs(upm - umm)) * 0.25 +
              eps * (fabs(upp) + fabs(ump) + fabs(upm) + fabs(umm)) * 0.25;
@@ -63,23 +51,60 @@ __device__ double loehner(const DevMesh &m, const S *Ub, int lev, int i, int j, 
   return den > 0.0 ? sqrt(num / den) : 0.0;
 }
 
-// One CTA per leaf: maximum over interior cells and over density and
-// pressure, into err_bits[leaf index] (bit pattern of a non-negative double;
-// zeroed by the caller).  Guards must be filled at depth 1.
+// Shared memory of k_regrid_err: a ring of three (2D: one) window planes of
+// density and pressure over the (n + 2)^2 radius-1 window of a plane.
+__host__ __device__ inline int regrid_err_smem(int ndim, int n) {
+  return (ndim == 3 ? 3 : 1) * 2 * (n + 2) * (n + 2) * (int)sizeof(double);
+}
+
+// One CTA per leaf, marching the interior along z with the ring above, so
+// that each cell's pressure is formed once rather than at every stencil
+// point.  Maximum over interior cells and over both fields, into
+// err_bits[leaf index] (bit pattern of a non-negative double; zeroed by the
+// caller).  Guards must be filled at depth 1.
 template <typename S>
 __global__ void k_regrid_err(DevMesh m, const S *__restrict__ U, const int *__restrict__ leaves,
                              double eps, unsigned long long *__restrict__ err_bits) {
+  extern __shared__ double win[];
   const int b = leaves[blockIdx.x];
-  const int n = m.nxb, ng = m.ng;
-  const int nz = m.ndim == 3 ? n : 1, kz = m.ndim == 3 ? ng : 0;
+  const int n = m.nxb, ng = m.ng, P = m.P, nd = m.ndim;
+  const int W = n + 2, WW = W * W;
+  const int nz = nd == 3 ? n : 1;
+  const long long vs = m.vstride;
   const S *Ub = U + (long long)b * m.bstride;
   const int lev = m.level[b];
+  // window plane kw: padded z = kw + ng - 1 in 3D (kw = 0 is the plane below
+  // the interior), the only plane in 2D; ring slot kw % 3
+  auto load = [&](int kw) {
+    double *dst = win + (nd == 3 ? kw % 3 : 0) * 2 * WW;
+    const int kp = nd == 3 ? kw + ng - 1 : 0;
+    for (int c = threadIdx.x; c < WW; c += blockDim.x) {
+      const int i = c % W, j = c / W;
+      const long long o = ((long long)kp * P + (j + ng - 1)) * P + (i + ng - 1);
+      double u[FX_MAXVAR];
+      for (int v = 0; v < m.nvar; ++v) u[v] = double(Ub[o + v * vs]);
+      dst[c] = u[0];
+      dst[WW + c] = ops::cons_pressure(m, u);
+    }
+  };
   double e = 0.0;
-  for (int c = threadIdx.x; c < n * n * nz; c += blockDim.x) {
-    const int i = c % n + ng, j = (c / n) % n + ng, k = c / (n * n) + kz;
-    const double er = loehner(m, Ub, lev, i, j, k, 0, eps);
-    const double ep = loehner(m, Ub, lev, i, j, k, 4, eps);
-    e = fmax(e, fmax(er, ep));
+  if (nd == 3) {
+    load(0);
+    load(1);
+  }
+  for (int k = 0; k < nz; ++k) {
+    load(nd == 3 ? k + 2 : 0);
+    __syncthreads();
+    const int s0 = nd == 3 ? (k + 1) % 3 : 0;      // ring slot of the cells' plane
+    const int lo[3] = {-1, -W, nd == 3 ? (k % 3 - s0) * 2 * WW : 0};
+    const int hi[3] = {1, W, nd == 3 ? ((k + 2) % 3 - s0) * 2 * WW : 0};
+    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+      const int c0 = s0 * 2 * WW + (c / n + 1) * W + (c % n + 1);
+      const double er = loehner(m, win, lo, hi, c0, lev, eps);
+      const double ep = loehner(m, win + WW, lo, hi, c0, lev, eps);
+      e = fmax(e, fmax(er, ep));
+    }
+    __syncthreads();   // the next load overwrites the slot of plane k
   }
   unsigned long long bits = __double_as_longlong(e);
   for (int o = 16; o > 0; o >>= 1) {
@@ -157,10 +182,17 @@ __global__ void k_regrid_transfer(DevMesh mo, const S *__restrict__ Uold, DevMes
 cudaError_t launch_regrid_err(const DevMesh &m, const void *U, int prec, const int *leaves, int n,
                               double eps, unsigned long long *err_bits, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  const int smem = regrid_err_smem(m.ndim, m.nxb);
+  if (smem > 48 * 1024) {
+    cudaError_t e = prec == 0
+        ? cudaFuncSetAttribute(k_regrid_err<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+        : cudaFuncSetAttribute(k_regrid_err<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
   if (prec == 0)
-    k_regrid_err<double><<<n, 256, 0, s>>>(m, static_cast<const double *>(U), leaves, eps, err_bits);
+    k_regrid_err<double><<<n, 256, smem, s>>>(m, static_cast<const double *>(U), leaves, eps, err_bits);
   else
-    k_regrid_err<float><<<n, 256, 0, s>>>(m, static_cast<const float *>(U), leaves, eps, err_bits);
+    k_regrid_err<float><<<n, 256, smem, s>>>(m, static_cast<const float *>(U), leaves, eps, err_bits);
   count_launch();
   return cudaGetLastError();
 }

@@ -16,17 +16,22 @@
 #include "fx_internal.h"
 
 #include <algorithm>
-#include <map>
-#include <set>
+#include <cstdint>
 #include <string>
-#include <tuple>
+#include <unordered_map>
 #include <vector>
 
 namespace fx {
 
 namespace {
 
-using Key = std::tuple<int, long long, long long, long long>;   // level, block x, y, z
+// (level, block x, y, z) packed into 64 bits: 6 bits of level, 19 per axis.
+constexpr int kAxisBits = 19;
+uint64_t key(int level, long long x, long long y, long long z) {
+  return ((uint64_t)level << (3 * kAxisBits)) | ((uint64_t)z << (2 * kAxisBits)) |
+         ((uint64_t)y << kAxisBits) | (uint64_t)x;
+}
+using Where = std::unordered_map<uint64_t, int>;
 
 }  // namespace
 
@@ -35,10 +40,19 @@ int regrid_plan(int ndim, int nxb, const int nroot[3], const int bc[6], int nb,
                 const std::vector<int> &parent, const std::vector<double> &err, double rc,
                 double dc, int max_level, RegridPlan *out, std::string *msg) {
   const int nch = 1 << ndim;
+  // block indices at the finest level present or planned must fit the key
+  int lcap = max_level + 1;
+  for (int b = 0; b < nb; ++b) lcap = std::max(lcap, level[b]);
+  for (int d = 0; d < 3; ++d)
+    if (((long long)nroot[d] << lcap) > (1LL << kAxisBits)) {
+      *msg = "regrid: block lattice too large";
+      return FX_ERR_ARG;
+    }
   std::vector<int> leaf(nb, 1), child(8 * (size_t)nb, -1);
-  std::map<Key, int> where;
+  Where where;
+  where.reserve(2 * (size_t)nb);
   for (int b = 0; b < nb; ++b)
-    where[Key(level[b], origin[3 * b] / nxb, origin[3 * b + 1] / nxb, origin[3 * b + 2] / nxb)] = b;
+    where[key(level[b], origin[3 * b] / nxb, origin[3 * b + 1] / nxb, origin[3 * b + 2] / nxb)] = b;
   for (int b = 0; b < nb; ++b) {
     const int p = parent[b];
     if (p < 0) continue;
@@ -50,11 +64,12 @@ int regrid_plan(int ndim, int nxb, const int nroot[3], const int bc[6], int nb,
   }
   // ---- touching leaves of every leaf
   std::vector<std::vector<int>> nbr(nb);
+  std::vector<int> found;
   for (int b = 0; b < nb; ++b) {
     if (!leaf[b]) continue;
     const int L = level[b];
     long long B[3] = {origin[3 * b] / nxb, origin[3 * b + 1] / nxb, origin[3 * b + 2] / nxb};
-    std::set<int> found;
+    found.clear();
     for (int sz = (ndim == 3 ? -1 : 0); sz <= (ndim == 3 ? 1 : 0); ++sz)
       for (int sy = -1; sy <= 1; ++sy)
         for (int sx = -1; sx <= 1; ++sx) {
@@ -72,10 +87,10 @@ int regrid_plan(int ndim, int nxb, const int nroot[3], const int bc[6], int nb,
             }
           }
           if (outside) continue;
-          auto it = where.find(Key(L, Q[0], Q[1], Q[2]));
+          auto it = where.find(key(L, Q[0], Q[1], Q[2]));
           if (it != where.end()) {
             const int q = it->second;
-            if (leaf[q]) { found.insert(q); continue; }
+            if (leaf[q]) { found.push_back(q); continue; }
             for (int oct = 0; oct < nch; ++oct) {   // children of q on b's side
               bool touches = true;
               for (int d = 0; d < ndim; ++d) {
@@ -85,18 +100,20 @@ int regrid_plan(int ndim, int nxb, const int nroot[3], const int bc[6], int nb,
               const int c = child[8 * q + oct];
               if (!touches) continue;
               if (c < 0 || !leaf[c]) { *msg = "regrid: mesh not 2:1 balanced"; return FX_ERR_MESH; }
-              found.insert(c);
+              found.push_back(c);
             }
           } else {
             if (L == 0) { *msg = "regrid: mesh does not cover the domain"; return FX_ERR_MESH; }
-            auto up = where.find(Key(L - 1, Q[0] >> 1, Q[1] >> 1, ndim == 3 ? Q[2] >> 1 : 0));
+            auto up = where.find(key(L - 1, Q[0] >> 1, Q[1] >> 1, ndim == 3 ? Q[2] >> 1 : 0));
             if (up == where.end() || !leaf[up->second]) {
               *msg = "regrid: mesh not 2:1 balanced";
               return FX_ERR_MESH;
             }
-            found.insert(up->second);
+            found.push_back(up->second);
           }
         }
+    std::sort(found.begin(), found.end());
+    found.erase(std::unique(found.begin(), found.end()), found.end());
     nbr[b].assign(found.begin(), found.end());
   }
   // ---- requests
@@ -158,9 +175,10 @@ int regrid_plan(int ndim, int nxb, const int nroot[3], const int bc[6], int nb,
     return a.o[0] < b.o[0];
   });
   const int nn = (int)e.size();
-  std::map<Key, int> at;
+  Where at;
+  at.reserve(2 * (size_t)nn);
   for (int j = 0; j < nn; ++j)
-    at[Key(e[j].level, e[j].o[0] / nxb, e[j].o[1] / nxb, e[j].o[2] / nxb)] = j;
+    at[key(e[j].level, e[j].o[0] / nxb, e[j].o[1] / nxb, e[j].o[2] / nxb)] = j;
   out->level.resize(nn);
   out->origin.resize(3 * (size_t)nn);
   out->parent.resize(nn);
@@ -171,7 +189,7 @@ int regrid_plan(int ndim, int nxb, const int nroot[3], const int bc[6], int nb,
     out->map[j] = make_int4(e[j].kind, e[j].src, e[j].oct, 0);
     out->parent[j] = -1;
     if (e[j].level > 0) {
-      auto it = at.find(Key(e[j].level - 1, (e[j].o[0] / nxb) >> 1, (e[j].o[1] / nxb) >> 1,
+      auto it = at.find(key(e[j].level - 1, (e[j].o[0] / nxb) >> 1, (e[j].o[1] / nxb) >> 1,
                             ndim == 3 ? (e[j].o[2] / nxb) >> 1 : 0));
       if (it == at.end()) { *msg = "regrid: block without parent"; return FX_ERR_MESH; }
       out->parent[j] = it->second;

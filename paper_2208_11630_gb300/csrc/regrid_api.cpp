@@ -26,11 +26,8 @@ int fx_regrid_plan(fx_ctx *ctx, fx_blocks *bs, double refine_cutoff, double dere
   // parents restricted and every guard layer filled (no leaf interior changes)
   int rc = fx_guardcell_fill(ctx, bs, stream);
   if (rc) return rc;
-  unsigned long long *d_err = nullptr;
-  if (cudaMalloc(&d_err, sizeof(unsigned long long) * bs->nleaves) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(ctx, FX_ERR_OOM, "cudaMalloc of the indicator buffer failed");
-  }
+  // the per-leaf indicator words use the totals scratch (nvar >= 5 doubles per leaf)
+  unsigned long long *d_err = reinterpret_cast<unsigned long long *>(bs->d_totals);
   std::vector<unsigned long long> h(bs->nleaves);
   cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(unsigned long long) * bs->nleaves, s);
   if (e == cudaSuccess)
@@ -40,7 +37,6 @@ int fx_regrid_plan(fx_ctx *ctx, fx_blocks *bs, double refine_cutoff, double dere
     e = cudaMemcpyAsync(h.data(), d_err, sizeof(unsigned long long) * bs->nleaves,
                         cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(d_err);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "regrid indicator");
   bs->plan_err.assign(bs->nb, -1.0);
   for (int i = 0; i < bs->nleaves; ++i) {
