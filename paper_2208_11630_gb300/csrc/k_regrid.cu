@@ -21,11 +21,15 @@ namespace {
 // filter eps times |q+| + 2|q0| + |q-|; off-diagonal pairs the mixed
 // difference / 4 over the two a-differences at b -+ 1 / 4 plus eps times the
 // four corner magnitudes / 4.  Zero where the denominator vanishes.
-__device__ double loehner(const DevMesh &m, const double *q, const int (&lo)[3],
-                          const int (&hi)[3], int c0, int lev, double eps) {
+// sc[a][b] = 1/(dx_a dx_b) at the block's level.
+template <int NDIM>
+__device__ __forceinline__ double loehner(const double *q, const int (&lo)[3], const int (&hi)[3],
+                                          int c0, const double (*sc)[3], double eps) {
   double num = 0.0, den = 0.0;
-  for (int a = 0; a < m.ndim; ++a)
-    for (int b = 0; b < m.ndim; ++b) {
+#pragma unroll
+  for (int a = 0; a < NDIM; ++a)
+#pragma unroll
+    for (int b = 0; b < NDIM; ++b) {
       double nu, de;
       if (a == b) {
         const double up = q[c0 + hi[a]];
@@ -42,9 +46,8 @@ __device__ double loehner(const DevMesh &m, const double *q, const int (&lo)[3],
         de = (fabs(upp - ump) + fabs(upm - umm)) * 0.25 +
              eps * (fabs(upp) + fabs(ump) + fabs(upm) + fabs(umm)) * 0.25;
       }
-      const double sc = 1.0 / (m.dx[lev][a] * m.dx[lev][b]);
-      nu = nu * sc;
-      de = de * sc;
+      nu = nu * sc[a][b];
+      de = de * sc[a][b];
       num = num + nu * nu;
       den = den + de * de;
     }
@@ -62,17 +65,22 @@ __host__ __device__ inline int regrid_err_smem(int ndim, int n) {
 // point.  Maximum over interior cells and over both fields, into
 // err_bits[leaf index] (bit pattern of a non-negative double; zeroed by the
 // caller).  Guards must be filled at depth 1.
-template <typename S>
+template <int NDIM, typename S>
 __global__ void k_regrid_err(DevMesh m, const S *__restrict__ U, const int *__restrict__ leaves,
                              double eps, unsigned long long *__restrict__ err_bits) {
   extern __shared__ double win[];
   const int b = leaves[blockIdx.x];
-  const int n = m.nxb, ng = m.ng, P = m.P, nd = m.ndim;
+  const int n = m.nxb, ng = m.ng, P = m.P;
+  constexpr int nd = NDIM;
   const int W = n + 2, WW = W * W;
   const int nz = nd == 3 ? n : 1;
   const long long vs = m.vstride;
   const S *Ub = U + (long long)b * m.bstride;
-  const int lev = m.level[b];
+  __shared__ double sc[3][3];
+  if (threadIdx.x < 9) {
+    const int lev = m.level[b], a = threadIdx.x / 3, c = threadIdx.x % 3;
+    sc[a][c] = 1.0 / (m.dx[lev][a] * m.dx[lev][c]);
+  }
   // window plane kw: padded z = kw + ng - 1 in 3D (kw = 0 is the plane below
   // the interior), the only plane in 2D; ring slot kw % 3
   auto load = [&](int kw) {
@@ -100,8 +108,8 @@ __global__ void k_regrid_err(DevMesh m, const S *__restrict__ U, const int *__re
     const int hi[3] = {1, W, nd == 3 ? ((k + 2) % 3 - s0) * 2 * WW : 0};
     for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
       const int c0 = s0 * 2 * WW + (c / n + 1) * W + (c % n + 1);
-      const double er = loehner(m, win, lo, hi, c0, lev, eps);
-      const double ep = loehner(m, win + WW, lo, hi, c0, lev, eps);
+      const double er = loehner<NDIM>(win, lo, hi, c0, sc, eps);
+      const double ep = loehner<NDIM>(win + WW, lo, hi, c0, sc, eps);
       e = fmax(e, fmax(er, ep));
     }
     __syncthreads();   // the next load overwrites the slot of plane k
@@ -183,16 +191,19 @@ cudaError_t launch_regrid_err(const DevMesh &m, const void *U, int prec, const i
                               double eps, unsigned long long *err_bits, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int smem = regrid_err_smem(m.ndim, m.nxb);
-  if (smem > 48 * 1024) {
-    cudaError_t e = prec == 0
-        ? cudaFuncSetAttribute(k_regrid_err<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
-        : cudaFuncSetAttribute(k_regrid_err<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-  }
-  if (prec == 0)
-    k_regrid_err<double><<<n, 256, smem, s>>>(m, static_cast<const double *>(U), leaves, eps, err_bits);
-  else
-    k_regrid_err<float><<<n, 256, smem, s>>>(m, static_cast<const float *>(U), leaves, eps, err_bits);
+  auto go = [&](auto kern, const auto *Ut) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<n, 256, smem, s>>>(m, Ut, leaves, eps, err_bits);
+    return cudaSuccess;
+  };
+  const double *U64 = static_cast<const double *>(U);
+  const float *U32 = static_cast<const float *>(U);
+  cudaError_t e = m.ndim == 3 ? (prec == 0 ? go(k_regrid_err<3, double>, U64) : go(k_regrid_err<3, float>, U32))
+                              : (prec == 0 ? go(k_regrid_err<2, double>, U64) : go(k_regrid_err<2, float>, U32));
+  if (e != cudaSuccess) return e;
   count_launch();
   return cudaGetLastError();
 }
