@@ -40,17 +40,12 @@ namespace {
 // powers of two is exact.  The sign tests run on the integer pipe.
 //
 // FP64: the minimum of the three non-negative magnitudes is taken on their bit
-// patterns (which order like the values), keeping it off the FP64 pipe; so is
-// the quarter of |a + b|, by lowering its biased exponent by 2 -- exact for
-// every normal result; a sum below 2^-1020, whose quarter would not be a
-// normal number, gives 0 (a slope 300 orders of magnitude below any state).
+// patterns (which order like the values), keeping it off the FP64 pipe.
 __device__ __forceinline__ double mc_half(double a, double b) {
   const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
   const bool same = ((ia ^ ib) >= 0) && (ia << 1) != 0 && (ib << 1) != 0;
   const long long ma = ia & 0x7fffffffffffffffll, mb = ib & 0x7fffffffffffffffll;
-  constexpr long long kQuarter = 2ll << 52, kMinNormal = 1ll << 52;
-  long long mq = (__double_as_longlong(a + b) & 0x7fffffffffffffffll) - kQuarter;
-  mq = mq < kMinNormal ? 0 : mq;
+  const long long mq = __double_as_longlong(0.25 * fabs(a + b));
   long long m = ma < mb ? ma : mb;
   m = mq < m ? mq : m;
   // sign of a on the minimum magnitude
