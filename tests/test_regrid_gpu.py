@@ -34,8 +34,11 @@ def _cases():
     m_sed = mesh_2level(4, 8, 4)
     m_2d = inputs.uniform_mesh(2, (6, 4), 16, 4, O_)
     m_w, W_w = _wall_problem(3, (2, 2, 2), 8, (0,), lambda c: c[0] == 0 and c[1] == 1, 41)[:2]
+    # 32^3 blocks: the indicator's shared-memory window exceeds 48 KB
+    m_32 = inputs.uniform_mesh(3, (2, 2, 2), 32, 4, P_)
     return {
         "smooth3d": (m_kh, inputs.random_smooth_state(m_kh, 43)),
+        "smooth3d_nxb32": (m_32, inputs.random_smooth_state(m_32, 44)),
         "sedov_amr": (m_sed, inputs.sedov_state(m_sed)),
         "blocky2d": (m_2d, inputs.random_blocky_state(m_2d, 42)),
         "walled_amr": (m_w, W_w),
@@ -57,7 +60,8 @@ def _cutoffs(err, lo_q=0.5, hi_q=0.85):
     return rc, dc
 
 
-@pytest.mark.parametrize("case", ["smooth3d", "sedov_amr", "blocky2d", "walled_amr"])
+@pytest.mark.parametrize("case", ["smooth3d", "smooth3d_nxb32", "sedov_amr", "blocky2d",
+                                  "walled_amr"])
 def test_plan_and_transfer_match_oracle(orc, fx, case):
     mesh, W = _cases()[case]
     bs = fx.BlockSet(mesh, 1.4)
