@@ -163,8 +163,10 @@ def oracle_sample(workload: str, target_s: float = 12.0, max_steps: int = 50):
 def measure_variants(args, fx, inputs, mesh, dev, cfl, zones, bs, ws, hbm_peak):
     """The same workload (i) as one request of a batch -- coarse-fine fill,
     persistent update and flux correction replayed as one CUDA graph per step,
-    launch choice autotuned -- and (ii) in the other precision, timed the same
-    way (CUDA events on the launching stream, warm-up first)."""
+    launch choice autotuned -- (ii) in the other precision, (v) as an FP64
+    state updated in double-word arithmetic, each timed the same way (CUDA
+    events on the launching stream, warm-up first), then (iv) with two
+    species and (iii) with regridding."""
     import torch
     out = {}
     stream = torch.cuda.Stream(device=dev)
@@ -222,6 +224,53 @@ def measure_variants(args, fx, inputs, mesh, dev, cfl, zones, bs, ws, hbm_peak):
                   "step_hbm_frac": bpz * (z / t) / ws / (hbm_peak * 1e9),
                   "ok": bs2.status() == 0}
     bs2.close()
+    # (v) FP64 state updated in double-word arithmetic (option f64_arith = 1):
+    # timed like (ii); its deviation from the FP64 update after one step from
+    # the same state, per cell relative to the variable's largest magnitude
+    # (the momentum components share the largest |m|)
+    mesh5, W5s, gamma5, _ = inputs.workload(args.workload, scale=args.scale)
+    bs5 = fx.BlockSet(mesh5, gamma5, precision=fx.FX_F64, device=dev, options={"f64_arith": 1})
+    bs5.set_primitive(W5s)
+    ref5 = fx.BlockSet(mesh5, gamma5, precision=fx.FX_F64, device=dev)
+    ref5.set_primitive(W5s)
+    del W5s
+    fx.fx_step(bs5.ctx, bs5.bs, cfl, bs5.dt.data_ptr(), sptr)
+    fx.fx_step(ref5.ctx, ref5.bs, cfl, ref5.dt.data_ptr(), sptr)
+    torch.cuda.synchronize()
+    g5 = mesh5.ng
+    sl = (slice(None), slice(None)) + ((slice(g5, g5 + mesh5.nxb),) if mesh5.ndim == 3 else
+                                       (slice(None),)) + (slice(g5, g5 + mesh5.nxb),) * 2
+    leaf5 = torch.as_tensor(mesh5.is_leaf().astype(bool), device=bs5.current.device)
+    a5, r5 = bs5.current[sl][leaf5], ref5.current[sl][leaf5]
+    scale5 = r5.abs().amax(dim=(0, 2, 3, 4), keepdim=True)
+    scale5[:, 1:4] = r5[:, 1:4].square().sum(dim=1).sqrt().amax()
+    scale5 = scale5.clamp_min(1e-300)
+    dev5 = float(((a5 - r5).abs() / torch.maximum(r5.abs(), scale5)).max())
+    del a5, r5
+    ref5.close()
+    dtp5 = bs5.dt.data_ptr()
+    for _ in range(args.warmup):
+        fx.fx_step(bs5.ctx, bs5.bs, cfl, dtp5, sptr)
+    stream.synchronize()
+    ev5 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    a.record(stream)
+    for k in range(args.steps):
+        fx.fx_compute_dt(bs5.ctx, bs5.bs, cfl, dtp5, sptr)
+        fx.fx_guardcell_fill_amr(bs5.ctx, bs5.bs, sptr)
+        ev5[k][0].record(stream)
+        fx.fx_hydro_advance(bs5.ctx, bs5.bs, dtp5, sptr)
+        ev5[k][1].record(stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3
+    hyd5 = float(np.mean([x.elapsed_time(y) for x, y in ev5])) / 1e3
+    z, t = aggregate(zones * args.steps, sec, dev)
+    out["f64_double_word"] = {
+        "value": z / t, "unit": UNIT, "ms_per_step": 1e3 * t / args.steps, "dtype": "f64 state, "
+        "double-word (2 x f32) arithmetic", "hydro_ms": hyd5 * 1e3,
+        "max_rel_dev_from_f64_after_one_step": dev5, "ok": bs5.status() == 0}
+    bs5.close()
     # (iv) multispecies perfect gas: the same workload carrying two species
     # (gamma 1.4 / A 28.96 inside the shear band, 5/3 / 4 outside)
     import dataclasses

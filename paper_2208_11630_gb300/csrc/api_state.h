@@ -21,6 +21,7 @@ struct fx_ctx {
   int cfl_form = 0;
   int reflux = 1;
   int integrator = 0;   // 0 MUSCL-Hancock, 1 SSP-RK2, 2 SSP-RK3
+  int f64_arith = 0;    // MUSCL-Hancock update of FP64 sets: 0 FP64, 1 double-word
   int nspec = 0;        // multispecies perfect gas: species and their constants
   double spa[FX_MAXSPEC] = {0, 0, 0, 0}, spb[FX_MAXSPEC] = {0, 0, 0, 0};
   int device = 0;
@@ -90,6 +91,13 @@ int cuda_fail(fx_ctx *ctx, cudaError_t e, const char *where);
 
 // Returns FX_ERR_CUDA from the enclosing entry point (whose block set is bs)
 // when call does not succeed.
+// The stage of a MUSCL-Hancock update of block set bs under context ctx.
+inline fx::HydroStage muscl_stage(const fx_ctx *ctx, const fx_blocks *bs) {
+  fx::HydroStage st;
+  st.dword = ctx->f64_arith && bs->prec == 0;
+  return st;
+}
+
 #define FX_CUDA(call, where)                                         \
   do {                                                               \
     cudaError_t e_ = (call);                                         \

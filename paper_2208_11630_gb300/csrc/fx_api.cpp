@@ -153,6 +153,11 @@ int fx_set_option(fx_ctx *ctx, const char *key, double value) {
     ctx->reflux = (int)value;
     return FX_OK;
   }
+  if (!strcmp(key, "f64_arith")) {
+    if (value != 0.0 && value != 1.0) return fail(ctx, FX_ERR_ARG, "f64_arith must be 0 or 1");
+    ctx->f64_arith = (int)value;
+    return FX_OK;
+  }
   if (!strcmp(key, "integrator")) {
     if (value != 0.0 && value != 1.0 && value != 2.0)
       return fail(ctx, FX_ERR_ARG, "integrator must be 0, 1 or 2");
@@ -587,7 +592,7 @@ int fx_hydro_advance(fx_ctx *ctx, fx_blocks *bs, const double *dt_dev, void *str
   FX_CUDA(cudaMemsetAsync(smax, 0, sizeof(unsigned long long), s), "signal max reset");
   FX_CUDA(fx::launch_hydro(bs->dm, Uo, Un, bs->prec, leaves, bs->nleaves,
                            dt_dev, bs->d_regs, bs->d_status, smax, refl ? bs->d_rmask : nullptr,
-                           ctx->cfl_form, s),
+                           ctx->cfl_form, s, muscl_stage(ctx, bs)),
           "hydro launch");
   if (refl)
     FX_CUDA(fx::launch_reflux(bs->dm, Un, bs->prec, bs->d_refl, bs->nrefl, dt_dev, bs->d_regs,

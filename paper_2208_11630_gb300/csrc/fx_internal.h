@@ -104,11 +104,18 @@ struct HydroStage {
   double wa = 0.5, wb = 0.5;  // blend weights
   double reg_w = 1.0;         // weight of the fluxes in the registers
   int reg_add = 0;            // 0 store, 1 add to the registers
+  int dword = 0;              // 1: FP64 state, double-word arithmetic (MUSCL-Hancock only)
 };
 
 // smax (may be null): receives atomicMax of the bit patterns of the new
 // state's CFL signal speeds (form 0 = sum over directions, 1 = max); cells on
 // the faces flagged in rmask[block] (bit 2d+s) are left to the reflux kernel.
+// The MUSCL-Hancock update of an FP64 block set in double-word arithmetic
+// (k_hydro_dw.cu).
+cudaError_t launch_hydro_dw(const DevMesh &m, const void *U, void *Unew, const int *leaves, int n,
+                            const double *dt, double *regs, int *status,
+                            unsigned long long *smax, const unsigned char *rmask, int form,
+                            cudaStream_t s);
 cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, const int *leaves,
                          int n, const double *dt, double *regs, int *status,
                          unsigned long long *smax, const unsigned char *rmask, int form,

@@ -93,7 +93,8 @@ int advance_and_download(fx_ctx *ctx, fx_blocks *bs, cudaStream_t s, void *W_out
     cudaStream_t a = bs->aux[c & 1];
     if (c < 2) FX_CUDA(cudaStreamWaitEvent(a, bs->ev_ready, 0), "stream wait");
     FX_CUDA(fx::launch_hydro(bs->dm, Uo, Un, bs->prec, bs->d_lists + bs->leaves_off + b0, b1 - b0,
-                             bs->d_dt, bs->d_regs, bs->d_status, smax, nullptr, ctx->cfl_form, a),
+                             bs->d_dt, bs->d_regs, bs->d_status, smax, nullptr, ctx->cfl_form, a,
+                             muscl_stage(ctx, bs)),
             "hydro launch");
     char *pk = static_cast<char *>(bs->d_pack) + pb * b0;
     FX_CUDA(fx::launch_pack(bs->dm, Un, bs->prec, pk, b0, b1 - b0, 1, a), "pack launch");

@@ -28,6 +28,7 @@
 // ulp at a tiny fraction of the cost of FP64 arithmetic on this GPU.
 #pragma once
 
+#include "dword.cuh"
 #include "eos.cuh"
 
 #include <type_traits>
@@ -85,6 +86,20 @@ __device__ __forceinline__ bool gt0(float x) { return x > 0.0f; }
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 
+// Double-word compute type (FP64 state): signs from the leading word, which
+// carries the sign of every nonzero value.
+__device__ __forceinline__ bool positive(dw x) { return x.hi > 0.0f; }
+__device__ __forceinline__ bool ge0(dw x) { return x.hi >= 0.0f; }
+__device__ __forceinline__ bool gt0(dw x) { return x.hi > 0.0f; }
+__device__ __forceinline__ dw rsqrt_r(dw x) { return rsqrt(x); }
+__device__ __forceinline__ dw mc_half(dw a, dw b) {
+  const bool same = (a.hi > 0.0f && b.hi > 0.0f) || (a.hi < 0.0f && b.hi < 0.0f);
+  const dw s = fabs(a + b);
+  const dw q(0.25f * s.hi, 0.25f * s.lo);          // exact scaling
+  const dw m = fmin(fmin(fabs(a), fabs(b)), q);
+  return same ? (a.hi < 0.0f ? -m : m) : dw(0.0f, 0.0f);
+}
+
 // Flux-register write: MUSCL-Hancock stores F; an SSP-RK stage stores or
 // adds st.reg_w F (stage-weighted sums).
 template <bool RK, typename R>
@@ -97,6 +112,7 @@ __device__ __forceinline__ void put_reg(double &r, R f, const HydroStage &st) {
 // Quotient and reciprocal: IEEE division in FP64; the fast (MUFU-based,
 // ~2 ulp) forms in FP32, whose error is far below the FP32 storage rounding.
 __device__ __forceinline__ double div_r(double a, double b) { return a / b; }
+__device__ __forceinline__ dw div_r(dw a, dw b) { return a / b; }
 __device__ __forceinline__ float div_r(float a, float b) { return __fdividef(a, b); }
 
 // c * (a - b) with the difference a - b taken exactly (Knuth's TwoSum error
@@ -145,11 +161,14 @@ __device__ __forceinline__ void hllc(const R (&WL)[5 + NS], const R (&WR)[5 + NS
   const R A = pR - pL + rL * uL * dL - rR * uR * dR;
   const R B = rL * dL - rR * dR;
   constexpr bool kF64 = std::is_same<R, double>::value;
+  constexpr bool kDW = std::is_same<R, dw>::value;
   R Sst = R(0);
   bool sst_ge0;
   if constexpr (kF64) {
     const long long ia = __double_as_longlong(A), ib = __double_as_longlong(B);
     sst_ge0 = (ia << 1) == 0 || (ia ^ ib) >= 0;
+  } else if constexpr (kDW) {
+    sst_ge0 = A.hi == 0.0f || ((A.hi < 0.0f) == (B.hi < 0.0f));
   } else {
     Sst = div_r(A, B);
     sst_ge0 = ge0(Sst);
@@ -177,7 +196,7 @@ __device__ __forceinline__ void hllc(const R (&WL)[5 + NS], const R (&WR)[5 + NS
   if (star) {
     const R dK = SK - uK;
     R inv;
-    if constexpr (kF64) {
+    if constexpr (kF64 || kDW) {
       // S_K - S* = Q / B with Q = S_K B - A:  r = 1/(B Q), S* = A Q r,
       // 1/(S_K - S*) = B B r
       const R Q = SK * B - A;
@@ -419,6 +438,8 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
   idx2[1] = R(2.0 * m.idx[lev][1]);
   idx2[2] = R(2.0 * m.idx[lev][2]);
   const double didx = m.idx[lev][0], didy = m.idx[lev][1], didz = m.idx[lev][2];
+  // the same in the compute type (FP64 and double-word updates)
+  const R rdx = R(didx), rdy = R(didy), rdz = R(didz), rdt = R(dt);
   const S *Ub = U + (long long)b * m.bstride;
   S *Unb = Unew + (long long)b * m.bstride;   // may alias Uavg (see above)
   const int ti = tid % T, tj = tid / T;
@@ -633,8 +654,8 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
           const float d = txy[v] + scaled_diff(fzl[v], Fz[v], cz);
           un[v] = float(Ub[o + v * vs]) + d;
         } else {
-          const double div = txy[v] + (fzl[v] - Fz[v]) * didz;
-          un[v] = double(Ub[o + v * vs]) + dt * div;
+          const R div = txy[v] + (fzl[v] - Fz[v]) * rdz;
+          un[v] = R(Ub[o + v * vs]) + rdt * div;
         }
         if constexpr (RK) {
           if (Uavg)
@@ -656,7 +677,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
         if constexpr (kF32) {
           txy[v] = scaled_diff(fxl, fxr, cx) + scaled_diff(fyl, fyr, cy);
         } else {
-          txy[v] = (fxl - fxr) * didx + (fyl - fyr) * didy;
+          txy[v] = (fxl - fxr) * rdx + (fyl - fyr) * rdy;
         }
         if (NDIM == 3) fzl[v] = Fz[v];
       }
@@ -666,7 +687,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
 #pragma unroll
         for (int v = 0; v < NF; ++v) {
           if constexpr (kF32) un[v] = float(Ub[o + v * vs]) + txy[v];
-          else un[v] = double(Ub[o + v * vs]) + dt * txy[v];
+          else un[v] = R(Ub[o + v * vs]) + rdt * txy[v];
           if constexpr (RK) {
             if (Uavg)
               un[v] = fma(R(st.wa), R(Uavg[(long long)b * m.bstride + o + v * vs]), R(st.wb) * un[v]);

@@ -147,6 +147,10 @@ cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, 
   if (!st.pred)     // an SSP Runge-Kutta stage (k_hydro_rk.cu)
     return launch_hydro_rk(m, U, Unew, prec, leaves, n, dt, regs, status, smax, rmask, form, s, st);
   if (st.Uavg || st.reg_add || st.reg_w != 1.0) return cudaErrorInvalidValue;
+  if (st.dword) {
+    if (prec != 0) return cudaErrorInvalidValue;
+    return launch_hydro_dw(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
+  }
   const int T = (m.nxb % 16 == 0) ? 16 : 8;
   if (prec == 0) {
     if (m.ndim == 3)

@@ -1,0 +1,62 @@
+// k_hydro_dw.cu -- the fused MUSCL-Hancock / HLLC update of FP64 block sets
+// computed in double-word arithmetic (dword.cuh): the state is read and
+// written in FP64, every operation of the tile body runs on pairs of FP32
+// numbers (about 2^-47 relative precision) on the FP32 pipe instead of the
+// FP64 one.  Selected per context with the option "f64_arith" = 1.
+//
+// Paper: Flash-X (arXiv 2208.11630), Section 2.2 (unsplit predictor-corrector
+// hydro) applied block by block (Section 2); the arithmetic is this GPU's
+// choice, not the paper's.
+#include "hydro_tile.cuh"
+
+namespace fx {
+namespace {
+
+template <int NDIM, int T>
+__global__ void __launch_bounds__(T *T, (T == 16 ? 2 : 6))
+k_hydro_dw(DevMesh m, const double *__restrict__ U, double *Unew, const int *__restrict__ leaves,
+           int tiles, const double *__restrict__ dtp, double *__restrict__ regs,
+           int *__restrict__ status, unsigned long long *__restrict__ smax_out,
+           const unsigned char *__restrict__ rmask, int cfl_form) {
+  const int tpb = tiles * tiles;
+  hydro_tile<NDIM, T, double, dw>(m, U, Unew, leaves[blockIdx.x / tpb], blockIdx.x % tpb, tiles,
+                                  *dtp, regs, status, smax_out, rmask, cfl_form);
+}
+
+template <int NDIM, int T>
+cudaError_t launch_dw_t(const DevMesh &m, const void *U, void *Unew, const int *leaves, int n,
+                        const double *dt, double *regs, int *status, unsigned long long *smax,
+                        const unsigned char *rmask, int form, cudaStream_t s) {
+  const int tiles = m.nxb / T;
+  const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(dw);
+  auto kern = k_hydro_dw<NDIM, T>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  kern<<<n * tiles * tiles, T * T, smem, s>>>(m, static_cast<const double *>(U),
+                                              static_cast<double *>(Unew), leaves, tiles, dt, regs,
+                                              status, smax, rmask, form);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_hydro_dw(const DevMesh &m, const void *U, void *Unew, const int *leaves, int n,
+                            const double *dt, double *regs, int *status,
+                            unsigned long long *smax, const unsigned char *rmask, int form,
+                            cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int T = (m.nxb % 16 == 0) ? 16 : 8;
+  if (m.ndim == 3)
+    return T == 16 ? launch_dw_t<3, 16>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
+                   : launch_dw_t<3, 8>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
+  return T == 16 ? launch_dw_t<2, 16>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
+                 : launch_dw_t<2, 8>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
+}
+
+}  // namespace fx

@@ -1,0 +1,106 @@
+"""GPU parity of the double-word update (fx_set_option "f64_arith" = 1).
+
+An FP64 block set updated in double-word arithmetic (pairs of FP32 numbers,
+about 2^-47 relative precision) is held to the same tolerances against the
+FP64 oracle as the FP64 update: 1e-12 relative per cell after one step, 1e-10
+after 100 steps.  The momentum components share one scale, the largest
+momentum magnitude (``max_rel_err_vec``): a component that vanishes over the
+whole domain, like m_z of the 3D shear layer after one step (at most 3e-4),
+would otherwise have its absolute roundoff judged against its own vanishing
+maximum.  A separate check shows that the mode is really in use (its result
+differs from the FP64 update's, by roundoff only).
+"""
+import numpy as np
+import pytest
+
+from tests.helpers import max_rel_err_vec
+from tests.test_parity_gpu import CASES, both_start
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+DW = {"f64_arith": 1}
+
+
+@pytest.fixture(scope="module")
+def fx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2208_11630_gb300 import fx as _fx
+    _fx.load()
+    return _fx
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_dword_one_step(orc, fx, case):
+    mesh, W = CASES[case]()
+    om, U, bs = both_start(orc, fx, mesh, W, options=DW)
+    bs.set_conserved(U)
+    Uo, dto = om.step(U)
+    bs.step(0.8)
+    assert bs.status() == 0
+    # the first dt comes from the FP64 reduction of the uploaded state
+    assert float(bs.dt.item()) == pytest.approx(dto, rel=1e-15)
+    err = max_rel_err_vec(mesh, bs.state(), Uo)
+    assert err <= 1e-12, err
+    bs.close()
+
+
+@pytest.mark.parametrize("case", ["sod2d", "kh64", "amr_sedov_small", "amr_3level_periodic",
+                                  "smooth3d_nxb32", "reflect3d_mixed", "amr_2d_reflect_wall"])
+def test_dword_100_steps(orc, fx, case):
+    mesh, W = CASES[case]()
+    om, U, bs = both_start(orc, fx, mesh, W, options=DW)
+    bs.set_conserved(U)
+    Uo, _, _ = om.run(U, nsteps=100)
+    bs.run(100, 0.8)
+    assert bs.status() == 0
+    err = max_rel_err_vec(mesh, bs.state(), Uo)
+    assert err <= 1e-10, err
+    bs.close()
+
+
+def test_dword_mode_is_in_use(orc, fx):
+    """Same start, one step each way: the double-word result is not the FP64
+    update's bit for bit, and the two agree to roundoff."""
+    mesh, W = CASES["kh64"]()
+    _, U, native = both_start(orc, fx, mesh, W)
+    _, _, dword = both_start(orc, fx, mesh, W, options=DW)
+    native.set_conserved(U)
+    dword.set_conserved(U)
+    native.step(0.8)
+    dword.step(0.8)
+    a, b = dword.state(), native.state()
+    assert not np.array_equal(mesh.interior(a), mesh.interior(b))
+    assert max_rel_err_vec(mesh, a, b) <= 1e-13
+    native.close()
+    dword.close()
+
+
+def test_dword_host_round_trip(fx):
+    """The overlapped host path (fx_run_host_interior) takes the option too:
+    its result equals stepping the same block set kind on the device."""
+    mesh, W = CASES["kh64"]()
+    bs = fx.BlockSet(mesh, 1.4, options=DW)
+    bs.set_primitive(W)
+    ref = fx.BlockSet(mesh, 1.4, options=DW)
+    ref.set_primitive(W)
+    host_in = torch.from_numpy(np.ascontiguousarray(mesh.interior(bs.state()))).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    bs.run_host_interior(host_in.numpy(), host_out.numpy(), 3, 0.8)
+    ref.run(3, 0.8)
+    assert np.array_equal(host_out.numpy(), mesh.interior(ref.state()))
+    bs.close()
+    ref.close()
+
+
+def test_dword_option_values(fx):
+    ctx = fx.fx_init(1.4, 16, 4)
+    try:
+        with pytest.raises(fx.FxError):
+            fx.fx_set_option(ctx, "f64_arith", 2)
+        fx.fx_set_option(ctx, "f64_arith", 1)
+        fx.fx_set_option(ctx, "f64_arith", 0)
+    finally:
+        fx.fx_finalize(ctx)
