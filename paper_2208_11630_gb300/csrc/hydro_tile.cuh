@@ -597,7 +597,38 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
           a = T; e = ff - T * T;
         }
         R WL[NF], WR[NF], F[NF];
-        if (!dir) {
+        if constexpr (std::is_same<R, dw>::value) {
+          // double-word tile: one inlined Riemann solver serves both
+          // directions (the y faces swap the u and v components), which
+          // keeps the kernel's code size down
+          R *sl = dir ? fyp + a * T + e : fxp + e * SM::W2 + a;
+          R *sr = dir ? fym + (a + 1) * T + e : fxm + e * SM::W2 + a + 1;
+          constexpr int VS = T * SM::W2;                 // component stride of all four arrays
+#pragma unroll
+          for (int v = 0; v < NF; ++v) {
+            WL[v] = sl[v * VS];
+            WR[v] = sr[v * VS];
+          }
+          if (dir) {
+            const R l1 = WL[1], r1 = WR[1];
+            WL[1] = WL[2]; WL[2] = l1;
+            WR[1] = WR[2]; WR[2] = r1;
+          }
+          hllc<0, R, NS>(WL, WR, g, igm1, m, F);
+          if (dir) {
+            const R f1 = F[1];
+            F[1] = F[2]; F[2] = f1;
+          }
+#pragma unroll
+          for (int v = 0; v < NF; ++v) sr[v * VS] = F[v];
+          const int o0 = dir ? y0 : x0;
+          if (reg && ((a == 0 && o0 == 0) || (a == T && o0 + T == n))) {
+            const int face = 2 * dir + (a == 0 ? 0 : 1);
+            const int t1 = (dir ? x0 : y0) + e, t2 = NDIM == 3 ? zglob : 0;
+#pragma unroll
+            for (int v = 0; v < NF; ++v) put_reg<RK>(reg[(face * NF + v) * nfc + t2 * n + t1], F[v], st);
+          }
+        } else if (!dir) {
 #pragma unroll
           for (int v = 0; v < NF; ++v) {
             WL[v] = fxp[v * T * SM::W2 + e * SM::W2 + a];
