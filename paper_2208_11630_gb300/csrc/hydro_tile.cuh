@@ -582,43 +582,52 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
     // ---- fluxes: x and y faces of inner planes (in place over the lower-face
     // state), z face below the thread's own cell
     const int zglob = p;  // interior z index of this plane
-    if (inner) {
-      for (int f = (tid + kFaceShift) % NT; f < 2 * (T + 1) * T; f += NT) {
-        const int dir = f >= (T + 1) * T;
-        const int ff = dir ? f - (T + 1) * T : f;
-        // a: face index along the normal (0..T), e: transverse index; the
-        // lanes of a warp take consecutive x so shared-memory rows stay
-        // contiguous for both directions
-        int a, e;
-        if (ff < T * T) {
-          if (!dir) { a = ff % T; e = ff / T; }
-          else { a = ff / T; e = ff % T; }
-        } else {
-          a = T; e = ff - T * T;
-        }
+    R Fz[NF];
+    if constexpr (std::is_same<R, dw>::value) {
+      // double-word tile: one inlined Riemann solver serves every face of the
+      // thread -- its x/y faces of inner planes, then its z face below -- with
+      // the normal velocity swapped into the x slot, to keep the code size down
+      constexpr int VS = T * SM::W2;                   // component stride of the face arrays
+      const int nxy = inner ? 2 * (T + 1) * T : 0;
+      int f = (tid + kFaceShift) % NT;
+      bool zpend = NDIM == 3 && p >= 0;
+      while (f < nxy || zpend) {
+        const bool zf = f >= nxy;
+        int dir = 2, a = 0, e = 0;
+        R *sr = nullptr;
         R WL[NF], WR[NF], F[NF];
-        if constexpr (std::is_same<R, dw>::value) {
-          // double-word tile: one inlined Riemann solver serves both
-          // directions (the y faces swap the u and v components), which
-          // keeps the kernel's code size down
-          R *sl = dir ? fyp + a * T + e : fxp + e * SM::W2 + a;
-          R *sr = dir ? fym + (a + 1) * T + e : fxm + e * SM::W2 + a + 1;
-          constexpr int VS = T * SM::W2;                 // component stride of all four arrays
+        if (!zf) {
+          dir = f >= (T + 1) * T;
+          const int ff = dir ? f - (T + 1) * T : f;
+          if (ff < T * T) {
+            if (!dir) { a = ff % T; e = ff / T; }
+            else { a = ff / T; e = ff % T; }
+          } else {
+            a = T; e = ff - T * T;
+          }
+          const R *sl = dir ? fyp + a * T + e : fxp + e * SM::W2 + a;
+          sr = dir ? fym + (a + 1) * T + e : fxm + e * SM::W2 + a + 1;
 #pragma unroll
           for (int v = 0; v < NF; ++v) {
             WL[v] = sl[v * VS];
             WR[v] = sr[v * VS];
           }
-          if (dir) {
-            const R l1 = WL[1], r1 = WR[1];
-            WL[1] = WL[2]; WL[2] = l1;
-            WR[1] = WR[2]; WR[2] = r1;
+        } else {
+#pragma unroll
+          for (int v = 0; v < NF; ++v) {
+            WL[v] = zprev[v];
+            WR[v] = zm[v];
           }
-          hllc<0, R, NS>(WL, WR, g, igm1, m, F);
-          if (dir) {
-            const R f1 = F[1];
-            F[1] = F[2]; F[2] = f1;
-          }
+        }
+        auto swap_normal = [&](R (&w)[NF]) {
+          if (dir == 1) { const R t = w[1]; w[1] = w[2]; w[2] = t; }
+          else if (dir == 2) { const R t = w[1]; w[1] = w[3]; w[3] = t; }
+        };
+        swap_normal(WL);
+        swap_normal(WR);
+        hllc<0, R, NS>(WL, WR, g, igm1, m, F);
+        swap_normal(F);
+        if (!zf) {
 #pragma unroll
           for (int v = 0; v < NF; ++v) sr[v * VS] = F[v];
           const int o0 = dir ? y0 : x0;
@@ -628,46 +637,74 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
 #pragma unroll
             for (int v = 0; v < NF; ++v) put_reg<RK>(reg[(face * NF + v) * nfc + t2 * n + t1], F[v], st);
           }
-        } else if (!dir) {
-#pragma unroll
-          for (int v = 0; v < NF; ++v) {
-            WL[v] = fxp[v * T * SM::W2 + e * SM::W2 + a];
-            WR[v] = fxm[v * T * SM::W2 + e * SM::W2 + a + 1];
-          }
-          hllc<0, R, NS>(WL, WR, g, igm1, m, F);
-#pragma unroll
-          for (int v = 0; v < NF; ++v) fxm[v * T * SM::W2 + e * SM::W2 + a + 1] = F[v];
-          if (reg && ((a == 0 && x0 == 0) || (a == T && x0 + T == n))) {
-            const int face = a == 0 ? 0 : 1;
-            const int t1 = y0 + e, t2 = NDIM == 3 ? zglob : 0;
-#pragma unroll
-            for (int v = 0; v < NF; ++v) put_reg<RK>(reg[(face * NF + v) * nfc + t2 * n + t1], F[v], st);
-          }
+          f += NT;
         } else {
 #pragma unroll
-          for (int v = 0; v < NF; ++v) {
-            WL[v] = fyp[v * SM::W2 * T + a * T + e];
-            WR[v] = fym[v * SM::W2 * T + (a + 1) * T + e];
+          for (int v = 0; v < NF; ++v) Fz[v] = F[v];
+          if (reg && (p == 0 || p == n)) {
+            const int face = p == 0 ? 4 : 5;
+#pragma unroll
+            for (int v = 0; v < NF; ++v) put_reg<RK>(reg[(face * NF + v) * nfc + (y0 + tj) * n + (x0 + ti)], Fz[v], st);
           }
-          hllc<1, R, NS>(WL, WR, g, igm1, m, F);
+          zpend = false;
+        }
+      }
+    } else {
+      if (inner) {
+        for (int f = (tid + kFaceShift) % NT; f < 2 * (T + 1) * T; f += NT) {
+          const int dir = f >= (T + 1) * T;
+          const int ff = dir ? f - (T + 1) * T : f;
+          // a: face index along the normal (0..T), e: transverse index; the
+          // lanes of a warp take consecutive x so shared-memory rows stay
+          // contiguous for both directions
+          int a, e;
+          if (ff < T * T) {
+            if (!dir) { a = ff % T; e = ff / T; }
+            else { a = ff / T; e = ff % T; }
+          } else {
+            a = T; e = ff - T * T;
+          }
+          R WL[NF], WR[NF], F[NF];
+          if (!dir) {
 #pragma unroll
-          for (int v = 0; v < NF; ++v) fym[v * SM::W2 * T + (a + 1) * T + e] = F[v];
-          if (reg && ((a == 0 && y0 == 0) || (a == T && y0 + T == n))) {
-            const int face = a == 0 ? 2 : 3;
-            const int t1 = x0 + e, t2 = NDIM == 3 ? zglob : 0;
+            for (int v = 0; v < NF; ++v) {
+              WL[v] = fxp[v * T * SM::W2 + e * SM::W2 + a];
+              WR[v] = fxm[v * T * SM::W2 + e * SM::W2 + a + 1];
+            }
+            hllc<0, R, NS>(WL, WR, g, igm1, m, F);
 #pragma unroll
-            for (int v = 0; v < NF; ++v) put_reg<RK>(reg[(face * NF + v) * nfc + t2 * n + t1], F[v], st);
+            for (int v = 0; v < NF; ++v) fxm[v * T * SM::W2 + e * SM::W2 + a + 1] = F[v];
+            if (reg && ((a == 0 && x0 == 0) || (a == T && x0 + T == n))) {
+              const int face = a == 0 ? 0 : 1;
+              const int t1 = y0 + e, t2 = NDIM == 3 ? zglob : 0;
+#pragma unroll
+              for (int v = 0; v < NF; ++v) put_reg<RK>(reg[(face * NF + v) * nfc + t2 * n + t1], F[v], st);
+            }
+          } else {
+#pragma unroll
+            for (int v = 0; v < NF; ++v) {
+              WL[v] = fyp[v * SM::W2 * T + a * T + e];
+              WR[v] = fym[v * SM::W2 * T + (a + 1) * T + e];
+            }
+            hllc<1, R, NS>(WL, WR, g, igm1, m, F);
+#pragma unroll
+            for (int v = 0; v < NF; ++v) fym[v * SM::W2 * T + (a + 1) * T + e] = F[v];
+            if (reg && ((a == 0 && y0 == 0) || (a == T && y0 + T == n))) {
+              const int face = a == 0 ? 2 : 3;
+              const int t1 = x0 + e, t2 = NDIM == 3 ? zglob : 0;
+#pragma unroll
+              for (int v = 0; v < NF; ++v) put_reg<RK>(reg[(face * NF + v) * nfc + t2 * n + t1], F[v], st);
+            }
           }
         }
       }
-    }
-    R Fz[NF];
-    if (NDIM == 3 && p >= 0) {
-      hllc<2, R, NS>(zprev, zm, g, igm1, m, Fz);
-      if (reg && (p == 0 || p == n)) {
-        const int face = p == 0 ? 4 : 5;
+      if (NDIM == 3 && p >= 0) {
+        hllc<2, R, NS>(zprev, zm, g, igm1, m, Fz);
+        if (reg && (p == 0 || p == n)) {
+          const int face = p == 0 ? 4 : 5;
 #pragma unroll
-        for (int v = 0; v < NF; ++v) put_reg<RK>(reg[(face * NF + v) * nfc + (y0 + tj) * n + (x0 + ti)], Fz[v], st);
+          for (int v = 0; v < NF; ++v) put_reg<RK>(reg[(face * NF + v) * nfc + (y0 + tj) * n + (x0 + ti)], Fz[v], st);
+        }
       }
     }
     __syncthreads();
