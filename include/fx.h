@@ -319,7 +319,9 @@ FX_API int fx_batch_create(fx_ctx *ctx, int max_requests, fx_batch **out);
 FX_API int fx_batch_destroy(fx_batch *b);
 /* fx_batch_add: add block set `bs` to advance `nsteps` steps with CFL number
  * `cfl` from its current state; *slot_out receives its slot.  It joins at the
- * next fx_batch_run (the graph is re-captured).  Synchronises `stream`. */
+ * next fx_batch_run (the graph is re-captured).  Synchronises `stream`.  The
+ * update of an FX_F64 block set whose context has "f64_arith" = 1 runs in
+ * double-word arithmetic inside the batch too (compute class 2 below). */
 FX_API int fx_batch_add(fx_batch *b, fx_blocks *bs, double cfl, int nsteps, void *stream,
                         int *slot_out);
 /* fx_batch_run: `nsteps` batched steps; every request with steps left
@@ -330,7 +332,7 @@ FX_API int fx_batch_poll(fx_batch *b, int *steps_left, void *stream);
 /* fx_batch_remove: release the block set in `slot` (cancelling it if steps
  * remain); its current buffer is whatever the batch produced.  Synchronises. */
 FX_API int fx_batch_remove(fx_batch *b, int slot, void *stream);
-/* fx_batch_tune: autotune the update launch of each (dimension, precision)
+/* fx_batch_tune: autotune the update launch of each (dimension, compute class)
  * group whose blocks allow 16x16 tiles: the tile edge (16 or 8) and the CTAs
  * per SM of the persistent kernel, by timing each candidate on a sample of
  * the batch's own work items with dt = 0 (after a coarse-fine guard fill;
@@ -340,7 +342,9 @@ FX_API int fx_batch_remove(fx_batch *b, int slot, void *stream);
  * microseconds per update of the group) triples, 0 terminated.
  * Synchronises. */
 FX_API int fx_batch_tune(fx_batch *b, void *stream, int *report);
-/* fx_batch_choice: the launch choice in use for a (ndim, precision) group. */
+/* fx_batch_choice: the launch choice in use for a (ndim, precision) group;
+ * precision is the update's compute class: FX_F64 (0), FX_F32BULK (1), or 2
+ * for FP64 block sets updated in double-word arithmetic. */
 FX_API int fx_batch_choice(const fx_batch *b, int ndim, int precision, int *tile,
                            int *ctas_per_sm);
 

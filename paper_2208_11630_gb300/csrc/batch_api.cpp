@@ -25,20 +25,28 @@ struct Range {
 };
 
 struct HydroGroup {
-  int ndim, tile, prec;
+  int ndim, tile, prec;   // prec: compute class (0 FP64, 1 FP32-bulk, 2 double-word)
   Range r;
   int ctas;   // CTAs per SM (0 = as many as fit)
 };
 
-// Tuned launch choice for one (ndim, precision) group of block sets whose
-// nxb allows 16x16 tiles: the tile edge and the CTAs per SM.
+// Tuned launch choice for one (ndim, compute class) group of block sets
+// whose nxb allows 16x16 tiles: the tile edge and the CTAs per SM.
 struct Choice {
   int tile = 16;
   int ctas = 0;
 };
 
-// (ndim, prec, SM count, mask of the 16-capable block edges in the group)
+// (ndim, compute class, SM count, mask of the 16-capable block edges in the group)
 std::map<std::tuple<int, int, int, int>, Choice> g_tune_cache;
+
+constexpr int kClasses = 3;
+
+// Compute class of a block set's update: its precision, or 2 for an FP64 set
+// whose context asks for double-word arithmetic.
+int compute_class(const fx_blocks *bs) {
+  return bs->prec == 0 && bs->ctx->f64_arith ? 2 : bs->prec;
+}
 
 }  // namespace
 
@@ -58,8 +66,8 @@ struct fx_batch {
   int lmax = 0;
   Range rst[2][FX_MAXLEV], cpy[2], pro[2][FX_MAXLEV], rfx[2];
   std::vector<HydroGroup> groups;
-  Choice choice[2][2];               // [ndim - 2][prec]
-  bool tuned[2][2] = {{false, false}, {false, false}};
+  Choice choice[2][kClasses];        // [ndim - 2][compute class]
+  bool tuned[2][kClasses] = {};
 };
 
 namespace {
@@ -67,7 +75,7 @@ namespace {
 constexpr int kMaxGroups = 8;
 
 // Work lists of the batched step for the current composition.
-int build_lists(fx_batch *b, const Choice (&ch)[2][2]) {
+int build_lists(fx_batch *b, const Choice (&ch)[2][kClasses]) {
   std::vector<int4> rst[2][FX_MAXLEV], cpy[2], pro[2][FX_MAXLEV], rfx[2];
   std::map<std::tuple<int, int, int>, std::vector<int4>> hyd;
   b->lmax = 0;
@@ -91,9 +99,10 @@ int build_lists(fx_batch *b, const Choice (&ch)[2][2]) {
       for (int k = 0; k < bs->PZ; ++k) cpy[pr].push_back(make_int4(r, L[bs->src_off + q], k, 0));
     for (int q = 0; q < bs->nrefl; ++q)
       for (int c = 0; c < chunks; ++c) rfx[pr].push_back(make_int4(r, q, c, chunks));
-    const int T = (n % 16 == 0) ? ch[nd - 2][pr].tile : 8;
+    const int hc = compute_class(bs);
+    const int T = (n % 16 == 0) ? ch[nd - 2][hc].tile : 8;
     const int tiles = n / T;
-    auto &H = hyd[std::make_tuple(nd, T, pr)];
+    auto &H = hyd[std::make_tuple(nd, T, hc)];
     for (int q = 0; q < bs->nleaves; ++q)
       for (int t = 0; t < tiles * tiles; ++t)
         H.push_back(make_int4(r, L[bs->leaves_off + q], t, tiles));
@@ -373,11 +382,12 @@ int fx_batch_tune(fx_batch *b, void *stream, int *report) {
   if (e != cudaSuccess) return cuda_fail(b->ctx, e, "tuning guard fill");
   int nrep = 0;
   for (int nd = 2; nd <= 3; ++nd)
-    for (int pr = 0; pr < 2; ++pr) {
+    for (int pr = 0; pr < kClasses; ++pr) {
       // is there a group of 16-capable block sets of this kind?
       int mask = 0;
       for (fx_blocks *bs : b->slot)
-        if (bs && bs->ndim == nd && bs->prec == pr && bs->nxb % 16 == 0) mask |= 1 << (bs->nxb / 16);
+        if (bs && bs->ndim == nd && compute_class(bs) == pr && bs->nxb % 16 == 0)
+          mask |= 1 << (bs->nxb / 16);
       if (!mask) continue;
       auto key = std::make_tuple(nd, pr, b->nsm, mask);
       auto hit = g_tune_cache.find(key);
@@ -393,9 +403,9 @@ int fx_batch_tune(fx_batch *b, void *stream, int *report) {
         e = fx::hydro_batch_fit(nd, tile, pr, &fit);
         if (e != cudaSuccess) break;
         for (int ctas = 1; ctas <= fit; ++ctas) {
-          Choice ch[2][2];
+          Choice ch[2][kClasses];
           for (int a = 0; a < 2; ++a)
-            for (int c = 0; c < 2; ++c) ch[a][c] = b->choice[a][c];
+            for (int c = 0; c < kClasses; ++c) ch[a][c] = b->choice[a][c];
           ch[nd - 2][pr].tile = tile;
           ch[nd - 2][pr].ctas = ctas;
           if (build_lists(b, ch)) break;
@@ -451,7 +461,7 @@ int fx_batch_tune(fx_batch *b, void *stream, int *report) {
 }
 
 int fx_batch_choice(const fx_batch *b, int ndim, int precision, int *tile, int *ctas_per_sm) {
-  if (!b || (ndim != 2 && ndim != 3) || (precision != 0 && precision != 1)) return FX_ERR_ARG;
+  if (!b || (ndim != 2 && ndim != 3) || precision < 0 || precision >= kClasses) return FX_ERR_ARG;
   if (tile) *tile = b->choice[ndim - 2][precision].tile;
   if (ctas_per_sm) *ctas_per_sm = b->choice[ndim - 2][precision].ctas;
   return FX_OK;

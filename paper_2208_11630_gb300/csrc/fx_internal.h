@@ -169,14 +169,19 @@ cudaError_t launch_signal_max(const DevMesh &m, const void *U, int prec, const i
                               int form, unsigned long long *max_out, unsigned long long *scratch,
                               cudaStream_t s, int accumulate = 0);
 // Occupancy of the batched hydro kernel (CTAs per SM), setting its shared
-// memory attribute on first use.
+// memory attribute on first use.  prec is the compute class of the update:
+// 0 FP64, 1 FP32-bulk, 2 FP64 state in double-word arithmetic.
 cudaError_t hydro_batch_fit(int ndim, int tile, int prec, int *fit);
+cudaError_t hydro_batch_fit_dw(int ndim, int tile, int *fit);
 
-// Batched persistent hydro kernel over (request, block, tile, tiles) items.
-// ctas_per_sm <= 0 means as many as fit.
+// Batched persistent hydro kernel over (request, block, tile, tiles) items
+// of one compute class (as above).  ctas_per_sm <= 0 means as many as fit.
 cudaError_t launch_hydro_batch(int ndim, int tile, int prec, const BatchReq *reqs,
                                const int4 *items, int nitems, unsigned int *counter,
                                int ctas_per_sm, int nsm, cudaStream_t s);
+cudaError_t launch_hydro_batch_dw(int ndim, int tile, const BatchReq *reqs, const int4 *items,
+                                  int nitems, unsigned int *counter, int ctas_per_sm, int nsm,
+                                  cudaStream_t s);
 
 // Host plan of a regrid (regrid.cpp): the new mesh sorted by (level, z, y,
 // x) and, per new block, (kind 0 keep / 1 new child, old block or old

@@ -5,7 +5,7 @@
 //
 // Paper: Flash-X (arXiv 2208.11630), Section 2.2 (unsplit predictor-corrector
 // hydro) applied block by block (Section 2).
-#include "hydro_tile.cuh"
+#include "hydro_batch.cuh"
 
 namespace fx {
 namespace {
@@ -19,30 +19,6 @@ k_hydro(DevMesh m, const S *__restrict__ U, S *Unew, const int *__restrict__ lea
   const int tpb = tiles * tiles;
   hydro_tile<NDIM, T, S, R>(m, U, Unew, leaves[blockIdx.x / tpb], blockIdx.x % tpb, tiles, *dtp,
                             regs, status, smax_out, rmask, cfl_form);
-}
-
-// Persistent batched kernel: the CTAs pull (request, leaf, tile) items from a
-// shared counter until the list is exhausted; items of finished requests are
-// skipped.  Each request brings its own mesh, buffers, dt and scratch.
-template <int NDIM, int T, typename S, typename R>
-__global__ void __launch_bounds__(T *T, (T == 16 ? (sizeof(R) == 4 ? 4 : 2) : 6))
-k_hydro_batch(const BatchReq *__restrict__ reqs, const int4 *__restrict__ items, int nitems,
-              unsigned int *__restrict__ counter) {
-  __shared__ int item_s;
-  for (;;) {
-    if (threadIdx.x == 0) item_s = (int)atomicAdd(counter, 1u);
-    __syncthreads();
-    const int it = item_s;
-    __syncthreads();
-    if (it >= nitems) return;
-    const int4 w = items[it];            // (request, block, tile, tiles per axis)
-    const BatchReq &r = reqs[w.x];
-    if (r.steps_left <= 0) continue;
-    const int c = r.cur;
-    hydro_tile<NDIM, T, S, R>(r.m, static_cast<const S *>(r.U[c]), static_cast<S *>(r.U[1 - c]),
-                              w.y, w.z, w.w, *r.dt, r.regs, r.status, r.scratch + 2, r.rmask,
-                              r.form);
-  }
 }
 
 template <int NDIM, int T, typename S, typename R>
@@ -65,43 +41,10 @@ cudaError_t launch_t(const DevMesh &m, const void *U, void *Unew, const int *lea
   return cudaGetLastError();
 }
 
-template <int NDIM, int T, typename S, typename R>
-cudaError_t launch_batch_t(const BatchReq *reqs, const int4 *items, int nitems,
-                           unsigned int *counter, int ctas_per_sm, int nsm, cudaStream_t s) {
-  const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(R);
-  auto kern = k_hydro_batch<NDIM, T, S, R>;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
-  int fit = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kern, T * T, smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = ctas_per_sm > 0 ? (ctas_per_sm < fit ? ctas_per_sm : fit) : fit;
-  if (per_sm < 1) per_sm = 1;
-  int grid = per_sm * nsm;
-  if (grid > nitems) grid = nitems;
-  if (grid < 1) return cudaSuccess;
-  kern<<<grid, T * T, smem, s>>>(reqs, items, nitems, counter);
-  count_launch();
-  return cudaGetLastError();
-}
-
-template <int NDIM, int T, typename S, typename R>
-cudaError_t fit_t(int *fit) {
-  const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(R);
-  auto kern = k_hydro_batch<NDIM, T, S, R>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(fit, kern, T * T, smem);
-}
-
 }  // namespace
 
 cudaError_t hydro_batch_fit(int ndim, int tile, int prec, int *fit) {
+  if (prec == 2) return hydro_batch_fit_dw(ndim, tile, fit);
   if (prec == 0) {
     if (ndim == 3) return tile == 16 ? fit_t<3, 16, double, double>(fit) : fit_t<3, 8, double, double>(fit);
     return tile == 16 ? fit_t<2, 16, double, double>(fit) : fit_t<2, 8, double, double>(fit);
@@ -114,6 +57,8 @@ cudaError_t launch_hydro_batch(int ndim, int tile, int prec, const BatchReq *req
                                const int4 *items, int nitems, unsigned int *counter,
                                int ctas_per_sm, int nsm, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
+  if (prec == 2)
+    return launch_hydro_batch_dw(ndim, tile, reqs, items, nitems, counter, ctas_per_sm, nsm, s);
   if (prec == 0) {
     if (ndim == 3)
       return tile == 16 ? launch_batch_t<3, 16, double, double>(reqs, items, nitems, counter, ctas_per_sm, nsm, s)
@@ -129,7 +74,7 @@ cudaError_t launch_hydro_batch(int ndim, int tile, int prec, const BatchReq *req
 }
 
 size_t hydro_smem_bytes(int ndim, int tile, int prec) {
-  const size_t el = prec == 0 ? sizeof(double) : sizeof(float);
+  const size_t el = prec == 1 ? sizeof(float) : sizeof(double);   // 2: double-words, 8 bytes
   const int np = ndim == 3 ? 3 : 1;
   return (tile == 16 ? Smem<16>::total(np) : Smem<8>::total(np)) * el;
 }

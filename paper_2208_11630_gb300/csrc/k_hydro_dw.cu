@@ -2,12 +2,13 @@
 // computed in double-word arithmetic (dword.cuh): the state is read and
 // written in FP64, every operation of the tile body runs on pairs of FP32
 // numbers (about 2^-47 relative precision) on the FP32 pipe instead of the
-// FP64 one.  Selected per context with the option "f64_arith" = 1.
+// FP64 one.  Selected per context with the option "f64_arith" = 1; the
+// per-block-set kernel and the batched persistent one (compute class 2).
 //
 // Paper: Flash-X (arXiv 2208.11630), Section 2.2 (unsplit predictor-corrector
 // hydro) applied block by block (Section 2); the arithmetic is this GPU's
 // choice, not the paper's.
-#include "hydro_tile.cuh"
+#include "hydro_batch.cuh"
 
 namespace fx {
 namespace {
@@ -57,6 +58,22 @@ cudaError_t launch_hydro_dw(const DevMesh &m, const void *U, void *Unew, const i
                    : launch_dw_t<3, 8>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
   return T == 16 ? launch_dw_t<2, 16>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
                  : launch_dw_t<2, 8>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
+}
+
+cudaError_t hydro_batch_fit_dw(int ndim, int tile, int *fit) {
+  if (ndim == 3) return tile == 16 ? fit_t<3, 16, double, dw>(fit) : fit_t<3, 8, double, dw>(fit);
+  return tile == 16 ? fit_t<2, 16, double, dw>(fit) : fit_t<2, 8, double, dw>(fit);
+}
+
+cudaError_t launch_hydro_batch_dw(int ndim, int tile, const BatchReq *reqs, const int4 *items,
+                                  int nitems, unsigned int *counter, int ctas_per_sm, int nsm,
+                                  cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  if (ndim == 3)
+    return tile == 16 ? launch_batch_t<3, 16, double, dw>(reqs, items, nitems, counter, ctas_per_sm, nsm, s)
+                      : launch_batch_t<3, 8, double, dw>(reqs, items, nitems, counter, ctas_per_sm, nsm, s);
+  return tile == 16 ? launch_batch_t<2, 16, double, dw>(reqs, items, nitems, counter, ctas_per_sm, nsm, s)
+                    : launch_batch_t<2, 8, double, dw>(reqs, items, nitems, counter, ctas_per_sm, nsm, s);
 }
 
 }  // namespace fx

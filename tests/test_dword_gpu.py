@@ -104,3 +104,51 @@ def test_dword_option_values(fx):
         fx.fx_set_option(ctx, "f64_arith", 0)
     finally:
         fx.fx_finalize(ctx)
+
+
+def test_dword_requests_in_a_batch(orc, fx):
+    """Double-word FP64 requests share a batch with FP64 and FP32-bulk ones:
+    each double-word request equals the same block set stepped alone (within
+    roundoff of the differently compiled batched kernel) and the oracle, the
+    FP64 request is untouched by its neighbours' mode, and the tuner picks a
+    launch for the double-word class."""
+    from paper_2208_11630_gb300 import inputs
+    from tests.test_batch_gpu import _cases
+    from tests.test_oracle_scheme import mesh_2level
+    by_name = {c[0]: c for c in _cases()}
+    m_sed = mesh_2level(4, 16, 4)
+    reqs = [  # (name, mesh, W, precision, steps, double-word)
+        ("kh_dw", *by_name["kh_f64"][1:3], 0, 7, True),
+        ("amr_dw", *by_name["amr_f64"][1:3], 0, 5, True),
+        ("sedov_dw", m_sed, inputs.sedov_state(m_sed), 0, 6, True),
+        ("kh_f64", *by_name["kh_f64"][1:3], 0, 7, False),
+        ("kh_f32", *by_name["kh_f32"][1:3], 1, 8, False),
+    ]
+    ctx = fx.fx_init(1.4, 16, 4)
+    batch = fx.Batch(ctx, 8)
+    sets, slots = [], []
+    for name, mesh, W, prec, k, dwm in reqs:
+        bs = fx.BlockSet(mesh, 1.4, precision=prec, options=DW if dwm else None)
+        bs.set_primitive(W)
+        slots.append(batch.add(bs, 0.8, k))
+        sets.append(bs)
+    batch.tune()
+    tile, ctas = batch.choice(3, 2)
+    assert tile in (8, 16) and ctas >= 1
+    batch.run(max(r[4] for r in reqs) + 1)
+    for (name, mesh, W, prec, k, dwm), bs, slot in zip(reqs, sets, slots):
+        batch.remove(slot)
+        assert bs.status() == 0, name
+        ref = fx.BlockSet(mesh, 1.4, precision=prec, options=DW if dwm else None)
+        ref.set_primitive(W)
+        ref.run(k, 0.8)
+        tol = 1e-5 if prec == 1 else 1e-12
+        assert max_rel_err_vec(mesh, bs.state(), ref.state()) <= tol, name
+        if prec == 0:
+            om = orc.OracleMesh(mesh)
+            Uo, _, _ = om.run(om.prim_to_cons(W), nsteps=k)
+            assert max_rel_err_vec(mesh, bs.state(), Uo) <= 1e-12, name
+        bs.close()
+        ref.close()
+    batch.close()
+    fx.fx_finalize(ctx)
