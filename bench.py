@@ -542,7 +542,9 @@ def run_ours(args):
 def run_serve(args):
     """Serving stream: capacity with every request present at t = 0, then
     Poisson streams at 0.5, 0.8 and 0.95 of that capacity (continuous
-    batching), and the plain per-request FP64 path on the 0.8 stream."""
+    batching), the plain per-request FP64 path on the 0.8 stream, and the
+    saturated and 0.8 streams again with the FP64 requests updated in
+    double-word arithmetic."""
     import torch
     from paper_2208_11630_gb300 import fx, serve
     ws, rank, local = dist_env()
@@ -566,6 +568,12 @@ def run_serve(args):
         runs[f"rate_{frac}"] = serve.serve(serve.with_arrivals(reqs, frac * cap), probs, budget)
     base = serve.serve_per_request(serve.with_arrivals(reqs, 0.8 * cap), probs,
                                    precision=fx.FX_F64)
+    # the same streams with the FP64 requests updated in double-word arithmetic
+    serve.serve(serve.with_arrivals(reqs, inf), probs, budget, realtime=False, f64_arith=1)
+    runs["saturated_f64_double_word"] = serve.serve(serve.with_arrivals(reqs, inf), probs, budget,
+                                                    realtime=False, f64_arith=1)
+    runs["rate_0.8_f64_double_word"] = serve.serve(serve.with_arrivals(reqs, 0.8 * cap), probs,
+                                                   budget, f64_arith=1)
     clk = clocks.stop()
     line = {"metric": "served zone-updates/s", "value": runs["rate_0.8"]["zone_updates_per_s"],
             "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "data": "synthetic",

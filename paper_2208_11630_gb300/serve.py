@@ -148,12 +148,15 @@ def _percentiles(reqs):
 
 
 def serve(reqs, problems, budget_bytes: float = 120e9, max_slots: int = 256, cfl: float = 0.8,
-          tune: bool = True, realtime: bool = True, keep=()):
+          tune: bool = True, realtime: bool = True, keep=(), f64_arith: int = 0):
     """Continuous batching.  Returns a stats dict; fills admitted/done/zones.
     Requests whose rid is in ``keep`` get their final state (host copy) in
-    ``req.extra["state"]``."""
+    ``req.extra["state"]``.  ``f64_arith`` = 1 updates the FP64 requests in
+    double-word arithmetic (fx_set_option "f64_arith")."""
     import torch
     ctx = fx.fx_init(1.4, 16, 4)
+    if f64_arith:
+        fx.fx_set_option(ctx, "f64_arith", f64_arith)
     batch = fx.Batch(ctx, max_slots)
     pending = deque(sorted(reqs, key=lambda r: r.arrival))
     active = {}
@@ -207,8 +210,8 @@ def serve(reqs, problems, budget_bytes: float = 120e9, max_slots: int = 256, cfl
                 used -= need
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        choices = {f"{nd}d_{'f64' if pr == 0 else 'f32bulk'}": batch.choice(nd, pr)
-                   for nd in (2, 3) for pr in (0, 1)}
+        choices = {f"{nd}d_{name}": batch.choice(nd, pr) for nd in (2, 3)
+                   for pr, name in ((0, "f64"), (1, "f32bulk"), (2, "f64_double_word"))}
     finally:
         batch.close()
         fx.fx_finalize(ctx)
