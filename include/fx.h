@@ -100,7 +100,7 @@ FX_API int fx_finalize(fx_ctx *ctx);
  *               correction, dt) is unchanged; results differ from the FP64
  *               update by the double-word rounding (about 1e-14 relative per
  *               step).  Ignored by FX_F32BULK, multispecies and SSP-RK
- *               stepping and by batches.
+ *               stepping; batches honour it per request (fx_batch_add).
  * Errors: FX_ERR_ARG for an unknown key or value. */
 FX_API int fx_set_option(fx_ctx *ctx, const char *key, double value);
 
