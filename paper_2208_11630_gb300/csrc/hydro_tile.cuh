@@ -21,11 +21,14 @@
 // fluxes in registers, so no z data touches shared memory.  Per plane: load
 // + primitives, predictor, fluxes, update, three barriers.
 //
-// Precision variants: FP64 state and arithmetic; or FP32-bulk -- FP32 state,
-// FP32 reconstruction and Riemann solver, and an update that adds to U the
-// exactly differenced fluxes (TwoSum) scaled by dt/dx with a single final
-// rounding, which matches an FP64 accumulation up to a fraction of an FP32
-// ulp at a tiny fraction of the cost of FP64 arithmetic on this GPU.
+// Precision variants (state type S, compute type R): FP64 state and
+// arithmetic; FP32-bulk -- FP32 state, FP32 reconstruction and Riemann
+// solver, and an update that adds to U the exactly differenced fluxes
+// (TwoSum) scaled by dt/dx with a single final rounding, which matches an
+// FP64 accumulation up to a fraction of an FP32 ulp at a tiny fraction of the
+// cost of FP64 arithmetic on this GPU; or FP64 state with double-word
+// arithmetic (R = dw, dword.cuh), where one inlined Riemann solver serves all
+// faces of a thread to keep the much larger code within instruction fetch.
 #pragma once
 
 #include "dword.cuh"
