@@ -91,7 +91,7 @@ FX_API int fx_finalize(fx_ctx *ctx);
  *               of U2, U <- 1/3 U + 2/3 (U2 + dt L(U2)), flux correction with
  *               the fluxes weighted 1/6, 1/6, 2/3.  Batches accept only
  *               integrator 0;
- *   "f64_arith" 0 = the MUSCL-Hancock update of FX_F64 block sets runs in
+ *   "f64_arith" 0 = the update of FX_F64 block sets runs in
  *               FP64 arithmetic (default); 1 = in double-word arithmetic:
  *               each value an unevaluated sum of two FP32 numbers (48
  *               significant bits, relative precision near 2^-47, FP32
@@ -99,7 +99,8 @@ FX_API int fx_finalize(fx_ctx *ctx);
  *               every other kernel (guard fill, prolongation, flux
  *               correction, dt) is unchanged; results differ from the FP64
  *               update by the double-word rounding (about 1e-14 relative per
- *               step).  Ignored by FX_F32BULK, multispecies and SSP-RK
+ *               step).  Applies to the MUSCL-Hancock update and to the
+ *               SSP-RK stages; ignored by FX_F32BULK and multispecies
  *               stepping; batches honour it per request (fx_batch_add).
  * Errors: FX_ERR_ARG for an unknown key or value. */
 FX_API int fx_set_option(fx_ctx *ctx, const char *key, double value);

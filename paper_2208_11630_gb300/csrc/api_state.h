@@ -91,7 +91,8 @@ int cuda_fail(fx_ctx *ctx, cudaError_t e, const char *where);
 
 // Returns FX_ERR_CUDA from the enclosing entry point (whose block set is bs)
 // when call does not succeed.
-// The stage of a MUSCL-Hancock update of block set bs under context ctx.
+// The stage of a MUSCL-Hancock update of block set bs under context ctx
+// (also the base of the SSP-RK stages): the arithmetic of its update.
 inline fx::HydroStage muscl_stage(const fx_ctx *ctx, const fx_blocks *bs) {
   fx::HydroStage st;
   st.dword = ctx->f64_arith && bs->prec == 0;

@@ -550,7 +550,7 @@ int fx_hydro_advance(fx_ctx *ctx, fx_blocks *bs, const double *dt_dev, void *str
       }
       FX_CUDA(cudaMemsetAsync(bs->d_U3, 0, bytes, s), "stage buffer clear");
     }
-    fx::HydroStage s1, s2, s3;
+    fx::HydroStage s1 = muscl_stage(ctx, bs), s2 = s1, s3 = s1;   // arithmetic (f64_arith)
     s1.pred = 0; s1.reg_w = rk3 ? 1.0 / 6.0 : 0.5;
     s2.pred = 0; s2.Uavg = Uo; s2.reg_add = 1;
     if (rk3) { s2.wa = 0.75; s2.wb = 0.25; s2.reg_w = 1.0 / 6.0; }

@@ -89,8 +89,13 @@ cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, 
     return launch_hydro_species(m, U, Unew, prec, leaves, n, dt, regs, status, smax, rmask, form,
                                 s);
   }
-  if (!st.pred)     // an SSP Runge-Kutta stage (k_hydro_rk.cu)
+  if (!st.pred) {   // an SSP Runge-Kutta stage (k_hydro_rk.cu; double-word: k_hydro_dw.cu)
+    if (st.dword) {
+      if (prec != 0) return cudaErrorInvalidValue;
+      return launch_hydro_rk_dw(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, st);
+    }
     return launch_hydro_rk(m, U, Unew, prec, leaves, n, dt, regs, status, smax, rmask, form, s, st);
+  }
   if (st.Uavg || st.reg_add || st.reg_w != 1.0) return cudaErrorInvalidValue;
   if (st.dword) {
     if (prec != 0) return cudaErrorInvalidValue;

@@ -45,7 +45,56 @@ cudaError_t launch_dw_t(const DevMesh &m, const void *U, void *Unew, const int *
   return cudaGetLastError();
 }
 
+// SSP Runge-Kutta stage in double-word arithmetic (plain PLM face states,
+// stage blend and weighted registers as in k_hydro_rk.cu).
+template <int NDIM, int T>
+__global__ void __launch_bounds__(T *T, (T == 16 ? 2 : 6))
+k_hydro_rk_dw(DevMesh m, const double *__restrict__ U, double *Unew,
+              const int *__restrict__ leaves, int tiles, const double *__restrict__ dtp,
+              double *__restrict__ regs, int *__restrict__ status,
+              unsigned long long *__restrict__ smax_out, const unsigned char *__restrict__ rmask,
+              int cfl_form, HydroStage st) {
+  const int tpb = tiles * tiles;
+  hydro_tile<NDIM, T, double, dw, true>(m, U, Unew, leaves[blockIdx.x / tpb], blockIdx.x % tpb,
+                                        tiles, *dtp, regs, status, smax_out, rmask, cfl_form, st);
+}
+
+template <int NDIM, int T>
+cudaError_t launch_rk_dw_t(const DevMesh &m, const void *U, void *Unew, const int *leaves, int n,
+                           const double *dt, double *regs, int *status, unsigned long long *smax,
+                           const unsigned char *rmask, int form, const HydroStage &st,
+                           cudaStream_t s) {
+  const int tiles = m.nxb / T;
+  const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(dw);
+  auto kern = k_hydro_rk_dw<NDIM, T>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  kern<<<n * tiles * tiles, T * T, smem, s>>>(m, static_cast<const double *>(U),
+                                              static_cast<double *>(Unew), leaves, tiles, dt, regs,
+                                              status, smax, rmask, form, st);
+  count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_hydro_rk_dw(const DevMesh &m, const void *U, void *Unew, const int *leaves,
+                               int n, const double *dt, double *regs, int *status,
+                               unsigned long long *smax, const unsigned char *rmask, int form,
+                               cudaStream_t s, const HydroStage &st) {
+  if (n <= 0) return cudaSuccess;
+  const int T = (m.nxb % 16 == 0) ? 16 : 8;
+  if (m.ndim == 3)
+    return T == 16 ? launch_rk_dw_t<3, 16>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, st, s)
+                   : launch_rk_dw_t<3, 8>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, st, s);
+  return T == 16 ? launch_rk_dw_t<2, 16>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, st, s)
+                 : launch_rk_dw_t<2, 8>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, st, s);
+}
 
 cudaError_t launch_hydro_dw(const DevMesh &m, const void *U, void *Unew, const int *leaves, int n,
                             const double *dt, double *regs, int *status,

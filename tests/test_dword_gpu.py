@@ -152,3 +152,23 @@ def test_dword_requests_in_a_batch(orc, fx):
         ref.close()
     batch.close()
     fx.fx_finalize(ctx)
+
+
+@pytest.mark.parametrize("integrator", [1, 2])
+@pytest.mark.parametrize("case", ["sod2d", "kh64", "amr_sedov_small", "amr_2d_reflect_wall"])
+def test_dword_ssp_rk(orc, fx, case, integrator):
+    """SSP-RK2 / SSP-RK3 stages in double-word arithmetic against the oracle's
+    integrator: one step at 1e-12, thirty more at 1e-10."""
+    mesh, W = CASES[case]()
+    om, U, bs = both_start(orc, fx, mesh, W, options={"integrator": integrator, **DW})
+    bs.set_conserved(U)
+    Uo, dto = om.step(U, integrator=integrator)
+    bs.step(0.8)
+    assert bs.status() == 0
+    assert float(bs.dt.item()) == pytest.approx(dto, rel=1e-15)
+    assert max_rel_err_vec(mesh, bs.state(), Uo) <= 1e-12
+    Uo2, _, _ = om.run(Uo, nsteps=30, integrator=integrator)
+    bs.run(30, 0.8)
+    assert bs.status() == 0
+    assert max_rel_err_vec(mesh, bs.state(), Uo2) <= 1e-10
+    bs.close()
