@@ -290,31 +290,33 @@ def measure_variants(args, fx, inputs, mesh, dev, cfl, zones, bs, ws, hbm_peak):
         else:
             W4[b4, 5, 0, g4:g4 + n4, g4:g4 + n4] = inner[0]
             W4[b4, 6, 0, g4:g4 + n4, g4:g4 + n4] = 1.0 - inner[0]
-    bs4 = fx.BlockSet(mesh4, gamma, precision=fx.FX_F64, device=dev)
-    bs4.set_primitive(W4)
+    # FP64 arithmetic, then the same in double-word arithmetic (f64_arith = 1)
+    for key4, opts4 in (("multispecies_2", None), ("multispecies_2_double_word", {"f64_arith": 1})):
+        bs4 = fx.BlockSet(mesh4, gamma, precision=fx.FX_F64, device=dev, options=opts4)
+        bs4.set_primitive(W4)
+        dtp4 = bs4.dt.data_ptr()
+        for _ in range(args.warmup):
+            fx.fx_step(bs4.ctx, bs4.bs, cfl, dtp4, sptr)
+        stream.synchronize()
+        ev4 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        a.record(stream)
+        for k in range(args.steps):
+            fx.fx_compute_dt(bs4.ctx, bs4.bs, cfl, dtp4, sptr)
+            fx.fx_guardcell_fill_amr(bs4.ctx, bs4.bs, sptr)
+            ev4[k][0].record(stream)
+            fx.fx_hydro_advance(bs4.ctx, bs4.bs, dtp4, sptr)
+            ev4[k][1].record(stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(b) / 1e3
+        hyd4 = float(np.mean([x.elapsed_time(y) for x, y in ev4])) / 1e3
+        z, t = aggregate(zones * args.steps, sec, dev)
+        out[key4] = {"value": z / t, "unit": UNIT, "ms_per_step": 1e3 * t / args.steps,
+                     "dtype": "f64" if opts4 is None else "f64 state, double-word (2 x f32) arithmetic",
+                     "nspec": 2, "hydro_ms": hyd4 * 1e3, "ok": bs4.status() == 0}
+        bs4.close()
     del W4
-    dtp4 = bs4.dt.data_ptr()
-    for _ in range(args.warmup):
-        fx.fx_step(bs4.ctx, bs4.bs, cfl, dtp4, sptr)
-    stream.synchronize()
-    ev4 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    a.record(stream)
-    for k in range(args.steps):
-        fx.fx_compute_dt(bs4.ctx, bs4.bs, cfl, dtp4, sptr)
-        fx.fx_guardcell_fill_amr(bs4.ctx, bs4.bs, sptr)
-        ev4[k][0].record(stream)
-        fx.fx_hydro_advance(bs4.ctx, bs4.bs, dtp4, sptr)
-        ev4[k][1].record(stream)
-    b.record(stream)
-    torch.cuda.synchronize()
-    sec = a.elapsed_time(b) / 1e3
-    hyd4 = float(np.mean([x.elapsed_time(y) for x, y in ev4])) / 1e3
-    z, t = aggregate(zones * args.steps, sec, dev)
-    out["multispecies_2"] = {"value": z / t, "unit": UNIT, "ms_per_step": 1e3 * t / args.steps,
-                             "dtype": "f64", "nspec": 2, "hydro_ms": hyd4 * 1e3,
-                             "ok": bs4.status() == 0}
-    bs4.close()
     # (iii) dynamic AMR: the Sedov blast on its 2-level mesh, regridded every
     # 4 steps (Loehner indicator on density and pressure, up to level 2);
     # wall-clock time between synchronisations, since the plan runs on the host

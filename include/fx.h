@@ -99,9 +99,9 @@ FX_API int fx_finalize(fx_ctx *ctx);
  *               every other kernel (guard fill, prolongation, flux
  *               correction, dt) is unchanged; results differ from the FP64
  *               update by the double-word rounding (about 1e-14 relative per
- *               step).  Applies to the MUSCL-Hancock update and to the
- *               SSP-RK stages; ignored by FX_F32BULK and multispecies
- *               stepping; batches honour it per request (fx_batch_add).
+ *               step).  Applies to the single-gas and multispecies
+ *               MUSCL-Hancock updates and to the SSP-RK stages; ignored by
+ *               FX_F32BULK; batches honour it per request (fx_batch_add).
  * Errors: FX_ERR_ARG for an unknown key or value. */
 FX_API int fx_set_option(fx_ctx *ctx, const char *key, double value);
 

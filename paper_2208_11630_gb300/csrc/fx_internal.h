@@ -110,12 +110,17 @@ struct HydroStage {
 // smax (may be null): receives atomicMax of the bit patterns of the new
 // state's CFL signal speeds (form 0 = sum over directions, 1 = max); cells on
 // the faces flagged in rmask[block] (bit 2d+s) are left to the reflux kernel.
-// The MUSCL-Hancock update and the SSP-RK stages of an FP64 block set in
-// double-word arithmetic (k_hydro_dw.cu).
+// The MUSCL-Hancock update, the multispecies update and the SSP-RK stages
+// of an FP64 block set in double-word arithmetic (k_hydro_dw.cu,
+// k_hydro_sp_dw.cu).
 cudaError_t launch_hydro_dw(const DevMesh &m, const void *U, void *Unew, const int *leaves, int n,
                             const double *dt, double *regs, int *status,
                             unsigned long long *smax, const unsigned char *rmask, int form,
                             cudaStream_t s);
+cudaError_t launch_hydro_species_dw(const DevMesh &m, const void *U, void *Unew,
+                                    const int *leaves, int n, const double *dt, double *regs,
+                                    int *status, unsigned long long *smax,
+                                    const unsigned char *rmask, int form, cudaStream_t s);
 cudaError_t launch_hydro_rk_dw(const DevMesh &m, const void *U, void *Unew, const int *leaves,
                                int n, const double *dt, double *regs, int *status,
                                unsigned long long *smax, const unsigned char *rmask, int form,

@@ -86,6 +86,10 @@ cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, 
   if (n <= 0) return cudaSuccess;
   if (m.nspec > 0) {   // multispecies gas (k_hydro_sp.cu): MUSCL-Hancock only
     if (!st.pred || st.Uavg || st.reg_add || st.reg_w != 1.0) return cudaErrorInvalidValue;
+    if (st.dword) {
+      if (prec != 0) return cudaErrorInvalidValue;
+      return launch_hydro_species_dw(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
+    }
     return launch_hydro_species(m, U, Unew, prec, leaves, n, dt, regs, status, smax, rmask, form,
                                 s);
   }

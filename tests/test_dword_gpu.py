@@ -172,3 +172,26 @@ def test_dword_ssp_rk(orc, fx, case, integrator):
     assert bs.status() == 0
     assert max_rel_err_vec(mesh, bs.state(), Uo2) <= 1e-10
     bs.close()
+
+
+@pytest.mark.parametrize("case", ["smooth3d_2sp", "amr_3sp", "blocky2d_4sp",
+                                  "smooth3d_1sp_nxb8"])
+def test_dword_species(orc, fx, case):
+    """The multispecies update in double-word arithmetic against the oracle:
+    one step at 1e-12, twenty more at 1e-10."""
+    from tests.test_species_gpu import CASES as SP_CASES
+    mesh, W = SP_CASES[case]()
+    om = orc.OracleMesh(mesh)
+    U = om.prim_to_cons(W)
+    bs = fx.BlockSet(mesh, 1.4, options=DW)
+    bs.set_conserved(U)
+    Uo, dto = om.step(U)
+    bs.step(0.8)
+    assert bs.status() == 0
+    assert float(bs.dt.item()) == pytest.approx(dto, rel=1e-15)
+    assert max_rel_err_vec(mesh, bs.state(), Uo) <= 1e-12
+    Uo2, _, _ = om.run(Uo, nsteps=20)
+    bs.run(20, 0.8)
+    assert bs.status() == 0
+    assert max_rel_err_vec(mesh, bs.state(), Uo2) <= 1e-10
+    bs.close()
