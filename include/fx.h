@@ -380,6 +380,17 @@ FX_API int fx_compute_dt_noalloc(const double *U_dev, int ndim, int nblocks, int
  * the process so far (all contexts).  Diagnostics for benchmarks. */
 FX_API long long fx_kernel_launches(void);
 
+/* fx_dword_selftest: apply one operation of the double-word arithmetic of
+ * the "f64_arith" option element by element, for testing it against FP64:
+ * out[i] = op(a[i], b[i]) with both inputs converted to double-words and the
+ * result converted back.  op: 0 a + b, 1 a - b, 2 a * b, 3 a / b, 4 sqrt(a),
+ * 5 1/sqrt(a), 6 a (the conversion round trip), 7 fma(a, b, a).  a_dev,
+ * b_dev, out_dev: caller-owned device arrays of n doubles (b_dev unused by
+ * ops 4-6).  Asynchronous on `stream`.
+ * Errors: FX_ERR_ARG for a bad op, n < 0 or a null array; FX_ERR_CUDA. */
+FX_API int fx_dword_selftest(int op, const double *a_dev, const double *b_dev, double *out_dev,
+                             int n, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -677,6 +677,15 @@ int fx_status(fx_ctx *ctx, fx_blocks *bs) {
 
 long long fx_kernel_launches(void) { return fx::launch_count(); }
 
+int fx_dword_selftest(int op, const double *a_dev, const double *b_dev, double *out_dev, int n,
+                      void *stream) {
+  if (op < 0 || op > 7 || n < 0 || !a_dev || !out_dev || ((op <= 3 || op == 7) && !b_dev))
+    return FX_ERR_ARG;
+  return fx::launch_dword_test(op, a_dev, b_dev, out_dev, n, (cudaStream_t)stream) == cudaSuccess
+             ? FX_OK
+             : FX_ERR_CUDA;
+}
+
 const double *fx_block_fluxes(const fx_blocks *bs, int b) {
   if (!bs || b < 0 || b >= bs->nb || bs->regidx[b] < 0 || !bs->d_regs) return nullptr;
   const int nfc = bs->ndim == 3 ? bs->nxb * bs->nxb : bs->nxb;

@@ -205,6 +205,10 @@ int regrid_plan(int ndim, int nxb, const int nroot[3], const int bc[6], int nb,
                 const std::vector<int> &parent, const std::vector<double> &err, double rc,
                 double dc, int max_level, RegridPlan *out, std::string *msg);
 
+// Element-wise double-word operation for fx_dword_selftest (k_dword_test.cu).
+cudaError_t launch_dword_test(int op, const double *a, const double *b, double *out, int n,
+                              cudaStream_t s);
+
 // Process-wide count of kernels launched by the library.
 void count_launch(int n = 1);
 long long launch_count();

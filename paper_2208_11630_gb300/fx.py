@@ -81,6 +81,7 @@ def load(build: bool = True):
             "fx_regrid_apply": (c_int, [vp, vp, vp, vp, vp]),
             "fx_block_fluxes": (vp, [vp, c_int]),
             "fx_kernel_launches": (ctypes.c_longlong, []),
+            "fx_dword_selftest": (c_int, [c_int, vp, vp, vp, c_int, vp]),
             "fx_batch_create": (c_int, [vp, c_int, ctypes.POINTER(vp)]),
             "fx_batch_destroy": (c_int, [vp]),
             "fx_batch_add": (c_int, [vp, vp, c_double, c_int, vp, ip]),
@@ -311,6 +312,19 @@ class Batch:
         _check(self.ctx, load().fx_batch_choice(self.h, int(ndim), int(precision), ctypes.byref(t),
                                                 ctypes.byref(c)))
         return t.value, c.value
+
+
+def fx_dword_selftest(op: int, a, b=None, stream=None):
+    """One double-word operation element by element on device tensors of
+    doubles (fx_dword_selftest); returns the result tensor."""
+    import torch
+    out = torch.empty_like(a)
+    bp = b.data_ptr() if b is not None else None
+    rc = load().fx_dword_selftest(int(op), a.data_ptr(), bp, out.data_ptr(), int(a.numel()),
+                                  _stream_ptr(stream))
+    if rc != FX_OK:
+        raise FxError(rc, "fx_dword_selftest")
+    return out
 
 
 # ---------------------------------------------------------------- convenience

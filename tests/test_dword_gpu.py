@@ -195,3 +195,39 @@ def test_dword_species(orc, fx, case):
     assert bs.status() == 0
     assert max_rel_err_vec(mesh, bs.state(), Uo2) <= 1e-10
     bs.close()
+
+
+def test_dword_operations_within_their_bounds(fx):
+    """Each double-word operation against FP64 on 2^18 random operands with
+    magnitudes log-uniform over 1e-15..1e15 and both signs: the error of the
+    result, relative to the scale the operation's bound refers to, stays
+    within a few units of 2^-47 (the conversion within 2^-48)."""
+    rng = np.random.default_rng(2024)
+    n = 1 << 18
+
+    def draw(signed=True):
+        x = 10.0 ** rng.uniform(-15, 15, n)
+        return x * (rng.choice([-1.0, 1.0], n) if signed else 1.0)
+
+    a, b, pos = draw(), draw(), draw(signed=False)
+    dev = lambda x: torch.from_numpy(x).cuda()
+    run = lambda op, x, y=None: fx.fx_dword_selftest(op, dev(x), None if y is None else dev(y)).cpu().numpy()
+    u = 2.0 ** -47
+    checks = [  # op, inputs, exact (FP64) result, scale of the bound, bound in units of u
+        (6, (a,), a, np.abs(a), 0.5),
+        (0, (a, b), a + b, np.abs(a) + np.abs(b), 4),
+        (1, (a, b), a - b, np.abs(a) + np.abs(b), 4),
+        (2, (a, b), a * b, np.abs(a * b), 4),
+        (3, (a, b), a / b, np.abs(a / b), 16),
+        (4, (pos,), np.sqrt(pos), np.sqrt(pos), 4),
+        (5, (pos,), 1.0 / np.sqrt(pos), 1.0 / np.sqrt(pos), 8),
+        (7, (a, b), a * b + a, np.abs(a * b) + np.abs(a), 8),
+    ]
+    for op, args, exact, scale, k in checks:
+        got = run(op, *args)
+        err = np.abs(got - exact) / scale
+        print(f"op {op}: max error {err.max() / u:.3f} x 2^-47 (bound {k})")
+        # FP64's own rounding of the reference is 2^-53, far inside the bound
+        assert err.max() <= k * u, (op, err.max() / u)
+    with pytest.raises(fx.FxError):
+        fx.fx_dword_selftest(9, dev(a), dev(b))
