@@ -133,18 +133,14 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 
 def oracle_sample(workload: str, target_s: float = 12.0, max_steps: int = 50):
-    """Time the FP64 oracle, as it is, on a bounded sample of the workload:
-    the same block size, physics and boundaries on 4^3 blocks (64^3 cells),
-    full steps (dt, guard fill, update) on all host cores."""
+    """Time the FP64 oracle, as it is, on a bounded sample of the workload
+    (REFERENCE_SAMPLE_SCALE: the same block size, physics and boundaries on
+    fewer blocks), full steps (dt, guard fill, update) on all host cores."""
     import oracle
     from paper_2208_11630_gb300 import inputs
-    if workload == "kh3d":
-        mesh = inputs.uniform_mesh(3, (4, 4, 4), 16, 4, inputs.PERIODIC)
-        W = inputs.kh_state(mesh)
-        desc = "KH shear layer, 64^3 cells as 4^3 blocks of 16^3 (+4 guard), periodic"
-    else:
-        mesh, W, _, _ = inputs.workload(workload, scale=None if workload != "advection3d" else 4)
-        desc = f"{workload} sample"
+    mesh, W, _, _ = inputs.workload(workload, scale=REFERENCE_SAMPLE_SCALE.get(workload))
+    desc = (f"FP64 CPU oracle on {workload_name(workload, mesh)} ({mesh.nb} blocks of "
+            f"{mesh.nxb}^{mesh.ndim} + {mesh.ng} guard), the same workload at a bounded size")
     om = oracle.OracleMesh(mesh, 1.4)
     U = om.prim_to_cons(W)
     zones = mesh.leaf_zones()
@@ -350,6 +346,17 @@ def measure_variants(args, fx, inputs, mesh, dev, cfl, zones, bs, ws, hbm_peak):
     return out
 
 
+def workload_name(name, mesh):
+    edge = mesh.nroot[0] * mesh.nxb
+    return {"kh3d": f"kh3d_{edge}^3", "advection3d": f"advection3d_{edge}^3",
+            "sod2d": f"sod2d_{edge}^2", "sedov_amr": f"sedov_amr_{edge}^3_base_2level"}.get(name, name)
+
+
+# bounded sample of each workload that the oracle steps on the host cores
+# (blocks per axis of the sample; sod2d runs whole)
+REFERENCE_SAMPLE_SCALE = {"kh3d": 4, "advection3d": 4, "sedov_amr": 4, "sod2d": None}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -357,9 +364,11 @@ def run_reference(args):
     import oracle
     from paper_2208_11630_gb300 import inputs
     oracle.build()
-    mesh = inputs.uniform_mesh(3, (4, 4, 4), 16, 4, inputs.PERIODIC)
-    om = oracle.OracleMesh(mesh, 1.4)
-    U = om.prim_to_cons(inputs.kh_state(mesh))
+    # the line carries the GPU arm's configuration; the oracle steps a sample
+    full = inputs.workload_mesh(args.workload, args.scale)
+    mesh, W, gamma, _ = inputs.workload(args.workload, scale=REFERENCE_SAMPLE_SCALE[args.workload])
+    om = oracle.OracleMesh(mesh, gamma)
+    U = om.prim_to_cons(W)
     zones = mesh.leaf_zones()
     for _ in range(args.warmup):
         U, _ = om.step(U)
@@ -368,13 +377,14 @@ def run_reference(args):
         U, _ = om.step(U)
     sec = time.perf_counter() - t0
     v = zones * args.steps / sec
-    sample = ("FP64 CPU oracle, KH shear layer 64^3 cells as 4^3 blocks of 16^3 (+4 guard), "
-              f"periodic; each step one full step of that sample; {args.steps} steps")
+    sample = (f"FP64 CPU oracle on {workload_name(args.workload, mesh)} ({mesh.nb} blocks of "
+              f"{mesh.nxb}^{mesh.ndim} + {mesh.ng} guard), the same workload at a bounded size; "
+              f"each step one full step of that sample; {args.steps} steps")
     line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args, "kh3d_64^3_sample"),
+            "config": workload_config(args, workload_name(args.workload, full), full) | {"replicas": 1},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.get_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -382,10 +392,7 @@ def run_reference(args):
     return 0
 
 
-def workload_config(args, name, mesh=None):
-    if mesh is None:
-        return {"workload": name, "blocks": 64, "nxb": 16, "nguard": 4, "cells": 64 ** 3,
-                "bc": "periodic", "cfl": 0.8, "precision": args.precision}
+def workload_config(args, name, mesh):
     state_bytes = mesh.nb * mesh.nvar * mesh.PZ * mesh.P * mesh.P * (8 if args.precision == "f64" else 4)
     bc = "periodic" if mesh.bc[0][0] == 1 else "outflow"
     return {"workload": name, "blocks": mesh.nb, "leaf_blocks": int(mesh.is_leaf().sum()),
@@ -416,10 +423,7 @@ def run_ours(args):
     prec = fx.FX_F64 if args.precision == "f64" else fx.FX_F32BULK
     mesh, W, gamma, cfl = inputs.workload(args.workload, scale=args.scale)
     zones_per_step = mesh.leaf_zones()
-    edge = mesh.nroot[0] * mesh.nxb
-    wname = {"kh3d": f"kh3d_{edge}^3", "advection3d": f"advection3d_{edge}^3",
-             "sod2d": f"sod2d_{edge}^2", "sedov_amr": f"sedov_amr_{edge}^3_base_2level"}.get(
-                 args.workload, args.workload)
+    wname = workload_name(args.workload, mesh)
     kname = f"k_hydro<{mesh.ndim},{16 if mesh.nxb % 16 == 0 else 8},{'double' if prec == 0 else 'float'}>"
     bs = fx.BlockSet(mesh, gamma, precision=prec, device=dev)
     bs.set_primitive(W)

@@ -394,6 +394,22 @@ def random_blocky_state(mesh: Mesh, seed: int = 11) -> np.ndarray:
 # named workloads
 # ----------------------------------------------------------------------------
 
+def workload_mesh(name: str, scale: int | None = None) -> Mesh:
+    """The mesh of a named workload (see ``workload``), without its state."""
+    if name == "sod2d":
+        n = scale or 8
+        return uniform_mesh(2, (n, n), 16, 4, OUTFLOW, name="sod2d")
+    if name == "kh3d":
+        n = scale or 16
+        return uniform_mesh(3, (n, n, n), 16, 4, PERIODIC, name="kh3d")
+    if name == "sedov_amr":
+        return sedov_mesh(scale or 8, 16, 4, OUTFLOW)
+    if name == "advection3d":
+        n = scale or 32
+        return uniform_mesh(3, (n, n, n), 16, 4, PERIODIC, name="advection3d")
+    raise KeyError(name)
+
+
 def workload(name: str, scale: int | None = None):
     """Return ``(mesh, W0, gamma, cfl)`` for a named workload.
 
@@ -403,20 +419,7 @@ def workload(name: str, scale: int | None = None):
     * ``advection3d``: [0,1]^3, ``scale``^3 blocks of 16^3 (32 -> 512^3), periodic.
     """
     gamma, cfl = 1.4, 0.8
-    if name == "sod2d":
-        n = scale or 8
-        mesh = uniform_mesh(2, (n, n), 16, 4, OUTFLOW, name="sod2d")
-        return mesh, sod_state(mesh), gamma, cfl
-    if name == "kh3d":
-        n = scale or 16
-        mesh = uniform_mesh(3, (n, n, n), 16, 4, PERIODIC, name="kh3d")
-        return mesh, kh_state(mesh), gamma, cfl
-    if name == "sedov_amr":
-        n = scale or 8
-        mesh = sedov_mesh(n, 16, 4, OUTFLOW)
-        return mesh, sedov_state(mesh, gamma=gamma), gamma, cfl
-    if name == "advection3d":
-        n = scale or 32
-        mesh = uniform_mesh(3, (n, n, n), 16, 4, PERIODIC, name="advection3d")
-        return mesh, advection_state(mesh), gamma, cfl
-    raise KeyError(name)
+    mesh = workload_mesh(name, scale)
+    state = {"sod2d": sod_state, "kh3d": kh_state, "advection3d": advection_state,
+             "sedov_amr": lambda m: sedov_state(m, gamma=gamma)}[name]
+    return mesh, state(mesh), gamma, cfl
