@@ -187,25 +187,83 @@ __device__ __forceinline__ void prolong_guard_cell(const DevMesh &m, S *__restri
 
 // Leaf b, neighbour slot `slot` ((sx+1) + 3 (sy+1) + 9 (sz+1)) covered by a
 // coarser leaf: every guard cell of that slot within `depth` of the
-// interior, cells [first, ...) strided by `stride`.  The work is the slot's
-// own cells (depth x n x n for a face slot, depth^2 x n for an edge, depth^3
-// for a corner), not the whole padded block.
+// interior, work items [first, ...) strided by `stride`.  The work is the
+// slot's own cells (depth x n x n for a face slot, depth^2 x n for an edge,
+// depth^3 for a corner), not the whole padded block.
+//
+// With an even depth and nxb (block origins are multiples of nxb), the two
+// fine cells of every aligned pair along an axis map to one coarse cell under
+// each boundary mapping (interior, periodic shift, reflecting mirror, outflow
+// clamp), so a work item is one coarse cell: its MC slopes are formed once
+// and its 2^d fine children written with the per-cell formula of
+// prolong_guard_cell (same operations, same order, same values).  Otherwise
+// a work item is one fine cell.
 template <typename S, typename C = double>
 __device__ __forceinline__ void guard_prolong_slot(const DevMesh &m, S *__restrict__ U, int b,
                                                    int slot, int depth, int first, int stride) {
-  const int n = m.nxb, ng = m.ng;
+  const int n = m.nxb, ng = m.ng, nd = m.ndim;
   const int2 sl = m.slots[b * 27 + slot];
   const int s3[3] = {slot % 3, (slot / 3) % 3, slot / 9};
   int lo[3], w[3];
   for (int d = 0; d < 3; ++d) {
-    if (d >= m.ndim) { lo[d] = 0; w[d] = 1; continue; }
+    if (d >= nd) { lo[d] = 0; w[d] = 1; continue; }
     lo[d] = s3[d] == 0 ? ng - depth : (s3[d] == 1 ? ng : ng + n);
     w[d] = s3[d] == 1 ? n : depth;
   }
-  const int ncell = w[0] * w[1] * w[2];
-  for (int c = first; c < ncell; c += stride) {
-    const int i = lo[0] + c % w[0], j = lo[1] + (c / w[0]) % w[1], k = lo[2] + c / (w[0] * w[1]);
-    prolong_guard_cell<S, C>(m, U, b, sl.y, i, j, k);
+  if ((depth & 1) || (n & 1)) {
+    const int ncell = w[0] * w[1] * w[2];
+    for (int c = first; c < ncell; c += stride) {
+      const int i = lo[0] + c % w[0], j = lo[1] + (c / w[0]) % w[1], k = lo[2] + c / (w[0] * w[1]);
+      prolong_guard_cell<S, C>(m, U, b, sl.y, i, j, k);
+    }
+    return;
+  }
+  const int P = m.P, lev = m.level[b], cb = sl.y;
+  const long long sP = P, sPP = (long long)P * P;
+  const long long step[3] = {1, sP, sPP};
+  const int h[3] = {w[0] / 2, w[1] / 2, nd == 3 ? w[2] / 2 : 1};
+  const int nco = h[0] * h[1] * h[2];
+  const int nch = nd == 3 ? 8 : 4;
+  for (int c = first; c < nco; c += stride) {
+    const int q[3] = {c % h[0], (c / h[0]) % h[1], c / (h[0] * h[1])};
+    // the children's padded indices and, per axis, their lattice indices and
+    // mirror flags after the boundary mapping (the pair shares its coarse cell)
+    int fi[3][2], gi[3][2];
+    bool mir[3] = {false, false, false};
+    for (int d = 0; d < 3; ++d) {
+      for (int e = 0; e < 2; ++e) {
+        fi[d][e] = lo[d] + (d < nd ? 2 * q[d] + e : 0);
+        gi[d][e] = d < nd ? apply_bc(m.origin[3 * b + d] + fi[d][e] - ng, m.ncell[lev][d],
+                                     m.bc[d][0], m.bc[d][1], mir[d])
+                          : 0;
+      }
+    }
+    const int cx = (gi[0][0] >> 1) - m.origin[3 * cb] + ng;
+    const int cy = (gi[1][0] >> 1) - m.origin[3 * cb + 1] + ng;
+    const int cz = nd == 3 ? (gi[2][0] >> 1) - m.origin[3 * cb + 2] + ng : 0;
+    const S *Cc = U + (long long)cb * m.bstride + (cz * sPP + cy * sP + cx);
+    S *Ub = U + (long long)b * m.bstride;
+    for (int v = 0; v < m.nvar; ++v) {
+      const S *cv = Cc + v * m.vstride;
+      const C uc = C(*cv);
+      C sig[3];
+      for (int d = 0; d < nd; ++d) {
+        const C um = C(cv[-step[d]]), up = C(cv[step[d]]);
+        sig[d] = mc_lim_c<C>(uc - um, up - uc);
+      }
+      const bool neg = v >= 1 && v <= 3 && mir[v - 1];
+      for (int ch = 0; ch < nch; ++ch) {
+        const int e[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
+        C val = uc;
+        for (int d = 0; d < nd; ++d) {
+          const C off = (gi[d][e[d]] & 1) ? C(0.25) : C(-0.25);
+          val = val + off * sig[d];
+        }
+        if (neg) val = -val;
+        const int k = nd == 3 ? fi[2][e[2]] : 0;
+        Ub[((long long)k * P + fi[1][e[1]]) * P + fi[0][e[0]] + v * m.vstride] = S(val);
+      }
+    }
   }
 }
 
