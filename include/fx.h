@@ -163,7 +163,8 @@ FX_API int fx_blocks_destroy(fx_blocks *bs);
 /* fx_blocks_mark_dirty: tell the library that the caller wrote the current
  * state buffer directly (not through an fx_* call), so that the next
  * fx_compute_dt reads the state instead of reusing the signal-speed maximum
- * of the last update. */
+ * of the last update, and the next guard fill restricts the parents again
+ * instead of relying on the restriction that ended the last update. */
 FX_API int fx_blocks_mark_dirty(fx_blocks *bs);
 
 /* fx_blocks_current: index (0 or 1) of the buffer that holds the current

@@ -61,6 +61,7 @@ struct fx_blocks {
   int in_batch = 0;                         // owned by a batch: stepped only through it
   long long epoch = 0;                      // bumped on every write of the current state
   long long next_epoch = -1;                // epoch described by d_scratch[2]
+  long long restricted_epoch = -1;          // epoch whose parents are restricted
   int next_form = 0;
   int *d_status = nullptr;
   double *d_dt = nullptr;                   // dt scratch for fx_run_host

@@ -586,6 +586,7 @@ int fx_hydro_advance(fx_ctx *ctx, fx_blocks *bs, const double *dt_dev, void *str
               "restrict launch");
     ++bs->epoch;                      // the new state is in the same buffer
     bs->next_epoch = bs->epoch;
+    bs->restricted_epoch = bs->epoch;
     bs->next_form = ctx->cfl_form;
     return FX_OK;
   }
@@ -605,15 +606,19 @@ int fx_hydro_advance(fx_ctx *ctx, fx_blocks *bs, const double *dt_dev, void *str
   ++bs->epoch;
   bs->next_epoch = bs->epoch;
   bs->next_form = ctx->cfl_form;
+  bs->restricted_epoch = bs->epoch;   // the update ends with the restriction
   return FX_OK;
 }
 
 // The part of the guard fill that the fused hydro kernel still needs: parents
 // restricted (they are same-level sources), the guards of coarse leaves that
 // feed a prolongation, and the prolonged guards themselves.  Same-level guards
-// of every other leaf are read by the hydro kernel from the neighbours.
+// of every other leaf are read by the hydro kernel from the neighbours.  The
+// restriction is skipped for the current state when the update that wrote it
+// already restricted it and nothing has written it since (state epochs).
 static int fill_for_fused_advance(fx_ctx *ctx, fx_blocks *bs, cudaStream_t s, void *U) {
-  for (int l = bs->lmax; l >= 0; --l)
+  const bool restricted = U == bs->U[bs->cur] && bs->restricted_epoch == bs->epoch;
+  for (int l = bs->lmax; l >= 0 && !restricted; --l)
     FX_CUDA(fx::launch_restrict(bs->dm, U, bs->prec, bs->d_lists + bs->par_off[l], bs->par_cnt[l], s),
             "restrict launch");
   FX_CUDA(fx::launch_guard_copy(bs->dm, U, bs->prec, bs->d_lists + bs->src_off, bs->nsrc,
