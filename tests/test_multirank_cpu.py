@@ -38,7 +38,7 @@ def _worker(rank, ws, port, out):
 def test_aggregate_two_ranks():
     ws = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of a multi-threaded process
     out = mgr.dict()
     mp.spawn(_worker, args=(ws, port, out), nprocs=ws, join=True)
     for r in range(ws):
