@@ -12,6 +12,7 @@
 #pragma once
 
 #include "eos.cuh"
+#include "slot_map.cuh"
 
 namespace fx {
 namespace ops {
@@ -103,38 +104,34 @@ __device__ __forceinline__ int outside(int i, int lo, int hi) {
 template <typename S>
 __device__ __forceinline__ void guard_copy_plane(const DevMesh &m, S *__restrict__ U, int b,
                                                  int k, int depth) {
+  // per slot: its kind and its source as a linear map (slot_map.cuh)
   __shared__ int2 sl[27];
+  __shared__ long long soff[27];
+  __shared__ int4 smap[27];
   __syncthreads();
-  if (threadIdx.x < 27) sl[threadIdx.x] = m.slots[b * 27 + threadIdx.x];
+  if (threadIdx.x < 27) {
+    sl[threadIdx.x] = m.slots[b * 27 + threadIdx.x];
+    guard_source(m, b, threadIdx.x, soff[threadIdx.x], smap[threadIdx.x]);
+  }
   __syncthreads();
-  const int P = m.P, ng = m.ng, n = m.nxb, lev = m.level[b];
+  const int P = m.P, ng = m.ng, n = m.nxb;
   const int dz = m.ndim == 3 ? outside(k, ng, ng + n) : 0;
   if (dz > depth) return;
   const int sz = m.ndim == 3 ? slot_of(k, ng, ng + n) : 1;
-  const int ox = m.origin[3 * b], oy = m.origin[3 * b + 1], oz = m.origin[3 * b + 2];
+  const long long vs = m.vstride;
   S *Ub = U + (long long)b * m.bstride;
-  for (int c = threadIdx.x; c < P * P; c += blockDim.x) {
-    const int i = c % P, j = c / P;
-    if (outside(i, ng, ng + n) > depth || outside(j, ng, ng + n) > depth) continue;
-    const int sx = slot_of(i, ng, ng + n), sy = slot_of(j, ng, ng + n);
-    if (sx == 1 && sy == 1 && sz == 1) continue;
-    const int2 s = sl[sx + 3 * sy + 9 * sz];
-    if (s.x != SLOT_COPY) continue;
-    bool mir[3] = {false, false, false};
-    const int gx = apply_bc(ox + i - ng, m.ncell[lev][0], m.bc[0][0], m.bc[0][1], mir[0]);
-    const int gy = apply_bc(oy + j - ng, m.ncell[lev][1], m.bc[1][0], m.bc[1][1], mir[1]);
-    const int src = s.y;
-    const int lx = gx - m.origin[3 * src] + ng, ly = gy - m.origin[3 * src + 1] + ng;
-    int lz = 0;
-    if (m.ndim == 3) {
-      const int gz = apply_bc(oz + k - ng, m.ncell[lev][2], m.bc[2][0], m.bc[2][1], mir[2]);
-      lz = gz - m.origin[3 * src + 2] + ng;
-    }
-    const S *Us = U + (long long)src * m.bstride + ((long long)lz * P + ly) * P + lx;
+  // the plane's cells within `depth` of the interior: a window of W x W
+  const int W = n + 2 * depth, i0 = ng - depth;
+  for (int c = threadIdx.x; c < W * W; c += blockDim.x) {
+    const int i = i0 + c % W, j = i0 + c / W;
+    const int q = slot_of(i, ng, ng + n) + 3 * slot_of(j, ng, ng + n) + 9 * sz;
+    if (q == 13 || sl[q].x != SLOT_COPY) continue;
+    const int4 mq = smap[q];
+    const S *Us = U + (soff[q] + (i * mq.x + j * mq.y + k * mq.z));
     S *Ud = Ub + ((long long)k * P + j) * P + i;
     for (int v = 0; v < m.nvar; ++v) {
-      const S x = Us[v * m.vstride];
-      Ud[v * m.vstride] = (v >= 1 && v <= 3 && mir[v - 1]) ? -x : x;
+      const S x = Us[v * vs];
+      Ud[v * vs] = (v >= 1 && v <= 3 && ((mq.w >> (v - 1)) & 1)) ? -x : x;
     }
   }
 }
