@@ -77,6 +77,29 @@ def aggregate(zones_local: float, seconds_local: float, device=None):
     return float(z.item()), float(t.item())
 
 
+def link_bandwidth(host_in, host_out, stream, reps: int = 3):
+    """Host->device and device->host GB/s of one copy of a pinned buffer
+    (CUDA events on `stream`, median of `reps` after one warm-up copy)."""
+    import torch
+    dbuf = torch.empty(host_in.shape, dtype=host_in.dtype, device=stream.device)
+    nbytes = host_in.numel() * host_in.element_size()
+    out = []
+    for copy in (lambda: dbuf.copy_(host_in, non_blocking=True),
+                 lambda: host_out.copy_(dbuf, non_blocking=True)):
+        ts = []
+        with torch.cuda.stream(stream):
+            for _ in range(reps + 1):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                copy()
+                b.record(stream)
+                stream.synchronize()
+                ts.append(a.elapsed_time(b) / 1e3)
+        out.append(nbytes / float(np.median(ts[1:])) / 1e9)
+    del dbuf
+    return out[0], out[1]
+
+
 # ---------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------
@@ -497,6 +520,11 @@ def run_ours(args):
         state_bytes = host_in.numel() * host_in.element_size()
         e2e = {"value": ez / esec, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                "d2h_bytes_per_step": state_bytes, "call": "fx_run_host_interior"}
+        # the host link alone (one copy of the same bytes each way): the
+        # upload cannot overlap the update, whose dt needs the whole state
+        h2d, d2h = link_bandwidth(host_in, host_out, stream)
+        e2e.update({"link_gbs": {"h2d": h2d, "d2h": d2h},
+                    "upload_ms": state_bytes / h2d / 1e6, "ms_per_step": esec / e2e_steps * 1e3})
 
     peaks, peak_kind = load_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
