@@ -296,6 +296,35 @@ FX_API int fx_regrid_mesh(const fx_blocks *bs, int *level, int64_t *origin, int 
 FX_API int fx_regrid_apply(fx_ctx *ctx, fx_blocks *bs, void *U0_new, void *U1_new,
                            void *stream);
 
+/* fx_regrid_plan_host: the planning step of fx_regrid_plan alone -- marking
+ * and 2:1 balance, the same rules and the same sorted result -- for a mesh
+ * and per-block indicator values given in host arrays.  Host code only: it
+ * needs no context and no GPU (plan on another host, or check the planner
+ * against an independent implementation).  Paper: Section 2 (the Grid unit
+ * refines and derefines the octree).
+ *   ndim, nxb, nroot[3], bc[6] (x-, x+, y-, y+, z-, z+), nblocks, level,
+ *   origin [nblocks][3] (cell index in the block's level lattice), parent:
+ *   as for fx_blocks_create, and checked by the same rules.
+ *   err [nblocks]: indicator of each leaf (ignored for parents).
+ *   refine_cutoff, derefine_cutoff, max_level: as for fx_regrid_plan.
+ *   cap: entries of the caller-owned output arrays level_new [cap],
+ *   origin_new [cap][3], parent_new [cap] (as fx_regrid_mesh writes them)
+ *   and map_new [cap][3] = (kind 0 kept / 1 new child, old block if kept
+ *   else old parent, octant: bit d set for the upper half along axis d).
+ *   *nblocks_new receives the planned block count, also when it exceeds
+ *   cap (then FX_ERR_ARG and no output written; cap = 0 asks for the count).
+ *   msg (may be null): receives a NUL-terminated reason on error, at most
+ *   msg_len bytes.
+ * Errors: FX_ERR_ARG (null or out-of-range argument, cap too small),
+ *   FX_ERR_MESH (a mesh fx_blocks_create would refuse; not covering the
+ *   domain, not 2:1 balanced, or a lattice too large for the planner). */
+FX_API int fx_regrid_plan_host(int ndim, int nxb, const int nroot[3], const int bc[6],
+                               int nblocks, const int *level, const int64_t *origin,
+                               const int *parent, const double *err, double refine_cutoff,
+                               double derefine_cutoff, int max_level, int cap, int *nblocks_new,
+                               int *level_new, int64_t *origin_new, int *parent_new, int *map_new,
+                               char *msg, int msg_len);
+
 /* fx_block_fluxes: device pointer to the flux registers of block `b`
  * ([2*ndim faces x-,x+,y-,y+,z-,z+][nvar][nxb^(ndim-1)], lower transverse axis
  * fastest) written by the last fx_hydro_advance, or NULL if the block has no

@@ -205,6 +205,24 @@ class OracleMesh:
         self.restrict_parents(U)
         self.guardcell_fill(U)
         err = self.regrid_errors(U, eps)
+        level, origin, parent, kind, src, octs = self.regrid_plan(err, refine_cutoff,
+                                                                 derefine_cutoff, max_level)
+        new_mesh = dataclasses.replace(m, level=level, origin=origin, parent=parent, extra={})
+        om = OracleMesh(new_mesh, self.gamma)
+        Unew = np.zeros(new_mesh.shape)
+        maps = (kind, src, octs)
+        lib().or_regrid_transfer(self._h, _dp(U), om._h, _ip(maps[0]), _ip(maps[1]),
+                                 _ip(maps[2]), _dp(Unew))
+        om.restrict_parents(Unew)
+        return om, Unew, err, maps
+
+    def regrid_plan(self, err: np.ndarray, refine_cutoff: float, derefine_cutoff: float,
+                    max_level: int):
+        """Marking and 2:1 balance for per-block indicator values ``err``
+        (or_regrid_plan).  Returns ``(level, origin, parent, kind, src,
+        oct)`` of the new mesh, sorted by (level, z, y, x of the origin)."""
+        m = self.mesh
+        err = np.ascontiguousarray(err, dtype=np.float64)
         cap = m.nb * (1 + 2 ** m.ndim)
         level = np.zeros(cap, dtype=np.int32)
         origin = np.zeros((cap, 3), dtype=np.int64)
@@ -213,21 +231,12 @@ class OracleMesh:
         src = np.zeros(cap, dtype=np.int32)
         octs = np.zeros(cap, dtype=np.int32)
         nn = lib().or_regrid_plan(self._h, _dp(err), float(refine_cutoff), float(derefine_cutoff),
-                                  max_level, cap, _ip(level),
+                                  int(max_level), cap, _ip(level),
                                   origin.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                   _ip(parent), _ip(kind), _ip(src), _ip(octs))
         if nn < 0:
             raise RuntimeError(lib().or_last_error().decode())
-        new_mesh = dataclasses.replace(m, level=level[:nn].copy(), origin=origin[:nn].copy(),
-                                       parent=parent[:nn].copy(), extra={})
-        om = OracleMesh(new_mesh, self.gamma)
-        Unew = np.zeros(new_mesh.shape)
-        maps = (np.ascontiguousarray(kind[:nn]), np.ascontiguousarray(src[:nn]),
-                np.ascontiguousarray(octs[:nn]))
-        lib().or_regrid_transfer(self._h, _dp(U), om._h, _ip(maps[0]), _ip(maps[1]),
-                                 _ip(maps[2]), _dp(Unew))
-        om.restrict_parents(Unew)
-        return om, Unew, err, maps
+        return tuple(a[:nn].copy() for a in (level, origin, parent, kind, src, octs))
 
     def restrict_parents(self, U: np.ndarray) -> None:
         lib().or_restrict_parents(self._h, _dp(U))

@@ -6,6 +6,9 @@
 // derefines PARAMESH blocks as the solution evolves.
 #include "api_state.h"
 
+#include <algorithm>
+#include <array>
+#include <cstdio>
 #include <cstring>
 #include <utility>
 
@@ -105,6 +108,107 @@ int fx_regrid_apply(fx_ctx *ctx, fx_blocks *bs, void *U0_new, void *U1_new, void
   // the handle keeps its identity: swap in the new mesh, free the old one
   std::swap(*bs, *nbs);
   fx_blocks_destroy(nbs);
+  return FX_OK;
+}
+
+int fx_regrid_plan_host(int ndim, int nxb, const int nroot[3], const int bc[6], int nblocks,
+                        const int *level, const int64_t *origin, const int *parent,
+                        const double *err, double refine_cutoff, double derefine_cutoff,
+                        int max_level, int cap, int *nblocks_new, int *level_new,
+                        int64_t *origin_new, int *parent_new, int *map_new, char *msg,
+                        int msg_len) {
+  auto bad = [&](int code, const char *text) {
+    if (msg && msg_len > 0) std::snprintf(msg, (size_t)msg_len, "%s", text);
+    return code;
+  };
+  if (msg && msg_len > 0) msg[0] = '\0';
+  if (nblocks_new) *nblocks_new = 0;
+  if ((ndim != 2 && ndim != 3) || nblocks < 1 || !nroot || !bc || !level || !origin || !parent ||
+      !err || !nblocks_new || cap < 0 || max_level < 0 || max_level >= FX_MAXLEV - 1)
+    return bad(FX_ERR_ARG, "null or out-of-range argument");
+  if (cap > 0 && (!level_new || !origin_new || !parent_new || !map_new))
+    return bad(FX_ERR_ARG, "null output array");
+  if (nxb < 8 || nxb > 64 || nxb % 8) return bad(FX_ERR_ARG, "nxb must be a multiple of 8 in [8, 64]");
+  int root[3], bcs[6];
+  for (int d = 0; d < 3; ++d) {
+    root[d] = d < ndim ? nroot[d] : 1;
+    if (root[d] < 1) return bad(FX_ERR_ARG, "bad nroot");
+  }
+  for (int i = 0; i < 6; ++i) bcs[i] = i < 2 * ndim ? bc[i] : FX_BC_OUTFLOW;
+  for (int d = 0; d < ndim; ++d) {
+    for (int s = 0; s < 2; ++s)
+      if (bcs[2 * d + s] != FX_BC_OUTFLOW && bcs[2 * d + s] != FX_BC_PERIODIC &&
+          bcs[2 * d + s] != FX_BC_REFLECT)
+        return bad(FX_ERR_ARG, "bad boundary kind");
+    if ((bcs[2 * d] == FX_BC_PERIODIC) != (bcs[2 * d + 1] == FX_BC_PERIODIC))
+      return bad(FX_ERR_ARG, "periodic boundaries must be set on both sides of an axis");
+  }
+  // the mesh: the same rules as fx_blocks_create (levels, origins on the
+  // block lattice of their level, distinct positions, parents one level up
+  // with every child present)
+  const int nb = nblocks, nch = 1 << ndim;
+  int lmax = 0;
+  for (int b = 0; b < nb; ++b) {
+    if (level[b] < 0 || level[b] >= FX_MAXLEV) return bad(FX_ERR_MESH, "level out of range");
+    lmax = std::max(lmax, level[b]);
+  }
+  for (int d = 0; d < 3; ++d)
+    if ((((long long)root[d] * nxb) << lmax) > (1LL << 30)) return bad(FX_ERR_MESH, "lattice too large");
+  std::vector<int> lv(level, level + nb), pa(parent, parent + nb), org(3 * (size_t)nb);
+  std::vector<std::array<long long, 4>> at(nb);
+  for (int b = 0; b < nb; ++b) {
+    at[b][0] = level[b];
+    for (int d = 0; d < 3; ++d) {
+      const long long o = d < ndim ? origin[3 * b + d] : 0;
+      const long long N = d < ndim ? ((long long)root[d] * nxb) << level[b] : 1;
+      if (o % nxb || o < 0 || o >= N)
+        return bad(FX_ERR_MESH, "block origin not on the block lattice of its level");
+      org[3 * b + d] = (int)o;
+      at[b][1 + d] = o;
+    }
+  }
+  std::sort(at.begin(), at.end());
+  if (std::adjacent_find(at.begin(), at.end()) != at.end())
+    return bad(FX_ERR_MESH, "two blocks at the same position");
+  std::vector<int> child(8 * (size_t)nb, -1), leaf(nb, 1);
+  for (int b = 0; b < nb; ++b) {
+    const int p = parent[b];
+    if (p < 0) {
+      if (p != -1 || level[b] != 0) return bad(FX_ERR_MESH, "block above level 0 without a parent");
+      continue;
+    }
+    if (p >= nb || level[p] != level[b] - 1) return bad(FX_ERR_MESH, "parent on the wrong level");
+    int oct = 0;
+    for (int d = 0; d < ndim; ++d) {
+      const int rel = org[3 * b + d] - 2 * org[3 * p + d];
+      if (rel != 0 && rel != nxb) return bad(FX_ERR_MESH, "child outside its parent");
+      if (rel) oct |= 1 << d;
+    }
+    if (child[8 * p + oct] >= 0) return bad(FX_ERR_MESH, "duplicate child");
+    child[8 * p + oct] = b;
+    leaf[p] = 0;
+  }
+  for (int b = 0; b < nb; ++b)
+    if (!leaf[b])
+      for (int c = 0; c < nch; ++c)
+        if (child[8 * b + c] < 0) return bad(FX_ERR_MESH, "parent with a missing child");
+  fx::RegridPlan plan;
+  std::string text;
+  const int rc = fx::regrid_plan(ndim, nxb, root, bcs, nb, lv, org, pa,
+                                 std::vector<double>(err, err + nb), refine_cutoff,
+                                 derefine_cutoff, max_level, &plan, &text);
+  if (rc) return bad(rc, text.c_str());
+  const int n = (int)plan.level.size();
+  *nblocks_new = n;
+  if (n > cap) return bad(FX_ERR_ARG, "capacity below the planned block count");
+  for (int j = 0; j < n; ++j) {
+    level_new[j] = plan.level[j];
+    parent_new[j] = plan.parent[j];
+    for (int d = 0; d < 3; ++d) origin_new[3 * j + d] = plan.origin[3 * j + d];
+    map_new[3 * j] = plan.map[j].x;
+    map_new[3 * j + 1] = plan.map[j].y;
+    map_new[3 * j + 2] = plan.map[j].z;
+  }
   return FX_OK;
 }
 

@@ -79,6 +79,9 @@ def load(build: bool = True):
             "fx_regrid_errors": (c_int, [vp, dp]),
             "fx_regrid_mesh": (c_int, [vp, ip, i64p, ip]),
             "fx_regrid_apply": (c_int, [vp, vp, vp, vp, vp]),
+            "fx_regrid_plan_host": (c_int, [c_int, c_int, ip, ip, c_int, ip, i64p, ip, dp,
+                                            c_double, c_double, c_int, c_int, ip, ip, i64p, ip,
+                                            ip, ctypes.c_char_p, c_int]),
             "fx_block_fluxes": (vp, [vp, c_int]),
             "fx_kernel_launches": (ctypes.c_longlong, []),
             "fx_dword_selftest": (c_int, [c_int, vp, vp, vp, c_int, vp]),
@@ -312,6 +315,44 @@ class Batch:
         _check(self.ctx, load().fx_batch_choice(self.h, int(ndim), int(precision), ctypes.byref(t),
                                                 ctypes.byref(c)))
         return t.value, c.value
+
+
+def regrid_plan_host(mesh, err, refine_cutoff: float = 0.8, derefine_cutoff: float = 0.2,
+                     max_level: int | None = None):
+    """Plan a regrid of ``mesh`` for per-block indicator values ``err`` on
+    the host (fx_regrid_plan_host; no GPU needed).  Returns ``(level, origin,
+    parent, map)`` of the planned mesh, ``map[j] = (kind, source, octant)``."""
+    L = load()
+    ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    i64p = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    level = np.ascontiguousarray(mesh.level, dtype=np.int32)
+    origin = np.ascontiguousarray(mesh.origin, dtype=np.int64)
+    parent = np.ascontiguousarray(mesh.parent, dtype=np.int32)
+    nroot = np.array(mesh.nroot, dtype=np.int32)
+    bc = np.ascontiguousarray(mesh.bc_flat(), dtype=np.int32)
+    err = np.ascontiguousarray(err, dtype=np.float64)
+    if err.shape != (mesh.nb,):
+        raise ValueError("one indicator value per block")
+    max_level = int(mesh.level.max()) + 1 if max_level is None else int(max_level)
+    msg = ctypes.create_string_buffer(256)
+    n = ctypes.c_int(0)
+    cap = 0
+    while True:
+        lv = np.zeros(max(cap, 1), dtype=np.int32)
+        og = np.zeros((max(cap, 1), 3), dtype=np.int64)
+        pa = np.zeros(max(cap, 1), dtype=np.int32)
+        mp = np.zeros((max(cap, 1), 3), dtype=np.int32)
+        rc = L.fx_regrid_plan_host(mesh.ndim, mesh.nxb, ip(nroot), ip(bc), mesh.nb, ip(level),
+                                   i64p(origin), ip(parent),
+                                   err.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   float(refine_cutoff), float(derefine_cutoff), max_level, cap,
+                                   ctypes.byref(n), ip(lv), i64p(og), ip(pa), ip(mp), msg, 256)
+        if rc == FX_OK:
+            return lv[:n.value], og[:n.value], pa[:n.value], mp[:n.value]
+        if rc == -1 and n.value > cap:   # FX_ERR_ARG: capacity below the count
+            cap = n.value
+            continue
+        raise FxError(rc, msg.value.decode())
 
 
 def fx_dword_selftest(op: int, a, b=None, stream=None):
