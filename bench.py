@@ -155,10 +155,12 @@ class ClockSampler:
 # CPU oracle baseline
 # ---------------------------------------------------------------------------
 
-def oracle_sample(workload: str, target_s: float = 12.0, max_steps: int = 50):
+def oracle_sample(workload: str, target_s: float = 12.0, max_steps: int = 50,
+                  single_s: float = 4.0):
     """Time the FP64 oracle, as it is, on a bounded sample of the workload
     (REFERENCE_SAMPLE_SCALE: the same block size, physics and boundaries on
-    fewer blocks), full steps (dt, guard fill, update) on all host cores."""
+    fewer blocks), full steps (dt, guard fill, update) on all host cores, then
+    for about ``single_s`` seconds on one thread."""
     import oracle
     from paper_2208_11630_gb300 import inputs
     mesh, W, _, _ = inputs.workload(workload, scale=REFERENCE_SAMPLE_SCALE.get(workload))
@@ -167,16 +169,30 @@ def oracle_sample(workload: str, target_s: float = 12.0, max_steps: int = 50):
     om = oracle.OracleMesh(mesh, 1.4)
     U = om.prim_to_cons(W)
     zones = mesh.leaf_zones()
-    t0 = time.perf_counter()
-    steps = 0
-    while steps < max_steps:
-        U, _ = om.step(U, cfl=0.8)
-        steps += 1
-        if time.perf_counter() - t0 > target_s:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": zones * steps / dt, "unit": UNIT, "cores": oracle.get_threads(),
-            "kind": "oracle", "sample": f"{desc}; {steps} full steps in {dt:.1f} s"}
+
+    def timed(budget_s, cap):
+        nonlocal U
+        t0 = time.perf_counter()
+        steps = 0
+        while steps < cap:
+            U, _ = om.step(U, cfl=0.8)
+            steps += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        return steps, time.perf_counter() - t0
+
+    cores = oracle.get_threads()
+    steps, dt = timed(target_s, max_steps)
+    out = {"value": zones * steps / dt, "unit": UNIT, "cores": cores,
+           "kind": "oracle", "sample": f"{desc}; {steps} full steps in {dt:.1f} s"}
+    oracle.set_threads(1)
+    try:
+        s1, t1 = timed(single_s, max_steps)
+    finally:
+        oracle.set_threads(cores)
+    out["single_thread"] = {"value": zones * s1 / t1, "unit": UNIT, "cores": 1,
+                            "sample": f"the same sample; {s1} full steps in {t1:.1f} s"}
+    return out
 
 
 def measure_variants(args, fx, inputs, mesh, dev, cfl, zones, bs, ws, hbm_peak):

@@ -38,3 +38,13 @@ def test_reference_arm_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_cpu_baseline_all_cores_and_one_thread():
+    import oracle
+    before = oracle.get_threads()
+    cb = bench.oracle_sample("sod2d", target_s=0.05, max_steps=2, single_s=0.05)
+    assert cb["kind"] == "oracle" and cb["value"] > 0 and cb["cores"] == before
+    one = cb["single_thread"]
+    assert one["cores"] == 1 and one["value"] > 0 and one["unit"] == bench.UNIT
+    assert oracle.get_threads() == before   # the thread count is restored
