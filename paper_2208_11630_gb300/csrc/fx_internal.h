@@ -213,7 +213,4 @@ cudaError_t launch_dword_test(int op, const double *a, const double *b, double *
 void count_launch(int n = 1);
 long long launch_count();
 
-// Shared memory the hydro kernel needs for a given configuration (bytes).
-size_t hydro_smem_bytes(int ndim, int tile, int prec);
-
 }  // namespace fx

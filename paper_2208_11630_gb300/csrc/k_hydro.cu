@@ -73,12 +73,6 @@ cudaError_t launch_hydro_batch(int ndim, int tile, int prec, const BatchReq *req
                     : launch_batch_t<2, 8, float, float>(reqs, items, nitems, counter, ctas_per_sm, nsm, s);
 }
 
-size_t hydro_smem_bytes(int ndim, int tile, int prec) {
-  const size_t el = prec == 1 ? sizeof(float) : sizeof(double);   // 2: double-words, 8 bytes
-  const int np = ndim == 3 ? 3 : 1;
-  return (tile == 16 ? Smem<16>::total(np) : Smem<8>::total(np)) * el;
-}
-
 cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, const int *leaves,
                          int n, const double *dt, double *regs, int *status,
                          unsigned long long *smax, const unsigned char *rmask, int form,
