@@ -326,6 +326,29 @@ def test_sod_mirror_symmetry(orc):
         assert np.abs(Ga[v] - Gm[v]).max() <= 1e-14 * s
 
 
+def test_shear_layer_mirror_symmetry(orc):
+    """The shear layer with its random perturbation replaced by one mode,
+    v_y = 0.01 sin(2 pi x) sin(4 pi y) -- odd about y = 1/2, while the band
+    |y - 1/2| < 1/4 and v_x are even -- is symmetric under y -> 1 - y with
+    v_y -> -v_y, and the scheme keeps it so to roundoff (periodic, 2D, with
+    the transverse predictor terms and both flux directions active)."""
+    mesh = inputs.uniform_mesh(2, (4, 4), 16, 4, inputs.PERIODIC)
+    W = inputs.kh_state(mesh)
+    I = mesh.interior(W)
+    for b in range(mesh.nb):
+        x, y, _ = mesh.cell_centers(b)
+        I[b, 2] = 0.01 * np.sin(2 * np.pi * x) * np.sin(4 * np.pi * y)
+    om = orc.OracleMesh(mesh)
+    U, _, _ = om.run(om.prim_to_cons(W), nsteps=30)
+    G = assemble(mesh, U)
+    Gm = G[:, :, ::-1, :].copy()
+    Gm[2] = -Gm[2]
+    assert np.abs(G[2]).max() > 1e-3   # the mode is there and has grown
+    for v in range(5):
+        s = np.abs(G[v]).max()
+        assert np.abs(G[v] - Gm[v]).max() <= 1e-12 * s, v
+
+
 def test_sod_axis_equivalence(orc):
     """Sod along y equals the transposed Sod along x."""
     mesh = inputs.uniform_mesh(2, (4, 4), 16, 4, inputs.OUTFLOW)
