@@ -14,6 +14,11 @@
  * Conventions shared by every call:
  *   - Return value: FX_OK (0) or a negative FX_ERR_* code; nothing throws.
  *     The text of the last error of a context is in fx_last_error().
+ *   - Null handles: a call given a null context, block set or batch (or a
+ *     null required pointer) returns FX_ERR_ARG without touching the device;
+ *     exceptions: fx_finalize(NULL) does nothing and returns FX_OK,
+ *     fx_last_error(NULL) returns "null context", fx_block_fluxes(NULL, b)
+ *     returns NULL.
  *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
  *     default stream).  Every call is stream-ordered and asynchronous unless
  *     its comment says it synchronises.
