@@ -31,7 +31,7 @@ The plan here (this design's choice; the paper prints none):
   exchange would pack only the cells the receiver reads, a shell two cells
   deep around its region (plus one coarse cell of slope support at
   coarse-fine faces).  For the 256^3 shear layer on 8 ranks (8^3 blocks of
-  16^3 each) that shell is 132^3 - 128^3 cells, 3 % of a rank's state,
+  16^3 each) that shell is 132^3 - 128^3 cells, 9.7 % of a rank's state,
   against 0.95x for one ring of whole blocks and 4.4x for three.
 * dt is the CFL limit of each rank's own data, combined by a MIN reduction
   (the CFL number divided by the largest signal speed is monotone in that
