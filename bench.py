@@ -580,7 +580,7 @@ def run_ours(args):
     if not args.no_variants:
         line["variants"] = measure_variants(args, fx, inputs, mesh, dev, cfl, zones_per_step, bs,
                                             ws, hbm_peak)
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:   # the CPU oracle at N = 1 only
         try:
             line["cpu_baseline"] = oracle_sample(args.workload)
         except Exception as e:  # report, never fake
