@@ -48,3 +48,17 @@ def test_cpu_baseline_all_cores_and_one_thread():
     one = cb["single_thread"]
     assert one["cores"] == 1 and one["value"] > 0 and one["unit"] == bench.UNIT
     assert oracle.get_threads() == before   # the thread count is restored
+
+
+def test_reference_arm_other_ranks_do_no_work(monkeypatch):
+    """Under torchrun only rank 0 times the oracle and prints; the others
+    exit 0 without work or output."""
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    args = argparse.Namespace(workload="kh3d", scale=None, precision="f64", steps=2, warmup=3,
+                              gpus=2)
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        assert bench.run_reference(args) == 0
+    assert buf.getvalue() == ""
