@@ -22,9 +22,13 @@ The plan here (this design's choice; the paper prints none):
   In practice one ring suffices for blocks of 8 or more cells: a leaf that
   touches no owned leaf lies at least one block of the next finer level (4
   cells of the owned leaf's level) away, beyond the two-cell stencil and the
-  one coarse cell of slope support it could feed.  The CPU tests find one
-  ring bit-identical to the unsharded run on every mesh they step (two and
-  three levels, periodic and outflow); the default keeps the safe bound.
+  one coarse cell of slope support it could feed.  The CPU tests confirm it
+  by brute force (perturbing each block in turn, one step reaches only the
+  leaves touching it, and a parent reaches nothing) and find one ring
+  bit-identical to the unsharded run on every mesh they step (8-cell blocks,
+  two and three levels, periodic and outflow).  That holds per stage: an
+  SSP-RK step would exchange its halo before each stage, or take a ring per
+  stage.  The default keeps the safe bound.
 * ``exchange_lists``: for each ordered pair of ranks, the blocks the first
   owns that lie in the second's halo -- one message per pair and step.  The
   lists name whole blocks, which is what the CPU emulation moves; a GPU

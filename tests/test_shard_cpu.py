@@ -214,3 +214,36 @@ def test_without_a_halo_the_result_differs():
     to the other rank's region come out different."""
     res = _run("amr3d_periodic", rings=0)
     assert not any(r[0] for r in res)
+
+
+@pytest.mark.parametrize("case", ["amr3d_periodic", "amr2d_outflow", "amr2d_three_levels"])
+def test_one_step_reads_only_touching_leaves(orc, case):
+    """Brute-force dependency check with the oracle: perturb one block at a
+    time, take one step at a fixed dt, and record which leaves change.  Every
+    leaf a perturbation reaches is the perturbed leaf or touches it -- one
+    touch-step, so one ring of halo suffices on these meshes -- and a parent
+    reaches nothing (the step restricts it from its children first)."""
+    mesh, W = CASES[case]()
+    om = orc.OracleMesh(mesh)
+    U0 = om.prim_to_cons(W)
+    dt = om.compute_dt(U0)
+    I0 = mesh.interior(om.step(U0, dt=dt)[0]).reshape(mesh.nb, -1)
+    adj = shard.leaf_adjacency(mesh)
+    leaf = mesh.is_leaf() == 1
+    reach = 0
+    for b in range(mesh.nb):
+        U = U0.copy()
+        I = mesh.interior(U)
+        I[b, 0] *= 1.001
+        I[b, 4] *= 1.001
+        changed = np.flatnonzero(np.any(
+            mesh.interior(om.step(U, dt=dt)[0]).reshape(mesh.nb, -1) != I0, axis=1))
+        changed = changed[leaf[changed]]
+        if not leaf[b]:
+            assert len(changed) == 0, (b, changed)
+            continue
+        assert b in changed
+        outside = [int(c) for c in changed if c != b and c not in set(adj[b].tolist())]
+        assert not outside, (b, outside)
+        reach = max(reach, len(changed))
+    assert reach > 1   # perturbations do cross block boundaries
