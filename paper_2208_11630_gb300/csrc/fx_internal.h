@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -208,6 +209,14 @@ int regrid_plan(int ndim, int nxb, const int nroot[3], const int bc[6], int nb,
 // Element-wise double-word operation for fx_dword_selftest (k_dword_test.cu).
 cudaError_t launch_dword_test(int op, const double *a, const double *b, double *out, int n,
                               cudaStream_t s);
+
+// Raises the dynamic shared-memory limit of kernel `func` to `bytes` on the
+// current device, once per device: the attribute belongs to that device's
+// context, so one flag per process would skip a second device and its launch
+// would fail.  `done` holds one bit per device ordinal (ordinals >= 64 set the
+// attribute on every call); two threads that race on a first call both set
+// the same value, which is harmless.
+cudaError_t set_smem_once(const void *func, size_t bytes, std::atomic<unsigned long long> &done);
 
 // Process-wide count of kernels launched by the library.
 void count_launch(int n = 1);

@@ -40,13 +40,9 @@ cudaError_t launch_batch_t(const BatchReq *reqs, const int4 *items, int nitems,
                            unsigned int *counter, int ctas_per_sm, int nsm, cudaStream_t s) {
   const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(R);
   auto kern = k_hydro_batch<NDIM, T, S, R>;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static std::atomic<unsigned long long> attr_devs{0};
+  if (cudaError_t e = set_smem_once((const void *)kern, smem, attr_devs); e != cudaSuccess)
+    return e;
   int fit = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kern, T * T, smem);
   if (e != cudaSuccess) return e;

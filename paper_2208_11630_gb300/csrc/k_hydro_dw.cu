@@ -31,13 +31,9 @@ cudaError_t launch_dw_t(const DevMesh &m, const void *U, void *Unew, const int *
   const int tiles = m.nxb / T;
   const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(dw);
   auto kern = k_hydro_dw<NDIM, T>;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static std::atomic<unsigned long long> attr_devs{0};
+  if (cudaError_t e = set_smem_once((const void *)kern, smem, attr_devs); e != cudaSuccess)
+    return e;
   kern<<<n * tiles * tiles, T * T, smem, s>>>(m, static_cast<const double *>(U),
                                               static_cast<double *>(Unew), leaves, tiles, dt, regs,
                                               status, smax, rmask, form);
@@ -67,13 +63,9 @@ cudaError_t launch_rk_dw_t(const DevMesh &m, const void *U, void *Unew, const in
   const int tiles = m.nxb / T;
   const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(dw);
   auto kern = k_hydro_rk_dw<NDIM, T>;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static std::atomic<unsigned long long> attr_devs{0};
+  if (cudaError_t e = set_smem_once((const void *)kern, smem, attr_devs); e != cudaSuccess)
+    return e;
   kern<<<n * tiles * tiles, T * T, smem, s>>>(m, static_cast<const double *>(U),
                                               static_cast<double *>(Unew), leaves, tiles, dt, regs,
                                               status, smax, rmask, form, st);

@@ -30,13 +30,9 @@ cudaError_t launch_rk_t(const DevMesh &m, const void *U, void *Unew, const int *
   const int tiles = m.nxb / T;
   const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(R);
   auto kern = k_hydro_rk<NDIM, T, S, R>;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static std::atomic<unsigned long long> attr_devs{0};
+  if (cudaError_t e = set_smem_once((const void *)kern, smem, attr_devs); e != cudaSuccess)
+    return e;
   kern<<<n * tiles * tiles, T * T, smem, s>>>(m, static_cast<const S *>(U), static_cast<S *>(Unew),
                                               leaves, tiles, dt, regs, status, smax, rmask, form,
                                               st);
