@@ -210,7 +210,9 @@ FX_API int fx_guardcell_fill_amr(fx_ctx *ctx, fx_blocks *bs, void *stream);
  * When the current state was produced by fx_hydro_advance and nothing wrote
  * it since, the update already reduced its signal speeds and only the final
  * division runs; otherwise the state is read again.  A caller that writes
- * the state buffers itself must call fx_blocks_mark_dirty afterwards. */
+ * the state buffers itself must call fx_blocks_mark_dirty afterwards.  A
+ * leaf cell with negative pressure (no sound speed) makes dt NaN in both
+ * forms, wherever it sits. */
 FX_API int fx_compute_dt(fx_ctx *ctx, fx_blocks *bs, double cfl, double *dt_dev, void *stream);
 
 /* fx_hydro_advance: one unsplit second-order step of all leaves with the
@@ -393,8 +395,12 @@ FX_API int fx_batch_choice(const fx_batch *b, int ndim, int precision, int *tile
  * bookkeeping, a process whose device memory belongs to another runtime, a
  * loop that forbids allocation after start-up).  The paper has no counterpart;
  * this entry point exists only so that such callers need no block set.
- *   U_dev      caller-owned device state, FP64, layout of a state buffer
- *              (nblocks blocks of one refinement level; every block counts);
+ *   U_dev      caller-owned device state, FP64, layout of a single-gas state
+ *              buffer: nblocks blocks of 5 variables [block][5][PZ][P][P]
+ *              (rho, mx, my, mz, E), one refinement level, every block
+ *              counted.  A multispecies buffer (5 + nspec variables per cell,
+ *              fx_set_species) is outside this call's contract: it would be
+ *              read at the wrong block stride with the wrong EOS;
  *   dx[3]      cell widths (dx[2] ignored in 2D); gamma, cfl, cfl_form as in
  *              fx_init / fx_compute_dt / fx_set_option("cfl_form");
  *   dt_dev     caller-owned device double that receives dt;
@@ -405,7 +411,10 @@ FX_API int fx_batch_choice(const fx_batch *b, int ndim, int precision, int *tile
  * current; make that first call before any stream capture.  The call clears
  * the scratch counter on `stream` before the kernel.  All calls share the
  * scratch: calls that may overlap on the GPU race and must be ordered by the
- * caller.  Errors: FX_ERR_ARG (including nblocks > FX_NOALLOC_MAX_BLOCKS),
+ * caller.  A cell with negative pressure (no sound speed) makes dt NaN, in
+ * both CFL forms and wherever the cell sits, as with fx_compute_dt; no status
+ * word is latched, so a caller that cannot rule such states out checks dt.
+ * Errors: FX_ERR_ARG (including nblocks > FX_NOALLOC_MAX_BLOCKS),
  * FX_ERR_CUDA. */
 FX_API int fx_compute_dt_noalloc(const double *U_dev, int ndim, int nblocks, int nxb, int nguard,
                                  const double dx[3], double gamma, double cfl, int cfl_form,

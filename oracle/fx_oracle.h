@@ -79,7 +79,10 @@ int or_guardcell_fill(const or_mesh *m, double *U);
 
 /* CFL time step: dt = cfl / max over leaf interior cells of
  * sum_d (|u_d| + c) / dx_d (form 0) or max_d (|u_d| + c) / dx_d (form 1).
- * Pinned: uniform-state closed form, order independence. */
+ * A cell with no sound speed (p / rho < 0 gives NaN) makes dt NaN in both
+ * forms, wherever it sits; returns -4 when dt is not finite.
+ * Pinned: uniform-state closed form, order independence, a planted
+ * negative-pressure cell giving NaN. */
 int or_compute_dt(const or_mesh *m, const double *U, double cfl, int form, double *dt);
 
 /* One hydro step of the leaves: reads U (guards filled), writes interiors of

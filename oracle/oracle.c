@@ -397,14 +397,24 @@ int or_guardcell_fill(const or_mesh *m, double *U) {
 /* time step                                                                 */
 /* ------------------------------------------------------------------------ */
 
+/* Larger of two signal speeds, where a NaN wins and stays: a cell with
+ * non-positive density or pressure has no sound speed, and the time step of a
+ * state holding one is NaN rather than a finite value that hides the cell. */
+static double sig_max(double a, double b) {
+  if (isnan(a)) return a;
+  if (isnan(b)) return b;
+  return b > a ? b : a;
+}
+
 int or_compute_dt(const or_mesh *m, const double *U, double cfl, int form, double *dt) {
-  double smax = 0.0;
   int n = m->nxb, ng = m->ng;
   int nz = m->ndim == 3 ? n : 1, kz = m->ndim == 3 ? ng : 0;
-#pragma omp parallel for schedule(static) num_threads(or_get_threads()) reduction(max : smax)
+  double *bmax = (double *)calloc((size_t)m->nb, sizeof(double));  /* per-block maxima */
+#pragma omp parallel for schedule(static) num_threads(or_get_threads())
   for (int b = 0; b < m->nb; b++) {
     if (!m->leaf[b]) continue;
     const double *dx = m->dx[m->level[b]];
+    double smax = 0.0;
     for (int k = 0; k < nz; k++)
       for (int j = 0; j < n; j++)
         for (int i = 0; i < n; i++) {
@@ -416,11 +426,15 @@ int or_compute_dt(const or_mesh *m, const double *U, double cfl, int form, doubl
           for (int d = 0; d < m->ndim; d++) {
             double sd = (fabs(w[1 + d]) + c) / dx[d];
             if (form == 0) s = s + sd;
-            else s = fmax(s, sd);
+            else s = sig_max(s, sd);
           }
-          if (!(s <= smax)) smax = s;   /* NaN propagates */
+          smax = sig_max(smax, s);
         }
+    bmax[b] = smax;
   }
+  double smax = 0.0;
+  for (int b = 0; b < m->nb; b++) smax = sig_max(smax, bmax[b]);
+  free(bmax);
   *dt = cfl / smax;
   return isfinite(*dt) ? 0 : -4;
 }

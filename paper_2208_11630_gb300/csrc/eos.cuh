@@ -6,6 +6,7 @@
 // over the mass fractions X_k = (rho X_k) / rho.
 #pragma once
 
+#include "dword.cuh"
 #include "fx_internal.h"
 
 #include <type_traits>
@@ -28,6 +29,26 @@ __device__ __forceinline__ void mix_gamma(const DevMesh &m, const R *X, int ns, 
   }
   g = R(1) + q1 / q2;
   gm1 = g - R(1);
+}
+
+// Larger of two CFL signal speeds.  A signal speed is non-negative, or NaN
+// for a cell with non-positive density or pressure; on the bit patterns the
+// non-negative values order like the values and every NaN sorts above them,
+// so a NaN wins and stays in a running maximum (the time step of such a state
+// comes out NaN instead of a finite value that hides the bad cell).  An
+// integer maximum, off the floating-point pipes.
+__device__ __forceinline__ double sig_max(double a, double b) {
+  const unsigned long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  return __longlong_as_double((long long)(ia > ib ? ia : ib));
+}
+__device__ __forceinline__ float sig_max(float a, float b) {
+  const unsigned ia = __float_as_uint(a), ib = __float_as_uint(b);
+  return __uint_as_float(ia > ib ? ia : ib);
+}
+__device__ __forceinline__ dword::dw sig_max(dword::dw a, dword::dw b) {
+  if (a.hi != a.hi) return a;
+  if (b.hi != b.hi) return b;
+  return a < b ? b : a;
 }
 
 // Per-block constants of cell_signal in precision R, formed once outside
@@ -80,7 +101,7 @@ __device__ __forceinline__ R cell_signal(const DevMesh &m, const R *u, int ns,
     if constexpr (std::is_same<R, double>::value) idx_d = m.idx[k0.lev][d];
     else idx_d = k0.idx[d];
     const R sd = (fabs(u[1 + d] * ir) + cs) * idx_d;
-    sg = form == 0 ? sg + sd : fmax(sg, sd);
+    sg = form == 0 ? sg + sd : sig_max(sg, sd);
   };
   if constexpr (NDIM > 0) {
 #pragma unroll

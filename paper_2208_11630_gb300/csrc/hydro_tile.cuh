@@ -475,7 +475,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
     // it rolled, which measured faster there
     constexpr int kSigDim = std::is_same<R, float>::value ? NDIM : 0;
     const R sg = cell_signal<R, kSigDim>(m, u, NS, sconst, cfl_form);
-    if (!(sg <= smax_t)) smax_t = sg;   // keeps a NaN
+    smax_t = sig_max(smax_t, sg);   // a NaN stays
   };
 
 

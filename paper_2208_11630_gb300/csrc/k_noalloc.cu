@@ -18,6 +18,7 @@
 // All calls share the array, so calls that overlap on the GPU (two streams, or
 // two threads) race on it; the caller must order them.
 #include "../../include/fx.h"
+#include "eos.cuh"
 #include "fx_internal.h"
 
 #include <atomic>
@@ -65,9 +66,9 @@ __global__ void k_dt_noalloc(const double *__restrict__ U, int ndim, int nxb, in
     double s = 0.0;
     for (int d = 0; d < ndim; ++d) {
       const double sd = (fabs(vel[d]) + cs) * idx[d];
-      s = form == 0 ? s + sd : fmax(s, sd);
+      s = form == 0 ? s + sd : fx::sig_max(s, sd);
     }
-    if (!(s <= smax)) smax = s;  // keeps a NaN
+    smax = fx::sig_max(smax, s);  // a NaN stays: dt comes out NaN
   }
   unsigned long long bits = __double_as_longlong(smax);
   for (int o = 16; o > 0; o >>= 1) {

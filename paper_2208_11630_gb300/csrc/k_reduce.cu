@@ -36,7 +36,7 @@ __global__ void k_dt(DevMesh m, const S *__restrict__ U, const int *__restrict__
     for (int v = 0; v < m.nvar; ++v) uc[v] = u[v * vs];
     const SignalConsts<C> k0(m, m.level[b]);
     const C s = cell_signal<C>(m, uc, m.nspec, k0, form);
-    if (!(s <= smax)) smax = s;   // keeps a NaN
+    smax = sig_max(smax, s);   // a NaN stays
   }
   // warp and CTA maximum on the bit patterns (non-negative doubles and NaN
   // order like their bits)

@@ -497,6 +497,31 @@ def test_dt_uniform_closed_form(orc):
     assert om.compute_dt(U, 0.8, 1) == pytest.approx(0.8 / sp.max(), rel=1e-14)
 
 
+@pytest.mark.parametrize("where", ["first", "middle", "last"])
+def test_dt_of_a_cell_without_sound_speed_is_nan(orc, where):
+    """A cell whose energy is below its kinetic energy has negative pressure
+    and no sound speed; the CFL bound of a state that holds it is undefined,
+    so dt is NaN in both forms wherever the cell sits (first cell a thread
+    visits, or last), on one thread and on several."""
+    mesh = inputs.uniform_mesh(3, (2, 2, 1), 8, 4, inputs.PERIODIC)
+    om = orc.OracleMesh(mesh)
+    U = om.prim_to_cons(inputs.uniform_state(mesh, rho=1.0, vel=(0.5, 0, 0), p=1.0))
+    g, n = mesh.ng, mesh.nxb
+    b, k, j, i = {"first": (0, 0, 0, 0), "middle": (1, 3, 5, 2),
+                  "last": (mesh.nb - 1, n - 1, n - 1, n - 1)}[where]
+    U[b, 4, g + k, g + j, g + i] = 0.01          # E < |m|^2 / (2 rho) = 0.125
+    old = orc.get_threads()
+    try:
+        for nthreads in (1, 4):
+            orc.set_threads(nthreads)
+            for form in (0, 1):
+                assert np.isnan(om.compute_dt(U, 0.8, form)), (nthreads, form)
+    finally:
+        orc.set_threads(old)
+    U[b, 4, g + k, g + j, g + i] = 1.0 / (GAMMA - 1.0) + 0.125   # physical again
+    assert np.isfinite(om.compute_dt(U, 0.8, 1))
+
+
 def test_positivity_fallback_keeps_123_problem_positive(orc):
     """Two strong rarefactions (Toro's test 2) push face states towards
     vacuum; the first-order fallback keeps every cell positive."""
