@@ -424,6 +424,19 @@ FX_API int fx_compute_dt_noalloc(const double *U_dev, int ndim, int nblocks, int
  * the process so far (all contexts).  Diagnostics for benchmarks. */
 FX_API long long fx_kernel_launches(void);
 
+/* fx_fma_probe: a measurement aid with no counterpart in the paper.  Runs
+ * `ctas` CTAs of 256 threads, each thread 8 independent chains of `iters`
+ * fused multiply-adds in FP64 (precision FX_F64) or FP32 (FX_F32BULK), and
+ * writes one value per CTA to the caller-owned device array out_dev (ctas
+ * elements of that type).  *flops (if not null) receives the flops the launch
+ * performs, 2 * 8 * iters * ctas * 256.  Timed with events around it on
+ * `stream`, it gives the FMA pipe's throughput under the clocks of the
+ * moment, the peak that the FP64 update's arithmetic is set against.
+ * Asynchronous.  Errors: FX_ERR_ARG (bad precision, ctas < 1, iters < 1,
+ * null out_dev), FX_ERR_CUDA. */
+FX_API int fx_fma_probe(int precision, int ctas, int iters, void *out_dev, void *stream,
+                        double *flops);
+
 /* fx_dword_selftest: apply one operation of the double-word arithmetic of
  * the "f64_arith" option element by element, for testing it against FP64:
  * out[i] = op(a[i], b[i]) with both inputs converted to double-words and the

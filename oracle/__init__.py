@@ -39,51 +39,87 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+def _bind(L):
+    """Argument and result types of the oracle's C entry points on library L."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    L.or_mesh_create.restype = ctypes.c_void_p
+    L.or_mesh_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ip, ip, i64p, ip, dp, dp, ip, ctypes.c_double]
+    L.or_mesh_destroy.argtypes = [ctypes.c_void_p]
+    L.or_last_error.restype = ctypes.c_char_p
+    L.or_set_threads.argtypes = [ctypes.c_int]
+    L.or_get_threads.restype = ctypes.c_int
+    L.or_prim_to_cons.argtypes = [ctypes.c_void_p, dp, dp]
+    L.or_cons_to_prim.argtypes = [ctypes.c_void_p, dp, dp]
+    L.or_guardcell_fill.argtypes = [ctypes.c_void_p, dp]
+    L.or_compute_dt.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_int, dp]
+    L.or_hydro_advance.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_double, ctypes.c_int,
+                                   dp, ctypes.c_int, ip]
+    L.or_conserved_totals.argtypes = [ctypes.c_void_p, dp, dp]
+    L.or_restrict_parents.argtypes = [ctypes.c_void_p, dp]
+    L.or_hydro_advance_rk2.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_double,
+                                       ctypes.c_int, dp]
+    L.or_hydro_advance_rk3.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_double,
+                                       ctypes.c_int, dp]
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    L.or_mesh_set_species.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, dp]
+    L.or_riemann_star2.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp]
+    L.or_riemann_sample2.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, dp]
+    L.or_regrid_errors.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, dp]
+    L.or_regrid_plan.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_int, ctypes.c_int, ip, i64p, ip, ip, ip, ip]
+    L.or_regrid_transfer.argtypes = [ctypes.c_void_p, dp, ctypes.c_void_p, ip, ip, ip,
+                                     dp]
+    L.or_mc.restype = ctypes.c_double
+    L.or_mc.argtypes = [ctypes.c_double, ctypes.c_double]
+    L.or_hllc.argtypes = [dp, dp, ctypes.c_int, ctypes.c_double, dp]
+    L.or_riemann_star.argtypes = [dp, dp, ctypes.c_double, dp]
+    L.or_riemann_sample.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(_SO)
-            dp = ctypes.POINTER(ctypes.c_double)
-            ip = ctypes.POINTER(ctypes.c_int)
-            i64p = ctypes.POINTER(ctypes.c_int64)
-            L.or_mesh_create.restype = ctypes.c_void_p
-            L.or_mesh_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                         ip, ip, i64p, ip, dp, dp, ip, ctypes.c_double]
-            L.or_mesh_destroy.argtypes = [ctypes.c_void_p]
-            L.or_last_error.restype = ctypes.c_char_p
-            L.or_set_threads.argtypes = [ctypes.c_int]
-            L.or_get_threads.restype = ctypes.c_int
-            L.or_prim_to_cons.argtypes = [ctypes.c_void_p, dp, dp]
-            L.or_cons_to_prim.argtypes = [ctypes.c_void_p, dp, dp]
-            L.or_guardcell_fill.argtypes = [ctypes.c_void_p, dp]
-            L.or_compute_dt.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_int, dp]
-            L.or_hydro_advance.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_double, ctypes.c_int,
-                                           dp, ctypes.c_int, ip]
-            L.or_conserved_totals.argtypes = [ctypes.c_void_p, dp, dp]
-            L.or_restrict_parents.argtypes = [ctypes.c_void_p, dp]
-            L.or_hydro_advance_rk2.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_double,
-                                               ctypes.c_int, dp]
-            L.or_hydro_advance_rk3.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_double,
-                                               ctypes.c_int, dp]
-            i64p = ctypes.POINTER(ctypes.c_int64)
-            L.or_mesh_set_species.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, dp]
-            L.or_riemann_star2.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp]
-            L.or_riemann_sample2.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double,
-                                             ctypes.c_double, dp]
-            L.or_regrid_errors.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, dp]
-            L.or_regrid_plan.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_double,
-                                         ctypes.c_int, ctypes.c_int, ip, i64p, ip, ip, ip, ip]
-            L.or_regrid_transfer.argtypes = [ctypes.c_void_p, dp, ctypes.c_void_p, ip, ip, ip,
-                                             dp]
-            L.or_mc.restype = ctypes.c_double
-            L.or_mc.argtypes = [ctypes.c_double, ctypes.c_double]
-            L.or_hllc.argtypes = [dp, dp, ctypes.c_int, ctypes.c_double, dp]
-            L.or_riemann_star.argtypes = [dp, dp, ctypes.c_double, dp]
-            L.or_riemann_sample.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp]
+            L = _bind(ctypes.CDLL(_SO))
             _lib = L
     return _lib
+
+
+_OPC_SO = os.path.join(_HERE, "liboracle_opcount.so")
+_opc_lib = None
+
+
+def opcount_lib():
+    """The op-counting build of the oracle (opcount.cpp: oracle.c compiled as
+    C++ with a counting double type, single-threaded), with the same entry
+    points plus or_opcount_reset / or_opcount_get / or_opcount_close."""
+    global _opc_lib
+    with _lock:
+        if _opc_lib is None:
+            srcs = [os.path.join(_HERE, f) for f in ("opcount.cpp", "riemann_exact.c",
+                                                      "oracle.c", "fx_oracle.h")]
+            newest = max(os.path.getmtime(f) for f in srcs)
+            if not os.path.exists(_OPC_SO) or os.path.getmtime(_OPC_SO) < newest:
+                tmp = _OPC_SO + f".tmp{os.getpid()}"
+                obj = tmp + ".riemann.o"
+                subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-c", "-ffp-contract=off",
+                                "-fno-fast-math", "-o", obj, srcs[1]], check=True)
+                subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared",
+                                "-ffp-contract=off", "-fno-fast-math", "-o", tmp, srcs[0], obj,
+                                "-lm"], check=True)
+                os.unlink(obj)
+                os.replace(tmp, _OPC_SO)
+            L = _bind(ctypes.CDLL(_OPC_SO))
+            u64p = ctypes.POINTER(ctypes.c_uint64)
+            L.or_opcount_get.argtypes = [u64p, u64p]
+            _opc_lib = L
+    return _opc_lib
 
 
 def _dp(a: np.ndarray):
@@ -107,8 +143,8 @@ def get_threads() -> int:
 class OracleMesh:
     """The oracle's view of a block set; ``mesh`` is an ``inputs.Mesh``."""
 
-    def __init__(self, mesh, gamma: float = 1.4):
-        L = lib()
+    def __init__(self, mesh, gamma: float = 1.4, library=None):
+        L = self._L = lib() if library is None else library
         self.mesh = mesh
         self.gamma = float(gamma)
         self._level = np.ascontiguousarray(mesh.level, dtype=np.int32)
@@ -134,28 +170,28 @@ class OracleMesh:
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            lib().or_mesh_destroy(h)
+            self._L.or_mesh_destroy(h)
             self._h = None
 
     # -- EOS ------------------------------------------------------------
     def prim_to_cons(self, W: np.ndarray) -> np.ndarray:
         U = np.zeros_like(W)
-        lib().or_prim_to_cons(self._h, _dp(W), _dp(U))
+        self._L.or_prim_to_cons(self._h, _dp(W), _dp(U))
         return U
 
     def cons_to_prim(self, U: np.ndarray) -> np.ndarray:
         W = np.zeros_like(U)
-        lib().or_cons_to_prim(self._h, _dp(U), _dp(W))
+        self._L.or_cons_to_prim(self._h, _dp(U), _dp(W))
         return W
 
     # -- step pieces ------------------------------------------------------
     def guardcell_fill(self, U: np.ndarray) -> None:
-        if lib().or_guardcell_fill(self._h, _dp(U)):
-            raise RuntimeError(lib().or_last_error().decode())
+        if self._L.or_guardcell_fill(self._h, _dp(U)):
+            raise RuntimeError(self._L.or_last_error().decode())
 
     def compute_dt(self, U: np.ndarray, cfl: float = 0.8, form: int = 0) -> float:
         dt = np.zeros(1)
-        lib().or_compute_dt(self._h, _dp(U), float(cfl), int(form), _dp(dt))
+        self._L.or_compute_dt(self._h, _dp(U), float(cfl), int(form), _dp(dt))
         return float(dt[0])
 
     def hydro_advance(self, U: np.ndarray, dt: float, reflux: bool = True,
@@ -172,24 +208,24 @@ class OracleMesh:
             bflux = np.zeros((m.nb, 2 * m.ndim, 5 + int(getattr(m, "nspec", 0)), nf))
             bptr = _dp(bflux)
         if integrator == 1:
-            st = lib().or_hydro_advance_rk2(self._h, _dp(U), _dp(Unew), float(dt), int(reflux), bptr)
+            st = self._L.or_hydro_advance_rk2(self._h, _dp(U), _dp(Unew), float(dt), int(reflux), bptr)
             return Unew, st, bflux
         if integrator == 2:
-            st = lib().or_hydro_advance_rk3(self._h, _dp(U), _dp(Unew), float(dt), int(reflux), bptr)
+            st = self._L.or_hydro_advance_rk3(self._h, _dp(U), _dp(Unew), float(dt), int(reflux), bptr)
             return Unew, st, bflux
         if select is not None:
             sel = np.ascontiguousarray(select, dtype=np.int32)
-            st = lib().or_hydro_advance(self._h, _dp(U), _dp(Unew), float(dt), int(reflux), bptr,
+            st = self._L.or_hydro_advance(self._h, _dp(U), _dp(Unew), float(dt), int(reflux), bptr,
                                         len(sel), _ip(sel))
         else:
-            st = lib().or_hydro_advance(self._h, _dp(U), _dp(Unew), float(dt), int(reflux), bptr,
+            st = self._L.or_hydro_advance(self._h, _dp(U), _dp(Unew), float(dt), int(reflux), bptr,
                                         0, None)
         return Unew, st, bflux
 
     def regrid_errors(self, U: np.ndarray, eps: float = 0.01) -> np.ndarray:
         """Loehner indicator per block (U guard-filled; -1 for parents)."""
         err = np.zeros(self.mesh.nb)
-        lib().or_regrid_errors(self._h, _dp(U), float(eps), _dp(err))
+        self._L.or_regrid_errors(self._h, _dp(U), float(eps), _dp(err))
         return err
 
     def regrid(self, U: np.ndarray, refine_cutoff: float = 0.8, derefine_cutoff: float = 0.2,
@@ -208,10 +244,10 @@ class OracleMesh:
         level, origin, parent, kind, src, octs = self.regrid_plan(err, refine_cutoff,
                                                                  derefine_cutoff, max_level)
         new_mesh = dataclasses.replace(m, level=level, origin=origin, parent=parent, extra={})
-        om = OracleMesh(new_mesh, self.gamma)
+        om = OracleMesh(new_mesh, self.gamma, self._L)
         Unew = np.zeros(new_mesh.shape)
         maps = (kind, src, octs)
-        lib().or_regrid_transfer(self._h, _dp(U), om._h, _ip(maps[0]), _ip(maps[1]),
+        self._L.or_regrid_transfer(self._h, _dp(U), om._h, _ip(maps[0]), _ip(maps[1]),
                                  _ip(maps[2]), _dp(Unew))
         om.restrict_parents(Unew)
         return om, Unew, err, maps
@@ -230,20 +266,20 @@ class OracleMesh:
         kind = np.zeros(cap, dtype=np.int32)
         src = np.zeros(cap, dtype=np.int32)
         octs = np.zeros(cap, dtype=np.int32)
-        nn = lib().or_regrid_plan(self._h, _dp(err), float(refine_cutoff), float(derefine_cutoff),
+        nn = self._L.or_regrid_plan(self._h, _dp(err), float(refine_cutoff), float(derefine_cutoff),
                                   int(max_level), cap, _ip(level),
                                   origin.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                   _ip(parent), _ip(kind), _ip(src), _ip(octs))
         if nn < 0:
-            raise RuntimeError(lib().or_last_error().decode())
+            raise RuntimeError(self._L.or_last_error().decode())
         return tuple(a[:nn].copy() for a in (level, origin, parent, kind, src, octs))
 
     def restrict_parents(self, U: np.ndarray) -> None:
-        lib().or_restrict_parents(self._h, _dp(U))
+        self._L.or_restrict_parents(self._h, _dp(U))
 
     def conserved_totals(self, U: np.ndarray) -> np.ndarray:
         out = np.zeros(5 + int(getattr(self.mesh, "nspec", 0)))
-        lib().or_conserved_totals(self._h, _dp(U), _dp(out))
+        self._L.or_conserved_totals(self._h, _dp(U), _dp(out))
         return out
 
     def step(self, U: np.ndarray, cfl: float = 0.8, dt: float | None = None, form: int = 0,

@@ -38,6 +38,15 @@
 #include <omp.h>
 #endif
 
+/* Op-count instrumentation: OR_STEP(k) opens one unit of work of step k of
+ * the scheme (one cell's primitives, one cell's slopes and predictor, one
+ * face's flux, one cell's update, one cell's signal speed); the counting
+ * build (opcount.cpp) attributes the arithmetic that follows to it.  It
+ * compiles to nothing here and changes no arithmetic. */
+#ifndef OR_STEP
+#define OR_STEP(k) ((void)0)
+#endif
+
 #define OR_MAXLEV 16
 #define OR_MAXSP 4                /* species of the multispecies perfect gas */
 #define OR_MAXV (5 + OR_MAXSP)    /* conserved variables per cell, at most */
@@ -418,6 +427,7 @@ int or_compute_dt(const or_mesh *m, const double *U, double cfl, int form, doubl
     for (int k = 0; k < nz; k++)
       for (int j = 0; j < n; j++)
         for (int i = 0; i < n; i++) {
+          OR_STEP(5);   /* CFL signal speed of one cell */
           double u[OR_MAXV], w[OR_MAXV];
           for (int v = 0; v < m->nv; v++) u[v] = U[cell_index(m, b, v, k + kz, j + ng, i + ng)];
           prim_from_cons(m, u, w);
@@ -525,6 +535,7 @@ static int advance_block(const or_mesh *m, const double *U, double *Unew, double
   for (int k = 0; k < PZ; k++)
     for (int j = 0; j < P; j++)
       for (int i = 0; i < P; i++) {
+        OR_STEP(0);   /* primitives of one cell */
         double u[OR_MAXV], q[OR_MAXV];
         for (int v = 0; v < nv; v++) u[v] = U[cell_index(m, b, v, k, j, i)];
         prim_from_cons(m, u, q);
@@ -534,6 +545,7 @@ static int advance_block(const or_mesh *m, const double *U, double *Unew, double
   for (int k = lo[2] - (nd == 3); k < hi[2] + (nd == 3); k++)
     for (int j = lo[1] - 1; j < hi[1] + 1; j++)
       for (int i = lo[0] - 1; i < hi[0] + 1; i++) {
+        OR_STEP(1);   /* slopes, predictor and face states of one cell */
         double W0[OR_MAXV], dW[3][OR_MAXV] = {{0}}, Wh[OR_MAXV], fm[3][OR_MAXV], fp[3][OR_MAXV];
         for (int v = 0; v < nv; v++) W0[v] = w->W[wi(m, v, k, j, i)];
         for (int d = 0; d < nd; d++) {
@@ -585,6 +597,7 @@ static int advance_block(const or_mesh *m, const double *U, double *Unew, double
     for (int k = lo[2]; k < hk; k++)
       for (int j = lo[1]; j < hj; j++)
         for (int i = lo[0]; i < hii; i++) {
+          OR_STEP(2);   /* flux through one face */
           int o[3] = {i, j, k};
           o[d] -= 1;
           double WL[OR_MAXV], WR[OR_MAXV], F[OR_MAXV];
@@ -601,6 +614,7 @@ static int advance_block(const or_mesh *m, const double *U, double *Unew, double
   for (int k = lo[2]; k < hi[2]; k++)
     for (int j = lo[1]; j < hi[1]; j++)
       for (int i = lo[0]; i < hi[0]; i++) {
+        OR_STEP(3);   /* conservative update of one cell */
         double un[OR_MAXV];
         for (int v = 0; v < nv; v++) {
           double div = 0.0;
@@ -615,6 +629,7 @@ static int advance_block(const or_mesh *m, const double *U, double *Unew, double
           if (Uavg) un[v] = wa * Uavg[cell_index(m, b, v, k, j, i)] + wb * un[v];
           Unew[cell_index(m, b, v, k, j, i)] = un[v];
         }
+        OR_STEP(4);   /* positivity check of the new cell (a diagnostic) */
         double q[OR_MAXV];
         prim_from_cons(m, un, q);
         if (!(q[0] > 0.0) || !(q[4] > 0.0)) bad = 1;
