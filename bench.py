@@ -32,10 +32,14 @@ sys.path.insert(0, ROOT)
 METRIC = "zone-updates/s"
 UNIT = "zone-updates/s"
 HBM_BYTES_PER_ZONE = {"f64": 80.0, "f32bulk": 40.0}
-# FP64 arithmetic per zone update, counted on the scheme's definition
-# (each +, -, *, /, sqrt = 1): primitives 12, MC slopes 105, Hancock predictor
-# 77, face states 60, HLLC 3 x 98, update 55.
-ALGO_FLOPS_PER_ZONE = 603.0
+# FP64 arithmetic per zone update (each +, -, *, / and sqrt = 1): one
+# primitive conversion, one cell's slopes/predictor/face states, ndim HLLC
+# face fluxes, one conservative update and one CFL signal speed, counted on
+# the oracle's op-counting build ("python -m oracle.opcount <workload> 4 10",
+# one full step after 10; profiles/flops_per_zone.md).  The HLLC branch mix,
+# and with it the count, depends a little on the flow.
+ALGO_FLOPS_PER_ZONE = {"kh3d": 619.9, "sedov_amr": 597.2, "advection3d": 602.3,
+                       "sod2d": 411.8}
 # FP64 peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz.
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 # DRAM bytes (read + written) per zone of the update kernel, from one ncu
@@ -43,6 +47,29 @@ FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 # over 2,097,152 zones); the full launch's traffic scales with its zones.
 # Valid for the kernel build those counters were taken on.
 TRAFFIC_BYTES_PER_ZONE = {"f64": 102.3, "f32bulk": 67.0}
+
+
+def measure_fma_peak(fx, stream, precision, reps: int = 3):
+    """FMA-pipe throughput (flop/s) of this GPU now: the library's probe
+    kernel (independent FMA chains on every SM), best of `reps` launches timed
+    with CUDA events on `stream`."""
+    import torch
+    nsm = torch.cuda.get_device_properties(stream.device).multi_processor_count
+    ctas = nsm * 8
+    dtype = torch.float64 if precision == fx.FX_F64 else torch.float32
+    out = torch.empty(ctas, dtype=dtype, device=stream.device)
+    iters = 4000 if precision == fx.FX_F64 else 100000
+    best = 0.0
+    with torch.cuda.stream(stream):
+        fx.fx_fma_probe(precision, ctas, 64, out.data_ptr(), stream)   # warm-up
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            flops = fx.fx_fma_probe(precision, ctas, iters, out.data_ptr(), stream)
+            b.record(stream)
+            stream.synchronize()
+            best = max(best, flops / (a.elapsed_time(b) / 1e3))
+    return best
 
 
 def load_peaks():
@@ -301,13 +328,14 @@ def measure_variants(args, fx, inputs, mesh, dev, cfl, zones, bs, ws, hbm_peak):
     sec = a.elapsed_time(b) / 1e3
     hyd5 = float(np.mean([x.elapsed_time(y) for x, y in ev5])) / 1e3
     z, t = aggregate(zones * args.steps, sec, dev)
-    eq5 = ALGO_FLOPS_PER_ZONE * zones / hyd5
+    eq5 = ALGO_FLOPS_PER_ZONE[args.workload] * zones / hyd5
     out["f64_double_word"] = {
         "value": z / t, "unit": UNIT, "ms_per_step": 1e3 * t / args.steps, "dtype": "f64 state, "
         "double-word (2 x f32) arithmetic", "hydro_ms": hyd5 * 1e3,
         "fp64_equivalent_tflops": eq5 / 1e12,
         "fp64_equivalent_frac_of_fp64_peak": eq5 / FP64_PEAK_FLOPS,
-        "note": "the scheme's 603 FP64 flops per zone per update, computed on the FP32 pipe",
+        "note": f"the scheme's {ALGO_FLOPS_PER_ZONE[args.workload]} FP64 flops per zone update, "
+                "computed on the FP32 pipe",
         "max_rel_dev_from_f64_after_one_step": dev5, "ok": bs5.status() == 0}
     bs5.close()
     # (iv) multispecies perfect gas: the same workload carrying two species
@@ -427,7 +455,12 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args, workload_name(args.workload, full), full) | {"replicas": 1},
+            "config": workload_config(args, workload_name(args.workload, full), full)
+            | {"replicas": 1,
+               # what the oracle stepped: a bounded sample of that workload
+               "ran": {"workload": workload_name(args.workload, mesh), "blocks": mesh.nb,
+                       "cells": mesh.leaf_zones(), "nxb": mesh.nxb, "nguard": mesh.ng,
+                       "sample_of": workload_name(args.workload, full)}},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.get_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -544,17 +577,23 @@ def run_ours(args):
 
     peaks, peak_kind = load_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved_flops = ALGO_FLOPS_PER_ZONE * zones_per_step / hydro_s
+    flops_per_zone = ALGO_FLOPS_PER_ZONE[args.workload]
+    achieved_flops = flops_per_zone * zones_per_step / hydro_s
     bpz = HBM_BYTES_PER_ZONE[args.precision]
     if args.precision == "f64":
+        fp64_meas = measure_fma_peak(fx, stream, fx.FX_F64)
         roof = {"bound": "alu", "kernel": kname,
                 "achieved": achieved_flops / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
                 "unit": "TFLOP/s", "frac": achieved_flops / FP64_PEAK_FLOPS,
                 "traffic": TRAFFIC_BYTES_PER_ZONE["f64"] * zones_per_step
                 if args.workload == "kh3d" else None,
                 "peak_kind": "derived FP64 DFMA rate (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "peak_measured": fp64_meas / 1e12,
+                "frac_of_measured": achieved_flops / fp64_meas,
+                "peak_measured_kind": "FP64 FMA probe (fx_fma_probe) timed in this run",
                 "traffic_note": "bytes per launch: ncu DRAM read+write of the 128^3 case scaled by zones",
-                "algorithmic_flops_per_zone": ALGO_FLOPS_PER_ZONE}
+                "algorithmic_flops_per_zone": flops_per_zone,
+                "algorithmic_flops_source": "oracle op-counting build (oracle/opcount.py)"}
     else:
         gbs = bpz * zones_per_step / hydro_s / 1e9
         roof = {"bound": "hbm", "kernel": kname, "achieved": gbs,

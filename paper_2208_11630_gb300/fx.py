@@ -85,6 +85,7 @@ def load(build: bool = True):
             "fx_block_fluxes": (vp, [vp, c_int]),
             "fx_kernel_launches": (ctypes.c_longlong, []),
             "fx_dword_selftest": (c_int, [c_int, vp, vp, vp, c_int, vp]),
+            "fx_fma_probe": (c_int, [c_int, c_int, c_int, vp, vp, ctypes.POINTER(ctypes.c_double)]),
             "fx_batch_create": (c_int, [vp, c_int, ctypes.POINTER(vp)]),
             "fx_batch_destroy": (c_int, [vp]),
             "fx_batch_add": (c_int, [vp, vp, c_double, c_int, vp, ip]),
@@ -366,6 +367,17 @@ def fx_dword_selftest(op: int, a, b=None, stream=None):
     if rc != FX_OK:
         raise FxError(rc, "fx_dword_selftest")
     return out
+
+
+def fx_fma_probe(precision: int, ctas: int, iters: int, out_ptr: int, stream=None) -> float:
+    """Launch the FMA throughput probe (fx_fma_probe) on ``stream``; returns the
+    flops the launch performs (time it with events on the same stream)."""
+    flops = ctypes.c_double(0.0)
+    rc = load().fx_fma_probe(int(precision), int(ctas), int(iters), ctypes.c_void_p(out_ptr),
+                             _stream_ptr(stream), ctypes.byref(flops))
+    if rc != FX_OK:
+        raise FxError(rc, "fx_fma_probe")
+    return flops.value
 
 
 # ---------------------------------------------------------------- convenience

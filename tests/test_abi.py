@@ -97,6 +97,7 @@ calls = {
  "fx_compute_dt_noalloc": lambda: L.fx_compute_dt_noalloc(None, 3, 1, 16, 4, None, d(1.4), d(0.8),
                                                           0, None, None, None, ctypes.c_size_t(0)),
  "fx_dword_selftest": lambda: L.fx_dword_selftest(0, None, None, None, 4, None),
+ "fx_fma_probe": lambda: L.fx_fma_probe(0, 1, 1, None, None, None),
 }
 for name, f in calls.items():
     print(name, f(), flush=True)

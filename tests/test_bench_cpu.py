@@ -35,6 +35,9 @@ def test_reference_arm_line():
     assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
     assert line["config"]["workload"] == bench.workload_name("sod2d", full)
     assert line["config"]["cells"] == full.leaf_zones()
+    sample = inputs.workload_mesh("sod2d", bench.REFERENCE_SAMPLE_SCALE["sod2d"])
+    assert line["config"]["ran"]["cells"] == sample.leaf_zones()   # what the oracle stepped
+    assert line["config"]["ran"]["sample_of"] == line["config"]["workload"]
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
