@@ -213,6 +213,10 @@ def test_conservation_and_uniform_state(orc, fx):
     T0 = bs.totals()
     np.testing.assert_allclose(T0, om.conserved_totals(U), rtol=1e-14, atol=1e-15)
     bs.run(100, 0.8)
+    # Roundoff of a conserved total is bounded by a small multiple of eps times
+    # the magnitudes summed, at the start and at the end: sum |U(0)| alone is
+    # no scale for a component that starts at exactly zero, such as m_z here
+    # (v_z = 0 initially; pressure gradients along z make it nonzero).
     A = om.conserved_totals(np.abs(U)) + om.conserved_totals(np.abs(bs.state()))
     assert np.all(np.abs(bs.totals() - T0) / A <= 1e-13)
     for mesh in (mesh_2level(4, 8, 4), inputs.uniform_mesh(2, (3, 2), 16, 4)):
@@ -393,6 +397,7 @@ def test_rk2_variant(orc, fx, case, integrator):
     assert bs.status() == 0
     assert max_rel_err(mesh, bs.state(), Uo2) <= 1e-10
     if mesh.bc[0][0] == inputs.PERIODIC:
+        # scale: magnitudes at both ends, as in the conservation test above
         A = om.conserved_totals(np.abs(U)) + om.conserved_totals(np.abs(Uo2))
         A = np.where(A == 0, 1.0, A)      # m_z of a 2D run is zero everywhere
         assert np.all(np.abs(bs.totals() - om.conserved_totals(U)) / A <= 1e-13)
