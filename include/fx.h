@@ -107,6 +107,15 @@ FX_API int fx_finalize(fx_ctx *ctx);
  *               step).  Applies to the single-gas and multispecies
  *               MUSCL-Hancock updates and to the SSP-RK stages; ignored by
  *               FX_F32BULK; batches honour it per request (fx_batch_add).
+ *               2 = in FP32 arithmetic (the other reading of an FP32 path,
+ *               kept as an ablation of FX_F32BULK): the state stays FP64
+ *               (80 bytes of HBM per zone update), primitives, slopes,
+ *               predictor and HLLC run in FP32, the flux divergence is
+ *               added to the FP64 state in FP64 and the next dt is reduced
+ *               in FP64; errors of FP32 arithmetic (about 1e-7 relative per
+ *               step).  Single-gas MUSCL-Hancock only: fx_hydro_advance
+ *               refuses it with the SSP-RK integrators or species, and
+ *               fx_batch_add refuses such block sets (FX_ERR_ARG).
  * Errors: FX_ERR_ARG for an unknown key or value. */
 FX_API int fx_set_option(fx_ctx *ctx, const char *key, double value);
 

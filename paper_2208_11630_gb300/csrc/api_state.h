@@ -21,7 +21,7 @@ struct fx_ctx {
   int cfl_form = 0;
   int reflux = 1;
   int integrator = 0;   // 0 MUSCL-Hancock, 1 SSP-RK2, 2 SSP-RK3
-  int f64_arith = 0;    // MUSCL-Hancock update of FP64 sets: 0 FP64, 1 double-word
+  int f64_arith = 0;    // MUSCL-Hancock update of FP64 sets: 0 FP64, 1 double-word, 2 FP32
   int nspec = 0;        // multispecies perfect gas: species and their constants
   double spa[FX_MAXSPEC] = {0, 0, 0, 0}, spb[FX_MAXSPEC] = {0, 0, 0, 0};
   int device = 0;
@@ -96,7 +96,7 @@ int cuda_fail(fx_ctx *ctx, cudaError_t e, const char *where);
 // (also the base of the SSP-RK stages): the arithmetic of its update.
 inline fx::HydroStage muscl_stage(const fx_ctx *ctx, const fx_blocks *bs) {
   fx::HydroStage st;
-  st.dword = ctx->f64_arith && bs->prec == 0;
+  st.dword = bs->prec == 0 ? ctx->f64_arith : 0;
   return st;
 }
 

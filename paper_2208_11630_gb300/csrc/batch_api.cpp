@@ -45,7 +45,7 @@ constexpr int kClasses = 3;
 // Compute class of a block set's update: its precision, or 2 for an FP64 set
 // whose context asks for double-word arithmetic.
 int compute_class(const fx_blocks *bs) {
-  return bs->prec == 0 && bs->ctx->f64_arith ? 2 : bs->prec;
+  return bs->prec == 0 && bs->ctx->f64_arith == 1 ? 2 : bs->prec;
 }
 
 }  // namespace
@@ -273,6 +273,8 @@ int fx_batch_add(fx_batch *b, fx_blocks *bs, double cfl, int nsteps, void *strea
   if (bs->ctx->integrator != 0)
     return fail(b->ctx, FX_ERR_ARG, "batches step MUSCL-Hancock block sets only");
   if (bs->nvar != 5) return fail(b->ctx, FX_ERR_ARG, "batches step single-gas block sets only");
+  if (bs->prec == 0 && bs->ctx->f64_arith == 2)
+    return fail(b->ctx, FX_ERR_ARG, "FP32 arithmetic on FP64 state (f64_arith = 2) is not batched");
   int s = -1;
   for (int r = 0; r < b->max_req; ++r)
     if (!b->slot[r]) { s = r; break; }

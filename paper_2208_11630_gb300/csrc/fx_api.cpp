@@ -166,7 +166,8 @@ int fx_set_option(fx_ctx *ctx, const char *key, double value) {
     return FX_OK;
   }
   if (!strcmp(key, "f64_arith")) {
-    if (value != 0.0 && value != 1.0) return fail(ctx, FX_ERR_ARG, "f64_arith must be 0 or 1");
+    if (value != 0.0 && value != 1.0 && value != 2.0)
+      return fail(ctx, FX_ERR_ARG, "f64_arith must be 0, 1 or 2");
     ctx->f64_arith = (int)value;
     return FX_OK;
   }
@@ -545,6 +546,9 @@ int fx_hydro_advance(fx_ctx *ctx, fx_blocks *bs, const double *dt_dev, void *str
   const int *leaves = bs->d_lists + bs->leaves_off;
   if ((ctx->integrator == 1 || ctx->integrator == 2) && bs->nvar > 5)
     return fail(ctx, FX_ERR_ARG, "the SSP-RK integrators step a single gas only");
+  if (ctx->f64_arith == 2 && bs->prec == 0 && (ctx->integrator != 0 || bs->nvar > 5))
+    return fail(ctx, FX_ERR_ARG,
+                "FP32 arithmetic on FP64 state (f64_arith = 2) is the single-gas MUSCL-Hancock update only");
   if (ctx->integrator == 1 || ctx->integrator == 2) {
     // SSP-RK2: U1 = U + dt L(U) into the other buffer; coarse-fine fill of
     // U1; U = (U + (U1 + dt L(U1))) / 2 in place; registers hold the stage

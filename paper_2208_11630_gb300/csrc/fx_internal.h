@@ -105,7 +105,8 @@ struct HydroStage {
   double wa = 0.5, wb = 0.5;  // blend weights
   double reg_w = 1.0;         // weight of the fluxes in the registers
   int reg_add = 0;            // 0 store, 1 add to the registers
-  int dword = 0;              // 1: FP64 state, double-word arithmetic (MUSCL-Hancock only)
+  int dword = 0;              // FP64 state: 1 double-word arithmetic (MUSCL-Hancock only),
+                              // 2 FP32 arithmetic (single gas, MUSCL-Hancock only)
 };
 
 // smax (may be null): receives atomicMax of the bit patterns of the new

@@ -508,19 +508,35 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
     sconst.idx[1] = kcf[11];
     sconst.idx[2] = kcf[12];
   }
-  auto signal = [&](const R (&u)[NF], int ci, int cj, int ck) {
+  // FP64 state with FP32 arithmetic (S = double, R = float): the flux
+  // divergence, formed in FP32, is added to the FP64 state in FP64, and the
+  // new state's signal speed is taken in FP64 from the stored values -- the
+  // computation of the standalone reduction of an FP64 block set, so that
+  // the fused dt equals a fresh one
+  constexpr bool kAbl = std::is_same<S, double>::value && std::is_same<R, float>::value;
+  [[maybe_unused]] const SignalConsts<double> sconst_d(m, lev);
+  [[maybe_unused]] double smax_d = 0.0;
+  auto masked = [&](int ci, int cj, int ck) {
     if (fmask) {
       const int cc[3] = {ci, cj, ck};
       for (int d = 0; d < NDIM; ++d) {
-        if (((fmask >> (2 * d)) & 1u) && cc[d] == 0) return;
-        if (((fmask >> (2 * d + 1)) & 1u) && cc[d] == n - 1) return;
+        if (((fmask >> (2 * d)) & 1u) && cc[d] == 0) return true;
+        if (((fmask >> (2 * d + 1)) & 1u) && cc[d] == n - 1) return true;
       }
     }
+    return false;
+  };
+  auto signal = [&](const R (&u)[NF], int ci, int cj, int ck) {
+    if (masked(ci, cj, ck)) return;
     // FP32: the direction loop unrolled; FP64 (at its register limit) keeps
     // it rolled, which measured faster there
     constexpr int kSigDim = std::is_same<R, float>::value ? NDIM : 0;
     const R sg = cell_signal<R, kSigDim>(m, u, NS, sconst, cfl_form);
     smax_t = sig_max(smax_t, sg);   // a NaN stays
+  };
+  [[maybe_unused]] auto signal_d = [&](const double (&u)[NF], int ci, int cj, int ck) {
+    if (masked(ci, cj, ck)) return;
+    smax_d = sig_max(smax_d, cell_signal<double, 0>(m, u, NS, sconst_d, cfl_form));
   };
 
 
@@ -718,11 +734,17 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
     if (NDIM == 3 && p >= 1) {
       const long long o = ((long long)(p - 1 + ng) * P + (y0 + tj + ng)) * P + (x0 + ti + ng);
       R un[NF];
+      [[maybe_unused]] double ud[NF];
 #pragma unroll
       for (int v = 0; v < NF; ++v) {
         if constexpr (kF32) {
           const float d = txy[v] + scaled_diff(fzl[v], Fz[v], cz);
-          un[v] = float(Ub[o + v * vs]) + d;
+          if constexpr (kAbl) {
+            ud[v] = Ub[o + v * vs] + double(d);
+            un[v] = float(ud[v]);
+          } else {
+            un[v] = float(Ub[o + v * vs]) + d;
+          }
         } else {
           const R div = txy[v] + (fzl[v] - Fz[v]) * rdz;
           un[v] = R(Ub[o + v * vs]) + rdt * div;
@@ -731,11 +753,15 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
           if (Uavg)
             un[v] = fma(R(st.wa), R(Uavg[(long long)b * m.bstride + o + v * vs]), R(st.wb) * un[v]);
         }
-        Unb[o + v * vs] = S(un[v]);
+        if constexpr (kAbl) Unb[o + v * vs] = ud[v];
+        else Unb[o + v * vs] = S(un[v]);
       }
       if (!(un[0] > R(0)) || !(R(2) * un[4] * un[0] > un[1] * un[1] + un[2] * un[2] + un[3] * un[3]))
         atomicOr(status, 1);
-      if (smax_out) signal(un, x0 + ti, y0 + tj, p - 1);
+      if (smax_out) {
+        if constexpr (kAbl) signal_d(ud, x0 + ti, y0 + tj, p - 1);
+        else signal(un, x0 + ti, y0 + tj, p - 1);
+      }
     }
     if (inner) {
       const R *Fx = fxm + tj * SM::W2 + ti + 1;
@@ -754,20 +780,31 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
       if (NDIM == 2) {
         const long long o = (long long)(y0 + tj + ng) * P + (x0 + ti + ng);
         R un[NF];
+        [[maybe_unused]] double ud[NF];
 #pragma unroll
         for (int v = 0; v < NF; ++v) {
-          if constexpr (kF32) un[v] = float(Ub[o + v * vs]) + txy[v];
-          else un[v] = R(Ub[o + v * vs]) + rdt * txy[v];
+          if constexpr (kAbl) {
+            ud[v] = Ub[o + v * vs] + double(txy[v]);
+            un[v] = float(ud[v]);
+          } else if constexpr (kF32) {
+            un[v] = float(Ub[o + v * vs]) + txy[v];
+          } else {
+            un[v] = R(Ub[o + v * vs]) + rdt * txy[v];
+          }
           if constexpr (RK) {
             if (Uavg)
               un[v] = fma(R(st.wa), R(Uavg[(long long)b * m.bstride + o + v * vs]), R(st.wb) * un[v]);
           }
-          Unb[o + v * vs] = S(un[v]);
+          if constexpr (kAbl) Unb[o + v * vs] = ud[v];
+          else Unb[o + v * vs] = S(un[v]);
         }
         if (!(un[0] > R(0)) ||
             !(R(2) * un[4] * un[0] > un[1] * un[1] + un[2] * un[2] + un[3] * un[3]))
           atomicOr(status, 1);
-        if (smax_out) signal(un, x0 + ti, y0 + tj, 0);
+        if (smax_out) {
+          if constexpr (kAbl) signal_d(ud, x0 + ti, y0 + tj, 0);
+          else signal(un, x0 + ti, y0 + tj, 0);
+        }
       }
     }
 #pragma unroll
@@ -775,7 +812,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
   }
   if (smax_out) {
     // maximum over the CTA on the bit patterns of non-negative doubles
-    unsigned long long bits = __double_as_longlong(double(smax_t));
+    unsigned long long bits = __double_as_longlong(kAbl ? smax_d : double(smax_t));
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned long long other = __shfl_down_sync(0xffffffffu, bits, o);
       bits = other > bits ? other : bits;

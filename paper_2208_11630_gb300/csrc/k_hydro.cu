@@ -77,7 +77,7 @@ cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, 
   if (m.nspec > 0) {   // multispecies gas (k_hydro_sp.cu): MUSCL-Hancock only
     if (!st.pred || st.Uavg || st.reg_add || st.reg_w != 1.0) return cudaErrorInvalidValue;
     if (st.dword) {
-      if (prec != 0) return cudaErrorInvalidValue;
+      if (prec != 0 || st.dword != 1) return cudaErrorInvalidValue;
       return launch_hydro_species_dw(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
     }
     return launch_hydro_species(m, U, Unew, prec, leaves, n, dt, regs, status, smax, rmask, form,
@@ -85,17 +85,25 @@ cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, 
   }
   if (!st.pred) {   // an SSP Runge-Kutta stage (k_hydro_rk.cu; double-word: k_hydro_dw.cu)
     if (st.dword) {
-      if (prec != 0) return cudaErrorInvalidValue;
+      if (prec != 0 || st.dword != 1) return cudaErrorInvalidValue;
       return launch_hydro_rk_dw(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, st);
     }
     return launch_hydro_rk(m, U, Unew, prec, leaves, n, dt, regs, status, smax, rmask, form, s, st);
   }
   if (st.Uavg || st.reg_add || st.reg_w != 1.0) return cudaErrorInvalidValue;
+  const int T = (m.nxb % 16 == 0) ? 16 : 8;
+  if (st.dword == 2) {   // FP64 state, FP32 arithmetic (option f64_arith = 2)
+    if (prec != 0) return cudaErrorInvalidValue;
+    if (m.ndim == 3)
+      return T == 16 ? launch_t<3, 16, double, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
+                     : launch_t<3, 8, double, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
+    return T == 16 ? launch_t<2, 16, double, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
+                   : launch_t<2, 8, double, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
+  }
   if (st.dword) {
     if (prec != 0) return cudaErrorInvalidValue;
     return launch_hydro_dw(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
   }
-  const int T = (m.nxb % 16 == 0) ? 16 : 8;
   if (prec == 0) {
     if (m.ndim == 3)
       return T == 16 ? launch_t<3, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)

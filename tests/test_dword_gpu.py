@@ -98,8 +98,10 @@ def test_dword_host_round_trip(fx):
 def test_dword_option_values(fx):
     ctx = fx.fx_init(1.4, 16, 4)
     try:
-        with pytest.raises(fx.FxError):
-            fx.fx_set_option(ctx, "f64_arith", 2)
+        for bad in (3, -1, 0.5):     # 0 FP64, 1 double-word, 2 FP32 arithmetic
+            with pytest.raises(fx.FxError):
+                fx.fx_set_option(ctx, "f64_arith", bad)
+        fx.fx_set_option(ctx, "f64_arith", 2)
         fx.fx_set_option(ctx, "f64_arith", 1)
         fx.fx_set_option(ctx, "f64_arith", 0)
     finally:

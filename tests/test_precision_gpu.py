@@ -149,3 +149,83 @@ def test_f32bulk_rk2_one_step(orc, fx, case, integrator):
     err = max_rel_err_vec(mesh, bs.state(), Uo)
     print(f"\nf32bulk SSP-RK{integrator + 1} one step {case}: max rel err {err:.3e}")
     assert err <= 1e-5, err
+
+
+# ---- the other FP32 reading: FP64 state, FP32 arithmetic (f64_arith = 2) --
+# Same FP32 arithmetic as FP32-bulk, but the state never rounds to FP32: the
+# flux divergence (formed and rounded in FP32) is added to the FP64 state in
+# FP64, and dt is reduced in FP64.  Its error against the FP64 oracle is that
+# of the FP32 arithmetic alone (the initial state is exact), so the FP32-bulk
+# tolerances bound it; the fused dt must equal an FP64 reduction of the state.
+
+def abl_blockset(fx, mesh, W):
+    bs = fx.BlockSet(mesh, 1.4, precision=fx.FX_F64, options={"f64_arith": 2})
+    bs.set_primitive(W)
+    return bs
+
+
+@pytest.mark.parametrize("case", ["sod2d", "kh64", "amr_sedov_small", "smooth3d_nxb32",
+                                  "blocky3d_outflow", "amr_smooth_periodic",
+                                  "reflect3d_mixed"])
+def test_f64_state_f32_arith_one_step(orc, fx, case):
+    mesh, W = CASES[case]()
+    om = orc.OracleMesh(mesh)
+    U = om.prim_to_cons(W)
+    bs = abl_blockset(fx, mesh, W)
+    bs.set_conserved(U)
+    Uo, dto = om.step(U)
+    bs.step(0.8)
+    assert bs.status() == 0
+    assert float(bs.dt.item()) == pytest.approx(dto, rel=1e-15)   # FP64 state, FP64 dt
+    err = max_rel_err_vec(mesh, bs.state(), Uo)
+    print(f"\nf64 state / f32 arithmetic one step {case}: max rel err {err:.3e}")
+    assert err <= 1e-5, err
+    # the dt the update reduced on the fly equals a fresh FP64 reduction
+    fused = bs.compute_dt(0.8)
+    fx.fx_blocks_mark_dirty(bs.bs)
+    assert fused == bs.compute_dt(0.8)
+
+
+@pytest.mark.parametrize("case", ["kh64", "amr_sedov_small"])
+def test_f64_state_f32_arith_100_steps(orc, fx, case):
+    mesh, W = CASES[case]()
+    om = orc.OracleMesh(mesh)
+    U = om.prim_to_cons(W)
+    bs = abl_blockset(fx, mesh, W)
+    bs.set_conserved(U)
+    Uo, _, _ = om.run(U, nsteps=100)
+    bs.run(100, 0.8)
+    assert bs.status() == 0
+    err = max_rel_err_vec(mesh, bs.state(), Uo)
+    f32 = f32_blockset(fx, mesh, W)
+    f32.run(100, 0.8)
+    err32 = max_rel_err_vec(mesh, f32.state(), Uo)
+    print(f"\n100 steps {case}: f64 state / f32 arithmetic {err:.3e}, f32-bulk {err32:.3e}")
+    assert err <= 1e-3, err
+
+
+def test_f64_state_f32_arith_conservation_and_refusals(orc, fx):
+    mesh = inputs.uniform_mesh(3, (2, 2, 2), 16, 4, inputs.PERIODIC)
+    bs = abl_blockset(fx, mesh, inputs.kh_state(mesh))
+    T0 = bs.totals()
+    bs.run(100, 0.8)
+    A = orc.OracleMesh(mesh).conserved_totals(np.abs(bs.state()))
+    drift = np.abs(bs.totals() - T0) / A
+    print(f"\nf64 state / f32 arithmetic conservation drift after 100 steps: {drift}")
+    # each cell's increment is rounded in FP32, so the increments of two
+    # neighbours through a shared face cancel only to FP32 rounding
+    assert np.all(drift <= 1e-6), drift
+    # never batched, and single-gas MUSCL-Hancock only
+    ctx = fx.fx_init(1.4, 16, 4)
+    fx.fx_set_option(ctx, "f64_arith", 2)
+    b2 = fx.BlockSet(mesh, 1.4, ctx=ctx)
+    b2.set_primitive(inputs.kh_state(mesh))
+    batch = fx.Batch(ctx, 2)
+    with pytest.raises(fx.FxError) as e:
+        batch.add(b2, 0.8, 1)
+    assert "not batched" in str(e.value)
+    batch.close()
+    fx.fx_set_option(ctx, "integrator", 1)
+    with pytest.raises(fx.FxError) as e:
+        b2.step(0.8)
+    assert "MUSCL-Hancock update only" in str(e.value)
