@@ -338,6 +338,49 @@ def measure_variants(args, fx, inputs, mesh, dev, cfl, zones, bs, ws, hbm_peak):
                 "computed on the FP32 pipe",
         "max_rel_dev_from_f64_after_one_step": dev5, "ok": bs5.status() == 0}
     bs5.close()
+    # (vi) the other FP32 reading: FP64 state (80 B/zone), FP32 arithmetic,
+    # FP64 accumulation of the update (option f64_arith = 2); timed like (ii),
+    # with its deviation from the FP64 update after one step
+    mesh6, W6, gamma6, _ = inputs.workload(args.workload, scale=args.scale)
+    bs6 = fx.BlockSet(mesh6, gamma6, precision=fx.FX_F64, device=dev, options={"f64_arith": 2})
+    bs6.set_primitive(W6)
+    ref6 = fx.BlockSet(mesh6, gamma6, precision=fx.FX_F64, device=dev)
+    ref6.set_primitive(W6)
+    del W6
+    fx.fx_step(bs6.ctx, bs6.bs, cfl, bs6.dt.data_ptr(), sptr)
+    fx.fx_step(ref6.ctx, ref6.bs, cfl, ref6.dt.data_ptr(), sptr)
+    torch.cuda.synchronize()
+    a6, r6 = bs6.current[sl][leaf5], ref6.current[sl][leaf5]
+    scale6 = r6.abs().amax(dim=(0, 2, 3, 4), keepdim=True)
+    scale6[:, 1:4] = r6[:, 1:4].square().sum(dim=1).sqrt().amax()
+    dev6 = float(((a6 - r6).abs() / torch.maximum(r6.abs(), scale6.clamp_min(1e-300))).max())
+    del a6, r6
+    ref6.close()
+    dtp6 = bs6.dt.data_ptr()
+    for _ in range(args.warmup):
+        fx.fx_step(bs6.ctx, bs6.bs, cfl, dtp6, sptr)
+    stream.synchronize()
+    ev6 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    a.record(stream)
+    for k in range(args.steps):
+        fx.fx_compute_dt(bs6.ctx, bs6.bs, cfl, dtp6, sptr)
+        fx.fx_guardcell_fill_amr(bs6.ctx, bs6.bs, sptr)
+        ev6[k][0].record(stream)
+        fx.fx_hydro_advance(bs6.ctx, bs6.bs, dtp6, sptr)
+        ev6[k][1].record(stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3
+    hyd6 = float(np.mean([x.elapsed_time(y) for x, y in ev6])) / 1e3
+    z, t = aggregate(zones * args.steps, sec, dev)
+    out["f64_state_f32_arith"] = {
+        "value": z / t, "unit": UNIT, "ms_per_step": 1e3 * t / args.steps,
+        "dtype": "f64 state, f32 arithmetic, f64 update accumulation", "hydro_ms": hyd6 * 1e3,
+        "hydro_hbm_frac": HBM_BYTES_PER_ZONE["f64"] * zones / hyd6 / (hbm_peak * 1e9),
+        "algorithmic_bytes_per_zone": HBM_BYTES_PER_ZONE["f64"],
+        "max_rel_dev_from_f64_after_one_step": dev6, "ok": bs6.status() == 0}
+    bs6.close()
     # (iv) multispecies perfect gas: the same workload carrying two species
     # (gamma 1.4 / A 28.96 inside the shear band, 5/3 / 4 outside)
     import dataclasses
@@ -414,6 +457,131 @@ def measure_variants(args, fx, inputs, mesh, dev, cfl, zones, bs, ws, hbm_peak):
         "levels": np.bincount(bs3.mesh.level).tolist(), "timing": "wall clock",
         "ok": bs3.status() == 0}
     bs3.close()
+    return out
+
+
+def timed_steps(fx, bs, cfl, stream, warmup, steps):
+    """Device time of `steps` full steps of block set `bs` on `stream` (dt,
+    coarse-fine fill, update = fx_step), after `warmup` untimed ones; returns
+    (seconds of the steps, mean seconds of one update launch), CUDA events."""
+    import torch
+    sptr = stream.cuda_stream
+    dtp = bs.dt.data_ptr()
+    for _ in range(warmup):
+        fx.fx_step(bs.ctx, bs.bs, cfl, dtp, sptr)
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for k in range(steps):
+        fx.fx_compute_dt(bs.ctx, bs.bs, cfl, dtp, sptr)
+        fx.fx_guardcell_fill_amr(bs.ctx, bs.bs, sptr)
+        ev[k][0].record(stream)
+        fx.fx_hydro_advance(bs.ctx, bs.bs, dtp, sptr)
+        ev[k][1].record(stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3, float(np.mean([x.elapsed_time(y) for x, y in ev])) / 1e3
+
+
+def timed_batch(fx, bs, cfl, stream, warmup, steps, nxb, ng):
+    """The same as one request of a batch: coarse-fine fill, persistent update
+    and flux correction replayed as one CUDA graph per step, launch choice
+    autotuned; returns (seconds of the `steps` timed steps, tile, CTAs/SM)."""
+    import torch
+    sptr = stream.cuda_stream
+    ctx = fx.fx_init(1.4, nxb, ng)
+    batch = fx.Batch(ctx, 1)
+    try:
+        slot = batch.add(bs, cfl, warmup + steps, stream=sptr)
+        batch.tune(stream=sptr)
+        batch.run(warmup, stream=sptr)
+        stream.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        batch.run(steps, stream=sptr)
+        b.record(stream)
+        torch.cuda.synchronize()
+        batch.remove(slot, stream=sptr)
+        tile, ctas = batch.choice(bs.mesh.ndim, bs.precision)
+    finally:
+        batch.close()
+        fx.fx_finalize(ctx)
+    return a.elapsed_time(b) / 1e3, tile, ctas
+
+
+def measure_configs(args, fx, inputs, dev, hbm_peak):
+    """The other workloads of the benchmark plan, each timed on the device:
+    the 2D Sod tube (50 steps, FP64 and FP32-bulk, per call and as a
+    graph-replayed batch), the 3D Sedov blast on its two-level octree through
+    the batched persistent kernel and CUDA graph (20 warm-up + 100 timed
+    steps; FP64 and FP32-bulk, and the per-call FP64 path beside it), and
+    smooth advection at 512^3 (FP64 and FP32-bulk)."""
+    import torch
+    stream = torch.cuda.Stream(device=dev)
+    out = {}
+    for prec_name, prec in (("f64", fx.FX_F64), ("f32bulk", fx.FX_F32BULK)):
+        bpz = HBM_BYTES_PER_ZONE[prec_name]
+        # 2D Sod: 128^2 as 8 x 8 blocks of 16^2, 50 steps (state 1.3 MB: L2-resident)
+        mesh, W, gamma, cfl = inputs.workload("sod2d")
+        zones = mesh.leaf_zones()
+        bs = fx.BlockSet(mesh, gamma, precision=prec, device=dev)
+        bs.set_primitive(W)
+        sec, hyd = timed_steps(fx, bs, cfl, stream, 5, 50)
+        ok = bs.status() == 0
+        bs.set_primitive(W)
+        gsec, tile, ctas = timed_batch(fx, bs, cfl, stream, 5, 50, mesh.nxb, mesh.ng)
+        out[f"sod2d_128^2_{prec_name}"] = {
+            "value": zones * 50 / sec, "unit": UNIT, "ms_per_step": 1e3 * sec / 50,
+            "hydro_ms": hyd * 1e3, "batched_graph": {"value": zones * 50 / gsec,
+                                                     "ms_per_step": 1e3 * gsec / 50,
+                                                     "tile": tile, "ctas_per_sm": ctas},
+            "steps": 50, "note": "1.3 MB state: L2-resident, launch-latency bound",
+            "ok": ok and bs.status() == 0}
+        bs.close()
+        # 3D Sedov on the 2-level octree (1408 leaves of 16^3): batched graph,
+        # 20 warm-up + 100 timed steps, and the per-call path
+        mesh, W, gamma, cfl = inputs.workload("sedov_amr")
+        zones = mesh.leaf_zones()
+        bs = fx.BlockSet(mesh, gamma, precision=prec, device=dev)
+        bs.set_primitive(W)
+        gsec, tile, ctas = timed_batch(fx, bs, cfl, stream, 20, 100, mesh.nxb, mesh.ng)
+        ok = bs.status() == 0
+        bs.set_primitive(W)
+        sec, hyd = timed_steps(fx, bs, cfl, stream, 20, 100)
+        entry = {"value": zones * 100 / gsec, "unit": UNIT, "ms_per_step": 1e3 * gsec / 100,
+                 "path": "batched persistent kernel, one CUDA graph per step, autotuned",
+                 "tile": tile, "ctas_per_sm": ctas, "warmup": 20, "steps": 100,
+                 "per_call": {"value": zones * 100 / sec, "ms_per_step": 1e3 * sec / 100,
+                              "hydro_ms": hyd * 1e3},
+                 "ok": ok and bs.status() == 0}
+        if prec_name == "f64":
+            entry["hydro_alu_frac_per_call"] = (ALGO_FLOPS_PER_ZONE["sedov_amr"] * zones / hyd
+                                                / FP64_PEAK_FLOPS)
+        else:
+            entry["hydro_hbm_frac_per_call"] = bpz * zones / hyd / (hbm_peak * 1e9)
+        out[f"sedov_amr_128^3_2level_{prec_name}"] = entry
+        bs.close()
+        del W
+    # smooth advection 512^3 (32768 blocks of 16^3): 18 GB per FP64 buffer
+    mesh, W, gamma, cfl = inputs.workload("advection3d")
+    zones = mesh.leaf_zones()
+    for prec_name, prec in (("f64", fx.FX_F64), ("f32bulk", fx.FX_F32BULK)):
+        bs = fx.BlockSet(mesh, gamma, precision=prec, device=dev)
+        bs.set_primitive(W)
+        torch.cuda.empty_cache()
+        sec, hyd = timed_steps(fx, bs, cfl, stream, 3, 10)
+        bpz = HBM_BYTES_PER_ZONE[prec_name]
+        entry = {"value": zones * 10 / sec, "unit": UNIT, "ms_per_step": 1e3 * sec / 10,
+                 "hydro_ms": hyd * 1e3, "steps": 10,
+                 "hydro_hbm_frac": bpz * zones / hyd / (hbm_peak * 1e9), "ok": bs.status() == 0}
+        if prec_name == "f64":
+            entry["hydro_alu_frac"] = ALGO_FLOPS_PER_ZONE["advection3d"] * zones / hyd / FP64_PEAK_FLOPS
+        out[f"advection3d_512^3_{prec_name}"] = entry
+        bs.close()
+        torch.cuda.empty_cache()
+    del W
     return out
 
 
@@ -619,6 +787,12 @@ def run_ours(args):
     if not args.no_variants:
         line["variants"] = measure_variants(args, fx, inputs, mesh, dev, cfl, zones_per_step, bs,
                                             ws, hbm_peak)
+    if not args.no_configs:
+        line["configs"] = measure_configs(args, fx, inputs, dev, hbm_peak)
+    if not args.no_serving and ws == 1:
+        # a bounded sample of the serving configuration (all block counts up
+        # to 4096, fewer requests; `bench.py --serve` runs more)
+        line["serving"] = serving_runs(24, 4096, args.serve_budget_gb, double_word=False)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:   # the CPU oracle at N = 1 only
         try:
             line["cpu_baseline"] = oracle_sample(args.workload)
@@ -632,52 +806,136 @@ def run_ours(args):
     return 0
 
 
-def run_serve(args):
-    """Serving stream: capacity with every request present at t = 0, then
-    Poisson streams at 0.5, 0.8 and 0.95 of that capacity (continuous
-    batching), the plain per-request FP64 path on the 0.8 stream, and the
-    saturated and 0.8 streams again with the FP64 requests updated in
-    double-word arithmetic."""
-    import torch
+def serving_runs(n_requests: int, max_blocks: int, budget_gb: float, double_word: bool = True):
+    """The serving configuration: Poisson streams of advance-k-steps requests
+    (seed 11630; 8..max_blocks blocks, log-uniform; nxb 8/16/32; k 1..20;
+    Sod/KH/Sedov/advection states), served with continuous batching under a
+    device-memory budget, against the plain per-request FP64 path on the same
+    arrivals.  Two request mixes: half FP64 / half FP32-bulk, and all
+    FP32-bulk (the served FP32-bulk path against per-request FP64 at a stated
+    p99).  Each mix: capacity with every request present at t = 0, then
+    Poisson arrivals at fractions of that capacity.  Wall clock on the host;
+    the requests' initial states wait in page-locked host memory."""
     from paper_2208_11630_gb300 import fx, serve
+    inf = float("inf")
+    budget = budget_gb * 1e9
+    out = {}
+    t_prep = time.perf_counter()
+    mixes = {"mixed": 0.5, "f32bulk": 1.0}
+    streams = {name: serve.make_stream(n_requests, inf, seed=11630, blocks=(8, max_blocks),
+                                       f32_frac=frac) for name, frac in mixes.items()}
+    # the two mixes share sizes, setups and k (same seed); only precision differs
+    probs = serve.prepare(streams["mixed"])
+    out["prep_s"] = time.perf_counter() - t_prep
+    for name, reqs in streams.items():
+        runs = {}
+        # warm-up pass: kernels loaded, launch choices tuned and cached
+        serve.serve(serve.with_arrivals(reqs, inf), probs, budget, realtime=False)
+        sat = serve.serve(serve.with_arrivals(reqs, inf), probs, budget, realtime=False)
+        cap = sat["requests_per_s"]
+        runs["saturated"] = sat
+        fracs = (0.5, 0.8, 0.95) if name == "mixed" else (0.8,)
+        for frac in fracs:
+            runs[f"rate_{frac}"] = serve.serve(serve.with_arrivals(reqs, frac * cap), probs, budget)
+        runs["per_request_fp64_at_0.8"] = serve.serve_per_request(
+            serve.with_arrivals(reqs, 0.8 * cap), probs, precision=fx.FX_F64)
+        if double_word and name == "mixed":
+            serve.serve(serve.with_arrivals(reqs, inf), probs, budget, realtime=False, f64_arith=1)
+            runs["saturated_f64_double_word"] = serve.serve(serve.with_arrivals(reqs, inf), probs,
+                                                            budget, realtime=False, f64_arith=1)
+            runs["rate_0.8_f64_double_word"] = serve.serve(serve.with_arrivals(reqs, 0.8 * cap),
+                                                           probs, budget, f64_arith=1)
+        out[name] = {"capacity_requests_per_s": cap, "runs": runs}
+    blocks = [r.nblocks for r in streams["mixed"]]
+    out["stream"] = {"requests": n_requests, "blocks": f"log-uniform 8..{max_blocks}",
+                     "blocks_max_drawn": int(max(blocks)), "blocks_median": float(np.median(blocks)),
+                     "nxb": "8/16/32", "k": "1..20", "setups": "sod/kh/sedov/advection",
+                     "budget_gb": budget_gb, "arrivals": "Poisson, seed 11630, rate = fraction "
+                     "of saturated capacity"}
+    return out
+
+
+def run_precision_study(args):
+    """Smooth advection at 512^3 (32768 blocks of 16^3, periodic) over one
+    domain crossing, t = 1 (the last step shortened to land on it), in
+    FP32-bulk and in FP64 on the GPU: the L1 error of the density of each
+    against the exact translated profile rho(x - v t), and the largest
+    per-cell deviation of FP32-bulk from FP64 (relative to the variable's
+    largest magnitude; the momenta share the largest |m|)."""
+    import torch
+    from paper_2208_11630_gb300 import fx, inputs
+    torch.cuda.set_device(0)
+    fx.load()
+    scale = args.scale or 32
+    mesh, W, gamma, cfl = inputs.workload("advection3d", scale=scale)
+    n, g = mesh.nxb, mesh.ng
+    sl = (slice(None), 0, slice(g, g + n), slice(g, g + n), slice(g, g + n))
+    x, y, z = mesh.cell_centers_all()
+    exact = inputs.advection_density(x, y, z, 1.0)          # [nb, n, n, n], t = 1
+    del x, y, z
+    vol = 1.0 / mesh.leaf_zones()
+    res = {}
+    finals = {}
+    for name, prec in (("f64", fx.FX_F64), ("f32bulk", fx.FX_F32BULK)):
+        bs = fx.BlockSet(mesh, gamma, precision=prec)
+        bs.set_primitive(W)
+        t, steps = 0.0, 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while t < 1.0:
+            fx.fx_compute_dt(bs.ctx, bs.bs, cfl, bs.dt.data_ptr(), None)
+            dt = float(bs.dt.item())
+            if t + dt > 1.0:
+                dt = 1.0 - t
+                bs.dt.fill_(dt)
+            fx.fx_guardcell_fill_amr(bs.ctx, bs.bs, None)
+            fx.fx_hydro_advance(bs.ctx, bs.bs, bs.dt.data_ptr(), None)
+            t += dt
+            steps += 1
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        rho = bs.current[sl].double().cpu().numpy()
+        l1 = float(np.abs(rho - exact).sum() * vol)
+        res[name] = {"steps": steps, "t": t, "wall_s": wall, "l1_rho_vs_exact": l1,
+                     "status": bs.status(), "zone_updates_per_s": mesh.leaf_zones() * steps / wall}
+        finals[name] = bs
+    a = finals["f32bulk"].current
+    r = finals["f64"].current
+    g2 = (slice(None), slice(None), slice(g, g + n), slice(g, g + n), slice(g, g + n))
+    dev = 0.0
+    for v in range(5):
+        rv = r[g2][:, v]
+        sc = rv.abs().amax() if v in (0, 4) else r[g2][:, 1:4].square().sum(dim=1).sqrt().amax()
+        dev = max(dev, float(((a[g2][:, v].double() - rv).abs() / torch.maximum(
+            rv.abs(), sc.clamp_min(1e-300))).max()))
+    res["max_rel_dev_f32bulk_from_f64"] = dev
+    res["l1_relative_difference"] = abs(res["f32bulk"]["l1_rho_vs_exact"] -
+                                        res["f64"]["l1_rho_vs_exact"]) / res["f64"]["l1_rho_vs_exact"]
+    line = {"metric": "precision study", "workload": f"advection3d_{scale * n}^3", "crossing_t": 1.0,
+            "blocks": mesh.nb, "zones": mesh.leaf_zones(), "cfl": cfl, "results": res,
+            "data": "synthetic (seed 2208)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Serving stream at the configuration's sizes (blocks up to 4096)."""
+    import torch
+    from paper_2208_11630_gb300 import fx
     ws, rank, local = dist_env()
     if rank != 0:
         return 0
     torch.cuda.set_device(0)
     fx.load()
-    inf = float("inf")
-    reqs = serve.make_stream(args.serve_requests, inf, seed=11630, blocks=(8, args.serve_max_blocks))
-    probs = serve.prepare(reqs)
-    budget = args.serve_budget_gb * 1e9
-    # warm-up pass over the whole stream: kernels loaded, launch choices tuned
-    # and cached for every (dimension, precision, block-edge) group
-    serve.serve(serve.with_arrivals(reqs, inf), probs, budget, realtime=False)
     clocks = ClockSampler(0)
     clocks.start()
-    sat = serve.serve(serve.with_arrivals(reqs, inf), probs, budget, realtime=False)
-    cap = sat["requests_per_s"]
-    runs = {"saturated": sat}
-    for frac in (0.5, 0.8, 0.95):
-        runs[f"rate_{frac}"] = serve.serve(serve.with_arrivals(reqs, frac * cap), probs, budget)
-    base = serve.serve_per_request(serve.with_arrivals(reqs, 0.8 * cap), probs,
-                                   precision=fx.FX_F64)
-    # the same streams with the FP64 requests updated in double-word arithmetic
-    serve.serve(serve.with_arrivals(reqs, inf), probs, budget, realtime=False, f64_arith=1)
-    runs["saturated_f64_double_word"] = serve.serve(serve.with_arrivals(reqs, inf), probs, budget,
-                                                    realtime=False, f64_arith=1)
-    runs["rate_0.8_f64_double_word"] = serve.serve(serve.with_arrivals(reqs, 0.8 * cap), probs,
-                                                   budget, f64_arith=1)
+    res = serving_runs(args.serve_requests, args.serve_max_blocks, args.serve_budget_gb)
     clk = clocks.stop()
-    line = {"metric": "served zone-updates/s", "value": runs["rate_0.8"]["zone_updates_per_s"],
+    line = {"metric": "served zone-updates/s",
+            "value": res["mixed"]["runs"]["rate_0.8"]["zone_updates_per_s"],
             "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-            "dtype": "mixed f64/f32bulk",
-            "config": {"workload": "serving stream", "requests": len(reqs),
-                       "blocks": f"log-uniform 8..{args.serve_max_blocks}", "nxb": "8/16/32",
-                       "k": "1..20", "precision": "50% FP64, 50% FP32-bulk",
-                       "setups": "sod/kh/sedov/advection", "budget_gb": args.serve_budget_gb,
-                       "arrivals": "Poisson, seed 11630, rate = fraction of saturated capacity"},
-            "capacity_requests_per_s": cap, "runs": runs,
-            "baseline_per_request_fp64_at_0.8": base, "clocks": clk,
+            "dtype": "mixed f64/f32bulk", "config": {"workload": "serving stream"} | res["stream"],
+            "serving": res, "clocks": clk,
             "timing": "wall clock on the host, requests' initial states in page-locked memory"}
     print(json.dumps(line), flush=True)
     return 0
@@ -697,9 +955,15 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the batched-graph and other-precision measurements")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (Sod 2D, Sedov AMR batched, advection 512^3)")
     ap.add_argument("--serve", action="store_true", help="run the serving stream instead")
-    ap.add_argument("--serve-requests", type=int, default=160)
-    ap.add_argument("--serve-max-blocks", type=int, default=512)
+    ap.add_argument("--precision-study", action="store_true",
+                    help="run the 512^3 advection crossing in FP32-bulk and FP64 instead")
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-max-blocks", type=int, default=4096)
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving sample in the default line")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:
@@ -708,6 +972,8 @@ def main(argv=None):
         return run_reference(args)
     if args.serve:
         return run_serve(args)
+    if args.precision_study:
+        return run_precision_study(args)
     return run_ours(args)
 
 

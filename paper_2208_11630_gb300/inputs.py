@@ -106,6 +106,38 @@ class Mesh:
         z = out[2].reshape(nz, 1, 1)
         return x, y, z
 
+    def cell_centers_all(self):
+        """``cell_centers`` of every block at once: (x, y, z) broadcastable to
+        ``[nb, k, j, i]`` (the same arithmetic per cell)."""
+        n = self.nxb
+        lev = np.asarray(self.level, dtype=np.int64)
+        out = []
+        for d in range(3):
+            if d >= self.ndim:
+                out.append(np.zeros((self.nb, 1)))
+                continue
+            ncell = np.array([self.cells_per_axis(int(l))[d] for l in range(int(lev.max()) + 1)])
+            dx = (self.hi[d] - self.lo[d]) / ncell[lev]
+            g = self.origin[:, d][:, None] + np.arange(n)[None, :]
+            out.append(self.lo[d] + (g + 0.5) * dx[:, None])
+        nz = n if self.ndim == 3 else 1
+        return (out[0].reshape(self.nb, 1, 1, n), out[1].reshape(self.nb, 1, n, 1),
+                out[2].reshape(self.nb, nz, 1, 1))
+
+    def global_index_all(self):
+        """``global_index`` of every block at once, broadcastable to
+        ``[nb, k, j, i]``."""
+        n = self.nxb
+        g = []
+        for d in range(3):
+            if d >= self.ndim:
+                g.append(np.zeros((self.nb, 1), dtype=np.int64))
+            else:
+                g.append(self.origin[:, d][:, None] + np.arange(n, dtype=np.int64)[None, :])
+        nz = n if self.ndim == 3 else 1
+        return (g[0].reshape(self.nb, 1, 1, n), g[1].reshape(self.nb, 1, n, 1),
+                g[2].reshape(self.nb, nz, 1, 1))
+
     def global_index(self, b: int):
         """Integer cell indices of block ``b``'s interior in its level lattice."""
         g = []
@@ -215,6 +247,18 @@ def _empty(mesh: Mesh) -> np.ndarray:
     return np.zeros(mesh.shape, dtype=np.float64)
 
 
+def _fill_all(mesh: Mesh, W: np.ndarray, fields) -> None:
+    """Interior of every block from fields broadcastable to ``[nb, k, j, i]``."""
+    g, n = mesh.ng, mesh.nxb
+    nz = n if mesh.ndim == 3 else 1
+    for v in range(len(fields)):
+        val = np.broadcast_to(fields[v], (mesh.nb, nz, n, n))
+        if mesh.ndim == 3:
+            W[:, v, g:g + n, g:g + n, g:g + n] = val
+        else:
+            W[:, v, 0, g:g + n, g:g + n] = val[:, 0]
+
+
 def _fill(mesh: Mesh, W: np.ndarray, b: int, fields) -> None:
     g, n = mesh.ng, mesh.nxb
     for v in range(len(fields)):
@@ -229,15 +273,14 @@ def sod_state(mesh: Mesh, axis: int = 0, mirror: bool = False) -> np.ndarray:
     """Sod shock tube: (rho, p) = (1, 1) for x < 0.5 and (0.125, 0.1) otherwise,
     at rest.  ``mirror`` swaps the two sides."""
     W = _empty(mesh)
-    for b in range(mesh.nb):
-        xyz = mesh.cell_centers(b)
-        left = xyz[axis] < 0.5
-        if mirror:
-            left = ~left
-        rho = np.where(left, 1.0, 0.125)
-        p = np.where(left, 1.0, 0.1)
-        z = np.zeros(1)
-        _fill(mesh, W, b, (rho, z, z, z, p))
+    xyz = mesh.cell_centers_all()
+    left = xyz[axis] < 0.5
+    if mirror:
+        left = ~left
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    z = np.zeros(1)
+    _fill_all(mesh, W, (rho, z, z, z, p))
     return W
 
 
@@ -246,9 +289,8 @@ def uniform_state(mesh: Mesh, rho=1.3, vel=(0.3, -0.2, 0.1), p=0.7) -> np.ndarra
     v = list(vel)
     if mesh.ndim == 2:
         v[2] = 0.0
-    for b in range(mesh.nb):
-        _fill(mesh, W, b, (np.array(rho), np.array(v[0]), np.array(v[1]), np.array(v[2]),
-                           np.array(p)))
+    _fill_all(mesh, W, (np.array(rho), np.array(v[0]), np.array(v[1]), np.array(v[2]),
+                        np.array(p)))
     return W
 
 
@@ -261,16 +303,14 @@ def kh_state(mesh: Mesh, seed: int = 1234, amp: float = 0.01) -> np.ndarray:
     n = mesh.cells_per_axis(0)
     rng = np.random.default_rng(seed)
     r = rng.random((n[2], n[1], n[0]))
-    for b in range(mesh.nb):
-        x, y, z = mesh.cell_centers(b)
-        gx, gy, gz = mesh.global_index(b)
-        inner = np.abs(y - 0.5) < 0.25
-        rho = np.where(inner, 2.0, 1.0)
-        vx = np.where(inner, 0.5, -0.5)
-        lev = int(mesh.level[b])
-        s = 2 ** lev
-        vy = amp * (2.0 * r[gz // s, gy // s, gx // s] - 1.0)
-        _fill(mesh, W, b, (rho, vx, vy, np.zeros(1), np.array(2.5)))
+    x, y, z = mesh.cell_centers_all()
+    gx, gy, gz = mesh.global_index_all()
+    inner = np.abs(y - 0.5) < 0.25
+    rho = np.where(inner, 2.0, 1.0)
+    vx = np.where(inner, 0.5, -0.5)
+    s = (2 ** np.asarray(mesh.level, dtype=np.int64)).reshape(mesh.nb, 1, 1, 1)
+    vy = amp * (2.0 * r[gz // s, gy // s, gx // s] - 1.0)
+    _fill_all(mesh, W, (rho, vx, vy, np.zeros(1), np.array(2.5)))
     return W
 
 
@@ -289,24 +329,19 @@ def sedov_state(mesh: Mesh, e_blast: float = 1.0, r_cells: float = 3.5,
     nf = mesh.cells_per_axis(lmax)
     dxf = [(mesh.hi[d] - mesh.lo[d]) / nf[d] for d in range(3)]
     ctr = [0.5 * (mesh.lo[d] + mesh.hi[d]) for d in range(3)]
-    leaf = mesh.is_leaf()
-    inside = []
-    count = 0
-    for b in range(mesh.nb):
-        x, y, z = mesh.cell_centers(b)
-        r2 = ((x - ctr[0]) / dxf[0]) ** 2 + ((y - ctr[1]) / dxf[1]) ** 2 + \
-             ((z - ctr[2]) / dxf[2]) ** 2
-        m = (r2 < r_cells ** 2) & (int(mesh.level[b]) == lmax)
-        inside.append(m)
-        if leaf[b]:
-            count += int(m.sum())
+    leaf = mesh.is_leaf().astype(bool)
+    x, y, z = mesh.cell_centers_all()
+    r2 = ((x - ctr[0]) / dxf[0]) ** 2 + ((y - ctr[1]) / dxf[1]) ** 2 + \
+         ((z - ctr[2]) / dxf[2]) ** 2
+    finest = (np.asarray(mesh.level) == lmax).reshape(mesh.nb, 1, 1, 1)
+    inside = (r2 < r_cells ** 2) & finest
+    count = int(inside[leaf].sum())
     if count == 0:
         raise ValueError("blast region holds no finest-level cells")
     dv = dxf[0] * dxf[1] * dxf[2]
     p_in = (gamma - 1.0) * e_blast / (count * dv)
-    for b in range(mesh.nb):
-        p = np.where(inside[b], p_in, 1e-5)
-        _fill(mesh, W, b, (np.array(1.0), np.zeros(1), np.zeros(1), np.zeros(1), p))
+    p = np.where(inside, p_in, 1e-5)
+    _fill_all(mesh, W, (np.array(1.0), np.zeros(1), np.zeros(1), np.zeros(1), p))
     mesh.extra["sedov_cells"] = count
     mesh.extra["sedov_p"] = p_in
     return W
@@ -341,11 +376,10 @@ def advection_state(mesh: Mesh, vel=(1.0, 0.5, 0.25), seed=2208, nmodes=8, kmax=
                     amp=0.1) -> np.ndarray:
     """Smooth advection: p = 1, uniform velocity, Fourier-mode density."""
     W = _empty(mesh)
-    for b in range(mesh.nb):
-        x, y, z = mesh.cell_centers(b)
-        rho = advection_density(x, y, z, 0.0, vel, seed, nmodes, kmax, amp)
-        _fill(mesh, W, b, (rho, np.array(vel[0]), np.array(vel[1]),
-                           np.array(vel[2] if mesh.ndim == 3 else 0.0), np.array(1.0)))
+    x, y, z = mesh.cell_centers_all()
+    rho = advection_density(x, y, z, 0.0, vel, seed, nmodes, kmax, amp)
+    _fill_all(mesh, W, (rho, np.array(vel[0]), np.array(vel[1]),
+                        np.array(vel[2] if mesh.ndim == 3 else 0.0), np.array(1.0)))
     return W
 
 

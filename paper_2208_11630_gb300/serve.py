@@ -160,6 +160,9 @@ def serve(reqs, problems, budget_bytes: float = 120e9, max_slots: int = 256, cfl
     batch = fx.Batch(ctx, max_slots)
     pending = deque(sorted(reqs, key=lambda r: r.arrival))
     active = {}
+    rem = {}          # slot -> steps the request still needs (host view)
+    step_s = 0.0      # running estimate of one batched step's wall time
+    syncs = 0
     used = 0
     max_used = 0
     max_active = 0
@@ -182,6 +185,7 @@ def serve(reqs, problems, budget_bytes: float = 120e9, max_slots: int = 256, cfl
                 bs = fx.BlockSet(mesh, 1.4, precision=req.precision, ctx=ctx)
                 bs.set_primitive(W)
                 slot = batch.add(bs, cfl, req.k)
+                rem[slot] = req.k
                 req.admitted = time.perf_counter() - t0
                 req.zones = mesh.leaf_zones() * req.k
                 active[slot] = (req, bs, need)
@@ -196,10 +200,28 @@ def serve(reqs, problems, budget_bytes: float = 120e9, max_slots: int = 256, cfl
             if added and not tuned:
                 batch.tune()
                 tuned = True
-            batch.run(1)
-            steps += 1
+            # Steps to run before the host looks again: up to the first
+            # completion (the host knows every request's remaining steps), or
+            # fewer if a waiting request arrives sooner and could be admitted;
+            # one host synchronisation per such run, not per step.
+            nrun = min(rem.values())
+            if pending and len(active) < max_slots:
+                head = pending[0]
+                fits = used + state_bytes(problems[head.rid][0], head.precision) <= budget_bytes
+                if fits:
+                    wait = head.arrival - (time.perf_counter() - t0)
+                    nrun = max(1, min(nrun, int(wait / step_s))) if step_s > 0 else 1
+            tr = time.perf_counter()
+            batch.run(nrun)
+            steps += nrun
             left = batch.poll()
+            syncs += 1
+            dt_run = (time.perf_counter() - tr) / nrun
+            step_s = dt_run if step_s == 0.0 else 0.8 * step_s + 0.2 * dt_run
+            for sl in rem:
+                rem[sl] -= nrun
             for slot in [s for s in active if left[s] == 0]:
+                rem.pop(slot)
                 req, bs, need = active.pop(slot)
                 batch.remove(slot)
                 req.status = bs.status()
@@ -217,7 +239,7 @@ def serve(reqs, problems, budget_bytes: float = 120e9, max_slots: int = 256, cfl
         fx.fx_finalize(ctx)
     zones = sum(r.zones for r in reqs)
     p50, p99, pmax = _percentiles(reqs)
-    return {"requests": len(reqs), "wall_s": wall, "batched_steps": steps,
+    return {"requests": len(reqs), "wall_s": wall, "batched_steps": steps, "host_syncs": syncs,
             "zone_updates_per_s": zones / wall, "requests_per_s": len(reqs) / wall,
             "p50_s": p50, "p99_s": p99, "max_s": pmax, "max_used_bytes": max_used,
             "max_concurrent": max_active, "launch_choices": choices,
