@@ -36,7 +36,7 @@ HBM_BYTES_PER_ZONE = {"f64": 80.0, "f32bulk": 40.0}
 # primitive conversion, one cell's slopes/predictor/face states, ndim HLLC
 # face fluxes, one conservative update and one CFL signal speed, counted on
 # the oracle's op-counting build ("python -m oracle.opcount <workload> 4 10",
-# one full step after 10; profiles/flops_per_zone.md).  The HLLC branch mix,
+# one full step after 10).  The HLLC branch mix,
 # and with it the count, depends a little on the flow.
 ALGO_FLOPS_PER_ZONE = {"kh3d": 619.9, "sedov_amr": 597.2, "advection3d": 602.3,
                        "sod2d": 411.8}
@@ -46,7 +46,7 @@ FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 # capture of the 128^3 KH case (dram__bytes_read.sum + dram__bytes_write.sum
 # over 2,097,152 zones); the full launch's traffic scales with its zones.
 # Valid for the kernel build those counters were taken on.
-TRAFFIC_BYTES_PER_ZONE = {"f64": 102.3, "f32bulk": 67.0}
+TRAFFIC_BYTES_PER_ZONE = {"f64": 102.1, "f32bulk": 67.6}
 
 
 def measure_fma_peak(fx, stream, precision, reps: int = 3):
@@ -749,7 +749,10 @@ def run_ours(args):
     achieved_flops = flops_per_zone * zones_per_step / hydro_s
     bpz = HBM_BYTES_PER_ZONE[args.precision]
     if args.precision == "f64":
-        fp64_meas = measure_fma_peak(fx, stream, fx.FX_F64)
+        pclk = ClockSampler(dev.index)
+        pclk.start()
+        fp64_meas = measure_fma_peak(fx, stream, fx.FX_F64, reps=10)
+        pclk = pclk.stop()
         roof = {"bound": "alu", "kernel": kname,
                 "achieved": achieved_flops / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
                 "unit": "TFLOP/s", "frac": achieved_flops / FP64_PEAK_FLOPS,
@@ -759,6 +762,7 @@ def run_ours(args):
                 "peak_measured": fp64_meas / 1e12,
                 "frac_of_measured": achieved_flops / fp64_meas,
                 "peak_measured_kind": "FP64 FMA probe (fx_fma_probe) timed in this run",
+                "peak_measured_clocks": pclk,
                 "traffic_note": "bytes per launch: ncu DRAM read+write of the 128^3 case scaled by zones",
                 "algorithmic_flops_per_zone": flops_per_zone,
                 "algorithmic_flops_source": "oracle op-counting build (oracle/opcount.py)"}
@@ -853,6 +857,26 @@ def serving_runs(n_requests: int, max_blocks: int, budget_gb: float, double_word
                      "budget_gb": budget_gb, "arrivals": "Poisson, seed 11630, rate = fraction "
                      "of saturated capacity"}
     return out
+
+
+def run_fma_probe(args):
+    """FMA-pipe throughput of this GPU (FP64 and FP32), the library's probe
+    kernel timed with CUDA events, with the SM clocks sampled meanwhile."""
+    import torch
+    from paper_2208_11630_gb300 import fx
+    torch.cuda.set_device(0)
+    fx.load()
+    stream = torch.cuda.Stream()
+    out = {"metric": "fma throughput", "unit": "TFLOP/s",
+           "derived_fp64_peak": FP64_PEAK_FLOPS / 1e12,
+           "derivation": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+    for name, prec in (("fp64", fx.FX_F64), ("fp32", fx.FX_F32BULK)):
+        clk = ClockSampler(0)
+        clk.start()
+        v = measure_fma_peak(fx, stream, prec, reps=50)
+        out[name] = {"tflops": v / 1e12, "clocks": clk.stop()}
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def run_precision_study(args):
@@ -958,6 +982,8 @@ def main(argv=None):
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workloads (Sod 2D, Sedov AMR batched, advection 512^3)")
     ap.add_argument("--serve", action="store_true", help="run the serving stream instead")
+    ap.add_argument("--fma-probe", action="store_true",
+                    help="measure the FP64 and FP32 FMA throughput instead")
     ap.add_argument("--precision-study", action="store_true",
                     help="run the 512^3 advection crossing in FP32-bulk and FP64 instead")
     ap.add_argument("--serve-requests", type=int, default=64)
@@ -974,6 +1000,8 @@ def main(argv=None):
         return run_serve(args)
     if args.precision_study:
         return run_precision_study(args)
+    if args.fma_probe:
+        return run_fma_probe(args)
     return run_ours(args)
 
 
