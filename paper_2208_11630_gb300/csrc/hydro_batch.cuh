@@ -38,7 +38,7 @@ k_hydro_batch(const BatchReq *__restrict__ reqs, const int4 *__restrict__ items,
 template <int NDIM, int T, typename S, typename R>
 cudaError_t launch_batch_t(const BatchReq *reqs, const int4 *items, int nitems,
                            unsigned int *counter, int ctas_per_sm, int nsm, cudaStream_t s) {
-  const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(R);
+  const size_t smem = tile_smem_bytes<NDIM, T, R>();
   auto kern = k_hydro_batch<NDIM, T, S, R>;
   static std::atomic<unsigned long long> attr_devs{0};
   if (cudaError_t e = set_smem_once((const void *)kern, smem, attr_devs); e != cudaSuccess)
@@ -58,7 +58,7 @@ cudaError_t launch_batch_t(const BatchReq *reqs, const int4 *items, int nitems,
 
 template <int NDIM, int T, typename S, typename R>
 cudaError_t fit_t(int *fit) {
-  const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(R);
+  const size_t smem = tile_smem_bytes<NDIM, T, R>();
   auto kern = k_hydro_batch<NDIM, T, S, R>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

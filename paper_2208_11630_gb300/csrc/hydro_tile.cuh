@@ -272,24 +272,46 @@ struct Smem {
 // Ring component of primitive variable v (the ring stores 1/rho at 5).
 __host__ __device__ constexpr int ring_comp(int v) { return v < 5 ? v : v + 1; }
 
+// Primitive ring of an instance.  FP32 3D single-gas tiles keep four planes
+// of five components (1/rho is recomputed where it is used, one fast
+// reciprocal per predicted cell), so that the next plane's load shares the
+// predictor phase instead of taking a phase of its own; the others keep three
+// planes of six (FP64: the stored 1/rho saves a division per predicted cell).
+template <int NDIM, typename R, bool RK, int NS>
+struct RingCfg {
+  static constexpr bool four = std::is_same<R, float>::value && NDIM == 3 && NS == 0 && !RK;
+  static constexpr int planes = NDIM == 3 ? (four ? 4 : 3) : 1;
+};
+template <int NDIM, int T, typename R, bool RK, int NS>
+__host__ __device__ constexpr int ring_plane_elems() {
+  return (RingCfg<NDIM, R, RK, NS>::four ? 5 : Smem<T, NS>::NV) * Smem<T, NS>::W4 * Smem<T, NS>::W4;
+}
+// Dynamic shared memory of one tile instance, in bytes.
+template <int NDIM, int T, typename R, bool RK = false, int NS = 0>
+__host__ __device__ constexpr size_t tile_smem_bytes() {
+  return (size_t)(RingCfg<NDIM, R, RK, NS>::planes * ring_plane_elems<NDIM, T, R, RK, NS>() +
+                  2 * Smem<T, NS>::FX + 2 * Smem<T, NS>::FY) * sizeof(R);
+}
+
 // Slopes, Hancock predictor and face states of the cell at tile-local (i, j)
 // of the plane in ring slot s0 (neighbour planes in sm, sp).  Works with half
 // slopes h = dW/2 throughout: the predictor is linear in the slopes, so
 // A(W) h (2/dx) is exactly A(W) dW / dx, and the face states are W* -+ h.
 // Returns the lower/upper face states per direction in fm/fp.
-template <int NDIM, int T, typename R, bool PRED = true, int NS = 0>
+template <int NDIM, int T, typename R, bool PRED = true, int NS = 0, bool RING4 = false>
 __device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int s0, int sp, int i,
                                         int j, R hdt, const R (&idx2)[3], R g,
                                         R (&fm)[3][5 + NS], R (&fp)[3][5 + NS]) {
   using SM = Smem<T, NS>;
   constexpr int NF = 5 + NS;
   constexpr int PL = SM::W4 * SM::W4;
+  constexpr int RS = RING4 ? 5 * PL : SM::RING;   // one ring plane
   const int c = (j + 2) * SM::W4 + (i + 2);
-  const R *p0 = ring + s0 * SM::RING;
+  const R *p0 = ring + s0 * RS;
   R W0[NF], h[3][NF];
 #pragma unroll
   for (int v = 0; v < NF; ++v) W0[v] = p0[ring_comp(v) * PL + c];
-  const R ir = p0[5 * PL + c];
+  const R ir = RING4 ? div_r(R(1), W0[0]) : p0[5 * PL + c];
   // the cell's gamma: the mesh's, or its mixture gamma (species)
   const R gc = NS > 0 ? p0[(6 + NS) * PL + c] : g;
 #pragma unroll
@@ -298,8 +320,8 @@ __device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int 
     h[0][v] = mc_half(W0[v] - q[-1], q[1] - W0[v]);
     h[1][v] = mc_half(W0[v] - q[-SM::W4], q[SM::W4] - W0[v]);
     if (NDIM == 3) {
-      const R wm = ring[sm * SM::RING + ring_comp(v) * PL + c];
-      const R wp = ring[sp * SM::RING + ring_comp(v) * PL + c];
+      const R wm = ring[sm * RS + ring_comp(v) * PL + c];
+      const R wp = ring[sp * RS + ring_comp(v) * PL + c];
       h[2][v] = mc_half(W0[v] - wm, wp - W0[v]);
     } else {
       h[2][v] = R(0);
@@ -374,10 +396,14 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
   using SM = Smem<T, NS>;
   constexpr int NF = 5 + NS;         // conserved variables, face-state components
   constexpr int NT = T * T;
-  constexpr int NPL = NDIM == 3 ? 3 : 1;
+  using RC = RingCfg<NDIM, R, RK, NS>;
+  constexpr bool R4 = RC::four;
+  constexpr int NPL = RC::planes;
+  constexpr int RS = ring_plane_elems<NDIM, T, R, RK, NS>();   // one ring plane
+  constexpr int NVR = R4 ? 5 : SM::NV;                          // components stored
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *ring = reinterpret_cast<R *>(smem_raw);
-  R *fxm = ring + NPL * SM::RING;   // x lower-face states, then x fluxes
+  R *fxm = ring + NPL * RS;         // x lower-face states, then x fluxes
   R *fxp = fxm + SM::FX;
   R *fym = fxp + SM::FX;            // y lower-face states, then y fluxes
   R *fyp = fym + SM::FY;
@@ -455,7 +481,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
   if (tid < 27) guard_source(m, b, tid, src_off[tid], src_map[tid]);
   __syncthreads();
   auto load_plane = [&](int p, int slot) {
-    R *dst = ring + slot * SM::RING;
+    R *dst = ring + slot * RS;
     const int zpad = p + zoff;
     const int sz = NDIM == 3 ? (zpad < ng ? 0 : (zpad >= ng + n ? 2 : 1)) : 1;
     for (int c = (tid + kLoadTail) % NT; c < SM::W4 * SM::W4; c += NT) {
@@ -475,10 +501,10 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
           if ((flip >> d) & 1u) w[1 + d] = -w[1 + d];
       }
 #pragma unroll
-      for (int v = 0; v < SM::NV; ++v) dst[v * SM::W4 * SM::W4 + c] = w[v];
+      for (int v = 0; v < NVR; ++v) dst[v * SM::W4 * SM::W4 + c] = w[v];
     }
   };
-  auto slot_of = [&](int p) { return NDIM == 3 ? ((p % 3) + 3) % 3 : 0; };
+  auto slot_of = [&](int p) { return NDIM == 3 ? (R4 ? (p & 3) : ((p % 3) + 3) % 3) : 0; };
 
   // register state of the thread's column: pending update of the cell below
   // (x+y part of its flux divergence, flux through its lower z face)
@@ -545,19 +571,26 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
   if (NDIM == 3) {
     load_plane(-2, slot_of(-2));
     load_plane(-1, slot_of(-1));
+    if (R4) load_plane(0, slot_of(0));
   }
   for (int p = pstart; p <= pend; ++p) {
     const bool inner = p >= 0 && p < (NDIM == 3 ? n : 1);
     const int s0 = slot_of(p), sm = slot_of(p - 1), sp = slot_of(p + 1);
-    if (NDIM == 3) load_plane(p + 1, sp);
-    else load_plane(0, 0);
-    __syncthreads();
+    if (R4) {
+      // four-plane ring: plane p + 1 is already in; plane p + 2 goes into the
+      // slot plane p - 2 left, in the same phase as the predictor below
+      __syncthreads();
+    } else {
+      if (NDIM == 3) load_plane(p + 1, sp);
+      else load_plane(0, 0);
+      __syncthreads();
+    }
 
     // ---- predictor: own column cell, then (inner planes) the radius-1 ring
     R zm[NF], zp[NF];
     {
       R fm[3][NF], fp[3][NF];
-      predict<NDIM, T, R, !RK, NS>(ring, sm, s0, sp, ti, tj, hdt, idx2, g, fm, fp);
+      predict<NDIM, T, R, !RK, NS, R4>(ring, sm, s0, sp, ti, tj, hdt, idx2, g, fm, fp);
       if (inner) {
 #pragma unroll
         for (int v = 0; v < NF; ++v) {
@@ -579,7 +612,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
         else if (side == 2) { i = e; j = -1; }
         else { i = e; j = T; }
         R fm[3][NF], fp[3][NF];
-        predict<NDIM, T, R, !RK, NS>(ring, sm, s0, sp, i, j, hdt, idx2, g, fm, fp);
+        predict<NDIM, T, R, !RK, NS, R4>(ring, sm, s0, sp, i, j, hdt, idx2, g, fm, fp);
         if (side < 2) {
 #pragma unroll
           for (int v = 0; v < NF; ++v) {
@@ -595,6 +628,7 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
         }
       }
     }
+    if (R4 && p + 2 <= pend + 1) load_plane(p + 2, slot_of(p + 2));
     __syncthreads();
 
     // ---- fluxes: x and y faces of inner planes (in place over the lower-face

@@ -26,7 +26,7 @@ cudaError_t launch_t(const DevMesh &m, const void *U, void *Unew, const int *lea
                      const double *dt, double *regs, int *status, unsigned long long *smax,
                      const unsigned char *rmask, int form, cudaStream_t s) {
   const int tiles = m.nxb / T;
-  const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(R);
+  const size_t smem = tile_smem_bytes<NDIM, T, R>();
   auto kern = k_hydro<NDIM, T, S, R>;
   static std::atomic<unsigned long long> attr_devs{0};
   if (cudaError_t e = set_smem_once((const void *)kern, smem, attr_devs); e != cudaSuccess)
