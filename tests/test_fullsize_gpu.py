@@ -64,3 +64,46 @@ def test_full_size_100_steps(orc, fx, name):
         a, b = mesh.interior(G)[par], mesh.interior(Uo)[par]
         s = np.maximum(np.abs(b).max(axis=(0, 2, 3, 4), keepdims=True), 1e-300)
         assert (np.abs(a - b) / np.maximum(np.abs(b), s)).max() <= 1e-10
+
+
+def test_sod_config_against_the_exact_solution(orc, fx):
+    """The Sod configuration (128^2 as 8 x 8 blocks of 16^2, outflow, 50 steps
+    at CFL 0.8) compared with the exact Riemann solution at the time reached:
+    every row equals the first (the transverse fluxes cancel exactly in FP64),
+    and the L1 density error along x equals the oracle's to roundoff (it is
+    about 3.4e-3 at this resolution; the oracle's first-order convergence to
+    the exact solution is pinned on CPU).  FP32-bulk's L1 agrees with FP64's
+    to 1e-4 relative."""
+    from tests.helpers import assemble
+    mesh, W, gamma, cfl = inputs.workload("sod2d")
+    om = orc.OracleMesh(mesh, gamma)
+    U = om.prim_to_cons(W)
+    Uo, t, n = om.run(U, nsteps=50, cfl=cfl)
+    Nx = mesh.cells_per_axis(0)[0]
+    x = (np.arange(Nx) + 0.5) / Nx
+
+    def l1(Ustate, t_reached):
+        rho = assemble(mesh, Ustate)[0, 0]
+        ex = orc.riemann_sample([1.0, 0.0, 1.0], [0.125, 0.0, 0.1], (x - 0.5) / t_reached, gamma)
+        return float(np.abs(rho - ex[:, 0]).mean(axis=1).max()), rho
+
+    l1o, _ = l1(Uo, t)
+    out = {}
+    for name, prec in (("f64", fx.FX_F64), ("f32bulk", fx.FX_F32BULK)):
+        bs = fx.BlockSet(mesh, gamma, precision=prec)
+        bs.set_primitive(W)
+        tg = 0.0
+        for _ in range(50):
+            bs.step(cfl)
+            tg += float(bs.dt.item())
+        assert bs.status() == 0
+        out[name], rho = l1(bs.state(), tg)
+        if prec == fx.FX_F64:
+            assert tg == pytest.approx(t, rel=1e-13)
+            assert np.array_equal(rho, np.broadcast_to(rho[0:1], rho.shape))
+        bs.close()
+    print(f"\nSod 128^2, 50 steps, t = {t:.6f}: L1(rho) oracle {l1o:.6e}, "
+          f"GPU FP64 {out['f64']:.6e}, FP32-bulk {out['f32bulk']:.6e}")
+    assert out["f64"] == pytest.approx(l1o, rel=1e-10)
+    assert out["f32bulk"] == pytest.approx(out["f64"], rel=1e-4)
+    assert l1o < 5e-3
