@@ -53,6 +53,9 @@ CASES = {
         inputs.uniform_mesh(3, (2, 1, 2), 32, 4, inputs.PERIODIC)),
     "smooth3d_nxb8_ng2": lambda: (lambda m: (m, inputs.random_smooth_state(m, 6)))(
         inputs.uniform_mesh(3, (3, 3, 2), 8, 2, inputs.PERIODIC)),
+    # an odd guard width: interior rows start at an odd element offset
+    "smooth3d_nxb16_ng3": lambda: (lambda m: (m, inputs.random_smooth_state(m, 24)))(
+        inputs.uniform_mesh(3, (2, 2, 1), 16, 3, ((O_, O_), (P_, P_), (P_, P_)))),
     "single_block_periodic": lambda: (lambda m: (m, inputs.random_smooth_state(m, 7)))(
         inputs.uniform_mesh(3, (1, 1, 1), 16, 4, inputs.PERIODIC)),
     "amr_sedov_small": lambda: (lambda m: (m, inputs.sedov_state(m)))(mesh_2level(4, 16, 4)),

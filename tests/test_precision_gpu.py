@@ -40,7 +40,8 @@ def f32_blockset(fx, mesh, W, options=None):
 
 
 @pytest.mark.parametrize("case", ["sod2d", "kh64", "amr_sedov_small", "smooth3d_nxb32",
-                                  "blocky3d_outflow", "amr_smooth_periodic"])
+                                  "blocky3d_outflow", "amr_smooth_periodic", "smooth3d_nxb16_ng3",
+                                  "smooth3d_nxb8_ng2"])
 def test_f32bulk_one_step(orc, fx, case):
     mesh, W = CASES[case]()
     om = orc.OracleMesh(mesh)
