@@ -14,12 +14,14 @@
 // GB300 design.  One CTA owns a T x T column tile of one block and marches it
 // along z.  Guard cells of same-level neighbours are read directly from the
 // neighbour's interior while the tile is loaded (the guard copy is fused
-// away); only guards covered by a coarser leaf come from the padded array.  Shared memory holds a ring of three primitive planes (radius-2
-// halo in x and y) and the x/y face states of the current plane; each face
-// flux is computed once by one thread and written over the face state it
-// consumed.  The thread owning column (i, j) keeps its z face states and z
-// fluxes in registers, so no z data touches shared memory.  Per plane: load
-// + primitives, predictor, fluxes, update, three barriers.
+// away); only guards covered by a coarser leaf come from the padded array.
+// Shared memory holds a ring of primitive planes (radius-2 halo in x and y)
+// and the x/y face states of the current plane; each face flux is computed
+// once by one thread and written over the face state it consumed.  The thread
+// owning column (i, j) keeps its z face states and z fluxes in registers, so
+// no z data touches shared memory.  Per plane, three barriers: load +
+// primitives, predictor, fluxes, update -- or, with the four-plane ring of the
+// FP32 3D single-gas instances, the next plane's load in the predictor phase.
 //
 // Precision variants (state type S, compute type R): FP64 state and
 // arithmetic; FP32-bulk -- FP32 state, FP32 reconstruction and Riemann
