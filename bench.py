@@ -224,8 +224,10 @@ def oracle_sample(workload: str, target_s: float = 12.0, max_steps: int = 50,
 
 def measure_variants(args, fx, inputs, mesh, dev, cfl, zones, bs, ws, hbm_peak):
     """The same workload (i) as one request of a batch -- coarse-fine fill,
-    persistent update and flux correction replayed as one CUDA graph per step,
-    launch choice autotuned -- (ii) in the other precision, (v) as an FP64
+    update and flux correction replayed as one CUDA graph per step (the
+    persistent update, autotuned, or the per-block-set kernels for a request
+    that fills the GPU) -- (ii) in the other precision, per call and as a
+    batch, (v) as an FP64
     state updated in double-word arithmetic, each timed the same way (CUDA
     events on the launching stream, warm-up first), then (iv) with two
     species and (iii) with regridding."""
@@ -246,6 +248,7 @@ def measure_variants(args, fx, inputs, mesh, dev, cfl, zones, bs, ws, hbm_peak):
     b.record(stream)
     torch.cuda.synchronize()
     sec = a.elapsed_time(b) / 1e3
+    path = batch.path(slot)
     batch.remove(slot, stream=sptr)
     ok = bs.status() == 0
     tile, ctas = batch.choice(mesh.ndim, bs.precision)
@@ -253,7 +256,8 @@ def measure_variants(args, fx, inputs, mesh, dev, cfl, zones, bs, ws, hbm_peak):
     fx.fx_finalize(ctx)
     z, t = aggregate(zones * args.steps, sec, dev)
     out["batched_graph"] = {"value": z / t, "unit": UNIT, "ms_per_step": 1e3 * t / args.steps,
-                            "tile": tile, "ctas_per_sm": ctas, "tuning_us": tuning, "ok": ok}
+                            "path": BATCH_PATHS[path], "tile": tile, "ctas_per_sm": ctas,
+                            "tuning_us": tuning, "ok": ok}
     # (ii) the other precision, plain per-call path
     other = "f32bulk" if args.precision == "f64" else "f64"
     prec = fx.FX_F32BULK if other == "f32bulk" else fx.FX_F64
@@ -280,11 +284,19 @@ def measure_variants(args, fx, inputs, mesh, dev, cfl, zones, bs, ws, hbm_peak):
     hyd = float(np.mean([x.elapsed_time(y) for x, y in ev])) / 1e3
     z, t = aggregate(zones * args.steps, sec, dev)
     bpz = HBM_BYTES_PER_ZONE[other]
+    ok2 = bs2.status() == 0
+    # the same as one request of a batch (continuing from this state)
+    gsec, gtile, gctas, gpath = timed_batch(fx, bs2, cfl, stream, args.warmup, args.steps,
+                                            mesh2.nxb, mesh2.ng)
+    gz, gt = aggregate(zones * args.steps, gsec, dev)
     out[other] = {"value": z / t, "unit": UNIT, "ms_per_step": 1e3 * t / args.steps,
                   "dtype": "f32" if other == "f32bulk" else "f64", "hydro_ms": hyd * 1e3,
                   "hydro_hbm_frac": bpz * zones / hyd / (hbm_peak * 1e9),
                   "step_hbm_frac": bpz * (z / t) / ws / (hbm_peak * 1e9),
-                  "ok": bs2.status() == 0}
+                  "batched_graph": {"value": gz / gt, "ms_per_step": 1e3 * gt / args.steps,
+                                    "path": BATCH_PATHS[gpath], "tile": gtile,
+                                    "ctas_per_sm": gctas},
+                  "ok": ok2 and bs2.status() == 0}
     bs2.close()
     # (v) FP64 state updated in double-word arithmetic (option f64_arith = 1):
     # timed like (ii); its deviation from the FP64 update after one step from
@@ -485,10 +497,16 @@ def timed_steps(fx, bs, cfl, stream, warmup, steps):
     return a.elapsed_time(b) / 1e3, float(np.mean([x.elapsed_time(y) for x, y in ev])) / 1e3
 
 
+BATCH_PATHS = {0: "batched phases and the persistent update kernel (autotuned), one CUDA graph per step",
+               1: "the per-block-set kernels on a branch of one CUDA graph per step (the request fills the GPU)"}
+
+
 def timed_batch(fx, bs, cfl, stream, warmup, steps, nxb, ng):
-    """The same as one request of a batch: coarse-fine fill, persistent update
-    and flux correction replayed as one CUDA graph per step, launch choice
-    autotuned; returns (seconds of the `steps` timed steps, tile, CTAs/SM)."""
+    """The same as one request of a batch: coarse-fine fill, update and flux
+    correction replayed as one CUDA graph per step (the persistent update with
+    its launch choice autotuned, or the per-block-set kernels for a request
+    that fills the GPU); returns (seconds of the `steps` timed steps, tile,
+    CTAs/SM, path)."""
     import torch
     sptr = stream.cuda_stream
     ctx = fx.fx_init(1.4, nxb, ng)
@@ -503,20 +521,21 @@ def timed_batch(fx, bs, cfl, stream, warmup, steps, nxb, ng):
         batch.run(steps, stream=sptr)
         b.record(stream)
         torch.cuda.synchronize()
+        path = batch.path(slot)
         batch.remove(slot, stream=sptr)
         tile, ctas = batch.choice(bs.mesh.ndim, bs.precision)
     finally:
         batch.close()
         fx.fx_finalize(ctx)
-    return a.elapsed_time(b) / 1e3, tile, ctas
+    return a.elapsed_time(b) / 1e3, tile, ctas, path
 
 
 def measure_configs(args, fx, inputs, dev, hbm_peak):
     """The other workloads of the benchmark plan, each timed on the device:
     the 2D Sod tube (50 steps, FP64 and FP32-bulk, per call and as a
-    graph-replayed batch), the 3D Sedov blast on its two-level octree through
-    the batched persistent kernel and CUDA graph (20 warm-up + 100 timed
-    steps; FP64 and FP32-bulk, and the per-call FP64 path beside it), and
+    graph-replayed batch), the 3D Sedov blast on its two-level octree as a
+    graph-replayed batch of one request (20 warm-up + 100 timed steps; FP64
+    and FP32-bulk, and the per-call path beside it), and
     smooth advection at 512^3 (FP64 and FP32-bulk)."""
     import torch
     stream = torch.cuda.Stream(device=dev)
@@ -531,12 +550,13 @@ def measure_configs(args, fx, inputs, dev, hbm_peak):
         sec, hyd = timed_steps(fx, bs, cfl, stream, 5, 50)
         ok = bs.status() == 0
         bs.set_primitive(W)
-        gsec, tile, ctas = timed_batch(fx, bs, cfl, stream, 5, 50, mesh.nxb, mesh.ng)
+        gsec, tile, ctas, path = timed_batch(fx, bs, cfl, stream, 5, 50, mesh.nxb, mesh.ng)
         out[f"sod2d_128^2_{prec_name}"] = {
             "value": zones * 50 / sec, "unit": UNIT, "ms_per_step": 1e3 * sec / 50,
             "hydro_ms": hyd * 1e3, "batched_graph": {"value": zones * 50 / gsec,
                                                      "ms_per_step": 1e3 * gsec / 50,
-                                                     "tile": tile, "ctas_per_sm": ctas},
+                                                     "tile": tile, "ctas_per_sm": ctas,
+                                                     "path": BATCH_PATHS[path]},
             "steps": 50, "note": "1.3 MB state: L2-resident, launch-latency bound",
             "ok": ok and bs.status() == 0}
         bs.close()
@@ -546,12 +566,12 @@ def measure_configs(args, fx, inputs, dev, hbm_peak):
         zones = mesh.leaf_zones()
         bs = fx.BlockSet(mesh, gamma, precision=prec, device=dev)
         bs.set_primitive(W)
-        gsec, tile, ctas = timed_batch(fx, bs, cfl, stream, 20, 100, mesh.nxb, mesh.ng)
+        gsec, tile, ctas, path = timed_batch(fx, bs, cfl, stream, 20, 100, mesh.nxb, mesh.ng)
         ok = bs.status() == 0
         bs.set_primitive(W)
         sec, hyd = timed_steps(fx, bs, cfl, stream, 20, 100)
         entry = {"value": zones * 100 / gsec, "unit": UNIT, "ms_per_step": 1e3 * gsec / 100,
-                 "path": "batched persistent kernel, one CUDA graph per step, autotuned",
+                 "path": "batch of one request: " + BATCH_PATHS[path],
                  "tile": tile, "ctas_per_sm": ctas, "warmup": 20, "steps": 100,
                  "per_call": {"value": zones * 100 / sec, "ms_per_step": 1e3 * sec / 100,
                               "hydro_ms": hyd * 1e3},

@@ -352,10 +352,14 @@ FX_API const double *fx_block_fluxes(const fx_blocks *bs, int b);
  * step is one CUDA graph replay in which every phase of the step -- dt,
  * coarse-fine guard fill, the fused update, flux correction, restriction --
  * is one kernel launch over a work list spanning all requests, the update
- * being a persistent kernel per (dimension, precision, tile) group.  Block
- * sets of different sizes, block counts, levels and precisions mix freely;
- * each keeps its own dt.  This is the paper's block-by-block update (Section
- * 2) organised for one GPU; the batching itself has no counterpart in the
+ * being a persistent kernel per (dimension, precision, tile) group.  A
+ * request whose update alone fills the GPU (at least one wave of the
+ * per-block-set update's CTAs: leaves x tiles per block >= CTAs per SM x SMs)
+ * is stepped instead by the kernels of fx_step, on a branch of the same
+ * graph; its result is bitwise that of stepping it alone.  Block sets of
+ * different sizes, block counts, levels and precisions mix freely; each
+ * keeps its own dt.  This is the paper's block-by-block update (Section 2)
+ * organised for one GPU; the batching itself has no counterpart in the
  * paper.  A block set in a batch must not be stepped or destroyed directly
  * until fx_batch_remove returns it. */
 typedef struct fx_batch fx_batch;
@@ -366,7 +370,9 @@ FX_API int fx_batch_create(fx_ctx *ctx, int max_requests, fx_batch **out);
 FX_API int fx_batch_destroy(fx_batch *b);
 /* fx_batch_add: add block set `bs` to advance `nsteps` steps with CFL number
  * `cfl` from its current state; *slot_out receives its slot.  It joins at the
- * next fx_batch_run (the graph is re-captured).  Synchronises `stream`.  The
+ * next fx_batch_run (the graph is re-captured); its parents are restricted
+ * on `stream` first if the state has changed since they last were.
+ * Synchronises `stream`.  The
  * update of an FX_F64 block set whose context has "f64_arith" = 1 runs in
  * double-word arithmetic inside the batch too (compute class 2 below). */
 FX_API int fx_batch_add(fx_batch *b, fx_blocks *bs, double cfl, int nsteps, void *stream,
@@ -386,7 +392,8 @@ FX_API int fx_batch_remove(fx_batch *b, int slot, void *stream);
  * neither changes any state) and scaling to the whole group.  Choices are
  * cached per (dimension, precision, SM count, set of block edges).  `report`
  * (may be NULL; room for 193 ints) receives (tile, ctas, estimated
- * microseconds per update of the group) triples, 0 terminated.
+ * microseconds per update of the group) triples, 0 terminated.  Requests
+ * stepped by the per-block-set kernels do not use the choice.
  * Synchronises. */
 FX_API int fx_batch_tune(fx_batch *b, void *stream, int *report);
 /* fx_batch_choice: the launch choice in use for a (ndim, precision) group;
@@ -394,6 +401,12 @@ FX_API int fx_batch_tune(fx_batch *b, void *stream, int *report);
  * for FP64 block sets updated in double-word arithmetic. */
 FX_API int fx_batch_choice(const fx_batch *b, int ndim, int precision, int *tile,
                            int *ctas_per_sm);
+/* fx_batch_path: how the request in `slot` is stepped: *path = 0 by the
+ * batched phases and the persistent update, 1 by the per-block-set kernels
+ * of fx_step on a branch of the graph (its update alone fills the GPU).
+ * Fixed by the request's mesh, precision and this GPU, not by the rest of
+ * the batch.  Errors: FX_ERR_ARG for a null pointer or an empty slot. */
+FX_API int fx_batch_path(const fx_batch *b, int slot, int *path);
 
 /* Largest block count fx_compute_dt_noalloc accepts (size of its fixed
  * device scratch, one 8-byte partial per block plus a counter: 256 KB). */

@@ -1,7 +1,14 @@
 // batch_api.cpp -- batched, graph-replayed stepping of many block sets
-// (requests): one persistent kernel per phase over the work items of all
-// requests, captured once into a CUDA graph and replayed per step, with the
-// tile and CTAs-per-SM choice made by timing the candidates on the device.
+// (requests): one kernel per phase over the work items of all requests,
+// captured once into a CUDA graph and replayed per step, with the tile and
+// CTAs-per-SM choice of the persistent update made by timing the candidates
+// on the device.  A request with enough tiles to fill the GPU by itself is
+// stepped by the per-block-set kernels instead (the launches of fx_step,
+// with mesh and buffers as kernel parameters rather than loaded from its
+// descriptor, each gated by its steps-left counter), on a branch of the
+// graph beside the batched phases; its buffers alternate between steps, so
+// the graph is captured twice, once per buffer parity, and the replays
+// alternate.
 //
 // Paper: Flash-X (arXiv 2208.11630), Section 2 -- each request is a Grid of
 // blocks advanced by the unsplit hydro step; a batch advances many of them
@@ -41,6 +48,7 @@ struct Choice {
 std::map<std::tuple<int, int, int, int>, Choice> g_tune_cache;
 
 constexpr int kClasses = 3;
+constexpr int kSide = 4;   // capture streams for the updates of the large requests
 
 // Compute class of a block set's update: its precision, or 2 for an FP64 set
 // whose context asks for double-word arithmetic.
@@ -61,7 +69,12 @@ struct fx_batch {
   size_t items_cap = 0;
   unsigned int *d_ctr = nullptr;     // work counters, one per hydro group
   cudaStream_t cap = nullptr;        // private capture stream
-  cudaGraphExec_t exec = nullptr;
+  cudaStream_t side[kSide] = {};     // branches of the large requests' updates
+  cudaEvent_t fork = nullptr, join[kSide] = {};
+  cudaGraphExec_t exec[2] = {};      // the step from buffer parity 0 and from parity 1
+  int phase = 0;                     // parity of the next replay (alternates if large requests)
+  std::vector<int> big;              // requests updated by the per-block-set kernel
+  std::vector<int> cur0;             // their current buffer when the graphs were captured
   bool dirty = true;
   int lmax = 0;
   Range rst[2][FX_MAXLEV], cpy[2], pro[2][FX_MAXLEV], rfx[2];
@@ -74,14 +87,32 @@ namespace {
 
 constexpr int kMaxGroups = 8;
 
-// Work lists of the batched step for the current composition.
-int build_lists(fx_batch *b, const Choice (&ch)[2][kClasses]) {
+// Does the request fill the GPU by itself: at least one full wave of the
+// per-block-set kernel's CTAs?
+bool fills_gpu(const fx_batch *b, const fx_blocks *bs) {
+  int fit = 0;
+  if (fx::hydro_set_fit(bs->ndim, bs->nxb, compute_class(bs), &fit) != cudaSuccess || fit < 1)
+    return false;
+  const int tiles = bs->nxb % 16 == 0 ? bs->nxb / 16 : bs->nxb / 8;
+  return (long long)bs->nleaves * tiles * tiles >= (long long)fit * b->nsm;
+}
+
+// Work lists of the batched step for the current composition.  split: leave
+// the requests that fill the GPU out of the batched phases' lists and list
+// them in b->big (the captured step); without it every request is in the
+// lists (the tuner's timing).
+int build_lists(fx_batch *b, const Choice (&ch)[2][kClasses], bool split) {
   std::vector<int4> rst[2][FX_MAXLEV], cpy[2], pro[2][FX_MAXLEV], rfx[2];
   std::map<std::tuple<int, int, int>, std::vector<int4>> hyd;
   b->lmax = 0;
+  b->big.clear();
   for (int r = 0; r < b->max_req; ++r) {
     fx_blocks *bs = b->slot[r];
     if (!bs) continue;
+    if (split && fills_gpu(b, bs)) {
+      b->big.push_back(r);
+      continue;
+    }
     const int pr = bs->prec, nd = bs->ndim, n = bs->nxb;
     const std::vector<int> &L = bs->h_lists;
     const int ncell = n * n * (nd == 3 ? n : 1);
@@ -145,14 +176,50 @@ int build_lists(fx_batch *b, const Choice (&ch)[2][kClasses]) {
   return FX_OK;
 }
 
-cudaError_t record_step(fx_batch *b, cudaStream_t s) {
-  cudaError_t e;
 #define FXB(call) do { e = (call); if (e != cudaSuccess) return e; } while (0)
+
+// The step of a request that fills the GPU: the launches of fx_step after
+// its dt (fx_guardcell_fill_amr, then fx_hydro_advance for the MUSCL-Hancock
+// integrator), from buffer c into 1 - c, each kernel gated by the request's
+// steps-left counter.  The signal-speed maximum was re-armed by the batch's
+// begin kernel.
+cudaError_t record_request(fx_batch *b, int r, int c, cudaStream_t s) {
+  cudaError_t e;
+  const fx_blocks *bs = b->slot[r];
+  const BatchReq &q = b->h_req[r];
+  const int *live = &b->d_req[r].steps_left;
+  void *U = bs->U[c], *Un = bs->U[1 - c];
+  FXB(fx::launch_guard_copy(bs->dm, U, bs->prec, bs->d_lists + bs->src_off, bs->nsrc,
+                            fx::kHydroGuardDepth, s, live));
+  for (int l = 1; l <= bs->lmax; ++l)
+    FXB(fx::launch_guard_prolong_slots(bs->dm, U, bs->prec, bs->d_pslots + bs->pslot_off[l],
+                                       bs->pslot_cnt[l], fx::kHydroGuardDepth, 1, s, live));
+  fx::HydroStage st;
+  st.dword = compute_class(bs) == 2 ? 1 : 0;
+  st.live = live;
+  FXB(fx::launch_hydro(bs->dm, U, Un, bs->prec, bs->d_lists + bs->leaves_off, bs->nleaves, q.dt,
+                       q.regs, q.status, q.scratch + 2, q.rmask, q.form, s, st));
+  if (q.reflux)
+    FXB(fx::launch_reflux(bs->dm, Un, bs->prec, q.refl, q.nrefl, q.dt, q.regs, q.status,
+                          q.scratch + 2, q.form, s, live));
+  for (int l = bs->lmax; l >= 0; --l)
+    FXB(fx::launch_restrict(bs->dm, Un, bs->prec, bs->d_lists + bs->par_off[l], bs->par_cnt[l], s,
+                            live));
+  return cudaSuccess;
+}
+
+// One batched step; parity 1 swaps the buffers of the large requests
+// relative to b->cur0 (the other graph of the pair).
+cudaError_t record_step(fx_batch *b, cudaStream_t s, int parity) {
+  cudaError_t e;
   FXB(fx::launch_batch_begin(b->d_req, b->max_req, s));
-  for (int l = b->lmax - 1; l >= 0; --l)
-    for (int p = 0; p < 2; ++p)
-      FXB(fx::launch_batch_phase(fx::BATCH_RESTRICT_PRE, p, b->d_req, b->d_items + b->rst[p][l].off,
-                                 b->rst[p][l].n, s));
+  const int nside = std::min<int>(kSide, (int)b->big.size());
+  if (nside > 0) {
+    FXB(cudaEventRecord(b->fork, s));
+    for (int j = 0; j < nside; ++j) FXB(cudaStreamWaitEvent(b->side[j], b->fork, 0));
+  }
+  for (size_t k = 0; k < b->big.size(); ++k)
+    FXB(record_request(b, b->big[k], b->cur0[k] ^ parity, b->side[k % kSide]));
   for (int p = 0; p < 2; ++p)
     FXB(fx::launch_batch_phase(fx::BATCH_COPY, p, b->d_req, b->d_items + b->cpy[p].off, b->cpy[p].n, s));
   for (int l = 1; l <= b->lmax; ++l)
@@ -169,22 +236,21 @@ cudaError_t record_step(fx_batch *b, cudaStream_t s) {
     FXB(fx::launch_batch_phase(fx::BATCH_REFLUX, p, b->d_req, b->d_items + b->rfx[p].off, b->rfx[p].n, s));
   for (int l = b->lmax - 1; l >= 0; --l)
     for (int p = 0; p < 2; ++p)
-      FXB(fx::launch_batch_phase(fx::BATCH_RESTRICT_POST, p, b->d_req, b->d_items + b->rst[p][l].off,
+      FXB(fx::launch_batch_phase(fx::BATCH_RESTRICT, p, b->d_req, b->d_items + b->rst[p][l].off,
                                  b->rst[p][l].n, s));
+  for (int j = 0; j < nside; ++j) {
+    FXB(cudaEventRecord(b->join[j], b->side[j]));
+    FXB(cudaStreamWaitEvent(s, b->join[j], 0));
+  }
   FXB(fx::launch_batch_end(b->d_req, b->max_req, s));
-#undef FXB
   return cudaSuccess;
 }
+#undef FXB
 
-// The coarse-fine fill of the current buffers (restriction, copies feeding
-// prolongation, prolongation): what an update needs to read valid guards.
+// The coarse-fine fill of the current buffers (copies feeding prolongation,
+// prolongation; parents are valid): what an update needs to read valid guards.
 cudaError_t record_fill(fx_batch *b, cudaStream_t s) {
   cudaError_t e;
-  for (int l = b->lmax - 1; l >= 0; --l)
-    for (int p = 0; p < 2; ++p)
-      if ((e = fx::launch_batch_phase(fx::BATCH_RESTRICT_PRE, p, b->d_req, b->d_items + b->rst[p][l].off,
-                                      b->rst[p][l].n, s)) != cudaSuccess)
-        return e;
   for (int p = 0; p < 2; ++p)
     if ((e = fx::launch_batch_phase(fx::BATCH_COPY, p, b->d_req, b->d_items + b->cpy[p].off,
                                     b->cpy[p].n, s)) != cudaSuccess)
@@ -197,31 +263,55 @@ cudaError_t record_fill(fx_batch *b, cudaStream_t s) {
   return cudaSuccess;
 }
 
+void drop_graphs(fx_batch *b) {
+  for (cudaGraphExec_t &x : b->exec)
+    if (x) {
+      cudaGraphExecDestroy(x);
+      x = nullptr;
+    }
+}
+
+// Captures the batched step of the current composition (the caller has
+// synchronised the stream the batch runs on).
 int capture(fx_batch *b) {
-  if (b->exec) {
-    cudaGraphExecDestroy(b->exec);
-    b->exec = nullptr;
-  }
-  int rc = build_lists(b, b->choice);
+  drop_graphs(b);
+  int rc = build_lists(b, b->choice, true);
   if (rc) return fail(b->ctx, rc, "building the batch work lists failed");
   for (const HydroGroup &G : b->groups) {   // attributes before capture
     int fit = 0;
     cudaError_t e = fx::hydro_batch_fit(G.ndim, G.tile, G.prec, &fit);
     if (e != cudaSuccess) return cuda_fail(b->ctx, e, "batched kernel set-up");
   }
-  cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return cuda_fail(b->ctx, e, "begin capture");
-  cudaError_t er = record_step(b, b->cap);
-  e = cudaStreamEndCapture(b->cap, &g);
-  if (er != cudaSuccess) {
-    if (g) cudaGraphDestroy(g);
-    return cuda_fail(b->ctx, er, "recording the batched step");
+  b->cur0.assign(b->big.size(), 0);
+  for (size_t k = 0; k < b->big.size(); ++k) {   // current buffers, as the device flipped them
+    cudaError_t e = cudaMemcpy(&b->cur0[k], &b->d_req[b->big[k]].cur, sizeof(int),
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(b->ctx, e, "descriptor read");
   }
-  if (e != cudaSuccess) return cuda_fail(b->ctx, e, "end capture");
-  e = cudaGraphInstantiate(&b->exec, g, 0);
-  cudaGraphDestroy(g);
-  if (e != cudaSuccess) return cuda_fail(b->ctx, e, "graph instantiate");
+  const int nexec = b->big.empty() ? 1 : 2;
+  for (int parity = 0; parity < nexec; ++parity) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(b->ctx, e, "begin capture");
+    cudaError_t er = record_step(b, b->cap, parity);
+    e = cudaStreamEndCapture(b->cap, &g);
+    if (er != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      drop_graphs(b);
+      return cuda_fail(b->ctx, er, "recording the batched step");
+    }
+    if (e != cudaSuccess) {
+      drop_graphs(b);
+      return cuda_fail(b->ctx, e, "end capture");
+    }
+    e = cudaGraphInstantiate(&b->exec[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      drop_graphs(b);
+      return cuda_fail(b->ctx, e, "graph instantiate");
+    }
+  }
+  b->phase = 0;
   b->dirty = false;
   return FX_OK;
 }
@@ -248,8 +338,18 @@ int fx_batch_create(fx_ctx *ctx, int max_requests, fx_batch **out) {
       cudaMemset(b->d_req, 0, sizeof(BatchReq) * max_requests) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
     cudaFree(b->d_req); cudaFree(b->d_dt); cudaFree(b->d_ctr);
+    if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
     return fail(ctx, FX_ERR_OOM, "batch allocation failed");
+  }
+  bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int j = 0; j < kSide && ok; ++j)
+    ok = cudaStreamCreateWithFlags(&b->side[j], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->join[j], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    fx_batch_destroy(b);
+    cudaGetLastError();
+    return fail(ctx, FX_ERR_CUDA, "batch stream set-up failed");
   }
   *out = b;
   return FX_OK;
@@ -260,8 +360,13 @@ int fx_batch_destroy(fx_batch *b) {
   cudaDeviceSynchronize();
   for (fx_blocks *bs : b->slot)
     if (bs) bs->in_batch = 0;
-  if (b->exec) cudaGraphExecDestroy(b->exec);
+  drop_graphs(b);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (int j = 0; j < kSide; ++j) {
+    if (b->side[j]) cudaStreamDestroy(b->side[j]);
+    if (b->join[j]) cudaEventDestroy(b->join[j]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   cudaFree(b->d_req); cudaFree(b->d_dt); cudaFree(b->d_ctr); cudaFree(b->d_items);
   delete b;
   return FX_OK;
@@ -298,6 +403,14 @@ int fx_batch_add(fx_batch *b, fx_blocks *bs, double cfl, int nsteps, void *strea
   q.scratch = bs->d_scratch;
   q.rmask = q.reflux ? bs->d_rmask : nullptr;
   q.refl = bs->d_refl;
+  // every batched step starts from restricted parents
+  if (bs->restricted_epoch != bs->epoch) {
+    for (int l = bs->lmax; l >= 0; --l)
+      FX_CUDA(fx::launch_restrict(bs->dm, bs->U[bs->cur], bs->prec, bs->d_lists + bs->par_off[l],
+                                  bs->par_cnt[l], st),
+              "restrict launch");
+    bs->restricted_epoch = bs->epoch;
+  }
   // the first batched step needs the signal-speed maximum of the current state
   if (!(bs->next_epoch == bs->epoch && bs->next_form == q.form)) {
     FX_CUDA(fx::launch_signal_max(bs->dm, bs->U[bs->cur], bs->prec, bs->d_lists + bs->leaves_off,
@@ -324,8 +437,9 @@ int fx_batch_run(fx_batch *b, int nsteps, void *stream) {
     if (rc) return rc;
   }
   for (int i = 0; i < nsteps; ++i) {
-    cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    cudaError_t e = cudaGraphLaunch(b->exec[b->phase], (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(b->ctx, e, "graph launch");
+    if (b->exec[1]) b->phase ^= 1;
   }
   return FX_OK;
 }
@@ -359,6 +473,7 @@ int fx_batch_remove(fx_batch *b, int slot, void *stream) {
   bs->cur = q.cur;
   ++bs->epoch;
   bs->next_epoch = bs->epoch;        // the last update left its signal maximum
+  bs->restricted_epoch = bs->epoch;  // restricted on admission and by every batched step
   bs->next_form = q.form;
   bs->in_batch = 0;
   b->slot[slot] = nullptr;           // free for reuse (a new occupant recaptures)
@@ -379,7 +494,7 @@ int fx_batch_tune(fx_batch *b, void *stream, int *report) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   // valid guards for every request before any timed update
-  if (build_lists(b, b->choice)) return fail(b->ctx, FX_ERR_OOM, "tuning work lists");
+  if (build_lists(b, b->choice, false)) return fail(b->ctx, FX_ERR_OOM, "tuning work lists");
   e = record_fill(b, st);
   if (e != cudaSuccess) return cuda_fail(b->ctx, e, "tuning guard fill");
   int nrep = 0;
@@ -410,7 +525,7 @@ int fx_batch_tune(fx_batch *b, void *stream, int *report) {
             for (int c = 0; c < kClasses; ++c) ch[a][c] = b->choice[a][c];
           ch[nd - 2][pr].tile = tile;
           ch[nd - 2][pr].ctas = ctas;
-          if (build_lists(b, ch)) break;
+          if (build_lists(b, ch, false)) break;
           const HydroGroup *G = nullptr;
           int gi = 0;
           for (size_t g = 0; g < b->groups.size(); ++g)
@@ -459,6 +574,12 @@ int fx_batch_tune(fx_batch *b, void *stream, int *report) {
   if (e != cudaSuccess) return cuda_fail(b->ctx, e, "tuning");
   if (report) report[3 * nrep] = 0;
   b->dirty = true;
+  return FX_OK;
+}
+
+int fx_batch_path(const fx_batch *b, int slot, int *path) {
+  if (!b || !path || slot < 0 || slot >= b->max_req || !b->slot[slot]) return FX_ERR_ARG;
+  *path = fills_gpu(b, b->slot[slot]) ? 1 : 0;
   return FX_OK;
 }
 

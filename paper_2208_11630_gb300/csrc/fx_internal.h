@@ -73,11 +73,14 @@ struct BatchReq {
   const RefluxItem *refl;         // reflux work items (or null)
 };
 
-// Launchers.  Each returns the launch status (cudaGetLastError).
+// Launchers.  Each returns the launch status (cudaGetLastError).  live (the
+// coarse-fine launchers, may be null): every CTA returns at once while
+// *live <= 0 -- the steps-left counter of a batched request whose step runs
+// these per-block-set kernels.
 cudaError_t launch_prim_to_cons(const DevMesh &m, const double *W, void *U, int prec,
                                 cudaStream_t s);
 cudaError_t launch_restrict(const DevMesh &m, void *U, int prec, const int *parents, int n,
-                            cudaStream_t s);
+                            cudaStream_t s, const int *live = nullptr);
 // Interior cells of blocks [b0, b0 + nblk): dir 0 scatters a packed array
 // [block][var][z][y][x] (relative to b0) into the padded layout, dir 1
 // gathers them into it.
@@ -87,12 +90,12 @@ cudaError_t launch_pack(const DevMesh &m, void *U, int prec, void *packed, int b
 // the interior; prolongation of FP32 state computes in FP32 when
 // state_precision_math is set (else FP64).
 cudaError_t launch_guard_copy(const DevMesh &m, void *U, int prec, const int *leaves, int n,
-                              int depth, cudaStream_t s);
+                              int depth, cudaStream_t s, const int *live = nullptr);
 // Prolonged guards of (leaf, slot) items -- slots covered by a coarser leaf
 // -- within `depth`; the work is proportional to the prolonged cells.
 cudaError_t launch_guard_prolong_slots(const DevMesh &m, void *U, int prec, const int2 *items,
                                        int n, int depth, int state_precision_math,
-                                       cudaStream_t s);
+                                       cudaStream_t s, const int *live = nullptr);
 // Guard depth the fused update reads (radius-2 stencil).
 constexpr int kHydroGuardDepth = 2;
 // Time-integration stage of one update launch (defaults: MUSCL-Hancock).
@@ -107,6 +110,8 @@ struct HydroStage {
   int reg_add = 0;            // 0 store, 1 add to the registers
   int dword = 0;              // FP64 state: 1 double-word arithmetic (MUSCL-Hancock only),
                               // 2 FP32 arithmetic (single gas, MUSCL-Hancock only)
+  const int *live = nullptr;  // single-gas MUSCL-Hancock update of a batched request: every
+                              // CTA returns at once while *live <= 0 (no steps left)
 };
 
 // smax (may be null): receives atomicMax of the bit patterns of the new
@@ -118,7 +123,7 @@ struct HydroStage {
 cudaError_t launch_hydro_dw(const DevMesh &m, const void *U, void *Unew, const int *leaves, int n,
                             const double *dt, double *regs, int *status,
                             unsigned long long *smax, const unsigned char *rmask, int form,
-                            cudaStream_t s);
+                            cudaStream_t s, const int *live = nullptr);
 cudaError_t launch_hydro_species_dw(const DevMesh &m, const void *U, void *Unew,
                                     const int *leaves, int n, const double *dt, double *regs,
                                     int *status, unsigned long long *smax,
@@ -131,6 +136,11 @@ cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, 
                          int n, const double *dt, double *regs, int *status,
                          unsigned long long *smax, const unsigned char *rmask, int form,
                          cudaStream_t s, const HydroStage &st = HydroStage());
+// CTAs per SM of the per-block-set single-gas MUSCL-Hancock kernel that
+// launch_hydro picks for blocks of edge nxb (compute class as for
+// hydro_batch_fit), setting its shared-memory attribute on first use.
+cudaError_t hydro_set_fit(int ndim, int nxb, int cls, int *fit);
+cudaError_t hydro_set_fit_dw(int ndim, int nxb, int *fit);
 // Regridding: per-leaf maximum of the Loehner indicator on density and
 // pressure (filter eps) into err_bits[i] for leaves[i] (bit patterns, zeroed
 // by the caller; guards filled); and the state transfer onto a new mesh,
@@ -151,7 +161,8 @@ cudaError_t launch_hydro_rk(const DevMesh &m, const void *U, void *Unew, int pre
                             cudaStream_t s, const HydroStage &st);
 cudaError_t launch_reflux(const DevMesh &m, void *Unew, int prec, const RefluxItem *items, int n,
                           const double *dt, const double *regs, int *status,
-                          unsigned long long *smax, int form, cudaStream_t s);
+                          unsigned long long *smax, int form, cudaStream_t s,
+                          const int *live = nullptr);
 // dt = cfl / (maximum held in *smax), then re-arms *smax to zero.
 cudaError_t launch_dt_finalize(unsigned long long *smax, double cfl, double *dt_out,
                                cudaStream_t s);
@@ -163,11 +174,10 @@ cudaError_t launch_totals(const DevMesh &m, const void *U, int prec, const int *
 
 // Phases of the batched step (see k_batch.cu).
 enum BatchPhase : int {
-  BATCH_RESTRICT_PRE = 0,
   BATCH_COPY = 1,
   BATCH_PROLONG = 2,
   BATCH_REFLUX = 3,
-  BATCH_RESTRICT_POST = 4
+  BATCH_RESTRICT = 4
 };
 cudaError_t launch_batch_begin(BatchReq *reqs, int n, cudaStream_t s);
 cudaError_t launch_batch_end(BatchReq *reqs, int n, cudaStream_t s);

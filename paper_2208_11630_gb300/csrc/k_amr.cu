@@ -16,7 +16,8 @@ template <typename S>
 __global__ void k_reflux(DevMesh m, S *__restrict__ Unew, const RefluxItem *__restrict__ items,
                          const double *__restrict__ dtp, const double *__restrict__ regs,
                          int *__restrict__ status, unsigned long long *__restrict__ smax,
-                         int form) {
+                         int form, const int *__restrict__ live) {
+  if (live != nullptr && *live <= 0) return;
   __shared__ RefluxItem it;
   if (threadIdx.x == 0) it = items[blockIdx.x];
   __syncthreads();
@@ -28,12 +29,12 @@ __global__ void k_reflux(DevMesh m, S *__restrict__ Unew, const RefluxItem *__re
 
 cudaError_t launch_reflux(const DevMesh &m, void *Unew, int prec, const RefluxItem *items, int n,
                           const double *dt, const double *regs, int *status,
-                          unsigned long long *smax, int form, cudaStream_t s) {
+                          unsigned long long *smax, int form, cudaStream_t s, const int *live) {
   if (n <= 0) return cudaSuccess;
   const int ncell = m.nxb * m.nxb * (m.ndim == 3 ? m.nxb : 1);
   dim3 grid(n, (ncell + 255) / 256);
-  if (prec == 0) k_reflux<double><<<grid, 256, 0, s>>>(m, static_cast<double *>(Unew), items, dt, regs, status, smax, form);
-  else k_reflux<float><<<grid, 256, 0, s>>>(m, static_cast<float *>(Unew), items, dt, regs, status, smax, form);
+  if (prec == 0) k_reflux<double><<<grid, 256, 0, s>>>(m, static_cast<double *>(Unew), items, dt, regs, status, smax, form, live);
+  else k_reflux<float><<<grid, 256, 0, s>>>(m, static_cast<float *>(Unew), items, dt, regs, status, smax, form, live);
   count_launch();
   return cudaGetLastError();
 }

@@ -6,14 +6,17 @@
 // Order of one batched step (each phase one launch over a work list that
 // spans all requests; items of requests with no steps left are skipped):
 //   begin     dt = cfl / (signal-speed maximum of the current state)
-//   restrict  parents from children, finest level first      (current buffer)
 //   copy      same-level guards of coarse leaves feeding a prolongation
 //   prolong   guards of leaves next to a coarser leaf, level by level, one
 //             CTA per (leaf, slot covered by the coarser leaf)
 //   hydro     fused MUSCL-Hancock/HLLC update (k_hydro_batch, persistent)
 //   reflux    fine-to-coarse flux correction                  (new buffer)
-//   restrict  parents of the new state
+//   restrict  parents of the new state, finest level first
 //   end       swap buffers, count the step
+// The parents of the current state are valid at every step: a request's are
+// restricted when it joins the batch, and each step ends by restricting them.
+// A request that fills the GPU by itself runs the per-block-set kernels of
+// these phases instead (batch_api.cpp), on a branch of the graph.
 // Paper: Flash-X (arXiv 2208.11630), Section 2 (block-by-block physics update
 // with Grid calls between updates); the batching across independent block
 // sets is this library's GPU design, not the paper's.
@@ -40,14 +43,13 @@ __global__ void k_batch_end(BatchReq *__restrict__ reqs, int n) {
   q.steps_left -= 1;
 }
 
-// items: (request, parent, chunk, -); post = 1 restricts the new buffer
+// items: (request, parent, chunk, -); restricts the new buffer
 template <typename S>
-__global__ void k_batch_restrict(const BatchReq *__restrict__ reqs, const int4 *__restrict__ items,
-                                 int post) {
+__global__ void k_batch_restrict(const BatchReq *__restrict__ reqs, const int4 *__restrict__ items) {
   const int4 w = items[blockIdx.x];
   const BatchReq &q = reqs[w.x];
   if (q.steps_left <= 0) return;
-  S *U = static_cast<S *>(q.U[post ? 1 - q.cur : q.cur]);
+  S *U = static_cast<S *>(q.U[1 - q.cur]);
   ops::restrict_cells<S>(q.m, U, w.y, w.z);
 }
 
@@ -103,13 +105,10 @@ cudaError_t launch_batch_phase(int phase, int prec, const BatchReq *reqs, const 
   if (n <= 0) return cudaSuccess;
   const bool f = prec != 0;
   switch (phase) {
-    case BATCH_RESTRICT_PRE:
-    case BATCH_RESTRICT_POST: {
-      const int post = phase == BATCH_RESTRICT_POST;
-      if (f) k_batch_restrict<float><<<n, 256, 0, s>>>(reqs, items, post);
-      else k_batch_restrict<double><<<n, 256, 0, s>>>(reqs, items, post);
+    case BATCH_RESTRICT:
+      if (f) k_batch_restrict<float><<<n, 256, 0, s>>>(reqs, items);
+      else k_batch_restrict<double><<<n, 256, 0, s>>>(reqs, items);
       break;
-    }
     case BATCH_COPY:
       if (f) k_batch_copy<float><<<n, 256, 0, s>>>(reqs, items);
       else k_batch_copy<double><<<n, 256, 0, s>>>(reqs, items);

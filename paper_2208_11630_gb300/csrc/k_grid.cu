@@ -49,14 +49,17 @@ __global__ void k_prim_to_cons(DevMesh m, const double *__restrict__ W, S *__res
 
 // One CTA per (parent, chunk of interior cells).
 template <typename S>
-__global__ void k_restrict(DevMesh m, S *__restrict__ U, const int *__restrict__ parents) {
+__global__ void k_restrict(DevMesh m, S *__restrict__ U, const int *__restrict__ parents,
+                           const int *__restrict__ live) {
+  if (live != nullptr && *live <= 0) return;
   ops::restrict_cells<S>(m, U, parents[blockIdx.x], blockIdx.y);
 }
 
 // One CTA per (leaf, padded z-plane): same-level guard copies up to `depth`.
 template <typename S>
 __global__ void k_guard_copy(DevMesh m, S *__restrict__ U, const int *__restrict__ leaves,
-                             int depth) {
+                             int depth, const int *__restrict__ live) {
+  if (live != nullptr && *live <= 0) return;
   ops::guard_copy_plane<S>(m, U, leaves[blockIdx.x], blockIdx.y, depth);
 }
 
@@ -89,7 +92,8 @@ __global__ void k_pack(DevMesh m, S *__restrict__ U, S *__restrict__ Pk, int b0,
 // of that slot within `depth`, in precision C.
 template <typename S, typename C>
 __global__ void k_guard_prolong_slots(DevMesh m, S *__restrict__ U, const int2 *__restrict__ items,
-                                      int depth) {
+                                      int depth, const int *__restrict__ live) {
+  if (live != nullptr && *live <= 0) return;
   const int2 it = items[blockIdx.x];
   ops::guard_prolong_slot<S, C>(m, U, it.x, it.y, depth, threadIdx.x, blockDim.x);
 }
@@ -129,36 +133,36 @@ cudaError_t launch_pack(const DevMesh &m, void *U, int prec, void *packed, int b
 }
 
 cudaError_t launch_restrict(const DevMesh &m, void *U, int prec, const int *parents, int n,
-                            cudaStream_t s) {
+                            cudaStream_t s, const int *live) {
   if (n <= 0) return cudaSuccess;
   const int ncell = m.nxb * m.nxb * (m.ndim == 3 ? m.nxb : 1);
   dim3 grid(n, (ncell + 255) / 256);
-  if (prec == 0) k_restrict<double><<<grid, 256, 0, s>>>(m, static_cast<double *>(U), parents);
-  else k_restrict<float><<<grid, 256, 0, s>>>(m, static_cast<float *>(U), parents);
+  if (prec == 0) k_restrict<double><<<grid, 256, 0, s>>>(m, static_cast<double *>(U), parents, live);
+  else k_restrict<float><<<grid, 256, 0, s>>>(m, static_cast<float *>(U), parents, live);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_guard_copy(const DevMesh &m, void *U, int prec, const int *leaves, int n,
-                              int depth, cudaStream_t s) {
+                              int depth, cudaStream_t s, const int *live) {
   if (n <= 0) return cudaSuccess;
   dim3 grid(n, m.PZ);
-  if (prec == 0) k_guard_copy<double><<<grid, 256, 0, s>>>(m, static_cast<double *>(U), leaves, depth);
-  else k_guard_copy<float><<<grid, 256, 0, s>>>(m, static_cast<float *>(U), leaves, depth);
+  if (prec == 0) k_guard_copy<double><<<grid, 256, 0, s>>>(m, static_cast<double *>(U), leaves, depth, live);
+  else k_guard_copy<float><<<grid, 256, 0, s>>>(m, static_cast<float *>(U), leaves, depth, live);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_guard_prolong_slots(const DevMesh &m, void *U, int prec, const int2 *items,
                                        int n, int depth, int state_precision_math,
-                                       cudaStream_t s) {
+                                       cudaStream_t s, const int *live) {
   if (n <= 0) return cudaSuccess;
   if (prec == 0)
-    k_guard_prolong_slots<double, double><<<n, 128, 0, s>>>(m, static_cast<double *>(U), items, depth);
+    k_guard_prolong_slots<double, double><<<n, 128, 0, s>>>(m, static_cast<double *>(U), items, depth, live);
   else if (state_precision_math)
-    k_guard_prolong_slots<float, float><<<n, 128, 0, s>>>(m, static_cast<float *>(U), items, depth);
+    k_guard_prolong_slots<float, float><<<n, 128, 0, s>>>(m, static_cast<float *>(U), items, depth, live);
   else
-    k_guard_prolong_slots<float, double><<<n, 128, 0, s>>>(m, static_cast<float *>(U), items, depth);
+    k_guard_prolong_slots<float, double><<<n, 128, 0, s>>>(m, static_cast<float *>(U), items, depth, live);
   count_launch();
   return cudaGetLastError();
 }

@@ -15,7 +15,8 @@ __global__ void __launch_bounds__(T *T, (T == 16 ? (sizeof(R) == 4 ? 4 : 2) : 6)
 k_hydro(DevMesh m, const S *__restrict__ U, S *Unew, const int *__restrict__ leaves,
         int tiles, const double *__restrict__ dtp, double *__restrict__ regs,
         int *__restrict__ status, unsigned long long *__restrict__ smax_out,
-        const unsigned char *__restrict__ rmask, int cfl_form) {
+        const unsigned char *__restrict__ rmask, int cfl_form, const int *__restrict__ live) {
+  if (live != nullptr && *live <= 0) return;   // a batched request with no steps left
   const int tpb = tiles * tiles;
   hydro_tile<NDIM, T, S, R>(m, U, Unew, leaves[blockIdx.x / tpb], blockIdx.x % tpb, tiles, *dtp,
                             regs, status, smax_out, rmask, cfl_form);
@@ -24,7 +25,7 @@ k_hydro(DevMesh m, const S *__restrict__ U, S *Unew, const int *__restrict__ lea
 template <int NDIM, int T, typename S, typename R>
 cudaError_t launch_t(const DevMesh &m, const void *U, void *Unew, const int *leaves, int n,
                      const double *dt, double *regs, int *status, unsigned long long *smax,
-                     const unsigned char *rmask, int form, cudaStream_t s) {
+                     const unsigned char *rmask, int form, cudaStream_t s, const int *live) {
   const int tiles = m.nxb / T;
   const size_t smem = tile_smem_bytes<NDIM, T, R>();
   auto kern = k_hydro<NDIM, T, S, R>;
@@ -32,12 +33,33 @@ cudaError_t launch_t(const DevMesh &m, const void *U, void *Unew, const int *lea
   if (cudaError_t e = set_smem_once((const void *)kern, smem, attr_devs); e != cudaSuccess)
     return e;
   kern<<<n * tiles * tiles, T * T, smem, s>>>(m, static_cast<const S *>(U), static_cast<S *>(Unew),
-                                              leaves, tiles, dt, regs, status, smax, rmask, form);
+                                              leaves, tiles, dt, regs, status, smax, rmask, form,
+                                              live);
   count_launch();
   return cudaGetLastError();
 }
 
+template <int NDIM, int T, typename S, typename R>
+cudaError_t set_fit_t(int *fit) {
+  const size_t smem = tile_smem_bytes<NDIM, T, R>();
+  auto kern = k_hydro<NDIM, T, S, R>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(fit, kern, T * T, smem);
+}
+
 }  // namespace
+
+cudaError_t hydro_set_fit(int ndim, int nxb, int cls, int *fit) {
+  if (cls == 2) return hydro_set_fit_dw(ndim, nxb, fit);
+  const bool t16 = nxb % 16 == 0;
+  if (cls == 0) {
+    if (ndim == 3) return t16 ? set_fit_t<3, 16, double, double>(fit) : set_fit_t<3, 8, double, double>(fit);
+    return t16 ? set_fit_t<2, 16, double, double>(fit) : set_fit_t<2, 8, double, double>(fit);
+  }
+  if (ndim == 3) return t16 ? set_fit_t<3, 16, float, float>(fit) : set_fit_t<3, 8, float, float>(fit);
+  return t16 ? set_fit_t<2, 16, float, float>(fit) : set_fit_t<2, 8, float, float>(fit);
+}
 
 cudaError_t hydro_batch_fit(int ndim, int tile, int prec, int *fit) {
   if (prec == 2) return hydro_batch_fit_dw(ndim, tile, fit);
@@ -74,6 +96,7 @@ cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, 
                          unsigned long long *smax, const unsigned char *rmask, int form,
                          cudaStream_t s, const HydroStage &st) {
   if (n <= 0) return cudaSuccess;
+  if (st.live && (m.nspec > 0 || !st.pred)) return cudaErrorInvalidValue;   // not batched
   if (m.nspec > 0) {   // multispecies gas (k_hydro_sp.cu): MUSCL-Hancock only
     if (!st.pred || st.Uavg || st.reg_add || st.reg_w != 1.0) return cudaErrorInvalidValue;
     if (st.dword) {
@@ -95,27 +118,27 @@ cudaError_t launch_hydro(const DevMesh &m, const void *U, void *Unew, int prec, 
   if (st.dword == 2) {   // FP64 state, FP32 arithmetic (option f64_arith = 2)
     if (prec != 0) return cudaErrorInvalidValue;
     if (m.ndim == 3)
-      return T == 16 ? launch_t<3, 16, double, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
-                     : launch_t<3, 8, double, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
-    return T == 16 ? launch_t<2, 16, double, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
-                   : launch_t<2, 8, double, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
+      return T == 16 ? launch_t<3, 16, double, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, st.live)
+                     : launch_t<3, 8, double, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, st.live);
+    return T == 16 ? launch_t<2, 16, double, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, st.live)
+                   : launch_t<2, 8, double, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, st.live);
   }
   if (st.dword) {
     if (prec != 0) return cudaErrorInvalidValue;
-    return launch_hydro_dw(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
+    return launch_hydro_dw(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, st.live);
   }
   if (prec == 0) {
     if (m.ndim == 3)
-      return T == 16 ? launch_t<3, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
-                     : launch_t<3, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
-    return T == 16 ? launch_t<2, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
-                   : launch_t<2, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
+      return T == 16 ? launch_t<3, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, st.live)
+                     : launch_t<3, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, st.live);
+    return T == 16 ? launch_t<2, 16, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, st.live)
+                   : launch_t<2, 8, double, double>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, st.live);
   }
   if (m.ndim == 3)
-    return T == 16 ? launch_t<3, 16, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
-                   : launch_t<3, 8, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
-  return T == 16 ? launch_t<2, 16, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
-                 : launch_t<2, 8, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
+    return T == 16 ? launch_t<3, 16, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, st.live)
+                   : launch_t<3, 8, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, st.live);
+  return T == 16 ? launch_t<2, 16, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, st.live)
+                 : launch_t<2, 8, float, float>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, st.live);
 }
 
 }  // namespace fx

@@ -18,7 +18,8 @@ __global__ void __launch_bounds__(T *T, (T == 16 ? 2 : 6))
 k_hydro_dw(DevMesh m, const double *__restrict__ U, double *Unew, const int *__restrict__ leaves,
            int tiles, const double *__restrict__ dtp, double *__restrict__ regs,
            int *__restrict__ status, unsigned long long *__restrict__ smax_out,
-           const unsigned char *__restrict__ rmask, int cfl_form) {
+           const unsigned char *__restrict__ rmask, int cfl_form, const int *__restrict__ live) {
+  if (live != nullptr && *live <= 0) return;   // a batched request with no steps left
   const int tpb = tiles * tiles;
   hydro_tile<NDIM, T, double, dw>(m, U, Unew, leaves[blockIdx.x / tpb], blockIdx.x % tpb, tiles,
                                   *dtp, regs, status, smax_out, rmask, cfl_form);
@@ -27,7 +28,7 @@ k_hydro_dw(DevMesh m, const double *__restrict__ U, double *Unew, const int *__r
 template <int NDIM, int T>
 cudaError_t launch_dw_t(const DevMesh &m, const void *U, void *Unew, const int *leaves, int n,
                         const double *dt, double *regs, int *status, unsigned long long *smax,
-                        const unsigned char *rmask, int form, cudaStream_t s) {
+                        const unsigned char *rmask, int form, cudaStream_t s, const int *live) {
   const int tiles = m.nxb / T;
   const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(dw);
   auto kern = k_hydro_dw<NDIM, T>;
@@ -36,9 +37,18 @@ cudaError_t launch_dw_t(const DevMesh &m, const void *U, void *Unew, const int *
     return e;
   kern<<<n * tiles * tiles, T * T, smem, s>>>(m, static_cast<const double *>(U),
                                               static_cast<double *>(Unew), leaves, tiles, dt, regs,
-                                              status, smax, rmask, form);
+                                              status, smax, rmask, form, live);
   count_launch();
   return cudaGetLastError();
+}
+
+template <int NDIM, int T>
+cudaError_t set_fit_dw_t(int *fit) {
+  const size_t smem = (size_t)Smem<T>::total(NDIM == 3 ? 3 : 1) * sizeof(dw);
+  auto kern = k_hydro_dw<NDIM, T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(fit, kern, T * T, smem);
 }
 
 // SSP Runge-Kutta stage in double-word arithmetic (plain PLM face states,
@@ -91,14 +101,20 @@ cudaError_t launch_hydro_rk_dw(const DevMesh &m, const void *U, void *Unew, cons
 cudaError_t launch_hydro_dw(const DevMesh &m, const void *U, void *Unew, const int *leaves, int n,
                             const double *dt, double *regs, int *status,
                             unsigned long long *smax, const unsigned char *rmask, int form,
-                            cudaStream_t s) {
+                            cudaStream_t s, const int *live) {
   if (n <= 0) return cudaSuccess;
   const int T = (m.nxb % 16 == 0) ? 16 : 8;
   if (m.ndim == 3)
-    return T == 16 ? launch_dw_t<3, 16>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
-                   : launch_dw_t<3, 8>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
-  return T == 16 ? launch_dw_t<2, 16>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s)
-                 : launch_dw_t<2, 8>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s);
+    return T == 16 ? launch_dw_t<3, 16>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, live)
+                   : launch_dw_t<3, 8>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, live);
+  return T == 16 ? launch_dw_t<2, 16>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, live)
+                 : launch_dw_t<2, 8>(m, U, Unew, leaves, n, dt, regs, status, smax, rmask, form, s, live);
+}
+
+cudaError_t hydro_set_fit_dw(int ndim, int nxb, int *fit) {
+  const bool t16 = nxb % 16 == 0;
+  if (ndim == 3) return t16 ? set_fit_dw_t<3, 16>(fit) : set_fit_dw_t<3, 8>(fit);
+  return t16 ? set_fit_dw_t<2, 16>(fit) : set_fit_dw_t<2, 8>(fit);
 }
 
 cudaError_t hydro_batch_fit_dw(int ndim, int tile, int *fit) {

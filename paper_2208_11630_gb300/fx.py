@@ -94,6 +94,7 @@ def load(build: bool = True):
             "fx_batch_remove": (c_int, [vp, c_int, vp]),
             "fx_batch_tune": (c_int, [vp, vp, ip]),
             "fx_batch_choice": (c_int, [vp, c_int, c_int, ip, ip]),
+            "fx_batch_path": (c_int, [vp, c_int, ip]),
             "fx_compute_dt_noalloc": (c_int, [vp, c_int, c_int, c_int, c_int, dp, c_double,
                                               c_double, c_int, vp, vp, ctypes.c_char_p,
                                               ctypes.c_size_t]),
@@ -310,6 +311,13 @@ class Batch:
                 break
             out.append((int(rep[3 * i]), int(rep[3 * i + 1]), int(rep[3 * i + 2])))
         return out
+
+    def path(self, slot: int) -> int:
+        """0: batched phases and persistent update; 1: the per-block-set
+        kernels on a graph branch (the request fills the GPU)."""
+        p = ctypes.c_int()
+        _check(self.ctx, load().fx_batch_path(self.h, int(slot), ctypes.byref(p)))
+        return p.value
 
     def choice(self, ndim: int, precision: int):
         t, c = ctypes.c_int(), ctypes.c_int()

@@ -94,6 +94,7 @@ calls = {
  "fx_batch_remove": lambda: L.fx_batch_remove(None, 0, None),
  "fx_batch_tune": lambda: L.fx_batch_tune(None, None, None),
  "fx_batch_choice": lambda: L.fx_batch_choice(None, 3, 0, None, None),
+ "fx_batch_path": lambda: L.fx_batch_path(None, 0, None),
  "fx_compute_dt_noalloc": lambda: L.fx_compute_dt_noalloc(None, 3, 1, 16, 4, None, d(1.4), d(0.8),
                                                           0, None, None, None, ctypes.c_size_t(0)),
  "fx_dword_selftest": lambda: L.fx_dword_selftest(0, None, None, None, 4, None),

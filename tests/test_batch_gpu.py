@@ -145,3 +145,64 @@ def test_tuning_leaves_states_unchanged_and_picks_a_choice(fx):
         assert max_rel_err_vec(mesh, bs.state(), ref.state()) <= tol, name
     batch.close()
     fx.fx_finalize(ctx)
+
+
+def test_large_requests_step_through_the_per_set_kernels(orc, fx):
+    """A request with at least one full wave of the per-block-set update's
+    CTAs (2 per SM for FP64 16x16 tiles, 4 for FP32-bulk; one tile per 16^3
+    block) is stepped by the per-block-set kernels of every phase (those of
+    fx_step) on a branch of the batch graph, its buffers alternating between
+    the two captured graphs; so its batched state is bitwise that of stepping
+    it alone.  Covered: FP64 and FP32-bulk uniform requests and an FP64 AMR
+    one (copies, prolongation, reflux, restriction) beside small requests in
+    the batched phases, step counts of both parities, a request admitted after
+    an odd number of replays (re-capture from the device's buffer parity),
+    finished requests left in the graph while others run on, and release back
+    to single-set stepping; the AMR request also against the oracle."""
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    m64 = inputs.uniform_mesh(3, (8, 8, 5), 16, 4, inputs.PERIODIC)
+    m32 = inputs.uniform_mesh(3, (8, 8, 10), 16, 4, inputs.PERIODIC)
+    mamr = mesh_2level(6, 16, 4, central=4)
+    if m64.nb < 2 * nsm or m32.nb < 4 * nsm or int(mamr.is_leaf().sum()) < 2 * nsm:
+        pytest.skip("meshes smaller than one wave on this GPU")
+    big = [("big_f64", m64, inputs.kh_state(m64), 0, 5),
+           ("big_f32", m32, inputs.kh_state(m32), 1, 4)]
+    small = _cases()[:3]
+    late = ("big_amr_f64", mamr, inputs.sedov_state(mamr), 0, 3)
+    ctx = fx.fx_init(1.4, 16, 4)
+    batch = fx.Batch(ctx, 8)
+    entries = []
+    for c in big + small:
+        bs = _blockset(fx, c[1], c[2], c[3])
+        entries.append((c, bs, batch.add(bs, 0.8, c[4])))
+    batch.run(1)                          # odd: the next capture starts from parity 1
+    bs = _blockset(fx, late[1], late[2], late[3])
+    entries.append((late, bs, batch.add(bs, 0.8, late[4])))
+    batch.run(11)                         # everyone finishes (the small ones take up to 12)
+    assert np.all(batch.poll()[:len(entries)] == 0)
+    for (name, mesh, W, prec, k), bs, slot in entries:
+        assert batch.path(slot) == (1 if name.startswith("big") else 0), name
+    for (name, mesh, W, prec, k), bs, slot in entries:
+        batch.remove(slot)
+        assert bs.status() == 0, name
+        ref = _blockset(fx, mesh, W, prec)
+        ref.run(k, 0.8)
+        tol = 1e-12 if prec == 0 else 1e-5
+        if name.startswith("big"):
+            assert np.array_equal(bs.state(), ref.state()), name
+        else:
+            assert max_rel_err_vec(mesh, bs.state(), ref.state()) <= tol, name
+        if "amr" in name:
+            om = orc.OracleMesh(mesh)
+            Uo, _, _ = om.run(om.prim_to_cons(W), nsteps=k)
+            assert max_rel_err(mesh, bs.state(), Uo) <= 1e-12, name
+        bs.step(0.8)                      # released: continues on its own
+        ref.step(0.8)
+        if name.startswith("big"):
+            assert np.array_equal(bs.state(), ref.state()), name
+        else:
+            assert max_rel_err_vec(mesh, bs.state(), ref.state()) <= tol, name
+        bs.close()
+        ref.close()
+    batch.close()
+    fx.fx_finalize(ctx)
