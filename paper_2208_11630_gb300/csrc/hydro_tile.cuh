@@ -89,24 +89,6 @@ __device__ __forceinline__ bool ge0(float x) { return x >= 0.0f; }
 __device__ __forceinline__ bool gt0(double x) { return __double_as_longlong(x) > 0; }
 __device__ __forceinline__ bool gt0(float x) { return x > 0.0f; }
 
-// FP64 minimum / maximum on the integer pipe instead of the FP64 one (where a
-// min or max costs as much as an FMA): flipping the magnitude bits of negative
-// values makes the signed integer order of the bit patterns the order of the
-// values, -0 below +0.  A NaN argument (a state that is already invalid) may
-// give another result than fmin/fmax.
-__device__ __forceinline__ long long order_key(double x) {
-  const long long i = __double_as_longlong(x);
-  return i ^ ((i >> 63) & 0x7fffffffffffffffll);
-}
-__device__ __forceinline__ double min_r(double a, double b) {
-  return order_key(a) <= order_key(b) ? a : b;
-}
-__device__ __forceinline__ double max_r(double a, double b) {
-  return order_key(a) >= order_key(b) ? a : b;
-}
-__device__ __forceinline__ float min_r(float a, float b) { return fminf(a, b); }
-__device__ __forceinline__ float max_r(float a, float b) { return fmaxf(a, b); }
-
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 
@@ -116,8 +98,6 @@ __device__ __forceinline__ bool positive(dw x) { return x.hi > 0.0f; }
 __device__ __forceinline__ bool ge0(dw x) { return x.hi >= 0.0f; }
 __device__ __forceinline__ bool gt0(dw x) { return x.hi > 0.0f; }
 __device__ __forceinline__ dw rsqrt_r(dw x) { return rsqrt(x); }
-__device__ __forceinline__ dw min_r(dw a, dw b) { return fmin(a, b); }
-__device__ __forceinline__ dw max_r(dw a, dw b) { return fmax(a, b); }
 __device__ __forceinline__ dw mc_half(dw a, dw b) {
   const bool same = (a.hi > 0.0f && b.hi > 0.0f) || (a.hi < 0.0f && b.hi < 0.0f);
   const dw s = fabs(a + b);
@@ -178,8 +158,8 @@ __device__ __forceinline__ void hllc(const R (&WL)[5 + NS], const R (&WR)[5 + NS
   const R gpL = gL * pL, gpR = gR * pR;
   const R qL = rsqrt_r(gpL * rL), qR = rsqrt_r(gpR * rR);
   const R cL = gpL * qL, cR = gpR * qR;
-  const R SL = min_r(uL - cL, uR - cR);
-  const R SR = max_r(uL + cL, uR + cR);
+  const R SL = fmin(uL - cL, uR - cR);
+  const R SR = fmax(uL + cL, uR + cR);
   const R dL = SL - uL, dR = SR - uR;
   // S* = A / B.  FP64: its sign (A = 0 or A, B of equal sign <=> S* >= 0)
   // picks the side, and S* and 1/(S_K - S*) both come from one reciprocal
