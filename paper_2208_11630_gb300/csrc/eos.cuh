@@ -74,12 +74,16 @@ struct SignalConsts<double> {
 // precision R: sum over directions (form 0) or maximum (form 1) of
 // (|u_d| + c) / dx_d, c = sqrt(gamma p / rho).  The fused epilogue of the
 // update, the flux correction and the standalone reduction all use it, so
-// that they agree bit for bit.
+// that they agree bit for bit.  FP32 takes 1/rho and the square root from
+// the approximate hardware instructions (a few units in the last place; the
+// FP32-bulk update's own rounding is larger), FP64 the correctly rounded ones.
 //   NDIM > 0: the dimension is known at compile time (the direction loop unrolls).
 template <typename R, int NDIM = 0>
 __device__ __forceinline__ R cell_signal(const DevMesh &m, const R *u, int ns,
                                          const SignalConsts<R> &k0, int form) {
-  const R ir = R(1) / u[0];
+  R ir;
+  if constexpr (std::is_same<R, float>::value) ir = __fdividef(1.0f, u[0]);
+  else ir = R(1) / u[0];
   R g, gm1;
   if constexpr (std::is_same<R, double>::value) {
     g = m.gamma;
@@ -94,7 +98,12 @@ __device__ __forceinline__ R cell_signal(const DevMesh &m, const R *u, int ns,
     mix_gamma<R>(m, X, ns, g, gm1);
   }
   const R pr = gm1 * (u[4] - R(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * ir);
-  const R cs = sqrt(g * pr * ir);
+  R cs;
+  if constexpr (std::is_same<R, float>::value) {
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(cs) : "f"(g * pr * ir));
+  } else {
+    cs = sqrt(g * pr * ir);
+  }
   R sg = R(0);
   auto term = [&](int d) {
     R idx_d;

@@ -60,14 +60,17 @@ __device__ __forceinline__ double mc_half(double a, double b) {
   return same ? __longlong_as_double(r) : 0.0;
 }
 
-// FP32: (sign(a)/2 + sign(b)/2) min(|a|, |b|, |a+b|/4), where the signed
-// halves are +-1/2 (exact sums +-1 or 0): equal signs give +-m, opposite
-// signs 0, and a zero argument makes m zero -- the same values as the FP64
-// form, without compares or selects (only the sign of a zero result can
+// FP32: PTX min.xorsign.abs gives u = min(|a|, |b|) carrying the sign
+// sign(a) xor sign(b) -- positive exactly when a and b agree in sign -- so
+// clamping u to [0, |a+b|/4] and giving it the sign of a + b (the sign of a
+// when they agree) is the same value as the FP64 form, in six instructions
+// and without compares or selects (only the sign of a zero result can
 // differ, which no later sum or product turns into a nonzero value).
 __device__ __forceinline__ float mc_half(float a, float b) {
-  const float m = fminf(fminf(fabsf(a), fabsf(b)), 0.25f * fabsf(a + b));
-  return (copysignf(0.5f, a) + copysignf(0.5f, b)) * m;
+  float u;
+  asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(u) : "f"(a), "f"(b));
+  const float s = a + b;
+  return copysignf(fmaxf(fminf(u, 0.25f * fabsf(s)), 0.0f), s);
 }
 
 // x > 0 (false for zero, negative and NaN; +inf counts as positive), tested on
