@@ -62,7 +62,10 @@ __device__ __forceinline__ int slot_of(int i, int lo, int hi) {
 
 // Parent p, interior cells [chunk*blockDim, (chunk+1)*blockDim): the pairwise
 // mean of the 2^d child cells (x pairs first, then y, then z), which restricts
-// a uniform field to itself exactly.
+// a uniform field to itself exactly.  Computed in the state's precision: an
+// FP32 state converted to FP64 would put eight conversions and eight
+// operations per value on the FP64 pipe, which this GPU runs at 1/64 of the
+// FP32 rate (parents are guard sources only, never updated leaves).
 template <typename S>
 __device__ __forceinline__ void restrict_cells(const DevMesh &m, S *__restrict__ U, int p,
                                                int chunk) {
@@ -81,15 +84,14 @@ __device__ __forceinline__ void restrict_cells(const DevMesh &m, S *__restrict__
   const int dk = m.ndim == 3 ? k + ng : 0;
   for (int v = 0; v < m.nvar; ++v) {
     const S *f = F + v * m.vstride + ((long long)fk * P + fj) * P + fi;
-    double r;
+    S r;
     if (m.ndim == 2) {
-      r = ((ld(f) + ld(f + 1)) + (ld(f + P) + ld(f + P + 1))) * 0.25;
+      r = ((f[0] + f[1]) + (f[P] + f[P + 1])) * S(0.25);
     } else {
       const S *g = f + (long long)P * P;
-      r = (((ld(f) + ld(f + 1)) + (ld(f + P) + ld(f + P + 1))) +
-           ((ld(g) + ld(g + 1)) + (ld(g + P) + ld(g + P + 1)))) * 0.125;
+      r = (((f[0] + f[1]) + (f[P] + f[P + 1])) + ((g[0] + g[1]) + (g[P] + g[P + 1]))) * S(0.125);
     }
-    st(D + v * m.vstride + ((long long)dk * P + (j + ng)) * P + (i + ng), r);
+    D[v * m.vstride + ((long long)dk * P + (j + ng)) * P + (i + ng)] = r;
   }
 }
 
