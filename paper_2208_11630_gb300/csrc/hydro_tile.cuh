@@ -291,11 +291,23 @@ template <int NDIM, int T, typename R, bool RK, int NS>
 __host__ __device__ constexpr int ring_plane_elems() {
   return (RingCfg<NDIM, R, RK, NS>::four ? 5 : Smem<T, NS>::NV) * Smem<T, NS>::W4 * Smem<T, NS>::W4;
 }
+// FP64 3D single-gas 16 x 16 tiles move the z faces of the halo-predictor
+// threads out of the predictor phase: those threads leave their two z face
+// states in shared memory, other threads solve these faces in the flux phase,
+// and every other thread solves its own z face right after its predictor, so
+// that neither phase waits at its barrier for warps with twice the work.
+template <int NDIM, int T, typename R, bool RK, int NS>
+struct ZDefer {
+  static constexpr bool on = std::is_same<R, double>::value && NDIM == 3 && T == 16 && !RK &&
+                             NS == 0;
+  static constexpr int elems = on ? 2 * (5 + NS) * 4 * T : 0;   // left and right states
+};
 // Dynamic shared memory of one tile instance, in bytes.
 template <int NDIM, int T, typename R, bool RK = false, int NS = 0>
 __host__ __device__ constexpr size_t tile_smem_bytes() {
   return (size_t)(RingCfg<NDIM, R, RK, NS>::planes * ring_plane_elems<NDIM, T, R, RK, NS>() +
-                  2 * Smem<T, NS>::FX + 2 * Smem<T, NS>::FY) * sizeof(R);
+                  2 * Smem<T, NS>::FX + 2 * Smem<T, NS>::FY + ZDefer<NDIM, T, R, RK, NS>::elems) *
+         sizeof(R);
 }
 
 // Slopes, Hancock predictor and face states of the cell at tile-local (i, j)
@@ -412,6 +424,12 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
   R *fxp = fxm + SM::FX;
   R *fym = fxp + SM::FX;            // y lower-face states, then y fluxes
   R *fyp = fym + SM::FY;
+  // deferred z faces: [left state | right state, then flux][component][4T]
+  constexpr bool kZD = ZDefer<NDIM, T, R, RK, NS>::on;
+  constexpr int kZT = 4 * T;                 // halo-predictor threads
+  constexpr int kZ0 = 4 * T + 32;            // their z faces: threads after the extra face round
+  R *zbuf = fyp + SM::FY;
+  (void)zbuf;
 
   // FP32 compute: the warp-level roles (the halo predictor on the first 4T
   // threads, the last partial rounds of the face and plane-load loops on
@@ -608,6 +626,25 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
 #pragma unroll
       for (int v = 0; v < NF; ++v) { zm[v] = fm[2][v]; zp[v] = fp[2][v]; }
     }
+    R Fz[NF];
+    if constexpr (kZD) {
+      if (p >= 0) {
+        if (inner && tid < kZT) {
+#pragma unroll
+          for (int v = 0; v < NF; ++v) {
+            zbuf[v * kZT + tid] = zprev[v];
+            zbuf[(NF + v) * kZT + tid] = zm[v];
+          }
+        } else {
+          hllc<2, R, NS>(zprev, zm, g, igm1, m, Fz);
+          if (reg && (p == 0 || p == n)) {
+            const int face = p == 0 ? 4 : 5;
+#pragma unroll
+            for (int v = 0; v < NF; ++v) put_reg<RK>(reg[(face * NF + v) * nfc + (y0 + tj) * n + (x0 + ti)], Fz[v], st);
+          }
+        }
+      }
+    }
     if (inner) {
       for (int c = tid; c < 4 * T; c += NT) {
         const int side = c / T, e = c % T;
@@ -639,7 +676,6 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
     // ---- fluxes: x and y faces of inner planes (in place over the lower-face
     // state), z face below the thread's own cell
     const int zglob = p;  // interior z index of this plane
-    R Fz[NF];
     if constexpr (std::is_same<R, dw>::value) {
       // double-word tile: one inlined Riemann solver serves every face of the
       // thread -- its x/y faces of inner planes, then its z face below -- with
@@ -755,7 +791,27 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
           }
         }
       }
-      if (NDIM == 3 && p >= 0) {
+      if constexpr (kZD) {
+        // the halo-predictor threads' z faces
+        const int dz = tid - kZ0;
+        if (inner && p >= 0 && dz >= 0 && dz < kZT) {
+          R WL[NF], WR[NF], F[NF];
+#pragma unroll
+          for (int v = 0; v < NF; ++v) {
+            WL[v] = zbuf[v * kZT + dz];
+            WR[v] = zbuf[(NF + v) * kZT + dz];
+          }
+          hllc<2, R, NS>(WL, WR, g, igm1, m, F);
+#pragma unroll
+          for (int v = 0; v < NF; ++v) zbuf[(NF + v) * kZT + dz] = F[v];
+          if (reg && (p == 0 || p == n)) {
+            const int face = p == 0 ? 4 : 5;
+            const int ci = x0 + dz % T, cj = y0 + dz / T;
+#pragma unroll
+            for (int v = 0; v < NF; ++v) put_reg<RK>(reg[(face * NF + v) * nfc + cj * n + ci], F[v], st);
+          }
+        }
+      } else if (NDIM == 3 && p >= 0) {
         hllc<2, R, NS>(zprev, zm, g, igm1, m, Fz);
         if (reg && (p == 0 || p == n)) {
           const int face = p == 0 ? 4 : 5;
@@ -765,6 +821,12 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
       }
     }
     __syncthreads();
+    if constexpr (kZD) {
+      if (inner && p >= 0 && tid < kZT) {
+#pragma unroll
+        for (int v = 0; v < NF; ++v) Fz[v] = zbuf[(NF + v) * kZT + tid];
+      }
+    }
 
     // ---- update: finish the cell below (3D), start this plane's cell.
     // FP64: U + dt ((Fx- - Fx+)/dx + (Fy- - Fy+)/dy + (Fz- - Fz+)/dz).
