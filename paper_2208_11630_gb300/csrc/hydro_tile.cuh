@@ -503,11 +503,12 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
   __shared__ int4 src_map[27];
   if (tid < 27) guard_source(m, b, tid, src_off[tid], src_map[tid]);
   __syncthreads();
-  auto load_plane = [&](int p, int slot) {
+  // plane p into ring slot `slot`, cells [first, ...) strided by `stride`
+  auto load_cells = [&](int p, int slot, int first, int stride) {
     R *dst = ring + slot * RS;
     const int zpad = p + zoff;
     const int sz = NDIM == 3 ? (zpad < ng ? 0 : (zpad >= ng + n ? 2 : 1)) : 1;
-    for (int c = (tid + kLoadTail) % NT; c < SM::W4 * SM::W4; c += NT) {
+    for (int c = first; c < SM::W4 * SM::W4; c += stride) {
       const int ii = c % SM::W4, jj = c / SM::W4;
       const int gx = x0 + ii - 2 + ng, gy = y0 + jj - 2 + ng;
       const int sx = gx < ng ? 0 : (gx >= ng + n ? 2 : 1);
@@ -527,6 +528,17 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
       for (int v = 0; v < NVR; ++v) dst[v * SM::W4 * SM::W4 + c] = w[v];
     }
   };
+  auto load_plane = [&](int p, int slot) { load_cells(p, slot, (tid + kLoadTail) % NT, NT); };
+  // FP64 tiles with the z-face move (ZDefer::on) load plane p + 2 in the flux
+  // phase of plane p, into the ring slot plane p - 1 left when the predictor
+  // phase ended, on the threads with two rounds of faces there: those of the
+  // halo predictor and those after the deferred z faces.  The loop top then
+  // loads nothing.
+  constexpr bool kLF = ZDefer<NDIM, T, R, RK, NS>::on;
+  constexpr int kLoaders = kZT + (NT - kZ0 - kZT);
+  const bool loader = tid < kZT || tid >= kZ0 + kZT;
+  const int lrank = tid < kZT ? tid : tid - (kZ0 + kZT) + kZT;
+  (void)kLoaders; (void)loader; (void)lrank;
   auto slot_of = [&](int p) { return NDIM == 3 ? (R4 ? (p & 3) : ((p % 3) + 3) % 3) : 0; };
 
   // register state of the thread's column: pending update of the cell below
@@ -594,14 +606,15 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
   if (NDIM == 3) {
     load_plane(-2, slot_of(-2));
     load_plane(-1, slot_of(-1));
-    if (R4) load_plane(0, slot_of(0));
+    if (R4 || kLF) load_plane(0, slot_of(0));
   }
   for (int p = pstart; p <= pend; ++p) {
     const bool inner = p >= 0 && p < (NDIM == 3 ? n : 1);
     const int s0 = slot_of(p), sm = slot_of(p - 1), sp = slot_of(p + 1);
-    if (R4) {
+    if (R4 || kLF) {
       // four-plane ring: plane p + 1 is already in; plane p + 2 goes into the
       // slot plane p - 2 left, in the same phase as the predictor below
+      // (FP64 with kLF: plane p + 1 came in the flux phase of plane p - 1)
       __syncthreads();
     } else {
       if (NDIM == 3) load_plane(p + 1, sp);
@@ -818,6 +831,9 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
 #pragma unroll
           for (int v = 0; v < NF; ++v) put_reg<RK>(reg[(face * NF + v) * nfc + (y0 + tj) * n + (x0 + ti)], Fz[v], st);
         }
+      }
+      if constexpr (kLF) {
+        if (loader && p + 2 <= pend + 1) load_cells(p + 2, slot_of(p + 2), lrank, kLoaders);
       }
     }
     __syncthreads();
