@@ -314,18 +314,17 @@ __host__ __device__ constexpr size_t tile_smem_bytes() {
 // of the plane in ring slot s0 (neighbour planes in sm, sp).  Works with half
 // slopes h = dW/2 throughout: the predictor is linear in the slopes, so
 // A(W) h (2/dx) is exactly A(W) dW / dx, and the face states are W* -+ h.
-// Returns the lower/upper face states per direction in fm/fp.
-template <int NDIM, int T, typename R, bool PRED = true, int NS = 0, bool RING4 = false>
-__device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int s0, int sp, int i,
-                                        int j, R hdt, const R (&idx2)[3], R g,
-                                        R (&fm)[3][5 + NS], R (&fp)[3][5 + NS]) {
+// Here: the cell's primitives W0, half slopes h and half-step state Wh.
+template <int NDIM, int T, typename R, bool PRED, int NS, bool RING4>
+__device__ __forceinline__ void predict_wh(const R *__restrict__ ring, int sm, int s0, int sp,
+                                           int i, int j, R hdt, const R (&idx2)[3], R g,
+                                           R (&W0)[5 + NS], R (&h)[3][5 + NS], R (&Wh)[5 + NS]) {
   using SM = Smem<T, NS>;
   constexpr int NF = 5 + NS;
   constexpr int PL = SM::W4 * SM::W4;
   constexpr int RS = RING4 ? 5 * PL : SM::RING;   // one ring plane
   const int c = (j + 2) * SM::W4 + (i + 2);
   const R *p0 = ring + s0 * RS;
-  R W0[NF], h[3][NF];
 #pragma unroll
   for (int v = 0; v < NF; ++v) W0[v] = p0[ring_comp(v) * PL + c];
   const R ir = RING4 ? div_r(R(1), W0[0]) : p0[5 * PL + c];
@@ -344,7 +343,6 @@ __device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int 
       h[2][v] = R(0);
     }
   }
-  R Wh[NF];
   if constexpr (PRED) {
     // primitive quasi-linear form: sum_d A_d(W) dW_d / dx_d
     R acc[NF];
@@ -373,6 +371,17 @@ __device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int 
 #pragma unroll
     for (int v = 0; v < NF; ++v) Wh[v] = W0[v];
   }
+}
+
+// Returns the lower/upper face states per direction in fm/fp (the cell's
+// primitives in all of them when one has non-positive density or pressure).
+template <int NDIM, int T, typename R, bool PRED = true, int NS = 0, bool RING4 = false>
+__device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int s0, int sp, int i,
+                                        int j, R hdt, const R (&idx2)[3], R g,
+                                        R (&fm)[3][5 + NS], R (&fp)[3][5 + NS]) {
+  constexpr int NF = 5 + NS;
+  R W0[NF], h[3][NF], Wh[NF];
+  predict_wh<NDIM, T, R, PRED, NS, RING4>(ring, sm, s0, sp, i, j, hdt, idx2, g, W0, h, Wh);
   bool ok = true;
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
@@ -389,6 +398,29 @@ __device__ __forceinline__ void predict(const R *__restrict__ ring, int sm, int 
     for (int d = 0; d < NDIM; ++d)
 #pragma unroll
       for (int v = 0; v < NF; ++v) { fm[d][v] = W0[v]; fp[d][v] = W0[v]; }
+  }
+}
+
+// A cell of the tile's radius-1 halo ring feeds one face of the tile: only
+// that face state -- direction dir (0 or 1), the upper one (Wh + h) if plus,
+// else the lower -- with the positivity fallback decided on the density and
+// pressure of all its face states, as in predict (the same values).
+template <int NDIM, int T, typename R, bool PRED = true, int NS = 0, bool RING4 = false>
+__device__ __forceinline__ void predict_face(const R *__restrict__ ring, int sm, int s0, int sp,
+                                             int i, int j, R hdt, const R (&idx2)[3], R g,
+                                             int dir, bool plus, R (&fs)[5 + NS]) {
+  constexpr int NF = 5 + NS;
+  R W0[NF], h[3][NF], Wh[NF];
+  predict_wh<NDIM, T, R, PRED, NS, RING4>(ring, sm, s0, sp, i, j, hdt, idx2, g, W0, h, Wh);
+  bool ok = true;
+#pragma unroll
+  for (int d = 0; d < NDIM; ++d)
+    ok = ok && positive(Wh[0] - h[d][0]) && positive(Wh[4] - h[d][4]) &&
+         positive(Wh[0] + h[d][0]) && positive(Wh[4] + h[d][4]);
+#pragma unroll
+  for (int v = 0; v < NF; ++v) {
+    const R hv = dir == 0 ? h[0][v] : h[1][v];
+    fs[v] = ok ? (plus ? Wh[v] + hv : Wh[v] - hv) : W0[v];
   }
 }
 
@@ -666,21 +698,16 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
         else if (side == 1) { i = T; j = e; }
         else if (side == 2) { i = e; j = -1; }
         else { i = e; j = T; }
-        R fm[3][NF], fp[3][NF];
-        predict<NDIM, T, R, !RK, NS, R4>(ring, sm, s0, sp, i, j, hdt, idx2, g, fm, fp);
-        if (side < 2) {
+        // the one face state the tile's faces read: the upper one of the
+        // lower rings (x face 0, y face 0), the lower one of the upper rings
+        R fs[NF];
+        predict_face<NDIM, T, R, !RK, NS, R4>(ring, sm, s0, sp, i, j, hdt, idx2, g, side >> 1,
+                                              (side & 1) == 0, fs);
+        R *dst = side == 0 ? fxp + j * SM::W2
+                           : (side == 1 ? fxm + j * SM::W2 + T + 1
+                                        : (side == 2 ? fyp + i : fym + (T + 1) * T + i));
 #pragma unroll
-          for (int v = 0; v < NF; ++v) {
-            fxm[v * T * SM::W2 + j * SM::W2 + i + 1] = fm[0][v];
-            fxp[v * T * SM::W2 + j * SM::W2 + i + 1] = fp[0][v];
-          }
-        } else {
-#pragma unroll
-          for (int v = 0; v < NF; ++v) {
-            fym[v * SM::W2 * T + (j + 1) * T + i] = fm[1][v];
-            fyp[v * SM::W2 * T + (j + 1) * T + i] = fp[1][v];
-          }
-        }
+        for (int v = 0; v < NF; ++v) dst[v * T * SM::W2] = fs[v];
       }
     }
     if (R4 && p + 2 <= pend + 1) load_plane(p + 2, slot_of(p + 2));
