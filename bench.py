@@ -46,7 +46,7 @@ FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 # capture of the 128^3 KH case (dram__bytes_read.sum + dram__bytes_write.sum
 # over 2,097,152 zones); the full launch's traffic scales with its zones.
 # Valid for the kernel build those counters were taken on.
-TRAFFIC_BYTES_PER_ZONE = {"f64": 100.9, "f32bulk": 66.7}
+TRAFFIC_BYTES_PER_ZONE = {"f64": 101.3, "f32bulk": 66.6}
 
 
 def measure_fma_peak(fx, stream, precision, reps: int = 3):
