@@ -18,10 +18,14 @@
 // Shared memory holds a ring of primitive planes (radius-2 halo in x and y)
 // and the x/y face states of the current plane; each face flux is computed
 // once by one thread and written over the face state it consumed.  The thread
-// owning column (i, j) keeps its z face states and z fluxes in registers, so
-// no z data touches shared memory.  Per plane, three barriers: load +
-// primitives, predictor, fluxes, update -- or, with the four-plane ring of the
-// FP32 3D single-gas instances, the next plane's load in the predictor phase.
+// owning column (i, j) keeps its z face states and z fluxes in registers.  Per
+// plane, three barriers: load + primitives, predictor, fluxes, update -- or,
+// with the four-plane ring of the FP32 3D single-gas instances, the next
+// plane's load in the predictor phase.  The FP64 3D single-gas 16 x 16 tile
+// balances the phases instead: the halo-predictor warps' z faces go through
+// shared memory to warps with a face round fewer, the other threads solve
+// their z face in the predictor phase, and the plane after next is loaded in
+// the flux phase by the warps with two face rounds (ZDefer).
 //
 // Precision variants (state type S, compute type R): FP64 state and
 // arithmetic; FP32-bulk -- FP32 state, FP32 reconstruction and Riemann
