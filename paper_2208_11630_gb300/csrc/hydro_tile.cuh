@@ -318,7 +318,8 @@ __host__ __device__ constexpr size_t tile_smem_bytes() {
 // of the plane in ring slot s0 (neighbour planes in sm, sp).  Works with half
 // slopes h = dW/2 throughout: the predictor is linear in the slopes, so
 // A(W) h (2/dx) is exactly A(W) dW / dx, and the face states are W* -+ h.
-// Here: the cell's primitives W0, half slopes h and half-step state Wh.
+// predict_wh forms the cell's primitives W0, half slopes h and half-step
+// state Wh; predict and predict_face form the face states from them.
 template <int NDIM, int T, typename R, bool PRED, int NS, bool RING4>
 __device__ __forceinline__ void predict_wh(const R *__restrict__ ring, int sm, int s0, int sp,
                                            int i, int j, R hdt, const R (&idx2)[3], R g,
@@ -464,6 +465,8 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
   constexpr bool kZD = ZDefer<NDIM, T, R, RK, NS>::on;
   constexpr int kZT = 4 * T;                 // halo-predictor threads
   constexpr int kZ0 = 4 * T + 32;            // their z faces: threads after the extra face round
+  static_assert(!kZD || (2 * (T + 1) * T) % NT == 32,
+                "the x/y face loop leaves one extra round of 32 faces on threads [4T, 4T + 32)");
   R *zbuf = fyp + SM::FY;
   (void)zbuf;
 
