@@ -206,3 +206,30 @@ def test_large_requests_step_through_the_per_set_kernels(orc, fx):
         ref.close()
     batch.close()
     fx.fx_finalize(ctx)
+
+
+def test_empty_batch_and_refused_requests(fx):
+    """A batch with no requests replays an empty step and polls as all-empty
+    slots; block sets the batch does not step (SSP-RK, species, the FP32
+    arithmetic ablation) are refused at admission with FX_ERR_ARG."""
+    ctx = fx.fx_init(1.4, 16, 4)
+    batch = fx.Batch(ctx, 4)
+    batch.run(3)
+    assert np.all(batch.poll() == -1)
+    m = inputs.uniform_mesh(3, (2, 2, 2), 16, 4, inputs.PERIODIC)
+    for opts in ({"integrator": 1}, {"f64_arith": 2}):
+        bs = fx.BlockSet(m, 1.4, options=opts)
+        bs.set_primitive(inputs.kh_state(m))
+        with pytest.raises(fx.FxError):
+            batch.add(bs, 0.8, 1)
+        bs.close()
+    # after the refusals the batch still steps an admitted request
+    bs = _blockset(fx, m, inputs.kh_state(m), 0)
+    slot = batch.add(bs, 0.8, 2)
+    batch.run(2)
+    assert batch.poll()[slot] == 0
+    batch.remove(slot)
+    assert bs.status() == 0
+    bs.close()
+    batch.close()
+    fx.fx_finalize(ctx)
