@@ -705,16 +705,37 @@ __device__ __forceinline__ void hydro_tile(const DevMesh &m, const S *__restrict
         else if (side == 1) { i = T; j = e; }
         else if (side == 2) { i = e; j = -1; }
         else { i = e; j = T; }
-        // the one face state the tile's faces read: the upper one of the
-        // lower rings (x face 0, y face 0), the lower one of the upper rings
-        R fs[NF];
-        predict_face<NDIM, T, R, !RK, NS, R4>(ring, sm, s0, sp, i, j, hdt, idx2, g, side >> 1,
-                                              (side & 1) == 0, fs);
-        R *dst = side == 0 ? fxp + j * SM::W2
-                           : (side == 1 ? fxm + j * SM::W2 + T + 1
-                                        : (side == 2 ? fyp + i : fym + (T + 1) * T + i));
+        if constexpr (std::is_same<R, dw>::value && NS == 0) {
+          // single-gas double-word tile: the one predictor body the kernel
+          // already inlines (a second one, for the face state alone, measured
+          // slower in this instruction-fetch-sensitive kernel)
+          R fm[3][NF], fp[3][NF];
+          predict<NDIM, T, R, !RK, NS, R4>(ring, sm, s0, sp, i, j, hdt, idx2, g, fm, fp);
+          if (side < 2) {
 #pragma unroll
-        for (int v = 0; v < NF; ++v) dst[v * T * SM::W2] = fs[v];
+            for (int v = 0; v < NF; ++v) {
+              fxm[v * T * SM::W2 + j * SM::W2 + i + 1] = fm[0][v];
+              fxp[v * T * SM::W2 + j * SM::W2 + i + 1] = fp[0][v];
+            }
+          } else {
+#pragma unroll
+            for (int v = 0; v < NF; ++v) {
+              fym[v * SM::W2 * T + (j + 1) * T + i] = fm[1][v];
+              fyp[v * SM::W2 * T + (j + 1) * T + i] = fp[1][v];
+            }
+          }
+        } else {
+          // the one face state the tile's faces read: the upper one of the
+          // lower rings (x face 0, y face 0), the lower one of the upper rings
+          R fs[NF];
+          predict_face<NDIM, T, R, !RK, NS, R4>(ring, sm, s0, sp, i, j, hdt, idx2, g, side >> 1,
+                                                (side & 1) == 0, fs);
+          R *dst = side == 0 ? fxp + j * SM::W2
+                             : (side == 1 ? fxm + j * SM::W2 + T + 1
+                                          : (side == 2 ? fyp + i : fym + (T + 1) * T + i));
+#pragma unroll
+          for (int v = 0; v < NF; ++v) dst[v * T * SM::W2] = fs[v];
+        }
       }
     }
     if (R4 && p + 2 <= pend + 1) load_plane(p + 2, slot_of(p + 2));
