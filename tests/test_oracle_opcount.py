@@ -57,3 +57,14 @@ def test_units_follow_the_block_loops(kh):
     # the algorithmic count per zone: within the range a hand count of the
     # scheme gives (HLLC about 100 flops per face, predictor about 220)
     assert 550 < kh["algorithmic_per_zone"] < 700
+
+
+@pytest.mark.parametrize("name,scale", [("kh3d", 4), ("sedov_amr", 4), ("advection3d", 4),
+                                        ("sod2d", 0)])
+def test_bench_flops_per_zone_are_the_counted_ones(name, scale):
+    """The benchmark's algorithmic flops per zone update (its FP64 roofline
+    numerator) are this build's counts for the documented commands
+    (`python -m oracle.opcount <workload> <scale> 10`), to the printed digit."""
+    import bench
+    r = opcount.count_step(name, scale=scale, warm=10)
+    assert round(r["algorithmic_per_zone"], 1) == bench.ALGO_FLOPS_PER_ZONE[name]
